@@ -1,0 +1,219 @@
+"""Oracle: plain FP64 iterative QUAPI with MACGIC pre-merging, mask and filter.
+
+TEST INFRASTRUCTURE (see oracle/__init__.py): never imported by the product.
+
+Definitions followed (paper sections and equations):
+  * reduced density matrix as a path sum over forward/backward system
+    points, Eq. quapi_red_rho, with the bare propagator of Eqs. SysP0/SysP,
+    S(q_j, q_{j-1}) = U[s+_j, s+_{j-1}] * conj(U[s-_j, s-_{j-1}]),
+    U = exp(-i H_S dt), and the influence functional of Eq. inf_fun with
+    Toeplitz coefficients eta_{k,k'} = eta_{k-k'} cut at the memory length
+    Delta k_max (Sec. 2, finite memory);
+  * MACGIC coarse graining: paths identical on the mask are merged, keeping
+    the path of largest weight and the summed weight (Sec. 2.1);
+  * the pre-merging order of Sec. 3.1: at step t the stored set Omega(t-1)
+    is merged on the mask shifted by one step (mask[i] -> mask[i] + 1 in the
+    paper's footnote, i.e. window positions P' = {p - 1 : p in P, p >= 1}
+    of the older set), then every merged entry is extended by the M^2 new
+    (s+, s-) pairs (routine propagation(), Sec. 3.2), children below the
+    filter threshold are dropped, and rho(t) is the sum of the surviving
+    children by end point.
+
+Readings where the paper is silent (each listed in the design doc):
+  R1 box convention: point k >= 1 carries the box ((k-1) dt, k dt]; point 0
+     (the initial state) carries none, so it enters S but not the influence
+     functional.  The newest point's influence is applied when it is created.
+  R2 window: a stored path holds the newest min(t+1, Delta k_max) points;
+     lags 0 .. Delta k_max - 1 enter the influence functional.
+  R3 the pre-merge runs only once the stored window is full
+     (t >= Delta k_max); before that nothing merges.  P' always holds
+     position 0, whose point is needed by the bare propagator.
+  R4 group sum = sum over all members; representative = the member of
+     largest |amplitude|; weights equal to a relative 1e-12 count as equal
+     and among equal weights the smaller packed key wins (the paper's
+     concurrent insert leaves the choice among equal weights open).
+  R5 filter: a child is kept when |amp|^2 >= theta^2, applied before rho.
+
+Packed key used for the tie-break order and for exporting paths: with
+bs = max(1, ceil(log2 M)) bits per state and b = 2 bs bits per point, window
+position p (0 = newest) occupies bits [b p, b p + b): s+ in the low bs bits,
+s- in the high bs bits.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from typing import List, Optional
+
+import numpy as np
+import scipy.linalg
+
+TIE_REL = 1e-12
+
+
+def short_time_propagator(hs: np.ndarray, dt: float) -> np.ndarray:
+    """U = exp(-i H_S dt) (hbar = 1)."""
+    return scipy.linalg.expm(-1j * np.asarray(hs, dtype=np.complex128) * dt)
+
+
+def state_bits(M: int):
+    bs = max(1, math.ceil(math.log2(M)))
+    return bs, 2 * bs
+
+
+def packed_keys(sp: np.ndarray, sm: np.ndarray, M: int) -> np.ndarray:
+    """Packed uint64 key of each path (rows of sp/sm, column p = window position p)."""
+    bs, b = state_bits(M)
+    n, L = sp.shape
+    key = np.zeros(n, dtype=np.uint64)
+    for p in range(L):
+        code = sp[:, p].astype(np.uint64) | (sm[:, p].astype(np.uint64) << np.uint64(bs))
+        key |= code << np.uint64(b * p)
+    return key
+
+
+def premerge_positions(mask, dkmax: int):
+    """P' = {p - 1 : p in P, p >= 1} together with position 0 (reading R3)."""
+    P = sorted(set(int(p) for p in mask))
+    return sorted(set([p - 1 for p in P if p >= 1] + [0]))
+
+
+def check_mask(mask, dkmax: int):
+    P = sorted(set(int(p) for p in mask))
+    if not P or P[0] < 0 or P[-1] >= dkmax:
+        raise ValueError("mask positions must lie in [0, dkmax)")
+    if 0 not in P or (dkmax >= 2 and 1 not in P):
+        raise ValueError("mask must contain positions 0 and 1")
+    return P
+
+
+@dataclass
+class Paths:
+    """Stored set Omega_vec(t): forward points sp, backward points sm (column 0 =
+    newest), complex amplitudes amp."""
+    sp: np.ndarray
+    sm: np.ndarray
+    amp: np.ndarray
+
+
+@dataclass
+class StepStats:
+    t: int
+    groups: int          # entries after the pre-merge (= parents of this step)
+    extended: int        # children generated, groups * M^2
+    kept: int            # children surviving the filter
+    near_tie: int        # group decisions within 1e-13 of the tie window edge
+    near_theta: int      # children within 2e-12 (relative, on |amp|^2) of theta^2
+
+
+@dataclass
+class Result:
+    rho: np.ndarray                      # (steps + 1, M, M)
+    paths: Paths
+    stats: List[StepStats] = field(default_factory=list)
+
+
+def initial_paths(rho0: np.ndarray) -> Paths:
+    a, b = np.nonzero(rho0)
+    return Paths(sp=a.reshape(-1, 1).astype(np.int64),
+                 sm=b.reshape(-1, 1).astype(np.int64),
+                 amp=rho0[a, b].astype(np.complex128))
+
+
+def premerge(paths: Paths, Pp, M: int):
+    """Merge paths identical on the window positions Pp.
+
+    Returns (rep_sp, rep_sm, S, near_tie): the representative path of each
+    group (largest |amp|, reading R4) and the summed amplitude S."""
+    cols = list(Pp)
+    gkey = packed_keys(paths.sp[:, cols], paths.sm[:, cols], M)
+    _, inv = np.unique(gkey, return_inverse=True)
+    G = int(inv.max()) + 1 if inv.size else 0
+    S = np.zeros(G, dtype=np.complex128)
+    np.add.at(S, inv, paths.amp)
+    w2 = paths.amp.real ** 2 + paths.amp.imag ** 2
+    wmax = np.zeros(G)
+    np.maximum.at(wmax, inv, w2)
+    edge = (1.0 - TIE_REL) * wmax[inv]
+    eligible = w2 >= edge
+    near_tie = int(np.count_nonzero((np.abs(w2 - edge) <= 1e-13 * np.maximum(edge, 1e-300))
+                                    & (w2 != wmax[inv])))
+    key = packed_keys(paths.sp, paths.sm, M)
+    best = np.full(G, np.iinfo(np.uint64).max, dtype=np.uint64)
+    np.minimum.at(best, inv[eligible], key[eligible])
+    is_rep = eligible & (key == best[inv])
+    idx = np.nonzero(is_rep)[0]
+    rep_of = np.empty(G, dtype=np.int64)
+    rep_of[inv[idx]] = idx
+    return paths.sp[rep_of], paths.sm[rep_of], S, near_tie
+
+
+def step(paths: Paths, t: int, U, q, eta, dkmax: int, Pp, theta: float, M: int):
+    """One propagation step t-1 -> t.  Returns (new paths, rho(t), stats)."""
+    if t >= dkmax:                                  # window full: pre-merge on P'
+        rsp, rsm, S, near_tie = premerge(paths, Pp, M)
+    else:                                           # nothing merges yet (R3)
+        rsp, rsm, S, near_tie = paths.sp, paths.sm, paths.amp, 0
+    G = S.size
+    n_act = min(t, dkmax)
+    # influence of the stored history on the new point: lags d = 1 .. n_act-1,
+    # the point d steps back sits at window position d-1 of the parent
+    H = np.zeros(G, dtype=np.complex128)
+    for d in range(1, n_act):
+        H += eta[d] * q[rsp[:, d - 1]] - np.conj(eta[d]) * q[rsm[:, d - 1]]
+    L_child = min(t + 1, dkmax)
+    rho = np.zeros((M, M), dtype=np.complex128)
+    new_sp, new_sm, new_amp = [], [], []
+    near_theta = 0
+    th2 = theta * theta
+    for a in range(M):
+        for b in range(M):
+            prop = U[a, rsp[:, 0]] * np.conj(U[b, rsm[:, 0]])
+            phase = -(q[a] - q[b]) * (H + eta[0] * q[a] - np.conj(eta[0]) * q[b])
+            child = S * prop * np.exp(phase)
+            w2 = child.real ** 2 + child.imag ** 2
+            keep = w2 >= th2
+            if th2 > 0:
+                near_theta += int(np.count_nonzero(np.abs(w2 - th2) <= 2e-12 * th2))
+            rho[a, b] = child[keep].sum()
+            k = int(np.count_nonzero(keep))
+            col_a = np.full((k, 1), a, dtype=np.int64)
+            col_b = np.full((k, 1), b, dtype=np.int64)
+            new_sp.append(np.hstack([col_a, rsp[keep, :L_child - 1]]))
+            new_sm.append(np.hstack([col_b, rsm[keep, :L_child - 1]]))
+            new_amp.append(child[keep])
+    out = Paths(sp=np.vstack(new_sp), sm=np.vstack(new_sm), amp=np.concatenate(new_amp))
+    st = StepStats(t=t, groups=G, extended=G * M * M, kept=out.amp.size,
+                   near_tie=near_tie, near_theta=near_theta)
+    return out, rho, st
+
+
+def propagate(M: int, q, hs, dt: float, eta, dkmax: int, mask, theta: float,
+              rho0, steps: int, keep_stats: bool = True) -> Result:
+    """Run `steps` propagation steps from rho0; rho[t] for t = 0 .. steps."""
+    q = np.asarray(q, dtype=np.float64)
+    eta = np.asarray(eta, dtype=np.complex128)
+    if eta.size < dkmax:
+        raise ValueError("need dkmax influence coefficients")
+    rho0 = np.asarray(rho0, dtype=np.complex128)
+    P = check_mask(range(dkmax) if mask is None else mask, dkmax)
+    Pp = premerge_positions(P, dkmax)
+    U = short_time_propagator(hs, dt)
+    paths = initial_paths(rho0)
+    rhos = [rho0.copy()]
+    stats = []
+    for t in range(1, steps + 1):
+        paths, rho, st = step(paths, t, U, q, eta, dkmax, Pp, theta, M)
+        rhos.append(rho)
+        if keep_stats:
+            stats.append(st)
+    return Result(rho=np.array(rhos), paths=paths, stats=stats)
+
+
+def propagate_workload(w, eta=None, steps: Optional[int] = None) -> Result:
+    """Convenience: run a workloads.Workload (eta from oracle.bath unless given)."""
+    if eta is None:
+        from .bath import eta_coefficients
+        eta = eta_coefficients(w.bath, w.dt, w.dkmax)
+    return propagate(w.M, w.q, w.hs_array(), w.dt, eta, w.dkmax, w.mask, w.theta,
+                     w.rho0_array(), w.steps if steps is None else steps)

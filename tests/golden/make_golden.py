@@ -1,0 +1,47 @@
+"""Write the stored oracle trajectories used by the GPU parity tests.
+
+Calls only oracle/ (and the input module workloads.py).  Each file holds one
+line per time step t: t, the number of stored paths after the step, then
+Re and Im of rho(t) row-major.  Regenerate with
+
+    python tests/golden/make_golden.py
+"""
+import os
+import sys
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+import workloads as W  # noqa: E402
+from oracle import bath, iquapi  # noqa: E402
+
+
+def write(w, steps, fname):
+    eta = bath.eta_coefficients(w.bath, w.dt, w.dkmax)
+    r = iquapi.propagate_workload(w, eta=eta, steps=steps)
+    counts = [int(np.count_nonzero(w.rho0_array()))] + [s.kept for s in r.stats]
+    with open(os.path.join(HERE, fname), "w") as f:
+        f.write(f"# oracle trajectory of workload {w.name}, {steps} steps; "
+                f"columns: t n_paths Re/Im rho row-major (M={w.M})\n")
+        for t in range(steps + 1):
+            vals = []
+            for z in r.rho[t].reshape(-1):
+                vals += [z.real, z.imag]
+            f.write(f"{t} {counts[t]} " + " ".join(f"{v:.17e}" for v in vals) + "\n")
+
+
+def load(fname):
+    rows = np.loadtxt(os.path.join(HERE, fname), comments="#")
+    t = rows[:, 0].astype(int)
+    n = rows[:, 1].astype(np.int64)
+    v = rows[:, 2:]
+    rho = v[:, 0::2] + 1j * v[:, 1::2]
+    M = int(round(np.sqrt(rho.shape[1])))
+    return t, n, rho.reshape(-1, M, M)
+
+
+if __name__ == "__main__":
+    write(W.SPIN_BOSON_OHMIC_DK8, W.SPIN_BOSON_OHMIC_DK8.steps, "spin_boson_ohmic_dk8_rho.txt")
+    write(W.SPIN_BOSON_STRUCTURED_DK16, 40, "spin_boson_structured_dk16_rho40.txt")

@@ -1,0 +1,308 @@
+"""Pins of the CPU oracle against results fixed by the mathematics.
+
+Every check here compares the oracle with something other than itself:
+closed forms of Q(t), closed forms of U, brute-force enumeration of the path
+sum, Rabi oscillation at zero coupling, exact pure dephasing at zero
+tunnelling, the Markov map at memory length 1, and invariants (trace,
+Hermiticity).  The mutation tests at the end plant typical mistakes in a
+copy of the oracle and check that at least one pin catches each.
+"""
+import math
+import types
+
+import numpy as np
+import pytest
+from scipy import special
+
+import workloads as W
+from oracle import bath as B
+from oracle import brute, iquapi
+
+
+# ---------------------------------------------------------------- closed forms
+
+def ohmic_Q_closed(alpha, wc, beta, t):
+    """Q(t) for J = (pi/2) alpha w e^{-w/wc}: Im part elementary, Re part from
+    coth(x/2) = 1 + 2 sum e^{-n x}, the product summed through log-Gamma."""
+    t = np.asarray(t, dtype=float)
+    c = 1.0 / (beta * wc)
+    x = t / beta
+    series = 2.0 * special.loggamma(1.0 + c).real - 2.0 * special.loggamma(1.0 + c + 1j * x).real
+    re = 0.5 * alpha * (0.5 * np.log1p((wc * t) ** 2) + series)
+    im = -0.5 * alpha * (wc * t - np.arctan(wc * t))
+    return re + 1j * im
+
+
+def resonance_Q_closed(w0, gamma, lam, beta, t, nmat=400000):
+    """Q(t) for the resonance of Eq. sharpSD (a damped-oscillator density),
+    by residues: the two upper poles w = +-w~ + i gamma/2 and the Matsubara
+    poles i nu_n of coth, then the double time integral term by term."""
+    A = 2.0 * lam * gamma * w0 ** 2 / np.pi
+    wt = np.sqrt(w0 ** 2 - gamma ** 2 / 4)
+    wp = wt + 0.5j * gamma
+    z = 1j * wp
+    C = 1.0 / np.tanh(beta * wp / 2)
+    n = np.arange(1, nmat + 1)
+    nu = 2 * np.pi * n / beta
+    D = (nu ** 2 + w0 ** 2) ** 2 - gamma ** 2 * nu ** 2
+    out = []
+    for tt in np.atleast_1d(t):
+        I = (np.exp(z * tt) - 1 - z * tt) / z ** 2
+        mats = np.sum((nu / D) * (np.expm1(-nu * tt) + nu * tt) / nu ** 2)
+        out.append(A / (2 * gamma * wt) * ((C * I).real - 1j * I.imag) - (2 * A / beta) * mats)
+    return np.array(out)
+
+
+@pytest.mark.parametrize("alpha,wc,beta", [(0.1, 5.0, 5.0), (0.05, 5.0, 10.0),
+                                           (2 / 16 / math.pi ** 2, 10.0, 5.0), (0.3, 2.0, 0.7)])
+def test_ohmic_Q_matches_closed_form(alpha, wc, beta):
+    ts = np.array([0.05, 0.25, 0.5, 1.3, 2.25, 4.2])
+    bath = W.Bath(beta=beta, ohmic_alpha=alpha, ohmic_wc=wc)
+    np.testing.assert_allclose(B.Q_of_t(bath, ts), ohmic_Q_closed(alpha, wc, beta, ts), rtol=0, atol=2e-14)
+
+
+@pytest.mark.parametrize("w0,gamma,lam,beta", [(1.0, 0.05, 0.1, 10.0), (1.7, 0.3, 0.2, 2.0)])
+def test_resonance_Q_matches_closed_form(w0, gamma, lam, beta):
+    ts = np.array([0.1, 0.5, 1.0, 1.7])
+    bath = W.Bath(beta=beta, res_w0=w0, res_gamma=gamma, res_lambda=lam)
+    np.testing.assert_allclose(B.Q_of_t(bath, ts), resonance_Q_closed(w0, gamma, lam, beta, ts),
+                               rtol=0, atol=1e-14)
+
+
+def test_resonance_reorganisation_energy():
+    from scipy import integrate
+    bath = W.Bath(beta=1.0, res_w0=1.3, res_gamma=0.2, res_lambda=0.17)
+    lam = integrate.quad(lambda w: B.spectral_density(bath, w) / w, 0, np.inf, points=None, limit=500)[0]
+    assert abs(lam - 0.17) < 1e-9
+
+
+def test_eta_is_box_integral_of_Q():
+    """eta_0 = Q(dt) and sum over the triangle of box integrals equals Q(n dt):
+    n eta_0 + sum_d (n-d) eta_d = Q(n dt) with Q from the closed form."""
+    alpha, wc, beta, dt = 0.1, 5.0, 5.0, 0.25
+    bath = W.Bath(beta=beta, ohmic_alpha=alpha, ohmic_wc=wc)
+    eta = B.eta_coefficients(bath, dt, 10)
+    for n in range(1, 11):
+        tri = n * eta[0] + sum((n - d) * eta[d] for d in range(1, n))
+        assert abs(tri - ohmic_Q_closed(alpha, wc, beta, n * dt)) < 1e-13
+
+
+# ---------------------------------------------------------------- propagator
+
+def test_propagator_two_level_closed_form():
+    dt, delta = 0.37, 1.3
+    hs = np.array([[0, delta / 2], [delta / 2, 0]], dtype=complex)
+    U = iquapi.short_time_propagator(hs, dt)
+    c, s = math.cos(delta * dt / 2), math.sin(delta * dt / 2)
+    np.testing.assert_allclose(U, np.array([[c, -1j * s], [-1j * s, c]]), atol=1e-15)
+
+
+def test_propagator_three_level_chain_closed_form():
+    dt = 0.1
+    hs = np.array(W.CHAIN3_STRUCTURED_DK12.hs, dtype=complex)
+    r2 = math.sqrt(2.0)
+    V = np.array([[0.5, 1 / r2, 0.5], [r2 / 2, 0.0, -r2 / 2], [0.5, -1 / r2, 0.5]])
+    lam = np.array([r2, 0.0, -r2])
+    Uc = V @ np.diag(np.exp(-1j * lam * dt)) @ V.T
+    U = iquapi.short_time_propagator(hs, dt)
+    np.testing.assert_allclose(U, Uc, atol=1e-15)
+    np.testing.assert_allclose(U @ U.conj().T, np.eye(3), atol=1e-15)
+
+
+# ---------------------------------------------------------------- brute force
+
+@pytest.mark.parametrize("M,dkmax,N,seed", [(2, 1, 5, 1), (2, 2, 5, 2), (2, 3, 6, 3), (2, 4, 5, 4),
+                                            (2, 7, 5, 5), (3, 1, 3, 6), (3, 2, 4, 7), (3, 3, 4, 8)])
+def test_iterative_equals_brute_force(M, dkmax, N, seed):
+    c = W.random_case(seed, M, dkmax)
+    rb = brute.rho_by_enumeration(M, c["q"], c["hs"], c["dt"], c["eta"], dkmax, c["rho0"], N)
+    r = iquapi.propagate(M, c["q"], c["hs"], c["dt"], c["eta"], dkmax, None, 0.0, c["rho0"], N)
+    np.testing.assert_allclose(r.rho[N], rb, rtol=0, atol=2e-14)
+
+
+# ---------------------------------------------------------------- special cases
+
+@pytest.mark.parametrize("mask,dkmax", [(None, 6), ((0, 1, 2, 4), 6), ((0, 1), 5), ((0, 1, 2, 3, 4, 5, 7), 9)])
+def test_rabi_at_zero_coupling(mask, dkmax):
+    """eta = 0: <sigma_z>(t) = cos(Delta t), rho_updown = (i/2) sin(Delta t); the
+    merge is exact here for any mask."""
+    delta, dt, steps = 1.0, 0.25, 24
+    hs = np.array([[0, delta / 2], [delta / 2, 0]], dtype=complex)
+    r = iquapi.propagate(2, [1.0, -1.0], hs, dt, np.zeros(dkmax), dkmax, mask, 0.0,
+                         np.array([[1, 0], [0, 0]], dtype=complex), steps)
+    t = dt * np.arange(steps + 1)
+    np.testing.assert_allclose((r.rho[:, 0, 0] - r.rho[:, 1, 1]).real, np.cos(delta * t), atol=1e-13)
+    np.testing.assert_allclose(r.rho[:, 0, 1], 0.5j * np.sin(delta * t), atol=1e-13)
+
+
+@pytest.mark.parametrize("dkmax,mask", [(6, None), (6, (0, 1, 3))])
+def test_pure_dephasing_exact(dkmax, mask):
+    """H_S = 0: rho_ab(t) = rho_ab(0) exp(-(q_a-q_b)(q_a Q - q_b Q*)) with Q the
+    closed-form Q(t) up to t = dkmax dt, and the truncated triangle sum after."""
+    alpha, wc, beta, dt, steps = 0.1, 5.0, 5.0, 0.25, 14
+    bath = W.Bath(beta=beta, ohmic_alpha=alpha, ohmic_wc=wc)
+    eta = B.eta_coefficients(bath, dt, dkmax)
+    for M, q in [(2, np.array([1.0, -1.0])), (3, np.array([-1.0, 0.0, 1.0]))]:
+        rho0 = np.full((M, M), 1.0 / M, dtype=complex)
+        r = iquapi.propagate(M, q, np.zeros((M, M)), dt, eta, dkmax, mask, 0.0, rho0, steps)
+        for n in range(steps + 1):
+            if n <= dkmax:
+                Q = ohmic_Q_closed(alpha, wc, beta, n * dt) if n else 0.0
+            else:  # truncated memory: triangle of box integrals with lags < dkmax
+                Q = n * eta[0] + sum((n - d) * eta[d] for d in range(1, dkmax))
+            expect = rho0 * np.exp(-(q[:, None] - q[None, :]) * (q[:, None] * Q - q[None, :] * np.conj(Q)))
+            np.testing.assert_allclose(r.rho[n], expect, atol=1e-13)
+
+
+def test_markov_map_at_memory_one():
+    """dkmax = 1: rho(t) = Phi^t rho0 with Phi the one-step map on coherences."""
+    M = 3
+    c = W.random_case(11, M, 1)
+    U = iquapi.short_time_propagator(c["hs"], c["dt"])
+    q, e0 = c["q"], c["eta"][0]
+    Phi = np.zeros((M * M, M * M), dtype=complex)
+    for a in range(M):
+        for b in range(M):
+            f = np.exp(-(q[a] - q[b]) * (e0 * q[a] - np.conj(e0) * q[b]))
+            for ap in range(M):
+                for bp in range(M):
+                    Phi[a * M + b, ap * M + bp] = U[a, ap] * np.conj(U[b, bp]) * f
+    r = iquapi.propagate(M, q, c["hs"], c["dt"], c["eta"], 1, None, 0.0, c["rho0"], 9)
+    for n in range(10):
+        np.testing.assert_allclose(r.rho[n].reshape(-1), np.linalg.matrix_power(Phi, n) @ c["rho0"].reshape(-1),
+                                   atol=1e-14)
+
+
+# ---------------------------------------------------------------- invariants
+
+def _structured_case(M=2, dkmax=8):
+    rng = np.random.default_rng(5)
+    q = np.array([1.0, -1.0]) if M == 2 else np.array([-1.0, 0.0, 1.0])
+    hs = W.random_hermitian(rng, M, 0.7)
+    eta = W.random_eta(rng, dkmax, 0.08)
+    rho0 = W.random_density_matrix(rng, M)
+    return q, hs, eta, rho0
+
+
+@pytest.mark.parametrize("M,mask", [(2, (0, 1, 2, 5)), (2, (0, 1, 4, 6)), (3, (0, 1, 3))])
+def test_trace_conserved_by_masked_merge(M, mask):
+    q, hs, eta, rho0 = _structured_case(M, 8 if M == 2 else 5)
+    dk = 8 if M == 2 else 5
+    r = iquapi.propagate(M, q, hs, 0.2, eta, dk, mask, 0.0, rho0, 16)
+    tr = np.trace(r.rho, axis1=1, axis2=2)
+    np.testing.assert_allclose(tr, np.ones_like(tr), atol=1e-13)
+
+
+def test_hermitian_without_mask():
+    q, hs, eta, rho0 = _structured_case(2, 6)
+    r = iquapi.propagate(2, q, hs, 0.2, eta, 6, None, 0.0, rho0, 12)
+    np.testing.assert_allclose(r.rho, np.conj(np.swapaxes(r.rho, 1, 2)), atol=1e-15)
+
+
+def test_full_mask_and_zero_theta_are_defaults():
+    q, hs, eta, rho0 = _structured_case(2, 5)
+    a = iquapi.propagate(2, q, hs, 0.2, eta, 5, None, 0.0, rho0, 9)
+    b = iquapi.propagate(2, q, hs, 0.2, eta, 5, tuple(range(5)), 0.0, rho0, 9)
+    np.testing.assert_array_equal(a.rho, b.rho)
+
+
+def test_filter_removes_paths_and_trace_loss_grows():
+    q, hs, eta, rho0 = _structured_case(2, 8)
+    losses, counts = [], []
+    for th in (0.0, 1e-6, 1e-4, 1e-3):
+        r = iquapi.propagate(2, q, hs, 0.2, eta, 8, (0, 1, 2, 5), th, rho0, 14)
+        losses.append(abs(1 - np.trace(r.rho[-1]).real))
+        counts.append(r.paths.amp.size)
+    assert counts == sorted(counts, reverse=True) and counts[0] > counts[-1]
+    assert losses[0] < 1e-13 and losses[-1] > losses[0]
+
+
+def test_mask_validation():
+    with pytest.raises(ValueError):
+        iquapi.check_mask((0, 2), 6)
+    with pytest.raises(ValueError):
+        iquapi.check_mask((0, 1, 6), 6)
+    assert iquapi.premerge_positions((0, 1, 2, 3, 4, 5, 6, 7, 8, 12), 16) == [0, 1, 2, 3, 4, 5, 6, 7, 11]
+    assert iquapi.premerge_positions((0,), 1) == [0]
+
+
+def test_packed_key_layout():
+    sp = np.array([[1, 0, 1]])
+    sm = np.array([[0, 1, 1]])
+    # position p uses bits [2p, 2p+2): s+ low bit, s- high bit
+    assert int(iquapi.packed_keys(sp, sm, 2)[0]) == (1 | 0 << 1) | ((0 | 1 << 1) << 2) | ((1 | 1 << 1) << 4)
+    sp3 = np.array([[2, 1]])
+    sm3 = np.array([[0, 2]])
+    assert int(iquapi.packed_keys(sp3, sm3, 3)[0]) == (2 | 0 << 2) | ((1 | 2 << 2) << 4)
+
+
+def test_representative_is_largest_weight_then_smallest_key():
+    """A group of three members, two with equal |amp| (to 1e-14 relative):
+    the representative is the smaller key of the two; the sum is over all."""
+    M = 2
+    sp = np.array([[0, 1, 0], [0, 1, 1], [0, 0, 1]])
+    sm = np.array([[0, 0, 1], [0, 0, 0], [0, 1, 0]])
+    amp = np.array([0.3 + 0.4j, 0.5 * (1 + 1e-14), 0.1j])
+    rsp, rsm, S, _ = iquapi.premerge(iquapi.Paths(sp, sm, amp), [0], M)
+    assert S.size == 1 and abs(S[0] - amp.sum()) < 1e-15
+    keys = iquapi.packed_keys(sp, sm, M)
+    want = int(min(keys[0], keys[1]))
+    assert int(iquapi.packed_keys(rsp, rsm, M)[0]) == want
+
+
+# ---------------------------------------------------------------- planted mistakes
+
+MUTATIONS = {
+    "dropped conjugate in history": ("- np.conj(eta[d]) * q[rsm[:, d - 1]]", "- eta[d] * q[rsm[:, d - 1]]"),
+    "history index off by one": ("q[rsp[:, d - 1]]", "q[rsp[:, d]]"),
+    "wrong sign of new-point term": ("(H + eta[0] * q[a] - np.conj(eta[0]) * q[b])",
+                                     "(H - eta[0] * q[a] - np.conj(eta[0]) * q[b])"),
+    "transposed propagator": ("prop = U[a, rsp[:, 0]] * np.conj(U[b, rsm[:, 0]])",
+                              "prop = U[rsp[:, 0], a] * np.conj(U[b, rsm[:, 0]])"),
+    "backward branch not conjugated": ("np.conj(U[b, rsm[:, 0]])", "U[b, rsm[:, 0]]"),
+    "history misses the last lag": ("for d in range(1, n_act):", "for d in range(1, n_act - 1):"),
+    "sum keeps one member per group": ("np.add.at(S, inv, paths.amp)", "S[inv] = paths.amp"),
+    "new point enters the history sum": ("for d in range(1, n_act):", "for d in range(0, n_act):"),
+}
+
+
+def _mutant(src_old, src_new):
+    import inspect
+    src = inspect.getsource(iquapi)
+    assert src_old in src, src_old
+    import sys
+    name = "iquapi_mutant"
+    mod = types.ModuleType(name)
+    sys.modules[name] = mod
+    try:
+        exec(compile(src.replace(src_old, src_new), name, "exec"), mod.__dict__)
+    finally:
+        del sys.modules[name]
+    return mod
+
+
+def _pins_pass(mod):
+    try:
+        for (M, dkmax, N, seed) in [(2, 3, 5, 3), (3, 2, 4, 7), (2, 2, 5, 12)]:
+            c = W.random_case(seed, M, dkmax)
+            rb = brute.rho_by_enumeration(M, c["q"], c["hs"], c["dt"], c["eta"], dkmax, c["rho0"], N)
+            r = mod.propagate(M, c["q"], c["hs"], c["dt"], c["eta"], dkmax, None, 0.0, c["rho0"], N)
+            if np.abs(r.rho[N] - rb).max() > 2e-14:
+                return False
+        q, hs, eta, rho0 = _structured_case(2, 8)
+        r = mod.propagate(2, q, hs, 0.2, eta, 8, (0, 1, 2, 5), 0.0, rho0, 16)
+        if np.abs(np.trace(r.rho, axis1=1, axis2=2) - 1).max() > 1e-13:
+            return False
+        return True
+    except Exception:
+        return False
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(name):
+    old, new = MUTATIONS[name]
+    assert not _pins_pass(_mutant(old, new)), f"pins missed: {name}"
+
+
+def test_unmutated_oracle_passes_mutation_harness():
+    assert _pins_pass(iquapi)
