@@ -1,0 +1,333 @@
+"""Benchmark of the MACGIC-iQUAPI per-step path update on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload NAME] [--precision fp64|c64]
+
+Workload (default): the structured-bath spin-boson model with memory 16 and
+the 10-point MACGIC mask, filter 1e-9 (workloads.SPIN_BOSON_STRUCTURED_DK16).
+The trajectory is propagated to t = T0 (steady path count), then W untimed
+steps, then K timed steps.  One benchmark step = one propagation step
+(pre-merge, extension, influence, filter, rho) over the whole stored set.
+Between timed steps the L2 cache is flushed (a 512 MB write on the same
+stream, outside the timed events).  Metric: extended paths per second =
+sum over timed steps of (groups * M^2) / sum of the steps' CUDA-event times.
+
+--impl reference times the FP64 CPU oracle (the deliberately plain
+reference) on the same workload and metric on the host cores.
+Multi-GPU (torchrun): independent replicas of the workload, one per rank.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+WORKLOADS = {
+    "spin_boson_structured_dk16": W.SPIN_BOSON_STRUCTURED_DK16,
+    "spin_boson_ohmic_dk8": W.SPIN_BOSON_OHMIC_DK8,
+    "chain3_structured_dk12": W.CHAIN3_STRUCTURED_DK12,
+    "tls_ohmic_full_dk14": W.TLS_OHMIC_FULL_DK14,
+}
+METRIC = "extended paths/s"
+T0_DEFAULT = 100
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.rows = []
+        self.proc = None
+        self.gpu = gpu_index
+        self.on = False
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            if self.on:
+                self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+                for n, v in zip(names, r[4:8]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def algorithmic_bytes(stats_rows, M, amp_bytes, merge):
+    """Per-kernel algorithmic DRAM bytes for a list of steps:
+    stored path = 8 B key + amp_bytes; merge-table slot 32 B + 8 B key."""
+    E = 8 + amp_bytes
+    ins = tie = exp = 0
+    for (t, groups, extended, kept), n_in in stats_rows:
+        if merge(t):
+            ins += n_in * (E + 4) + groups * 32
+            tie += n_in * (E + 4) + groups * 16
+            exp += groups * (4 + 8 + 32 + 40) + kept * E
+        else:
+            exp += n_in * E + kept * E
+    return np.array([ins, tie, exp, 0.0])
+
+
+def run_ours(args, rank, world):
+    import torch
+    from paper_2506_03127_gb300 import Propagator, build
+
+    if rank == 0:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+        build.build()
+    w = WORKLOADS[args.workload]
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    amp_bytes = 16 if args.precision == "fp64" else 8
+    t_setup = time.perf_counter()
+    p = Propagator.from_workload(w, precision=args.precision, max_paths=args.max_paths)
+    p.step(args.t0)
+    p.sync()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=f"cuda:{dev}")
+    for _ in range(args.warmup):
+        p.step(1)
+        with torch.cuda.stream(p.stream):
+            flush.zero_()
+    p.sync()
+    t_first = p.current()[0] + 1
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    smi_id = vis.split(",")[dev] if vis else str(dev)
+    clocks = ClockSampler(smi_id)
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.on = True
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        starts[k].record(p.stream)
+        p.step(1)
+        ends[k].record(p.stream)
+        with torch.cuda.stream(p.stream):
+            flush.zero_()
+    torch.cuda.synchronize()
+    wall1 = time.perf_counter()
+    if wall1 - wall0 < 1.0:
+        time.sleep(1.0 - (wall1 - wall0))
+    clocks.on = False
+    clocks.stop()
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms = np.array([s.elapsed_time(e) for s, e in zip(starts, ends)])
+    stats = p.stats(t_first, args.steps)
+    prev = p.stats(t_first - 1, args.steps)
+    n_in = [r[3] for r in prev]
+    extended = float(sum(r[2] for r in stats))
+    t_ms = float(step_ms.sum())
+    # roofline: per-kernel CUDA-event times over a further run of steps
+    nprof = min(args.steps, 200)
+    prof_first = p.current()[0] + 1
+    kern_ms = p.profile(nprof)
+    pstats = p.stats(prof_first, nprof)
+    pprev = p.stats(prof_first - 1, nprof)
+    merge = (lambda t: t >= w.dkmax)
+    abytes = algorithmic_bytes(list(zip(pstats, [r[3] for r in pprev])), w.M, amp_bytes, merge)
+    names = ["premerge_insert", "premerge_tiebreak", "expand_influence_filter_rho", "finalize"]
+    dom = int(np.argmax(kern_ms))
+    peak, peak_src = peaks()
+    achieved = abytes[dom] / (kern_ms[dom] / 1e3) / 1e9 if kern_ms[dom] > 0 else 0.0
+    roof = {"bound": "hbm", "kernel": names[dom], "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": None, "peak_source": peak_src,
+            "kernel_share": {n: round(float(m / kern_ms.sum()), 4) for n, m in zip(names, kern_ms)},
+            "kernel_avg_us": {n: round(float(m / nprof * 1e3), 2) for n, m in zip(names, kern_ms)}}
+
+    # end to end through the public API from host inputs: set eta/mask/rho0
+    # from host arrays, then per step qp_step + read rho(t) back to the host
+    e2e_steps = args.t0 + args.warmup + args.steps
+    from paper_2506_03127_gb300 import eta_from_bath
+    eta_h = eta_from_bath(w.bath, w.dt, w.dkmax)
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    p.set_eta(eta_h)
+    p.set_mask(w.mask)
+    p.set_rho0(w.rho0_array())
+    for s in range(e2e_steps):
+        p.step(1)
+        p.rho(s + 1, 1)
+    e1 = time.perf_counter()
+    e_stats = p.stats(1, e2e_steps)
+    e2e_ext = float(sum(r[2] for r in e_stats))
+    h2d = (eta_h.size * 16 + len(w.mask_list()) * 4 + w.M * w.M * 16) / e2e_steps
+    d2h = w.M * w.M * 16 + 64
+    p.close()
+
+    res = dict(ext=extended, t_ms=t_ms, wall=wall1 - wall0, e2e=e2e_ext / (e1 - e0), roof=roof,
+               clocks=clocks.summary(), h2d=h2d, d2h=d2h, step_ms=step_ms, stats=stats,
+               kernels_per_step=4)
+    return res
+
+
+def cpu_baseline(w, steps_total=60, timed_from=None):
+    """Oracle (FP64 CPU, as it stands) on a bounded sample of the workload:
+    propagate from t = 0 and time the steps after the window is full."""
+    from oracle import bath, iquapi
+    eta = bath.eta_coefficients(w.bath, w.dt, w.dkmax)
+    P = iquapi.check_mask(w.mask_list(), w.dkmax)
+    Pp = iquapi.premerge_positions(P, w.dkmax)
+    U = iquapi.short_time_propagator(w.hs_array(), w.dt)
+    q = np.asarray(w.q)
+    paths = iquapi.initial_paths(w.rho0_array())
+    timed_from = w.dkmax + 1 if timed_from is None else timed_from
+    ext, sec = 0, 0.0
+    for t in range(1, steps_total + 1):
+        t0 = time.perf_counter()
+        paths, rho, st = iquapi.step(paths, t, U, q, eta, w.dkmax, Pp, w.theta, w.M)
+        dt = time.perf_counter() - t0
+        if t >= timed_from:
+            ext += st.extended
+            sec += dt
+    return ext / sec, f"oracle steps 1..{steps_total} of {w.name}, timed steps {timed_from}..{steps_total}"
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="spin_boson_structured_dk16", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "c64"])
+    ap.add_argument("--t0", type=int, default=T0_DEFAULT)
+    ap.add_argument("--max-paths", type=int, default=1 << 21)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    assert args.warmup >= 3, "at least 3 warm-up steps"
+
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    w = WORKLOADS[args.workload]
+    cfg = {"workload": w.name, "M": w.M, "dkmax": w.dkmax, "mask": w.mask_list(), "theta": w.theta,
+           "dt": w.dt, "t0": args.t0, "precision": args.precision, "engine": "hash",
+           "l2": "flushed between timed steps (512 MB write)", "parallelism": f"replicas{args.gpus}"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        # each benchmark step = one oracle propagation step of the workload
+        from oracle import bath, iquapi
+        eta = bath.eta_coefficients(w.bath, w.dt, w.dkmax)
+        P = iquapi.check_mask(w.mask_list(), w.dkmax)
+        Pp = iquapi.premerge_positions(P, w.dkmax)
+        U = iquapi.short_time_propagator(w.hs_array(), w.dt)
+        paths = iquapi.initial_paths(w.rho0_array())
+        t = 0
+        t_start = w.dkmax + 1
+        while t < t_start + args.warmup:
+            t += 1
+            paths, _, _ = iquapi.step(paths, t, U, np.asarray(w.q), eta, w.dkmax, Pp, w.theta, w.M)
+        ext, sec = 0, 0.0
+        for _ in range(args.steps):
+            t += 1
+            a = time.perf_counter()
+            paths, _, st = iquapi.step(paths, t, U, np.asarray(w.q), eta, w.dkmax, Pp, w.theta, w.M)
+            sec += time.perf_counter() - a
+            ext += st.extended
+        v = ext / sec
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "paths/s", "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": dict(cfg, t0=t_start, precision="fp64", engine="oracle"),
+                "cpu_baseline": {"value": v, "unit": "paths/s", "cores": 1, "kind": "oracle",
+                                 "sample": f"{args.steps} oracle steps after t={t_start + args.warmup}"},
+                "e2e": {"value": v, "unit": "paths/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    res = run_ours(args, rank, world)
+    t_ms, ext = res["t_ms"], res["ext"]
+    if world > 1:
+        import torch
+        tt = torch.tensor([t_ms, ext], dtype=torch.float64, device="cuda")
+        mx = tt.clone()
+        torch.distributed.all_reduce(mx[:1], op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(tt[1:], op=torch.distributed.ReduceOp.SUM)
+        t_ms, ext = float(mx[0]), float(tt[1])
+    if rank != 0:
+        return
+    value = ext / (t_ms / 1e3)
+    line = {"metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "c64", "data": "synthetic",
+            "config": cfg, "clocks": res["clocks"], "roofline": res["roof"],
+            "e2e": {"value": res["e2e"], "unit": "paths/s", "h2d_bytes_per_step": round(res["h2d"], 2),
+                    "d2h_bytes_per_step": res["d2h"]},
+            "gpu_launches": args.steps * res["kernels_per_step"],
+            "s_per_step": t_ms / args.steps / 1e3,
+            "paths_per_step": {"extended_mean": ext / args.steps / max(1, world),
+                               "kept_last": int(res["stats"][-1][3])}}
+    if not args.no_cpu_baseline and world == 1:
+        v, sample = cpu_baseline(W.SPIN_BOSON_STRUCTURED_DK16 if args.workload == "spin_boson_structured_dk16"
+                                 else WORKLOADS[args.workload])
+        line["cpu_baseline"] = {"value": v, "unit": "paths/s", "cores": 1, "kind": "oracle", "sample": sample}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,193 @@
+/*
+ * qp.h - C ABI of the GB300 MACGIC-iQUAPI path-update library (libqp.so).
+ *
+ * The library propagates the reduced density matrix rho(t) of an M-state
+ * system linearly coupled to a harmonic bath (paper Sec. 2, Eq. tot_ham) by
+ * the iterative quasi-adiabatic path integral with the MACGIC mask and the
+ * pre-merging order of Sec. 3.1.  One call of qp_step advances the stored
+ * path set Omega(t-1) -> Omega(t):
+ *
+ *   1. pre-merge: paths identical on the shifted mask P' are merged; the
+ *      group keeps its largest-weight path and the summed weight
+ *      (Sec. 3.1 "Pre-merging", routine premerging());
+ *   2. extension by all M^2 new forward/backward points, each child weighted
+ *      by the bare propagator (Eqs. SysP0, SysP) and the influence factor of
+ *      the new point (Eq. inf_fun with Toeplitz coefficients eta_d);
+ *   3. filter: children with |amplitude| < theta are dropped (Sec. 2.1);
+ *   4. rho(t): surviving children summed by end point (Eq. quapi_red_rho).
+ *
+ * Conventions
+ *   - hbar = 1.  Every function returns qp_status and never aborts, throws or
+ *     prints; qp_last_error(ctx) gives a one-line reason for the last failure.
+ *   - Host arrays passed in are caller-owned and copied before the call
+ *     returns; host arrays passed out are written before the call returns.
+ *   - Device memory: the library performs no device allocation.  The caller
+ *     provides one device workspace (size from qp_workspace_size, 256-byte
+ *     aligned), which must outlive the context.  All device work is ordered
+ *     on the CUDA stream given to qp_create (a cudaStream_t passed as void*;
+ *     NULL = the legacy default stream).
+ *   - Calls that read results back (qp_read_*, qp_sync, qp_export_paths)
+ *     synchronise the stream and report device-side errors (capacity
+ *     overflow of the path buffers or of the merge table).  After such an
+ *     error the context refuses qp_step with QP_ERR_STATE until qp_set_rho0
+ *     restarts the propagation.
+ *   - Packed path key: a stored path is the window of its newest
+ *     min(t+1, dkmax) points.  With bs = max(1, ceil(log2 M)) bits per state
+ *     and b = 2*bs bits per point, window position p (0 = newest point)
+ *     occupies bits [b*p, b*p + b) of a uint64: s+ in the low bs bits, s- in
+ *     the high bs bits.  Requires b * dkmax <= 64.
+ *   - Supported system sizes: 2 <= M <= 4.
+ *   - Not thread-safe per context; distinct contexts are independent.
+ */
+#ifndef QP_H
+#define QP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    QP_OK = 0,
+    QP_ERR_ARG = 1,       /* invalid argument or configuration            */
+    QP_ERR_OOM = 2,       /* workspace too small / host allocation failed */
+    QP_ERR_CUDA = 3,      /* a CUDA runtime call failed                   */
+    QP_ERR_CAPACITY = 4,  /* path buffer or merge table overflowed        */
+    QP_ERR_TIMEOUT = 5,   /* a bounded device-side wait gave up           */
+    QP_ERR_STATE = 6      /* call not valid in the context's state        */
+} qp_status;
+
+enum { QP_FP64 = 0,       /* complex128 amplitudes, FP64 everywhere */
+       QP_C64 = 1 };      /* complex64 amplitudes, FP32 influence exponent
+                             with compensated sums; FP64 eta, merge sums, rho */
+
+enum { QP_ENGINE_AUTO = 0,    /* library picks                                 */
+       QP_ENGINE_HASH = 1,    /* device open-addressing table keyed by the
+                                 masked key (any mask)                          */
+       QP_ENGINE_STREAM = 2   /* order-preserving stream: groups stay
+                                 contiguous, merge = segmented reduction
+                                 (masks whose P' is a prefix {0..k-1})         */ };
+
+typedef struct {
+    int M;                 /* number of system states (DVR points), 2..4            */
+    int dkmax;             /* memory length Delta k_max (window points), >= 1       */
+    double dt;             /* Trotter time step                                     */
+    const double *q;       /* [M] coupling eigenvalues q_i of Eq. tot_ham           */
+    const double *hs_re;   /* [M*M] row-major real part of H_S (Hermitian)          */
+    const double *hs_im;   /* [M*M] row-major imaginary part of H_S (NULL = 0)      */
+    int precision;         /* QP_FP64 or QP_C64                                     */
+    int engine;            /* QP_ENGINE_*                                            */
+    double theta;          /* filter threshold on |amplitude| (0 = keep all)        */
+    int64_t max_paths;     /* capacity of each stored-path buffer, entries          */
+    int64_t max_groups;    /* capacity of the merge table, groups (0 = max_paths)   */
+    int rho_history;       /* rho(t) slots kept on the device, ring (0 = 4096)      */
+} qp_config;
+
+/* Spectral density J(w) = (pi/2) ohmic_alpha w exp(-w/ohmic_wc)
+ *                       + the resonance of Eq. sharpSD with Omega = res_w0,
+ *                         width 2 pi kappa Omega = res_gamma and amplitude
+ *                         fixed by lambda = int J/w dw = res_lambda.
+ * A part is off when its strength (ohmic_alpha, res_lambda) is 0.          */
+typedef struct {
+    double beta;           /* inverse temperature 1/kT                              */
+    double ohmic_alpha, ohmic_wc;
+    double res_w0, res_gamma, res_lambda;
+} qp_bath;
+
+typedef struct {
+    int64_t t;             /* time step index of the stored set              */
+    int64_t groups;        /* parents of the step (entries after pre-merge)  */
+    int64_t extended;      /* children generated, groups * M^2               */
+    int64_t kept;          /* children surviving the filter = stored paths   */
+} qp_step_stats;
+
+typedef struct qp_ctx qp_ctx;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int qp_version(void);
+
+/* Static string for a status code. */
+const char *qp_status_string(qp_status s);
+
+/* Device bytes the caller must provide to qp_create for this configuration.
+ * Validates cfg (QP_ERR_ARG on an invalid one).  Host only, no GPU needed.  */
+qp_status qp_workspace_size(const qp_config *cfg, size_t *bytes);
+
+/* Create a context on the current CUDA device.  d_workspace: device pointer,
+ * 256-byte aligned, at least qp_workspace_size bytes, owned by the caller.
+ * cuda_stream: cudaStream_t or NULL.  On success *out is a new context in
+ * the "no initial state" phase (call qp_set_eta, optionally qp_set_mask,
+ * then qp_set_rho0 before stepping).                                       */
+qp_status qp_create(const qp_config *cfg, void *d_workspace, size_t bytes,
+                    void *cuda_stream, qp_ctx **out);
+
+/* Release the host side of the context (the workspace stays the caller's).
+ * Safe on NULL.                                                              */
+void qp_destroy(qp_ctx *ctx);
+
+/* Influence coefficients eta_0 .. eta_{n-1} from a spectral density (paper
+ * Eq. inf_fun; explicit forms per its refs): with the point q_k held on the
+ * box ((k-1) dt, k dt] and alpha(t) = (1/pi) int J [coth(beta w/2) cos wt -
+ * i sin wt] dw,
+ *   eta_0 = (1/pi) int J/w^2 [coth(beta w/2)(1 - cos w dt) - i (w dt - sin w dt)] dw
+ *   eta_d = (4/pi) int J/w^2 sin^2(w dt/2) [coth(beta w/2) cos(w d dt) - i sin(w d dt)] dw.
+ * Host FP64 adaptive Gauss-Legendre quadrature; no GPU needed.  re/im: [n]
+ * caller-owned outputs.                                                     */
+qp_status qp_eta_from_bath(const qp_bath *bath, double dt, int n, double *eta_re, double *eta_im);
+
+/* Set eta_0 .. eta_{dkmax-1} (n >= dkmax; extra entries ignored).  Builds the
+ * device tables of the history sum and of propagator x new-point influence. */
+qp_status qp_set_eta(qp_ctx *ctx, const double *eta_re, const double *eta_im, int n);
+
+/* MACGIC mask P: the window positions at time t (0 = newest) on which paths
+ * must agree to merge (Sec. 2.1).  Must contain 0, and 1 when dkmax >= 2;
+ * positions in [0, dkmax).  The pre-merge uses P' = {p-1 : p in P, p >= 1}
+ * plus position 0 (the paper's mask[i] -> mask[i]+1 shift, Sec. 3.1).
+ * positions == NULL or n == 0: the full mask (plain iQUAPI).  Takes effect
+ * from the next qp_step.                                                     */
+qp_status qp_set_mask(qp_ctx *ctx, const int *positions, int n);
+
+/* Restart the propagation at t = 0 from rho(0) (M*M row-major, Hermitian):
+ * one stored path per nonzero element.  im may be NULL (real rho0).  Clears
+ * any device error state.  Requires qp_set_eta to have been called.         */
+qp_status qp_set_rho0(qp_ctx *ctx, const double *rho0_re, const double *rho0_im);
+
+/* Enqueue nsteps propagation steps on the context's stream (asynchronous;
+ * errors raised on the device surface at the next synchronising call).     */
+qp_status qp_step(qp_ctx *ctx, int nsteps);
+
+/* Wait for the stream; report a device-side error if one was raised.       */
+qp_status qp_sync(qp_ctx *ctx);
+
+/* Current time step and number of stored paths (synchronises).              */
+qp_status qp_current(qp_ctx *ctx, int64_t *t, int64_t *n_paths);
+
+/* rho(t) for count consecutive steps t0 .. t0+count-1 (synchronises).  Each
+ * step must be among the last rho_history steps.  re/im: [count*M*M].      */
+qp_status qp_read_rho(qp_ctx *ctx, int64_t t0, int count, double *rho_re, double *rho_im);
+
+/* Per-step path counts for steps t0 .. t0+count-1 (1 <= t, synchronises).   */
+qp_status qp_read_stats(qp_ctx *ctx, int64_t t0, int count, qp_step_stats *out);
+
+/* Copy the stored path set Omega(t) to host arrays: keys[cap] packed keys,
+ * amps[2*cap] interleaved (re, im) as FP64 whatever the precision.  *n gets
+ * the number of stored paths; QP_ERR_CAPACITY (nothing copied) if > cap.
+ * The order of the entries is unspecified.                                   */
+qp_status qp_export_paths(qp_ctx *ctx, uint64_t *keys, double *amps, int64_t cap, int64_t *n);
+
+/* Run nsteps propagation steps like qp_step, but launch the kernels one by
+ * one with CUDA events between them, and add each kernel's elapsed time in
+ * milliseconds to kernel_ms[k] (synchronises).  Kernel order: k = 0 merge
+ * insert, 1 merge tie-break, 2 extension/filter/rho, 3 step finalisation.
+ * nk = length of kernel_ms (at most 4 entries are written).               */
+qp_status qp_profile_steps(qp_ctx *ctx, int nsteps, double *kernel_ms, int nk);
+
+/* Last error message of the context ("" if none).                           */
+const char *qp_last_error(const qp_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QP_H */

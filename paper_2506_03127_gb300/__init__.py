@@ -1,0 +1,107 @@
+"""GB300-native MACGIC-iQUAPI per-step path update.
+
+The propagation runs in libqp (hand-written sm_103a CUDA behind the C ABI of
+include/qp.h).  This package holds the ctypes binding (``abi``), the build
+script (``build``) and ``Propagator``, a convenience wrapper that takes the
+device workspace and the CUDA stream from PyTorch.  PyTorch is used only for
+device memory and streams.
+"""
+from __future__ import annotations
+
+import importlib
+
+import numpy as np
+
+__all__ = ["abi", "Propagator", "eta_from_bath"]
+
+
+def _abi():
+    return importlib.import_module(".abi", __name__)
+
+
+def __getattr__(name):
+    # the binding loads libqp.so; import it on first use so that the build
+    # script (a submodule) can run before the library exists
+    if name == "abi":
+        return importlib.import_module(".abi", __name__)
+    raise AttributeError(name)
+
+
+def eta_from_bath(bath, dt: float, n: int) -> np.ndarray:
+    """Influence coefficients eta_0..eta_{n-1} (host FP64 quadrature in libqp)."""
+    return _abi().qp_eta_from_bath(bath, dt, n)
+
+
+class Propagator:
+    """One propagation context: owns a device workspace tensor and a stream."""
+
+    def __init__(self, M, dkmax, dt, q, hs, theta=0.0, precision="fp64", engine="auto",
+                 max_paths=1 << 20, max_groups=0, rho_history=4096, device=None, stream=None):
+        import torch
+        from . import abi
+        if not torch.cuda.is_available():
+            raise RuntimeError("Propagator needs a CUDA device")
+        self.M = M
+        self.dkmax = dkmax
+        prec = {"fp64": abi.QP_FP64, "c64": abi.QP_C64}[precision]
+        eng = {"auto": abi.QP_ENGINE_AUTO, "hash": abi.QP_ENGINE_HASH, "stream": abi.QP_ENGINE_STREAM}[engine]
+        self._cfg, self._keep = abi.make_config(M, dkmax, dt, q, hs, theta, prec, eng, max_paths, max_groups,
+                                                rho_history)
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+            self.nbytes = _abi().qp_workspace_size(self._cfg)
+            self.workspace = torch.empty(self.nbytes, dtype=torch.uint8, device=self.device)
+            self.ctx = _abi().qp_create(self._cfg, self.workspace.data_ptr(), self.nbytes, self.stream.cuda_stream)
+
+    @classmethod
+    def from_workload(cls, w, precision="fp64", engine="auto", max_paths=1 << 20, max_groups=0, **kw):
+        p = cls(w.M, w.dkmax, w.dt, w.q, w.hs_array(), w.theta, precision, engine, max_paths, max_groups, **kw)
+        p.set_eta(eta_from_bath(w.bath, w.dt, w.dkmax))
+        p.set_mask(w.mask)
+        p.set_rho0(w.rho0_array())
+        return p
+
+    def set_eta(self, eta):
+        _abi().qp_set_eta(self.ctx, eta)
+
+    def set_mask(self, positions):
+        _abi().qp_set_mask(self.ctx, positions)
+
+    def set_rho0(self, rho0):
+        _abi().qp_set_rho0(self.ctx, rho0)
+
+    def step(self, nsteps=1):
+        _abi().qp_step(self.ctx, nsteps)
+
+    def sync(self):
+        _abi().qp_sync(self.ctx)
+
+    def current(self):
+        return _abi().qp_current(self.ctx)
+
+    def rho(self, t0, count=1):
+        return _abi().qp_read_rho(self.ctx, t0, count, self.M)
+
+    def stats(self, t0, count=1):
+        return _abi().qp_read_stats(self.ctx, t0, count)
+
+    def profile(self, nsteps):
+        """Run nsteps steps kernel by kernel; per-kernel milliseconds (CUDA events)."""
+        return _abi().qp_profile_steps(self.ctx, nsteps)
+
+    def export_paths(self, cap=None):
+        if cap is None:
+            cap = self.current()[1]
+        return _abi().qp_export_paths(self.ctx, cap)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            _abi().qp_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

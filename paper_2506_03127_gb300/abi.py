@@ -1,0 +1,199 @@
+"""ctypes binding of libqp (include/qp.h): same names, argument marshalling only.
+
+Every computation of the path update runs in the library's CUDA kernels.
+Importing this module loads the in-tree libqp.so and fails loudly if it is
+missing; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libqp.so")
+
+QP_OK, QP_ERR_ARG, QP_ERR_OOM, QP_ERR_CUDA, QP_ERR_CAPACITY, QP_ERR_TIMEOUT, QP_ERR_STATE = range(7)
+QP_FP64, QP_C64 = 0, 1
+QP_ENGINE_AUTO, QP_ENGINE_HASH, QP_ENGINE_STREAM = 0, 1, 2
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+
+
+class qp_config(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int), ("dkmax", ctypes.c_int), ("dt", ctypes.c_double),
+                ("q", _dp), ("hs_re", _dp), ("hs_im", _dp),
+                ("precision", ctypes.c_int), ("engine", ctypes.c_int), ("theta", ctypes.c_double),
+                ("max_paths", ctypes.c_int64), ("max_groups", ctypes.c_int64), ("rho_history", ctypes.c_int)]
+
+
+class qp_bath(ctypes.Structure):
+    _fields_ = [("beta", ctypes.c_double), ("ohmic_alpha", ctypes.c_double), ("ohmic_wc", ctypes.c_double),
+                ("res_w0", ctypes.c_double), ("res_gamma", ctypes.c_double), ("res_lambda", ctypes.c_double)]
+
+
+class qp_step_stats(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_int64), ("groups", ctypes.c_int64), ("extended", ctypes.c_int64),
+                ("kept", ctypes.c_int64)]
+
+
+class QPError(RuntimeError):
+    def __init__(self, status, msg=""):
+        self.status = status
+        super().__init__(f"{lib.qp_status_string(status).decode()} ({status}): {msg}")
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libqp.so not built at {LIB_PATH}; run `python -m paper_2506_03127_gb300.build`")
+    L = ctypes.CDLL(LIB_PATH)
+    sig = {
+        "qp_version": (ctypes.c_int, []),
+        "qp_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+        "qp_workspace_size": (ctypes.c_int, [ctypes.POINTER(qp_config), ctypes.POINTER(ctypes.c_size_t)]),
+        "qp_create": (ctypes.c_int, [ctypes.POINTER(qp_config), ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                                     ctypes.POINTER(ctypes.c_void_p)]),
+        "qp_destroy": (None, [ctypes.c_void_p]),
+        "qp_eta_from_bath": (ctypes.c_int, [ctypes.POINTER(qp_bath), ctypes.c_double, ctypes.c_int, _dp, _dp]),
+        "qp_set_eta": (ctypes.c_int, [ctypes.c_void_p, _dp, _dp, ctypes.c_int]),
+        "qp_set_mask": (ctypes.c_int, [ctypes.c_void_p, _ip, ctypes.c_int]),
+        "qp_set_rho0": (ctypes.c_int, [ctypes.c_void_p, _dp, _dp]),
+        "qp_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+        "qp_sync": (ctypes.c_int, [ctypes.c_void_p]),
+        "qp_current": (ctypes.c_int, [ctypes.c_void_p, _i64p, _i64p]),
+        "qp_read_rho": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, _dp, _dp]),
+        "qp_read_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
+                                         ctypes.POINTER(qp_step_stats)]),
+        "qp_export_paths": (ctypes.c_int, [ctypes.c_void_p, _u64p, _dp, ctypes.c_int64, _i64p]),
+        "qp_profile_steps": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _dp, ctypes.c_int]),
+        "qp_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    return L
+
+
+lib = _load()
+
+
+def _arr(x, dtype=np.float64):
+    return np.ascontiguousarray(np.asarray(x, dtype=dtype))
+
+
+def _ptr(a, t=_dp):
+    return a.ctypes.data_as(t)
+
+
+def check(status, ctx=None):
+    if status != QP_OK:
+        msg = lib.qp_last_error(ctx).decode() if ctx else ""
+        raise QPError(status, msg)
+
+
+def make_config(M, dkmax, dt, q, hs, theta=0.0, precision=QP_FP64, engine=QP_ENGINE_AUTO,
+                max_paths=1 << 20, max_groups=0, rho_history=4096):
+    """qp_config plus the numpy arrays it points into (keep both alive)."""
+    q = _arr(q)
+    hs = np.asarray(hs, dtype=np.complex128)
+    hre, him = _arr(hs.real), _arr(hs.imag)
+    cfg = qp_config(M=M, dkmax=dkmax, dt=dt, q=_ptr(q), hs_re=_ptr(hre), hs_im=_ptr(him),
+                    precision=precision, engine=engine, theta=theta, max_paths=max_paths,
+                    max_groups=max_groups, rho_history=rho_history)
+    return cfg, (q, hre, him)
+
+
+def qp_workspace_size(cfg) -> int:
+    n = ctypes.c_size_t(0)
+    check(lib.qp_workspace_size(ctypes.byref(cfg), ctypes.byref(n)))
+    return n.value
+
+
+def qp_create(cfg, d_workspace: int, nbytes: int, stream: int):
+    h = ctypes.c_void_p()
+    check(lib.qp_create(ctypes.byref(cfg), ctypes.c_void_p(d_workspace), nbytes, ctypes.c_void_p(stream),
+                        ctypes.byref(h)))
+    return h
+
+
+def qp_destroy(ctx):
+    lib.qp_destroy(ctx)
+
+
+def qp_eta_from_bath(bath, dt: float, n: int) -> np.ndarray:
+    b = qp_bath(beta=bath.beta, ohmic_alpha=bath.ohmic_alpha, ohmic_wc=bath.ohmic_wc,
+                res_w0=bath.res_w0, res_gamma=bath.res_gamma, res_lambda=bath.res_lambda)
+    re, im = np.zeros(n), np.zeros(n)
+    check(lib.qp_eta_from_bath(ctypes.byref(b), dt, n, _ptr(re), _ptr(im)))
+    return re + 1j * im
+
+
+def qp_set_eta(ctx, eta):
+    eta = np.asarray(eta, dtype=np.complex128)
+    re, im = _arr(eta.real), _arr(eta.imag)
+    check(lib.qp_set_eta(ctx, _ptr(re), _ptr(im), eta.size), ctx)
+
+
+def qp_set_mask(ctx, positions):
+    if positions is None:
+        check(lib.qp_set_mask(ctx, None, 0), ctx)
+        return
+    p = _arr(list(positions), np.int32)
+    check(lib.qp_set_mask(ctx, _ptr(p, _ip), p.size), ctx)
+
+
+def qp_set_rho0(ctx, rho0):
+    r = np.asarray(rho0, dtype=np.complex128)
+    re, im = _arr(r.real), _arr(r.imag)
+    check(lib.qp_set_rho0(ctx, _ptr(re), _ptr(im)), ctx)
+
+
+def qp_step(ctx, nsteps: int = 1):
+    check(lib.qp_step(ctx, nsteps), ctx)
+
+
+def qp_sync(ctx):
+    check(lib.qp_sync(ctx), ctx)
+
+
+def qp_current(ctx):
+    t, n = ctypes.c_int64(), ctypes.c_int64()
+    check(lib.qp_current(ctx, ctypes.byref(t), ctypes.byref(n)), ctx)
+    return t.value, n.value
+
+
+def qp_read_rho(ctx, t0: int, count: int, M: int) -> np.ndarray:
+    re, im = np.zeros(count * M * M), np.zeros(count * M * M)
+    check(lib.qp_read_rho(ctx, t0, count, _ptr(re), _ptr(im)), ctx)
+    return (re + 1j * im).reshape(count, M, M)
+
+
+def qp_read_stats(ctx, t0: int, count: int):
+    arr = (qp_step_stats * count)()
+    check(lib.qp_read_stats(ctx, t0, count, arr), ctx)
+    return [(s.t, s.groups, s.extended, s.kept) for s in arr]
+
+
+def qp_export_paths(ctx, cap: int):
+    keys = np.zeros(cap, dtype=np.uint64)
+    amps = np.zeros(2 * cap, dtype=np.float64)
+    n = ctypes.c_int64()
+    check(lib.qp_export_paths(ctx, _ptr(keys, _u64p), _ptr(amps), cap, ctypes.byref(n)), ctx)
+    k = n.value
+    return keys[:k].copy(), amps[0:2 * k:2] + 1j * amps[1:2 * k:2]
+
+
+def qp_profile_steps(ctx, nsteps: int) -> np.ndarray:
+    """Per-kernel milliseconds summed over nsteps steps (insert, tie-break, expand, finalise)."""
+    ms = np.zeros(4)
+    check(lib.qp_profile_steps(ctx, nsteps, _ptr(ms), 4), ctx)
+    return ms
+
+
+def qp_last_error(ctx) -> str:
+    return lib.qp_last_error(ctx).decode()

@@ -1,0 +1,25 @@
+// Internal declarations shared by the host numerics and the CUDA translation
+// unit of libqp.  Not part of the public ABI (see include/qp.h).
+#pragma once
+#include <complex>
+#include <cstdint>
+#include <vector>
+
+#include "../../include/qp.h"
+
+namespace qp {
+
+using cplx = std::complex<double>;
+
+// U = exp(-i H dt) of a Hermitian M x M matrix (row-major), by scaling and
+// squaring of the Taylor series.  The short-time system propagator of Eq.
+// SysP (hbar = 1).
+std::vector<cplx> short_time_propagator(int M, const std::vector<cplx> &H, double dt);
+
+// Spectral density J(w) of the bath (ohmic part + Eq. sharpSD resonance).
+double spectral_density(const qp_bath &b, double w);
+
+// eta_0 .. eta_{n-1}, box double integrals of the bath correlation function.
+int eta_from_bath(const qp_bath &b, double dt, int n, std::vector<cplx> &eta);
+
+}  // namespace qp

@@ -1,0 +1,1057 @@
+// libqp: GB300 (sm_103a) kernels and C ABI of the MACGIC-iQUAPI path update.
+//
+// One propagation step Omega(t-1) -> Omega(t) (paper Sec. 3.1, routines
+// premerging() and propagation()) runs as a short, fixed sequence of kernels
+// on the context's stream.  Every kernel reads the step index and the path
+// counts from a small device-resident state block, so the host never waits
+// on a count and one captured CUDA graph replays any step:
+//
+//   k_insert    pre-merge pass 1 (window full only): each stored path
+//               inserts its masked key into the merge table (open
+//               addressing, atomicCAS claim), adds its amplitude into the
+//               group sum (FP64 atomics) and raises the group's maximum
+//               |amp|^2 (atomicMax on the FP64 bit pattern; non-negative
+//               doubles order like uint64).
+//   k_tiebreak  pre-merge pass 2: paths whose |amp|^2 is within a relative
+//               1e-12 of the group maximum compete for the representative
+//               with atomicMin on the packed key (deterministic choice
+//               among equal weights).
+//   k_expand    per group (or per stored path while the window fills): the
+//               history part H of the influence exponent from per-byte
+//               lookup tables, the M^2 children weighted by
+//               U[a,a'] conj(U[b,b']) exp(-(q_a-q_b)(H + eta_0 q_a - eta_0* q_b)),
+//               filter |amp|^2 >= theta^2, rho(t) accumulated in registers
+//               then reduced per block, survivors appended to the other
+//               ping-pong buffer (warp-aggregated atomic cursor).  The
+//               group's table slot is reset after it is read.
+//   k_finalize  one thread: publishes the new count, per-step statistics,
+//               advances t, zeroes the next rho accumulator.
+//
+// Precision (template parameter Amp): double2 amplitudes (QP_FP64) or
+// float2 amplitudes (QP_C64) with the influence exponent accumulated in FP32
+// with compensated (Kahan) sums; group sums, eta and rho stay FP64.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace {
+
+constexpr unsigned long long kEmpty = ~0ull;
+constexpr unsigned int kNoSlot = 0xffffffffu;
+constexpr int kMaxRuns = 8;
+constexpr int kMaxProbe = 64;
+constexpr double kTieRel = 1e-12;
+constexpr unsigned int kErrPaths = 1u, kErrGroups = 2u, kErrProbe = 4u;
+constexpr int kLutEntries = 256;
+
+struct __align__(32) Slot {
+    unsigned long long mk;     // masked key, kEmpty when free
+    unsigned long long wmax;   // bit pattern of max |amp|^2 (FP64)
+    double sre, sim;           // FP64 group sum
+};
+
+struct __align__(64) DevState {
+    unsigned long long t;        // time index of the stored set Omega(t)
+    unsigned long long n_cur;    // stored paths in buffer (t & 1)
+    unsigned long long n_groups; // groups claimed in the current step
+    unsigned long long n_out;    // children appended in the current step
+    unsigned int err;            // error bits, sticky until qp_set_rho0
+    unsigned int pad;
+    unsigned long long err_t;    // step at which the error was raised
+};
+
+struct StepRec { long long t, groups, extended, kept; };
+
+struct Params {
+    int M, bs, b, dkmax;
+    int nchunks;                       // bytes of the history part of a key
+    int dense;                         // 1: table index = compressed masked key
+    int nruns;
+    int run_shift[kMaxRuns];
+    int run_off[kMaxRuns];
+    unsigned long long run_mask[kMaxRuns];
+    unsigned long long pmask;          // bits of the pre-merge positions P'
+    unsigned int tcap_log2;
+    unsigned long long tcap_mask;
+    double theta2;
+    long long max_paths, max_groups;
+    int rho_hist;
+    unsigned long long *keys[2];
+    void *amps[2];
+    Slot *slots;
+    unsigned long long *repk;
+    unsigned int *slot_of;
+    unsigned int *groups;
+    const double2 *lut;                // [dkmax][nchunks][256] FP64 history tables
+    const float2 *lutf;                // same, FP32 hi part
+    const float2 *lutf_lo;             // FP32 residual (hi + lo = FP64 value)
+    const double2 *wtab;               // [M*M child][M*M parent newest] propagator x new-point influence
+    double2 *rho_ring;                 // [rho_hist][M*M]
+    StepRec *stats_ring;               // [rho_hist]
+    DevState *st;
+};
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+__device__ __forceinline__ double2 load_amp(const double2 *p, unsigned long long i) { return p[i]; }
+__device__ __forceinline__ double2 load_amp(const float2 *p, unsigned long long i) {
+    float2 v = p[i];
+    return make_double2(v.x, v.y);
+}
+
+__device__ __forceinline__ unsigned long long table_index(const Params &P, unsigned long long mk) {
+    if (P.dense) {
+        unsigned long long idx = 0;
+        for (int r = 0; r < P.nruns; ++r) idx |= ((mk >> P.run_shift[r]) & P.run_mask[r]) << P.run_off[r];
+        return idx;
+    }
+    return (mk * 0x9E3779B97F4A7C15ull) >> (64 - P.tcap_log2);
+}
+
+__device__ __forceinline__ void raise_err(DevState *st, unsigned int bit) {
+    atomicOr(&st->err, bit);
+}
+
+// ---------------------------------------------------------------- pre-merge
+
+template <typename Amp>
+__global__ void __launch_bounds__(256) k_insert(Params P) {
+    DevState *st = P.st;
+    if (st->err) return;
+    const unsigned long long t = st->t, tn = t + 1;
+    if (tn < (unsigned long long)P.dkmax) return;   // window not full: no merge
+    const unsigned long long n = st->n_cur;
+    const unsigned long long *keys = P.keys[t & 1];
+    const Amp *amps = static_cast<const Amp *>(P.amps[t & 1]);
+    const unsigned lane = lane_id();
+    const unsigned long long warp0 = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) - lane;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long base = warp0; base < n; base += stride) {
+        const unsigned long long i = base + lane;
+        const bool valid = i < n;
+        bool claimed = false, found = false;
+        unsigned long long h = 0;
+        double2 a = make_double2(0.0, 0.0);
+        if (valid) {
+            const unsigned long long key = keys[i];
+            a = load_amp(amps, i);
+            const unsigned long long mk = key & P.pmask;
+            h = table_index(P, mk);
+            for (int probe = 0; probe < kMaxProbe; ++probe) {
+                const unsigned long long cur = *(volatile unsigned long long *)&P.slots[h].mk;
+                if (cur == mk) { found = true; break; }
+                if (cur == kEmpty) {
+                    const unsigned long long prev = atomicCAS(&P.slots[h].mk, kEmpty, mk);
+                    if (prev == kEmpty) { claimed = found = true; break; }
+                    if (prev == mk) { found = true; break; }
+                }
+                h = (h + 1) & P.tcap_mask;
+            }
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, claimed);
+        if (bal) {
+            const int leader = __ffs(bal) - 1;
+            unsigned long long g0 = 0;
+            if ((int)lane == leader) g0 = atomicAdd(&st->n_groups, (unsigned long long)__popc(bal));
+            g0 = __shfl_sync(0xffffffffu, g0, leader);
+            if (claimed) {
+                const unsigned long long g = g0 + __popc(bal & ((1u << lane) - 1u));
+                if (g < (unsigned long long)P.max_groups) P.groups[g] = (unsigned int)h;
+                else raise_err(st, kErrGroups);
+            }
+        }
+        if (valid) {
+            if (found) {
+                atomicAdd(&P.slots[h].sre, a.x);
+                atomicAdd(&P.slots[h].sim, a.y);
+                const double w2 = a.x * a.x + a.y * a.y;
+                atomicMax(&P.slots[h].wmax, (unsigned long long)__double_as_longlong(w2));
+                P.slot_of[i] = (unsigned int)h;
+            } else {
+                P.slot_of[i] = kNoSlot;
+                raise_err(st, kErrProbe);
+            }
+        }
+    }
+}
+
+template <typename Amp>
+__global__ void __launch_bounds__(256) k_tiebreak(Params P) {
+    DevState *st = P.st;
+    if (st->err) return;
+    const unsigned long long t = st->t, tn = t + 1;
+    if (tn < (unsigned long long)P.dkmax) return;
+    const unsigned long long n = st->n_cur;
+    const unsigned long long *keys = P.keys[t & 1];
+    const Amp *amps = static_cast<const Amp *>(P.amps[t & 1]);
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n; i += stride) {
+        const unsigned int h = P.slot_of[i];
+        if (h == kNoSlot) continue;
+        const double2 a = load_amp(amps, i);
+        const double w2 = a.x * a.x + a.y * a.y;
+        const double wm = __longlong_as_double((long long)P.slots[h].wmax);
+        if (w2 >= (1.0 - kTieRel) * wm) atomicMin(&P.repk[h], keys[i]);
+    }
+}
+
+// ---------------------------------------------------------------- extension
+
+template <typename Amp> struct AmpOut;
+template <> struct AmpOut<double2> {
+    static __device__ __forceinline__ void store(double2 *p, unsigned long long i, double2 v) { p[i] = v; }
+};
+template <> struct AmpOut<float2> {
+    static __device__ __forceinline__ void store(float2 *p, unsigned long long i, double2 v) {
+        p[i] = make_float2((float)v.x, (float)v.y);
+    }
+};
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// History part H of the influence exponent, FP64: sum of per-byte table
+// entries of the representative's key (lags 1 .. n_act-1).
+__device__ __forceinline__ double2 history_fp64(const Params &P, const double2 *lut, unsigned long long rep) {
+    double hx = 0.0, hy = 0.0;
+    for (int j = 0; j < P.nchunks; ++j) {
+        const double2 v = __ldg(&lut[j * kLutEntries + ((rep >> (8 * j)) & 0xffu)]);
+        hx += v.x;
+        hy += v.y;
+    }
+    return make_double2(hx, hy);
+}
+
+// Same in FP32 with compensated summation: each table entry is split as
+// hi + lo (both FP32); the running sum is Kahan-compensated.
+__device__ __forceinline__ double2 history_fp32(const Params &P, const float2 *lut, const float2 *lutlo,
+                                                unsigned long long rep) {
+    float sx = 0.f, sy = 0.f, cx = 0.f, cy = 0.f;
+    for (int j = 0; j < P.nchunks; ++j) {
+        const int idx = j * kLutEntries + (int)((rep >> (8 * j)) & 0xffu);
+        const float2 hi = __ldg(&lut[idx]);
+        const float2 lo = __ldg(&lutlo[idx]);
+        float yx = (hi.x + lo.x) - cx;
+        float tx = sx + yx;
+        cx = (tx - sx) - yx;
+        sx = tx;
+        float yy = (hi.y + lo.y) - cy;
+        float ty = sy + yy;
+        cy = (ty - sy) - yy;
+        sy = ty;
+    }
+    return make_double2((double)sx - (double)cx, (double)sy - (double)cy);
+}
+
+template <int M, typename Amp>
+__global__ void __launch_bounds__(128) k_expand(Params P, const double *qv) {
+    constexpr int MM = M * M;
+    DevState *st = P.st;
+    if (st->err) return;
+    const unsigned long long t = st->t, tn = t + 1;
+    const bool merge = tn >= (unsigned long long)P.dkmax;
+    const unsigned long long n = merge ? st->n_groups : st->n_cur;
+    const int n_act = (int)min(tn, (unsigned long long)P.dkmax);
+    const int L_child = (int)min(tn + 1, (unsigned long long)P.dkmax);
+    const unsigned long long wmask = (P.b * L_child >= 64) ? ~0ull : ((1ull << (P.b * L_child)) - 1ull);
+    const unsigned long long *keys_in = P.keys[t & 1];
+    const Amp *amps_in = static_cast<const Amp *>(P.amps[t & 1]);
+    unsigned long long *keys_out = P.keys[tn & 1];
+    Amp *amps_out = static_cast<Amp *>(P.amps[tn & 1]);
+    const size_t lut_off = (size_t)(n_act - 1) * P.nchunks * kLutEntries;
+    const double2 *lut = P.lut + lut_off;
+    const float2 *lutf = P.lutf + lut_off;
+    const float2 *lutlo = P.lutf_lo + lut_off;
+    constexpr bool kC64 = sizeof(Amp) == sizeof(float2);
+
+    __shared__ double2 s_w[MM * MM];
+    __shared__ double s_q[M];
+    for (int i = threadIdx.x; i < MM * MM; i += blockDim.x) s_w[i] = P.wtab[i];
+    if (threadIdx.x < M) s_q[threadIdx.x] = qv[threadIdx.x];
+    __syncthreads();
+
+    const unsigned int smask = (1u << P.bs) - 1u;
+    const unsigned int cmask = (1u << P.b) - 1u;
+    double2 racc[MM];
+#pragma unroll
+    for (int k = 0; k < MM; ++k) racc[k] = make_double2(0.0, 0.0);
+
+    const unsigned lane = lane_id();
+    const unsigned long long warp0 = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) - lane;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long base = warp0; base < n; base += stride) {
+        const unsigned long long g = base + lane;
+        const bool valid = g < n;
+        unsigned int keepbits = 0;
+        double2 camp[MM];
+        unsigned long long rep = 0;
+        if (valid) {
+            double2 S;
+            if (merge) {
+                const unsigned int h = P.groups[g];
+                rep = P.repk[h];
+                S = make_double2(P.slots[h].sre, P.slots[h].sim);
+                Slot fresh;
+                fresh.mk = kEmpty;
+                fresh.wmax = 0ull;
+                fresh.sre = 0.0;
+                fresh.sim = 0.0;
+                P.slots[h] = fresh;
+                P.repk[h] = kEmpty;
+            } else {
+                rep = keys_in[g];
+                S = load_amp(amps_in, g);
+            }
+            const double2 H = kC64 ? history_fp32(P, lutf, lutlo, rep) : history_fp64(P, lut, rep);
+            const unsigned int c0 = (unsigned int)(rep & cmask);
+            const int pidx = (int)(c0 & smask) * M + (int)(c0 >> P.bs);
+            // E[a][b] = exp(-(q_a - q_b) H): one exp + sincos per unordered pair
+            double2 E[MM];
+#pragma unroll
+            for (int a = 0; a < M; ++a) E[a * M + a] = make_double2(1.0, 0.0);
+#pragma unroll
+            for (int a = 0; a < M; ++a)
+#pragma unroll
+                for (int b = a + 1; b < M; ++b) {
+                    const double dq = s_q[a] - s_q[b];
+                    if (dq == 0.0) {
+                        E[a * M + b] = E[b * M + a] = make_double2(1.0, 0.0);
+                    } else if (kC64) {
+                        const float zr = (float)(-dq * H.x), zi = (float)(-dq * H.y);
+                        float s, c;
+                        __sincosf(zi, &s, &c);
+                        const float m = __expf(zr);
+                        const float mi = 1.0f / m;
+                        E[a * M + b] = make_double2(m * c, m * s);
+                        E[b * M + a] = make_double2(mi * c, -mi * s);
+                    } else {
+                        const double zr = -dq * H.x, zi = -dq * H.y;
+                        double s, c;
+                        sincos(zi, &s, &c);
+                        const double m = exp(zr);
+                        const double mi = 1.0 / m;
+                        E[a * M + b] = make_double2(m * c, m * s);
+                        E[b * M + a] = make_double2(mi * c, -mi * s);
+                    }
+                }
+#pragma unroll
+            for (int k = 0; k < MM; ++k) {
+                const double2 f = cmul(s_w[k * MM + pidx], E[k]);
+                const double2 v = cmul(S, f);
+                camp[k] = v;
+                if (v.x * v.x + v.y * v.y >= P.theta2) {
+                    keepbits |= 1u << k;
+                    racc[k].x += v.x;
+                    racc[k].y += v.y;
+                }
+            }
+        }
+        // warp-aggregated append of the survivors
+        const unsigned int cnt = __popc(keepbits);
+        unsigned int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if ((int)lane >= o) incl += y;
+        }
+        const unsigned int total = __shfl_sync(0xffffffffu, incl, 31);
+        unsigned long long o0 = 0;
+        if (lane == 31 && total) o0 = atomicAdd(&st->n_out, (unsigned long long)total);
+        o0 = __shfl_sync(0xffffffffu, o0, 31);
+        if (total && o0 + total > (unsigned long long)P.max_paths) {
+            if (lane == 0) raise_err(st, kErrPaths);
+        } else if (cnt) {
+            unsigned long long o = o0 + (incl - cnt);
+            const unsigned long long shifted = rep << P.b;
+#pragma unroll
+            for (int k = 0; k < MM; ++k) {
+                if (keepbits & (1u << k)) {
+                    const unsigned long long code = (unsigned long long)((k / M) | ((k % M) << P.bs));
+                    keys_out[o] = (shifted | code) & wmask;
+                    AmpOut<Amp>::store(amps_out, o, camp[k]);
+                    ++o;
+                }
+            }
+        }
+    }
+    // rho(t): warp shuffle reduction, then one FP64 atomic per element per warp
+    double2 *rho = P.rho_ring + (size_t)(tn % (unsigned long long)P.rho_hist) * MM;
+#pragma unroll
+    for (int k = 0; k < MM; ++k) {
+        double x = racc[k].x, y = racc[k].y;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            x += __shfl_down_sync(0xffffffffu, x, o);
+            y += __shfl_down_sync(0xffffffffu, y, o);
+        }
+        if (lane == 0 && (x != 0.0 || y != 0.0)) {
+            atomicAdd(&rho[k].x, x);
+            atomicAdd(&rho[k].y, y);
+        }
+    }
+}
+
+__global__ void k_finalize(Params P, int MM) {
+    DevState *st = P.st;
+    if (st->err) { st->n_groups = 0; st->n_out = 0; return; }
+    const unsigned long long t = st->t, tn = t + 1;
+    const bool merge = tn >= (unsigned long long)P.dkmax;
+    const unsigned long long groups = merge ? st->n_groups : st->n_cur;
+    if (st->n_out > (unsigned long long)P.max_paths) {
+        st->err |= kErrPaths;
+        st->err_t = tn;
+        return;
+    }
+    StepRec r;
+    r.t = (long long)tn;
+    r.groups = (long long)groups;
+    r.extended = (long long)groups * MM;
+    r.kept = (long long)st->n_out;
+    P.stats_ring[tn % (unsigned long long)P.rho_hist] = r;
+    st->n_cur = st->n_out;
+    st->t = tn;
+    st->n_groups = 0;
+    st->n_out = 0;
+    double2 *nxt = P.rho_ring + (size_t)((tn + 1) % (unsigned long long)P.rho_hist) * MM;
+    for (int k = 0; k < MM; ++k) nxt[k] = make_double2(0.0, 0.0);
+}
+
+// ---------------------------------------------------------------- set-up kernels
+
+__global__ void k_clear_table(Slot *slots, unsigned long long *repk, unsigned long long n) {
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n; i += stride) {
+        Slot s;
+        s.mk = kEmpty;
+        s.wmax = 0ull;
+        s.sre = 0.0;
+        s.sim = 0.0;
+        slots[i] = s;
+        repk[i] = kEmpty;
+    }
+}
+
+// History tables: for n_act = 1..dkmax, chunk j (one byte of the key), byte
+// value v: sum over the positions p of the byte with p <= n_act - 2 of
+// eta_{p+1} q[s+_p] - conj(eta_{p+1}) q[s-_p] (lag p+1 of the new point).
+__global__ void k_build_lut(double2 *lut, float2 *lutf, float2 *lutlo, const double2 *eta, const double *q,
+                            int M, int bs, int b, int dkmax, int nchunks) {
+    const int total = dkmax * nchunks * kLutEntries;
+    const int ppc = 8 / b;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        const int v = i % kLutEntries;
+        const int j = (i / kLutEntries) % nchunks;
+        const int n_act = i / (kLutEntries * nchunks) + 1;
+        double hx = 0.0, hy = 0.0;
+        for (int k = 0; k < ppc; ++k) {
+            const int p = j * ppc + k;
+            if (p > n_act - 2) continue;
+            const int code = (v >> (b * k)) & ((1 << b) - 1);
+            const int sp = code & ((1 << bs) - 1), sm = code >> bs;
+            if (sp >= M || sm >= M) continue;   // codes that never occur
+            const double2 e = eta[p + 1];
+            // eta q+ - conj(eta) q-
+            hx += e.x * q[sp] - e.x * q[sm];
+            hy += e.y * q[sp] + e.y * q[sm];
+        }
+        lut[i] = make_double2(hx, hy);
+        const float fx = (float)hx, fy = (float)hy;
+        lutf[i] = make_float2(fx, fy);
+        lutlo[i] = make_float2((float)(hx - (double)fx), (float)(hy - (double)fy));
+    }
+}
+
+// W[(a,b)][(a',b')] = U[a,a'] conj(U[b,b']) exp(-(q_a - q_b)(eta_0 q_a - conj(eta_0) q_b))
+__global__ void k_build_w(double2 *w, const double2 *U, const double2 *eta, const double *q, int M) {
+    const int MM = M * M;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < MM * MM; i += gridDim.x * blockDim.x) {
+        const int child = i / MM, par = i % MM;
+        const int a = child / M, b = child % M, ap = par / M, bp = par % M;
+        const double2 ua = U[a * M + ap];
+        const double2 ub = U[b * M + bp];
+        const double2 prop = make_double2(ua.x * ub.x + ua.y * ub.y, ua.y * ub.x - ua.x * ub.y);  // ua * conj(ub)
+        const double dq = q[a] - q[b];
+        const double2 e0 = eta[0];
+        // z = -(dq) (e0 q_a - conj(e0) q_b)
+        const double inner_x = e0.x * q[a] - e0.x * q[b];
+        const double inner_y = e0.y * q[a] + e0.y * q[b];
+        const double zr = -dq * inner_x, zi = -dq * inner_y;
+        double s, c;
+        sincos(zi, &s, &c);
+        const double m = exp(zr);
+        w[i] = cmul(prop, make_double2(m * c, m * s));
+    }
+}
+
+// ---------------------------------------------------------------- host side
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct Layout {
+    size_t keys[2], amps[2], slots, repk, slot_of, groups, lut, lutf, lutlo, wtab, uprop, eta, q, rho, stats, state,
+        total;
+    unsigned long long tcap;
+    unsigned int tcap_log2;
+    int nchunks;
+};
+
+int bits_per_state(int M) {
+    int bs = 1;
+    while ((1 << bs) < M) ++bs;
+    return bs;
+}
+
+const char *validate(const qp_config *c) {
+    if (!c) return "null config";
+    if (c->M < 2 || c->M > 4) return "M must be 2..4";
+    if (c->dkmax < 1) return "dkmax must be >= 1";
+    const int b = 2 * bits_per_state(c->M);
+    if (b * c->dkmax > 64) return "b*dkmax exceeds the 64-bit key";
+    if (!(c->dt > 0.0) || !std::isfinite(c->dt)) return "dt must be positive";
+    if (!c->q || !c->hs_re) return "q and hs_re are required";
+    if (c->precision != QP_FP64 && c->precision != QP_C64) return "unknown precision";
+    if (c->engine < QP_ENGINE_AUTO || c->engine > QP_ENGINE_STREAM) return "unknown engine";
+    if (!(c->theta >= 0.0) || !std::isfinite(c->theta)) return "theta must be >= 0";
+    if (c->max_paths < 1 || c->max_paths > (int64_t(1) << 40)) return "max_paths out of range";
+    if (c->max_groups < 0 || c->max_groups > (int64_t(1) << 30)) return "max_groups out of range";
+    if (c->max_groups == 0 && c->max_paths > (int64_t(1) << 30)) return "set max_groups (<= 2^30) for max_paths > 2^30";
+    if (c->rho_history < 0 || c->rho_history > (1 << 24)) return "rho_history out of range";
+    for (int i = 0; i < c->M; ++i)
+        if (!std::isfinite(c->q[i])) return "q must be finite";
+    for (int i = 0; i < c->M * c->M; ++i) {
+        const int r = i / c->M, k = i % c->M;
+        const double im = c->hs_im ? c->hs_im[i] : 0.0, imT = c->hs_im ? c->hs_im[k * c->M + r] : 0.0;
+        if (!std::isfinite(c->hs_re[i]) || !std::isfinite(im)) return "H_S must be finite";
+        if (std::fabs(c->hs_re[i] - c->hs_re[k * c->M + r]) > 1e-12 || std::fabs(im + imT) > 1e-12)
+            return "H_S must be Hermitian";
+    }
+    return nullptr;
+}
+
+Layout make_layout(const qp_config *c) {
+    Layout L{};
+    const long long mp = c->max_paths;
+    const long long mg = c->max_groups ? c->max_groups : c->max_paths;
+    const size_t ampb = c->precision == QP_C64 ? sizeof(float2) : sizeof(double2);
+    unsigned int lg = 4;
+    while ((1ull << lg) < 2ull * (unsigned long long)mg) ++lg;
+    L.tcap = 1ull << lg;
+    L.tcap_log2 = lg;
+    const int b = 2 * bits_per_state(c->M);
+    L.nchunks = (c->dkmax - 1) * b > 0 ? ((c->dkmax - 1) * b + 7) / 8 : 0;
+    const int R = c->rho_history ? c->rho_history : 4096;
+    const int MM = c->M * c->M;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
+    L.state = take(sizeof(DevState));
+    L.keys[0] = take(mp * 8);
+    L.keys[1] = take(mp * 8);
+    L.amps[0] = take(mp * ampb);
+    L.amps[1] = take(mp * ampb);
+    L.slots = take(L.tcap * sizeof(Slot));
+    L.repk = take(L.tcap * 8);
+    L.slot_of = take(mp * 4);
+    L.groups = take(mg * 4);
+    const size_t nlut = (size_t)c->dkmax * std::max(1, L.nchunks) * kLutEntries;
+    L.lut = take(nlut * sizeof(double2));
+    L.lutf = take(nlut * sizeof(float2));
+    L.lutlo = take(nlut * sizeof(float2));
+    L.wtab = take(MM * MM * sizeof(double2));
+    L.uprop = take(MM * sizeof(double2));
+    L.eta = take(c->dkmax * sizeof(double2));
+    L.q = take(c->M * sizeof(double));
+    L.rho = take((size_t)R * MM * sizeof(double2));
+    L.stats = take((size_t)R * sizeof(StepRec));
+    L.total = off;
+    return L;
+}
+
+}  // namespace
+
+struct qp_ctx {
+    qp_config cfg;
+    std::vector<double> q;
+    std::vector<qp::cplx> hs, U;
+    Layout L;
+    char *ws = nullptr;
+    size_t ws_bytes = 0;
+    cudaStream_t stream = nullptr;
+    int device = 0, nsm = 0;
+    Params P{};
+    bool have_eta = false, have_state = false, failed = false;
+    std::vector<int> mask;
+    cudaGraphExec_t graph = nullptr;
+    bool graph_dirty = true;
+    bool use_graph = true;
+    std::string err;
+};
+
+namespace {
+
+qp_status fail(qp_ctx *c, qp_status s, const std::string &msg) {
+    if (c) c->err = msg;
+    return s;
+}
+
+#define QP_CUDA(ctx, call)                                                                    \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) return fail(ctx, QP_ERR_CUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
+    } while (0)
+
+constexpr int kStepKernels = 4;
+
+// Launch one step; if ev is given, record ev[k] before kernel k and
+// ev[kStepKernels] after the last one.
+template <int M, typename Amp>
+cudaError_t launch_step_t(qp_ctx *c, cudaEvent_t *ev) {
+    const int g_stream = c->nsm * 4;
+    if (ev) cudaEventRecord(ev[0], c->stream);
+    k_insert<Amp><<<g_stream, 256, 0, c->stream>>>(c->P);
+    if (ev) cudaEventRecord(ev[1], c->stream);
+    k_tiebreak<Amp><<<g_stream, 256, 0, c->stream>>>(c->P);
+    if (ev) cudaEventRecord(ev[2], c->stream);
+    k_expand<M, Amp><<<c->nsm * 4, 128, 0, c->stream>>>(c->P, reinterpret_cast<const double *>(c->ws + c->L.q));
+    if (ev) cudaEventRecord(ev[3], c->stream);
+    k_finalize<<<1, 1, 0, c->stream>>>(c->P, M * M);
+    if (ev) cudaEventRecord(ev[4], c->stream);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step(qp_ctx *c, cudaEvent_t *ev = nullptr) {
+    const bool c64 = c->cfg.precision == QP_C64;
+    switch (c->cfg.M) {
+        case 2: return c64 ? launch_step_t<2, float2>(c, ev) : launch_step_t<2, double2>(c, ev);
+        case 3: return c64 ? launch_step_t<3, float2>(c, ev) : launch_step_t<3, double2>(c, ev);
+        default: return c64 ? launch_step_t<4, float2>(c, ev) : launch_step_t<4, double2>(c, ev);
+    }
+}
+
+void set_mask_params(qp_ctx *c) {
+    Params &P = c->P;
+    const int b = P.b, dk = P.dkmax;
+    std::vector<int> Pp;   // P' = {p-1 : p in P, p >= 1} plus 0
+    std::vector<char> in(dk, 0);
+    in[0] = 1;
+    for (int p : c->mask)
+        if (p >= 1) in[p - 1] = 1;
+    unsigned long long pm = 0;
+    for (int p = 0; p < dk; ++p)
+        if (in[p]) {
+            Pp.push_back(p);
+            pm |= ((1ull << b) - 1ull) << (b * p);
+        }
+    P.pmask = pm;
+    // dense index: compress the runs of consecutive P' positions
+    int nruns = 0, off = 0;
+    bool ok = true;
+    for (size_t i = 0; i < Pp.size();) {
+        size_t j = i;
+        while (j + 1 < Pp.size() && Pp[j + 1] == Pp[j] + 1) ++j;
+        if (nruns == kMaxRuns) { ok = false; break; }
+        const int len = int(j - i + 1);
+        P.run_shift[nruns] = b * Pp[i];
+        P.run_mask[nruns] = (b * len >= 64) ? ~0ull : ((1ull << (b * len)) - 1ull);
+        P.run_off[nruns] = off;
+        off += b * len;
+        ++nruns;
+        i = j + 1;
+    }
+    P.nruns = nruns;
+    P.dense = (ok && off <= (int)c->L.tcap_log2) ? 1 : 0;
+}
+
+}  // namespace
+
+// ================================================================= C ABI
+
+extern "C" {
+
+int qp_version(void) { return 100; }
+
+const char *qp_status_string(qp_status s) {
+    switch (s) {
+        case QP_OK: return "ok";
+        case QP_ERR_ARG: return "invalid argument";
+        case QP_ERR_OOM: return "out of memory";
+        case QP_ERR_CUDA: return "CUDA error";
+        case QP_ERR_CAPACITY: return "capacity exceeded";
+        case QP_ERR_TIMEOUT: return "device wait timed out";
+        case QP_ERR_STATE: return "invalid state";
+    }
+    return "unknown status";
+}
+
+qp_status qp_workspace_size(const qp_config *cfg, size_t *bytes) {
+    if (!bytes) return QP_ERR_ARG;
+    if (validate(cfg)) return QP_ERR_ARG;
+    *bytes = make_layout(cfg).total;
+    return QP_OK;
+}
+
+qp_status qp_create(const qp_config *cfg, void *d_workspace, size_t bytes, void *cuda_stream, qp_ctx **out) {
+    if (!out) return QP_ERR_ARG;
+    *out = nullptr;
+    if (validate(cfg)) return QP_ERR_ARG;
+    if (!d_workspace || (reinterpret_cast<uintptr_t>(d_workspace) & 255u)) return QP_ERR_ARG;
+    const Layout L = make_layout(cfg);
+    if (bytes < L.total) return QP_ERR_OOM;
+    qp_ctx *c = new (std::nothrow) qp_ctx();
+    if (!c) return QP_ERR_OOM;
+    c->cfg = *cfg;
+    c->cfg.max_groups = cfg->max_groups ? cfg->max_groups : cfg->max_paths;
+    c->cfg.rho_history = cfg->rho_history ? cfg->rho_history : 4096;
+    c->cfg.q = nullptr;
+    c->cfg.hs_re = c->cfg.hs_im = nullptr;
+    const int M = cfg->M;
+    c->q.assign(cfg->q, cfg->q + M);
+    c->hs.resize(M * M);
+    for (int i = 0; i < M * M; ++i) c->hs[i] = qp::cplx(cfg->hs_re[i], cfg->hs_im ? cfg->hs_im[i] : 0.0);
+    c->U = qp::short_time_propagator(M, c->hs, cfg->dt);
+    c->L = L;
+    c->ws = static_cast<char *>(d_workspace);
+    c->ws_bytes = bytes;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    c->use_graph = c->stream != nullptr && !getenv("QP_NO_GRAPH");
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device);
+    if (e != cudaSuccess) {
+        delete c;
+        return QP_ERR_CUDA;
+    }
+    Params &P = c->P;
+    P.M = M;
+    P.bs = bits_per_state(M);
+    P.b = 2 * P.bs;
+    P.dkmax = cfg->dkmax;
+    P.nchunks = L.nchunks;
+    P.tcap_log2 = L.tcap_log2;
+    P.tcap_mask = L.tcap - 1;
+    P.theta2 = cfg->theta * cfg->theta;
+    P.max_paths = cfg->max_paths;
+    P.max_groups = c->cfg.max_groups;
+    P.rho_hist = c->cfg.rho_history;
+    for (int k = 0; k < 2; ++k) {
+        P.keys[k] = reinterpret_cast<unsigned long long *>(c->ws + L.keys[k]);
+        P.amps[k] = c->ws + L.amps[k];
+    }
+    P.slots = reinterpret_cast<Slot *>(c->ws + L.slots);
+    P.repk = reinterpret_cast<unsigned long long *>(c->ws + L.repk);
+    P.slot_of = reinterpret_cast<unsigned int *>(c->ws + L.slot_of);
+    P.groups = reinterpret_cast<unsigned int *>(c->ws + L.groups);
+    P.lut = reinterpret_cast<const double2 *>(c->ws + L.lut);
+    P.lutf = reinterpret_cast<const float2 *>(c->ws + L.lutf);
+    P.lutf_lo = reinterpret_cast<const float2 *>(c->ws + L.lutlo);
+    P.wtab = reinterpret_cast<const double2 *>(c->ws + L.wtab);
+    P.rho_ring = reinterpret_cast<double2 *>(c->ws + L.rho);
+    P.stats_ring = reinterpret_cast<StepRec *>(c->ws + L.stats);
+    P.st = reinterpret_cast<DevState *>(c->ws + L.state);
+    c->mask.clear();
+    for (int p = 0; p < cfg->dkmax; ++p) c->mask.push_back(p);
+    set_mask_params(c);
+    // device constants: q, U; zeroed state
+    std::vector<double2> Ud(M * M);
+    for (int i = 0; i < M * M; ++i) Ud[i] = make_double2(c->U[i].real(), c->U[i].imag());
+    e = cudaMemcpyAsync(c->ws + L.q, c->q.data(), M * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->ws + L.uprop, Ud.data(), M * M * sizeof(double2), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.state, 0, sizeof(DevState), c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        delete c;
+        return QP_ERR_CUDA;
+    }
+    *out = c;
+    return QP_OK;
+}
+
+void qp_destroy(qp_ctx *ctx) {
+    if (!ctx) return;
+    if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+    delete ctx;
+}
+
+qp_status qp_eta_from_bath(const qp_bath *bath, double dt, int n, double *eta_re, double *eta_im) {
+    if (!bath || !eta_re || !eta_im || n < 1 || n > 4096) return QP_ERR_ARG;
+    std::vector<qp::cplx> eta;
+    if (qp::eta_from_bath(*bath, dt, n, eta)) return QP_ERR_ARG;
+    for (int i = 0; i < n; ++i) {
+        eta_re[i] = eta[i].real();
+        eta_im[i] = eta[i].imag();
+    }
+    return QP_OK;
+}
+
+qp_status qp_set_eta(qp_ctx *c, const double *re, const double *im, int n) {
+    if (!c) return QP_ERR_ARG;
+    if (!re || !im || n < c->cfg.dkmax) return fail(c, QP_ERR_ARG, "need dkmax influence coefficients");
+    const int dk = c->cfg.dkmax, M = c->cfg.M;
+    std::vector<double2> e(dk);
+    for (int i = 0; i < dk; ++i) {
+        if (!std::isfinite(re[i]) || !std::isfinite(im[i])) return fail(c, QP_ERR_ARG, "eta must be finite");
+        e[i] = make_double2(re[i], im[i]);
+    }
+    QP_CUDA(c, cudaMemcpyAsync(c->ws + c->L.eta, e.data(), dk * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
+    const Params &P = c->P;
+    const double *qd = reinterpret_cast<const double *>(c->ws + c->L.q);
+    const double2 *ed = reinterpret_cast<const double2 *>(c->ws + c->L.eta);
+    if (P.nchunks > 0) {
+        k_build_lut<<<64, 256, 0, c->stream>>>(reinterpret_cast<double2 *>(c->ws + c->L.lut),
+                                               reinterpret_cast<float2 *>(c->ws + c->L.lutf),
+                                               reinterpret_cast<float2 *>(c->ws + c->L.lutlo), ed, qd, M, P.bs, P.b,
+                                               dk, P.nchunks);
+        QP_CUDA(c, cudaGetLastError());
+    }
+    k_build_w<<<1, 256, 0, c->stream>>>(reinterpret_cast<double2 *>(c->ws + c->L.wtab),
+                                        reinterpret_cast<const double2 *>(c->ws + c->L.uprop), ed, qd, M);
+    QP_CUDA(c, cudaGetLastError());
+    QP_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->have_eta = true;
+    return QP_OK;
+}
+
+qp_status qp_set_mask(qp_ctx *c, const int *positions, int n) {
+    if (!c) return QP_ERR_ARG;
+    const int dk = c->cfg.dkmax;
+    std::vector<int> m;
+    if (!positions || n == 0) {
+        for (int p = 0; p < dk; ++p) m.push_back(p);
+    } else {
+        if (n < 0 || n > dk) return fail(c, QP_ERR_ARG, "mask size out of range");
+        std::vector<char> seen(dk, 0);
+        for (int i = 0; i < n; ++i) {
+            const int p = positions[i];
+            if (p < 0 || p >= dk) return fail(c, QP_ERR_ARG, "mask position out of [0, dkmax)");
+            seen[p] = 1;
+        }
+        if (!seen[0] || (dk >= 2 && !seen[1])) return fail(c, QP_ERR_ARG, "mask must contain positions 0 and 1");
+        for (int p = 0; p < dk; ++p)
+            if (seen[p]) m.push_back(p);
+    }
+    c->mask = m;
+    set_mask_params(c);
+    c->graph_dirty = true;
+    return QP_OK;
+}
+
+qp_status qp_set_rho0(qp_ctx *c, const double *re, const double *im) {
+    if (!c) return QP_ERR_ARG;
+    if (!re) return fail(c, QP_ERR_ARG, "rho0 required");
+    if (!c->have_eta) return fail(c, QP_ERR_STATE, "qp_set_eta must come before qp_set_rho0");
+    const int M = c->cfg.M, MM = M * M;
+    const int bs = c->P.bs;
+    std::vector<unsigned long long> keys;
+    std::vector<double2> amps, rho(MM);
+    for (int a = 0; a < M; ++a)
+        for (int b = 0; b < M; ++b) {
+            const double x = re[a * M + b], y = im ? im[a * M + b] : 0.0;
+            if (!std::isfinite(x) || !std::isfinite(y)) return fail(c, QP_ERR_ARG, "rho0 must be finite");
+            rho[a * M + b] = make_double2(x, y);
+            if (x != 0.0 || y != 0.0) {
+                keys.push_back((unsigned long long)(a | (b << bs)));
+                amps.push_back(make_double2(x, y));
+            }
+        }
+    if ((int64_t)keys.size() > c->cfg.max_paths) return fail(c, QP_ERR_CAPACITY, "rho0 exceeds max_paths");
+    const size_t n = keys.size();
+    QP_CUDA(c, cudaMemcpyAsync(c->P.keys[0], keys.data(), n * 8, cudaMemcpyHostToDevice, c->stream));
+    if (c->cfg.precision == QP_C64) {
+        std::vector<float2> af(n);
+        for (size_t i = 0; i < n; ++i) af[i] = make_float2((float)amps[i].x, (float)amps[i].y);
+        QP_CUDA(c, cudaMemcpyAsync(c->P.amps[0], af.data(), n * sizeof(float2), cudaMemcpyHostToDevice, c->stream));
+        QP_CUDA(c, cudaStreamSynchronize(c->stream));
+    } else {
+        QP_CUDA(c, cudaMemcpyAsync(c->P.amps[0], amps.data(), n * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
+    }
+    DevState s{};
+    s.n_cur = n;
+    QP_CUDA(c, cudaMemcpyAsync(c->P.st, &s, sizeof(DevState), cudaMemcpyHostToDevice, c->stream));
+    QP_CUDA(c, cudaMemcpyAsync(c->P.rho_ring, rho.data(), MM * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
+    QP_CUDA(c, cudaMemsetAsync(c->P.rho_ring + MM, 0, MM * sizeof(double2), c->stream));
+    StepRec r0{0, 0, 0, (long long)n};
+    QP_CUDA(c, cudaMemcpyAsync(c->P.stats_ring, &r0, sizeof(StepRec), cudaMemcpyHostToDevice, c->stream));
+    k_clear_table<<<c->nsm * 4, 256, 0, c->stream>>>(c->P.slots, c->P.repk, c->L.tcap);
+    QP_CUDA(c, cudaGetLastError());
+    QP_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->have_state = true;
+    c->failed = false;
+    c->err.clear();
+    return QP_OK;
+}
+
+qp_status qp_step(qp_ctx *c, int nsteps) {
+    if (!c) return QP_ERR_ARG;
+    if (nsteps < 0) return fail(c, QP_ERR_ARG, "nsteps < 0");
+    if (!c->have_state) return fail(c, QP_ERR_STATE, "qp_set_rho0 must come before qp_step");
+    if (c->failed) return fail(c, QP_ERR_STATE, "context holds a device error; call qp_set_rho0");
+    if (nsteps == 0) return QP_OK;
+    if (c->use_graph) {
+        if (c->graph_dirty || !c->graph) {
+            if (c->graph) {
+                cudaGraphExecDestroy(c->graph);
+                c->graph = nullptr;
+            }
+            cudaGraph_t g;
+            QP_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+            cudaError_t le = launch_step(c);
+            cudaError_t ce = cudaStreamEndCapture(c->stream, &g);
+            if (le != cudaSuccess) return fail(c, QP_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(le));
+            if (ce != cudaSuccess) return fail(c, QP_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(ce));
+            cudaError_t ie = cudaGraphInstantiate(&c->graph, g, 0);
+            cudaGraphDestroy(g);
+            if (ie != cudaSuccess) return fail(c, QP_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(ie));
+            c->graph_dirty = false;
+        }
+        for (int s = 0; s < nsteps; ++s) QP_CUDA(c, cudaGraphLaunch(c->graph, c->stream));
+    } else {
+        for (int s = 0; s < nsteps; ++s) {
+            cudaError_t e = launch_step(c);
+            if (e != cudaSuccess) return fail(c, QP_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e));
+        }
+    }
+    return QP_OK;
+}
+
+static qp_status read_state(qp_ctx *c, DevState *s) {
+    QP_CUDA(c, cudaMemcpyAsync(s, c->P.st, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream));
+    QP_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (s->err) {
+        c->failed = true;
+        std::string what;
+        if (s->err & kErrPaths) what += " path buffer (max_paths)";
+        if (s->err & kErrGroups) what += " merge groups (max_groups)";
+        if (s->err & kErrProbe) what += " merge table probe limit";
+        return fail(c, QP_ERR_CAPACITY, "capacity exceeded at step " + std::to_string(s->t + 1) + ":" + what);
+    }
+    return QP_OK;
+}
+
+qp_status qp_sync(qp_ctx *c) {
+    if (!c) return QP_ERR_ARG;
+    DevState s;
+    return read_state(c, &s);
+}
+
+qp_status qp_current(qp_ctx *c, int64_t *t, int64_t *n) {
+    if (!c) return QP_ERR_ARG;
+    if (!c->have_state) return fail(c, QP_ERR_STATE, "no state");
+    DevState s;
+    qp_status r = read_state(c, &s);
+    if (t) *t = (int64_t)s.t;
+    if (n) *n = (int64_t)s.n_cur;
+    return r;
+}
+
+qp_status qp_read_rho(qp_ctx *c, int64_t t0, int count, double *re, double *im) {
+    if (!c) return QP_ERR_ARG;
+    if (!re || !im || count < 0) return fail(c, QP_ERR_ARG, "bad output");
+    if (!c->have_state) return fail(c, QP_ERR_STATE, "no state");
+    DevState s;
+    qp_status r = read_state(c, &s);
+    if (r != QP_OK) return r;
+    const int64_t R = c->cfg.rho_history, tc = (int64_t)s.t;
+    if (t0 < 0 || t0 + count - 1 > tc || t0 <= tc - R) return fail(c, QP_ERR_ARG, "step outside the kept rho history");
+    const int MM = c->cfg.M * c->cfg.M;
+    std::vector<double2> buf(MM);
+    for (int k = 0; k < count; ++k) {
+        const int64_t t = t0 + k;
+        QP_CUDA(c, cudaMemcpyAsync(buf.data(), c->P.rho_ring + (size_t)(t % R) * MM, MM * sizeof(double2),
+                                   cudaMemcpyDeviceToHost, c->stream));
+        QP_CUDA(c, cudaStreamSynchronize(c->stream));
+        for (int i = 0; i < MM; ++i) {
+            re[(size_t)k * MM + i] = buf[i].x;
+            im[(size_t)k * MM + i] = buf[i].y;
+        }
+    }
+    return QP_OK;
+}
+
+qp_status qp_read_stats(qp_ctx *c, int64_t t0, int count, qp_step_stats *out) {
+    if (!c) return QP_ERR_ARG;
+    if (!out || count < 0) return fail(c, QP_ERR_ARG, "bad output");
+    if (!c->have_state) return fail(c, QP_ERR_STATE, "no state");
+    DevState s;
+    qp_status r = read_state(c, &s);
+    if (r != QP_OK) return r;
+    const int64_t R = c->cfg.rho_history, tc = (int64_t)s.t;
+    if (t0 < 0 || t0 + count - 1 > tc || t0 <= tc - R) return fail(c, QP_ERR_ARG, "step outside the kept history");
+    for (int k = 0; k < count; ++k) {
+        StepRec rec;
+        QP_CUDA(c, cudaMemcpyAsync(&rec, c->P.stats_ring + (t0 + k) % R, sizeof(StepRec), cudaMemcpyDeviceToHost,
+                                   c->stream));
+        QP_CUDA(c, cudaStreamSynchronize(c->stream));
+        out[k].t = rec.t;
+        out[k].groups = rec.groups;
+        out[k].extended = rec.extended;
+        out[k].kept = rec.kept;
+    }
+    return QP_OK;
+}
+
+qp_status qp_export_paths(qp_ctx *c, uint64_t *keys, double *amps, int64_t cap, int64_t *n) {
+    if (!c) return QP_ERR_ARG;
+    if (!n || cap < 0 || (cap > 0 && (!keys || !amps))) return fail(c, QP_ERR_ARG, "bad output");
+    if (!c->have_state) return fail(c, QP_ERR_STATE, "no state");
+    DevState s;
+    qp_status r = read_state(c, &s);
+    if (r != QP_OK) return r;
+    *n = (int64_t)s.n_cur;
+    if ((int64_t)s.n_cur > cap) return fail(c, QP_ERR_CAPACITY, "export buffer too small");
+    const int buf = (int)(s.t & 1);
+    const size_t cnt = s.n_cur;
+    QP_CUDA(c, cudaMemcpyAsync(keys, c->P.keys[buf], cnt * 8, cudaMemcpyDeviceToHost, c->stream));
+    if (c->cfg.precision == QP_C64) {
+        std::vector<float2> tmp(cnt);
+        QP_CUDA(c, cudaMemcpyAsync(tmp.data(), c->P.amps[buf], cnt * sizeof(float2), cudaMemcpyDeviceToHost, c->stream));
+        QP_CUDA(c, cudaStreamSynchronize(c->stream));
+        for (size_t i = 0; i < cnt; ++i) {
+            amps[2 * i] = tmp[i].x;
+            amps[2 * i + 1] = tmp[i].y;
+        }
+    } else {
+        QP_CUDA(c, cudaMemcpyAsync(amps, c->P.amps[buf], cnt * sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
+        QP_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    return QP_OK;
+}
+
+qp_status qp_profile_steps(qp_ctx *c, int nsteps, double *kernel_ms, int nk) {
+    if (!c) return QP_ERR_ARG;
+    if (nsteps < 0 || !kernel_ms || nk < 0) return fail(c, QP_ERR_ARG, "bad arguments");
+    if (!c->have_state) return fail(c, QP_ERR_STATE, "qp_set_rho0 must come before qp_profile_steps");
+    if (c->failed) return fail(c, QP_ERR_STATE, "context holds a device error; call qp_set_rho0");
+    cudaEvent_t ev[kStepKernels + 1];
+    for (int k = 0; k <= kStepKernels; ++k) QP_CUDA(c, cudaEventCreate(&ev[k]));
+    qp_status st = QP_OK;
+    for (int s = 0; s < nsteps && st == QP_OK; ++s) {
+        cudaError_t e = launch_step(c, ev);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[kStepKernels]);
+        if (e != cudaSuccess) {
+            st = fail(c, QP_ERR_CUDA, std::string("profile: ") + cudaGetErrorString(e));
+            break;
+        }
+        for (int k = 0; k < kStepKernels && k < nk; ++k) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+            kernel_ms[k] += ms;
+        }
+    }
+    for (int k = 0; k <= kStepKernels; ++k) cudaEventDestroy(ev[k]);
+    if (st != QP_OK) return st;
+    DevState ds;
+    return read_state(c, &ds);
+}
+
+const char *qp_last_error(const qp_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+}  // extern "C"

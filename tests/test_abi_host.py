@@ -1,0 +1,85 @@
+"""Host-side checks of libqp that need no GPU: the library loads, exports
+every symbol include/qp.h declares, validates configurations, and its host
+eta quadrature agrees with the oracle's (an independent formula: box
+integrals vs second differences of Q(t))."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2506_03127_gb300 import build as qp_build
+
+qp_build.build()
+
+from paper_2506_03127_gb300 import abi  # noqa: E402
+import workloads as W  # noqa: E402
+from oracle import bath as B  # noqa: E402
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "qp.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(qp_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported():
+    names = declared_functions()
+    assert len(names) >= 15
+    L = ctypes.CDLL(abi.LIB_PATH)
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_version_and_status_strings():
+    assert abi.lib.qp_version() >= 100
+    assert abi.lib.qp_status_string(abi.QP_ERR_CAPACITY).decode() == "capacity exceeded"
+
+
+def _cfg(**kw):
+    args = dict(M=2, dkmax=8, dt=0.25, q=[1, -1], hs=np.array([[0, 0.5], [0.5, 0]]), theta=0.0)
+    args.update(kw)
+    return abi.make_config(**args)
+
+
+def test_workspace_size_grows_with_capacity():
+    c1, k1 = _cfg(max_paths=1 << 12)
+    c2, k2 = _cfg(max_paths=1 << 16)
+    assert abi.qp_workspace_size(c2) > abi.qp_workspace_size(c1) > 0
+
+
+@pytest.mark.parametrize("bad", [dict(M=1), dict(M=5), dict(dkmax=0), dict(M=2, dkmax=33), dict(M=3, q=[1, 0, -1],
+                                 hs=np.eye(3), dkmax=17), dict(dt=-1.0), dict(theta=-1.0), dict(max_paths=0),
+                                 dict(hs=np.array([[0, 0.5], [0.2, 0]])), dict(precision=7), dict(engine=9)])
+def test_invalid_configs_rejected(bad):
+    cfg, keep = _cfg(**bad)
+    n = ctypes.c_size_t()
+    assert abi.lib.qp_workspace_size(ctypes.byref(cfg), ctypes.byref(n)) == abi.QP_ERR_ARG
+
+
+def test_create_rejects_small_or_misaligned_workspace():
+    cfg, keep = _cfg()
+    h = ctypes.c_void_p()
+    need = abi.qp_workspace_size(cfg)
+    assert abi.lib.qp_create(ctypes.byref(cfg), ctypes.c_void_p(256 * 1000), need - 256, None,
+                             ctypes.byref(h)) == abi.QP_ERR_OOM
+    assert abi.lib.qp_create(ctypes.byref(cfg), ctypes.c_void_p(256 * 1000 + 8), need, None,
+                             ctypes.byref(h)) == abi.QP_ERR_ARG
+    assert abi.lib.qp_create(ctypes.byref(cfg), None, need, None, ctypes.byref(h)) == abi.QP_ERR_ARG
+
+
+@pytest.mark.parametrize("w", [W.SPIN_BOSON_OHMIC_DK8, W.SPIN_BOSON_STRUCTURED_DK16, W.CHAIN3_STRUCTURED_DK12,
+                               W.TLS_OHMIC_FULL_DK14, W.resonance_sweep(3)[2]], ids=lambda w: w.name)
+def test_library_eta_matches_oracle(w):
+    el = abi.qp_eta_from_bath(w.bath, w.dt, w.dkmax)
+    eo = B.eta_coefficients(w.bath, w.dt, w.dkmax)
+    np.testing.assert_allclose(el, eo, rtol=0, atol=1e-13)
+
+
+def test_eta_from_bath_rejects_bad_bath():
+    b = abi.qp_bath(beta=-1.0, ohmic_alpha=0.1, ohmic_wc=5.0)
+    re, im = np.zeros(4), np.zeros(4)
+    assert abi.lib.qp_eta_from_bath(ctypes.byref(b), 0.1, 4, abi._ptr(re), abi._ptr(im)) == abi.QP_ERR_ARG

@@ -1,0 +1,183 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Bar (FP64 path): every rho(t) within 1e-10 max-abs of the oracle's, per-step
+group and survivor counts equal, and the surviving key set bit-exact with
+amplitudes within 1e-10 -- the key comparison is made only where the
+oracle reports no decision within rounding distance of the tie window or of
+the filter threshold (reported as near_tie / near_theta).
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import iquapi
+from tests.golden.make_golden import load as load_golden
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU container
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_2506_03127_gb300 import Propagator, abi, build, eta_from_bath  # noqa: E402
+
+build.build()
+
+RHO_TOL = 1e-10
+
+
+def gpu_run(M, q, hs, dt, eta, dkmax, mask, theta, rho0, steps, precision="fp64", max_paths=1 << 20,
+            max_groups=0, engine="auto"):
+    p = Propagator(M, dkmax, dt, q, hs, theta, precision, engine, max_paths, max_groups)
+    p.set_eta(eta)
+    p.set_mask(mask)
+    p.set_rho0(rho0)
+    p.step(steps)
+    p.sync()
+    rho = p.rho(0, steps + 1)
+    stats = p.stats(1, steps) if steps else []
+    keys, amps = p.export_paths()
+    p.close()
+    return rho, stats, keys, amps
+
+
+def compare(res_gpu, res_or, M, check_keys=True, tol=RHO_TOL):
+    rho, stats, keys, amps = res_gpu
+    assert np.abs(rho - res_or.rho).max() <= tol, np.abs(rho - res_or.rho).max()
+    for s_g, s_o in zip(stats, res_or.stats):
+        assert s_g[0] == s_o.t
+        assert (s_g[1], s_g[3]) == (s_o.groups, s_o.kept), (s_g, s_o)
+    ambiguous = any(s.near_tie or s.near_theta for s in res_or.stats)
+    if check_keys and not ambiguous:
+        ko = iquapi.packed_keys(res_or.paths.sp, res_or.paths.sm, M)
+        assert keys.size == ko.size
+        # with dkmax = 1 children of different groups share a key until the
+        # next pre-merge, so compare the amplitude summed per distinct key
+        ug, ig = np.unique(keys, return_inverse=True)
+        uo, io = np.unique(ko, return_inverse=True)
+        np.testing.assert_array_equal(ug, uo)
+        sg = np.zeros(ug.size, dtype=complex)
+        so = np.zeros(uo.size, dtype=complex)
+        np.add.at(sg, ig, amps)
+        np.add.at(so, io, res_or.paths.amp)
+        assert np.abs(sg - so).max() <= tol
+    return ambiguous
+
+
+def run_both(case, mask, theta, steps, **kw):
+    M, dk = case["M"], case["dkmax"]
+    g = gpu_run(M, case["q"], case["hs"], case["dt"], case["eta"], dk, mask, theta, case["rho0"], steps, **kw)
+    o = iquapi.propagate(M, case["q"], case["hs"], case["dt"], case["eta"], dk, mask, theta, case["rho0"], steps)
+    return g, o
+
+
+@pytest.mark.parametrize("M,dkmax,steps,seed", [(2, 1, 10, 1), (2, 2, 12, 2), (2, 5, 14, 3), (2, 8, 12, 4),
+                                                (3, 1, 8, 5), (3, 3, 8, 6), (3, 4, 7, 7), (4, 2, 6, 8), (4, 3, 5, 9)])
+def test_unmasked_unfiltered_matches_oracle(M, dkmax, steps, seed):
+    case = W.random_case(seed, M, dkmax)
+    g, o = run_both(case, None, 0.0, steps)
+    compare(g, o, M)
+
+
+@pytest.mark.parametrize("M,dkmax,mask,theta,steps,seed", [
+    (2, 8, (0, 1, 2, 5), 1e-4, 20, 11),
+    (2, 10, (0, 1, 2, 3, 4, 5, 6, 8), 1e-6, 24, 12),
+    (2, 9, (0, 1, 2, 3, 5, 8), 0.0, 14, 13),
+    (2, 12, (0, 1, 2, 3, 4, 6, 9), 1e-5, 30, 14),
+    (3, 5, (0, 1, 3), 1e-5, 12, 15),
+    (3, 6, (0, 1, 2, 3), 0.0, 9, 16),
+    (4, 4, (0, 1, 3), 1e-4, 8, 17),
+])
+def test_masked_filtered_matches_oracle(M, dkmax, mask, theta, steps, seed):
+    case = W.random_case(seed, M, dkmax)
+    g, o = run_both(case, mask, theta, steps)
+    compare(g, o, M)
+
+
+def test_hashed_table_index_matches_oracle():
+    """dkmax 11 without mask: 20 masked-key bits exceed a 2^17-slot table, so
+    the merge table hashes (linear probing) instead of indexing directly."""
+    case = W.random_case(21, 2, 11)
+    g, o = run_both(case, None, 1e-7, 18, max_groups=1 << 16)
+    compare(g, o, 2)
+
+
+def test_spin_boson_ohmic_dk8_trajectory_against_stored_oracle():
+    w = W.SPIN_BOSON_OHMIC_DK8
+    eta = eta_from_bath(w.bath, w.dt, w.dkmax)
+    rho, stats, keys, amps = gpu_run(w.M, w.q, w.hs_array(), w.dt, eta, w.dkmax, w.mask, w.theta,
+                                     w.rho0_array(), w.steps)
+    t, n, rho_o = load_golden("spin_boson_ohmic_dk8_rho.txt")
+    assert np.abs(rho - rho_o).max() <= RHO_TOL
+    assert [s[3] for s in stats] == list(n[1:])
+    assert keys.size == 65536
+
+
+def test_spin_boson_structured_dk16_first_40_steps_against_stored_oracle():
+    w = W.SPIN_BOSON_STRUCTURED_DK16
+    eta = eta_from_bath(w.bath, w.dt, w.dkmax)
+    rho, stats, keys, amps = gpu_run(w.M, w.q, w.hs_array(), w.dt, eta, w.dkmax, w.mask, w.theta,
+                                     w.rho0_array(), 40, max_paths=1 << 21)
+    t, n, rho_o = load_golden("spin_boson_structured_dk16_rho40.txt")
+    assert np.abs(rho - rho_o).max() <= RHO_TOL
+    assert [s[3] for s in stats] == list(n[1:])
+
+
+def test_spin_boson_structured_dk16_full_length_properties():
+    """All 2000 steps at full size: physical properties that hold at any size
+    (trace loss only from the filter and small, Hermitian diagonal real and
+    non-negative to rounding, counts bounded by M^(2 dk_eff))."""
+    w = W.SPIN_BOSON_STRUCTURED_DK16
+    p = Propagator.from_workload(w, max_paths=1 << 21)
+    p.step(w.steps)
+    p.sync()
+    t, n = p.current()
+    assert t == w.steps and 0 < n <= 4 ** 10
+    rho = p.rho(w.steps - 999, 1000)
+    tr = np.trace(rho, axis1=1, axis2=2)
+    assert np.all(tr.real <= 1 + 1e-12) and np.all(tr.real > 0.95)
+    assert np.abs(tr.imag).max() < 1e-9
+    d = np.diagonal(rho, axis1=1, axis2=2)
+    assert d.real.min() > -1e-9
+    p.close()
+
+
+def test_all_paths_filtered_leaves_empty_set():
+    case = W.random_case(31, 2, 4)
+    g, o = run_both(case, None, 10.0, 6)
+    rho, stats, keys, amps = g
+    assert keys.size == 0 and np.abs(rho[1:]).max() == 0.0
+    assert all(s[3] == 0 for s in stats)
+
+
+def test_capacity_overflow_is_reported_and_recoverable():
+    case = W.random_case(41, 2, 6)
+    p = Propagator(2, 6, case["dt"], case["q"], case["hs"], 0.0, max_paths=300)
+    p.set_eta(case["eta"])
+    p.set_mask(None)
+    p.set_rho0(case["rho0"])
+    p.step(8)
+    with pytest.raises(abi.QPError) as e:
+        p.sync()
+    assert e.value.status == abi.QP_ERR_CAPACITY
+    with pytest.raises(abi.QPError) as e2:
+        p.step(1)
+    assert e2.value.status == abi.QP_ERR_STATE
+    p.set_rho0(case["rho0"])       # restart clears the error
+    p.step(3)
+    p.sync()
+    assert p.current()[0] == 3
+    p.close()
+
+
+def test_invalid_mask_rejected():
+    case = W.random_case(42, 2, 6)
+    p = Propagator(2, 6, case["dt"], case["q"], case["hs"], 0.0, max_paths=1 << 12)
+    for bad in [(0, 2), (1, 2), (0, 1, 6), (-1, 0, 1)]:
+        with pytest.raises(abi.QPError) as e:
+            p.set_mask(bad)
+        assert e.value.status == abi.QP_ERR_ARG
+    with pytest.raises(abi.QPError) as e:
+        p.step(1)                  # no rho0 yet
+    assert e.value.status == abi.QP_ERR_STATE
+    p.close()
