@@ -33,6 +33,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
 #include <complex>
 #include <cstdio>
@@ -49,9 +50,14 @@ constexpr unsigned long long kEmpty = ~0ull;
 constexpr unsigned int kNoSlot = 0xffffffffu;
 constexpr int kMaxRuns = 8;
 constexpr int kMaxProbe = 64;
-constexpr double kTieRel = 1e-12;
 constexpr unsigned int kErrPaths = 1u, kErrGroups = 2u, kErrProbe = 4u;
 constexpr int kLutEntries = 256;
+constexpr int kInsertThreads = 256;
+constexpr int kExpandThreads = 128;
+constexpr int kMaxExpandBlocks = 2048;
+constexpr int kMaxDelta = 12;
+constexpr double kTieRelFP64 = 1e-12;  // weights equal to this relative width are ties (R4)
+constexpr double kTieRelC64 = 1e-5;    // same, at complex64 resolution
 
 struct __align__(32) Slot {
     unsigned long long mk;     // masked key, kEmpty when free
@@ -95,7 +101,15 @@ struct Params {
     const float2 *lutf;                // same, FP32 hi part
     const float2 *lutf_lo;             // FP32 residual (hi + lo = FP64 value)
     const double2 *wtab;               // [M*M child][M*M parent newest] propagator x new-point influence
+    const float2 *wtabf;               // same, FP32
+    const double2 *etab;               // [dkmax][ndelta][nchunks][256] exp(-delta_d T) tables (FP64 path)
+    int ndelta;                        // distinct nonzero q_a - q_b
+    float deltaf[12];                  // their values (FP32 path)
+    signed char dsel[16];              // child k -> delta index, -1 when q_a == q_b
+    float theta2f;
+    double tie_rel;                    // relative window of equal weights (R4)
     double2 *rho_ring;                 // [rho_hist][M*M]
+    double2 *rho_part;                 // [expand blocks][M*M] per-block partial sums of rho(t)
     StepRec *stats_ring;               // [rho_hist]
     DevState *st;
 };
@@ -121,10 +135,55 @@ __device__ __forceinline__ void raise_err(DevState *st, unsigned int bit) {
     atomicOr(&st->err, bit);
 }
 
+// Block-wide append: exclusive offset of each thread's cnt items within the
+// block and the block's base in a global array, with one atomicAdd on the
+// global cursor per block.  All threads of the block must call it.
+struct Append {
+    unsigned long long base;
+    unsigned excl, total;
+};
+template <int NT>
+__device__ __forceinline__ Append block_append(unsigned cnt, unsigned long long *cursor) {
+    constexpr int NW = NT / 32;
+    __shared__ unsigned s_w[NW];
+    __shared__ unsigned s_tot;
+    __shared__ unsigned long long s_base;
+    const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    unsigned incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+        if ((int)lane >= o) incl += y;
+    }
+    if (lane == 31) s_w[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const unsigned v = lane < (unsigned)NW ? s_w[lane] : 0u;
+        unsigned vi = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, vi, o);
+            if ((int)lane >= o) vi += y;
+        }
+        if (lane < (unsigned)NW) s_w[lane] = vi - v;
+        if (lane == 31) {
+            s_tot = vi;
+            s_base = vi ? atomicAdd(cursor, (unsigned long long)vi) : 0ull;
+        }
+    }
+    __syncthreads();
+    Append r;
+    r.base = s_base;
+    r.total = s_tot;
+    r.excl = s_w[warp] + incl - cnt;
+    __syncthreads();
+    return r;
+}
+
 // ---------------------------------------------------------------- pre-merge
 
 template <typename Amp>
-__global__ void __launch_bounds__(256) k_insert(Params P) {
+__global__ void __launch_bounds__(kInsertThreads) k_insert(Params P) {
     DevState *st = P.st;
     if (st->err) return;
     const unsigned long long t = st->t, tn = t + 1;
@@ -132,16 +191,13 @@ __global__ void __launch_bounds__(256) k_insert(Params P) {
     const unsigned long long n = st->n_cur;
     const unsigned long long *keys = P.keys[t & 1];
     const Amp *amps = static_cast<const Amp *>(P.amps[t & 1]);
-    const unsigned lane = lane_id();
-    const unsigned long long warp0 = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) - lane;
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    for (unsigned long long base = warp0; base < n; base += stride) {
-        const unsigned long long i = base + lane;
-        const bool valid = i < n;
+    const unsigned long long stride = (unsigned long long)gridDim.x * kInsertThreads;
+    for (unsigned long long base = blockIdx.x * (unsigned long long)kInsertThreads; base < n; base += stride) {
+        const unsigned long long i = base + threadIdx.x;
         bool claimed = false, found = false;
         unsigned long long h = 0;
         double2 a = make_double2(0.0, 0.0);
-        if (valid) {
+        if (i < n) {
             const unsigned long long key = keys[i];
             a = load_amp(amps, i);
             const unsigned long long mk = key & P.pmask;
@@ -156,20 +212,6 @@ __global__ void __launch_bounds__(256) k_insert(Params P) {
                 }
                 h = (h + 1) & P.tcap_mask;
             }
-        }
-        const unsigned bal = __ballot_sync(0xffffffffu, claimed);
-        if (bal) {
-            const int leader = __ffs(bal) - 1;
-            unsigned long long g0 = 0;
-            if ((int)lane == leader) g0 = atomicAdd(&st->n_groups, (unsigned long long)__popc(bal));
-            g0 = __shfl_sync(0xffffffffu, g0, leader);
-            if (claimed) {
-                const unsigned long long g = g0 + __popc(bal & ((1u << lane) - 1u));
-                if (g < (unsigned long long)P.max_groups) P.groups[g] = (unsigned int)h;
-                else raise_err(st, kErrGroups);
-            }
-        }
-        if (valid) {
             if (found) {
                 atomicAdd(&P.slots[h].sre, a.x);
                 atomicAdd(&P.slots[h].sim, a.y);
@@ -180,6 +222,12 @@ __global__ void __launch_bounds__(256) k_insert(Params P) {
                 P.slot_of[i] = kNoSlot;
                 raise_err(st, kErrProbe);
             }
+        }
+        const Append ap = block_append<kInsertThreads>(claimed ? 1u : 0u, &st->n_groups);
+        if (claimed) {
+            const unsigned long long g = ap.base + ap.excl;
+            if (g < (unsigned long long)P.max_groups) P.groups[g] = (unsigned int)h;
+            else raise_err(st, kErrGroups);
         }
     }
 }
@@ -200,62 +248,141 @@ __global__ void __launch_bounds__(256) k_tiebreak(Params P) {
         const double2 a = load_amp(amps, i);
         const double w2 = a.x * a.x + a.y * a.y;
         const double wm = __longlong_as_double((long long)P.slots[h].wmax);
-        if (w2 >= (1.0 - kTieRel) * wm) atomicMin(&P.repk[h], keys[i]);
+        if (w2 >= (1.0 - P.tie_rel) * wm) atomicMin(&P.repk[h], keys[i]);
     }
 }
 
 // ---------------------------------------------------------------- extension
 
-template <typename Amp> struct AmpOut;
-template <> struct AmpOut<double2> {
-    static __device__ __forceinline__ void store(double2 *p, unsigned long long i, double2 v) { p[i] = v; }
-};
-template <> struct AmpOut<float2> {
-    static __device__ __forceinline__ void store(float2 *p, unsigned long long i, double2 v) {
-        p[i] = make_float2((float)v.x, (float)v.y);
-    }
-};
-
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
     return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
-
-// History part H of the influence exponent, FP64: sum of per-byte table
-// entries of the representative's key (lags 1 .. n_act-1).
-__device__ __forceinline__ double2 history_fp64(const Params &P, const double2 *lut, unsigned long long rep) {
-    double hx = 0.0, hy = 0.0;
-    for (int j = 0; j < P.nchunks; ++j) {
-        const double2 v = __ldg(&lut[j * kLutEntries + ((rep >> (8 * j)) & 0xffu)]);
-        hx += v.x;
-        hy += v.y;
-    }
-    return make_double2(hx, hy);
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
+__device__ __forceinline__ unsigned key_byte(unsigned long long k, int j) { return (unsigned)(k >> (8 * j)) & 0xffu; }
 
-// Same in FP32 with compensated summation: each table entry is split as
-// hi + lo (both FP32); the running sum is Kahan-compensated.
-__device__ __forceinline__ double2 history_fp32(const Params &P, const float2 *lut, const float2 *lutlo,
-                                                unsigned long long rep) {
-    float sx = 0.f, sy = 0.f, cx = 0.f, cy = 0.f;
-    for (int j = 0; j < P.nchunks; ++j) {
-        const int idx = j * kLutEntries + (int)((rep >> (8 * j)) & 0xffu);
-        const float2 hi = __ldg(&lut[idx]);
-        const float2 lo = __ldg(&lutlo[idx]);
-        float yx = (hi.x + lo.x) - cx;
-        float tx = sx + yx;
-        cx = (tx - sx) - yx;
-        sx = tx;
-        float yy = (hi.y + lo.y) - cy;
-        float ty = sy + yy;
-        cy = (ty - sy) - yy;
-        sy = ty;
+// Extension of one group (or one stored path while the window fills) to its
+// M^2 children.  The influence factor of child (a,b) is
+//   exp(-(q_a - q_b)(H + eta_0 q_a - eta_0* q_b)),
+// H = sum over the history lags of eta_d q+ - conj(eta_d) q-.  The part
+// that does not depend on the history, exp(-(q_a-q_b)(eta_0 q_a - eta_0* q_b)),
+// and the bare propagator U[a,a'] conj(U[b,b']) are folded into the table W.
+// FP64: H splits into per-byte terms T_j of the representative's key, so
+//   exp(-delta H) = prod_j exp(-delta T_j[byte_j]),
+// read from tables of exp(-delta T) (no transcendental per group).
+// C64: H is summed in FP32 with Kahan compensation over the per-byte terms
+// (each stored as an FP32 hi + lo pair), then exp/sincos in FP32.
+template <int M, bool C64>
+struct Expander {
+    static constexpr int MM = M * M;
+    static constexpr int ND = M * (M - 1);   // at most this many distinct nonzero q_a - q_b
+    using AmpT = typename std::conditional<C64, float2, double2>::type;
+
+    template <typename T>
+    static __device__ __forceinline__ T pick(const T *Ed, int d) {   // register select, no local memory
+        T e = Ed[0];
+#pragma unroll
+        for (int i = 1; i < ND; ++i)
+            if (i == d) e = Ed[i];
+        return e;
     }
-    return make_double2((double)sx - (double)cx, (double)sy - (double)cy);
-}
 
-template <int M, typename Amp>
-__global__ void __launch_bounds__(128) k_expand(Params P, const double *qv) {
+    // children of one group: v[k] amplitudes, returns the bit set of survivors
+    // rho accumulators of one thread: FP64 on the FP64 path; on the C64 path
+    // FP32 with a Kahan compensation term, widened to FP64 once per thread
+    using AccT = typename std::conditional<C64, float2, double2>::type;
+
+    static __device__ __forceinline__ void kahan_add(float2 &s, float2 &c, float2 a) {
+        const float yx = a.x - c.x, tx = s.x + yx;
+        c.x = (tx - s.x) - yx;
+        s.x = tx;
+        const float yy = a.y - c.y, ty = s.y + yy;
+        c.y = (ty - s.y) - yy;
+        s.y = ty;
+    }
+
+    static __device__ __forceinline__ unsigned children(const Params &P, int n_act, unsigned long long rep, double2 S,
+                                                        const double2 *s_w, const float2 *s_wf, AmpT *v,
+                                                        AccT *racc, AccT *rcmp) {
+        const unsigned c0 = (unsigned)(rep & ((1u << P.b) - 1u));
+        const int pidx = (int)(c0 & ((1u << P.bs) - 1u)) * M + (int)(c0 >> P.bs);
+        unsigned keep = 0;
+        if constexpr (C64) {
+            float2 Ed[ND];
+            if (P.ndelta) {
+                const size_t off = (size_t)(n_act - 1) * P.nchunks * kLutEntries;
+                float sx = 0.f, sy = 0.f, cx = 0.f, cy = 0.f, lx = 0.f, ly = 0.f;
+                for (int j = 0; j < P.nchunks; ++j) {
+                    const size_t idx = off + (size_t)j * kLutEntries + key_byte(rep, j);
+                    const float2 hi = __ldg(&P.lutf[idx]);
+                    const float2 lo = __ldg(&P.lutf_lo[idx]);
+                    const float yx = hi.x - cx, tx = sx + yx;
+                    cx = (tx - sx) - yx;
+                    sx = tx;
+                    const float yy = hi.y - cy, ty = sy + yy;
+                    cy = (ty - sy) - yy;
+                    sy = ty;
+                    lx += lo.x;
+                    ly += lo.y;
+                }
+                const float hx = sx + (lx - cx), hy = sy + (ly - cy);
+#pragma unroll
+                for (int d = 0; d < ND; ++d) {
+                    if (d >= P.ndelta) break;
+                    const float zr = -P.deltaf[d] * hx, zi = -P.deltaf[d] * hy;
+                    float sn, cs;
+                    sincosf(zi, &sn, &cs);
+                    const float m = expf(zr);
+                    Ed[d] = make_float2(m * cs, m * sn);
+                }
+            }
+            const float2 Sf = make_float2((float)S.x, (float)S.y);
+#pragma unroll
+            for (int k = 0; k < MM; ++k) {
+                float2 a = cmulf(Sf, s_wf[k * MM + pidx]);
+                const int d = P.dsel[k];
+                if (d >= 0) a = cmulf(a, pick(Ed, d));
+                v[k] = a;
+                if (a.x * a.x + a.y * a.y >= P.theta2f) {
+                    keep |= 1u << k;
+                    kahan_add(racc[k], rcmp[k], a);
+                }
+            }
+        } else {
+            double2 Ed[ND];
+            const size_t dstride = (size_t)P.nchunks * kLutEntries;
+            const double2 *et = P.etab + (size_t)(n_act - 1) * P.ndelta * dstride;
+#pragma unroll
+            for (int d = 0; d < ND; ++d) {
+                if (d >= P.ndelta) break;
+                double2 e = make_double2(1.0, 0.0);
+                for (int j = 0; j < P.nchunks; ++j) e = cmul(e, __ldg(&et[d * dstride + (size_t)j * kLutEntries + key_byte(rep, j)]));
+                Ed[d] = e;
+            }
+#pragma unroll
+            for (int k = 0; k < MM; ++k) {
+                double2 a = cmul(S, s_w[k * MM + pidx]);
+                const int d = P.dsel[k];
+                if (d >= 0) a = cmul(a, pick(Ed, d));
+                v[k] = a;
+                if (a.x * a.x + a.y * a.y >= P.theta2) {
+                    keep |= 1u << k;
+                    racc[k].x += a.x;
+                    racc[k].y += a.y;
+                }
+            }
+        }
+        return keep;
+    }
+};
+
+template <int M, bool C64>
+__global__ void __launch_bounds__(kExpandThreads) k_expand(Params P) {
+    using X = Expander<M, C64>;
+    using AmpT = typename X::AmpT;
     constexpr int MM = M * M;
+    constexpr int NW = kExpandThreads / 32;
     DevState *st = P.st;
     if (st->err) return;
     const unsigned long long t = st->t, tn = t + 1;
@@ -265,37 +392,33 @@ __global__ void __launch_bounds__(128) k_expand(Params P, const double *qv) {
     const int L_child = (int)min(tn + 1, (unsigned long long)P.dkmax);
     const unsigned long long wmask = (P.b * L_child >= 64) ? ~0ull : ((1ull << (P.b * L_child)) - 1ull);
     const unsigned long long *keys_in = P.keys[t & 1];
-    const Amp *amps_in = static_cast<const Amp *>(P.amps[t & 1]);
+    const AmpT *amps_in = static_cast<const AmpT *>(P.amps[t & 1]);
     unsigned long long *keys_out = P.keys[tn & 1];
-    Amp *amps_out = static_cast<Amp *>(P.amps[tn & 1]);
-    const size_t lut_off = (size_t)(n_act - 1) * P.nchunks * kLutEntries;
-    const double2 *lut = P.lut + lut_off;
-    const float2 *lutf = P.lutf + lut_off;
-    const float2 *lutlo = P.lutf_lo + lut_off;
-    constexpr bool kC64 = sizeof(Amp) == sizeof(float2);
+    AmpT *amps_out = static_cast<AmpT *>(P.amps[tn & 1]);
 
     __shared__ double2 s_w[MM * MM];
-    __shared__ double s_q[M];
-    for (int i = threadIdx.x; i < MM * MM; i += blockDim.x) s_w[i] = P.wtab[i];
-    if (threadIdx.x < M) s_q[threadIdx.x] = qv[threadIdx.x];
+    __shared__ float2 s_wf[MM * MM];
+    __shared__ double2 s_r[NW][MM];
+    for (int i = threadIdx.x; i < MM * MM; i += blockDim.x) {
+        s_w[i] = P.wtab[i];
+        s_wf[i] = P.wtabf[i];
+    }
     __syncthreads();
 
-    const unsigned int smask = (1u << P.bs) - 1u;
-    const unsigned int cmask = (1u << P.b) - 1u;
-    double2 racc[MM];
+    typename X::AccT racc[MM], rcmp[MM];
 #pragma unroll
-    for (int k = 0; k < MM; ++k) racc[k] = make_double2(0.0, 0.0);
+    for (int k = 0; k < MM; ++k) {
+        racc[k].x = racc[k].y = 0;
+        rcmp[k].x = rcmp[k].y = 0;
+    }
 
-    const unsigned lane = lane_id();
-    const unsigned long long warp0 = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) - lane;
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    for (unsigned long long base = warp0; base < n; base += stride) {
-        const unsigned long long g = base + lane;
-        const bool valid = g < n;
-        unsigned int keepbits = 0;
-        double2 camp[MM];
+    const unsigned long long stride = (unsigned long long)gridDim.x * kExpandThreads;
+    for (unsigned long long base = blockIdx.x * (unsigned long long)kExpandThreads; base < n; base += stride) {
+        const unsigned long long g = base + threadIdx.x;
+        unsigned keepbits = 0;
+        AmpT camp[MM];
         unsigned long long rep = 0;
-        if (valid) {
+        if (g < n) {
             double2 S;
             if (merge) {
                 const unsigned int h = P.groups[g];
@@ -312,99 +435,97 @@ __global__ void __launch_bounds__(128) k_expand(Params P, const double *qv) {
                 rep = keys_in[g];
                 S = load_amp(amps_in, g);
             }
-            const double2 H = kC64 ? history_fp32(P, lutf, lutlo, rep) : history_fp64(P, lut, rep);
-            const unsigned int c0 = (unsigned int)(rep & cmask);
-            const int pidx = (int)(c0 & smask) * M + (int)(c0 >> P.bs);
-            // E[a][b] = exp(-(q_a - q_b) H): one exp + sincos per unordered pair
-            double2 E[MM];
-#pragma unroll
-            for (int a = 0; a < M; ++a) E[a * M + a] = make_double2(1.0, 0.0);
-#pragma unroll
-            for (int a = 0; a < M; ++a)
-#pragma unroll
-                for (int b = a + 1; b < M; ++b) {
-                    const double dq = s_q[a] - s_q[b];
-                    if (dq == 0.0) {
-                        E[a * M + b] = E[b * M + a] = make_double2(1.0, 0.0);
-                    } else if (kC64) {
-                        const float zr = (float)(-dq * H.x), zi = (float)(-dq * H.y);
-                        float s, c;
-                        __sincosf(zi, &s, &c);
-                        const float m = __expf(zr);
-                        const float mi = 1.0f / m;
-                        E[a * M + b] = make_double2(m * c, m * s);
-                        E[b * M + a] = make_double2(mi * c, -mi * s);
-                    } else {
-                        const double zr = -dq * H.x, zi = -dq * H.y;
-                        double s, c;
-                        sincos(zi, &s, &c);
-                        const double m = exp(zr);
-                        const double mi = 1.0 / m;
-                        E[a * M + b] = make_double2(m * c, m * s);
-                        E[b * M + a] = make_double2(mi * c, -mi * s);
-                    }
-                }
-#pragma unroll
-            for (int k = 0; k < MM; ++k) {
-                const double2 f = cmul(s_w[k * MM + pidx], E[k]);
-                const double2 v = cmul(S, f);
-                camp[k] = v;
-                if (v.x * v.x + v.y * v.y >= P.theta2) {
-                    keepbits |= 1u << k;
-                    racc[k].x += v.x;
-                    racc[k].y += v.y;
-                }
-            }
+            keepbits = X::children(P, n_act, rep, S, s_w, s_wf, camp, racc, rcmp);
         }
-        // warp-aggregated append of the survivors
-        const unsigned int cnt = __popc(keepbits);
-        unsigned int incl = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned int y = __shfl_up_sync(0xffffffffu, incl, o);
-            if ((int)lane >= o) incl += y;
-        }
-        const unsigned int total = __shfl_sync(0xffffffffu, incl, 31);
-        unsigned long long o0 = 0;
-        if (lane == 31 && total) o0 = atomicAdd(&st->n_out, (unsigned long long)total);
-        o0 = __shfl_sync(0xffffffffu, o0, 31);
-        if (total && o0 + total > (unsigned long long)P.max_paths) {
-            if (lane == 0) raise_err(st, kErrPaths);
+        const unsigned cnt = __popc(keepbits);
+        const Append ap = block_append<kExpandThreads>(cnt, &st->n_out);
+        if (ap.total && ap.base + ap.total > (unsigned long long)P.max_paths) {
+            if (threadIdx.x == 0) raise_err(st, kErrPaths);
         } else if (cnt) {
-            unsigned long long o = o0 + (incl - cnt);
+            unsigned long long o = ap.base + ap.excl;
             const unsigned long long shifted = rep << P.b;
 #pragma unroll
             for (int k = 0; k < MM; ++k) {
                 if (keepbits & (1u << k)) {
                     const unsigned long long code = (unsigned long long)((k / M) | ((k % M) << P.bs));
                     keys_out[o] = (shifted | code) & wmask;
-                    AmpOut<Amp>::store(amps_out, o, camp[k]);
+                    amps_out[o] = camp[k];
                     ++o;
                 }
             }
         }
     }
-    // rho(t): warp shuffle reduction, then one FP64 atomic per element per warp
-    double2 *rho = P.rho_ring + (size_t)(tn % (unsigned long long)P.rho_hist) * MM;
+    // rho(t): per-block partial sums (warp shuffles, then across warps); the
+    // finalize kernel adds the partials in block order (deterministic)
+    const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < MM; ++k) {
-        double x = racc[k].x, y = racc[k].y;
+        double x = (double)racc[k].x - (double)rcmp[k].x, y = (double)racc[k].y - (double)rcmp[k].y;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             x += __shfl_down_sync(0xffffffffu, x, o);
             y += __shfl_down_sync(0xffffffffu, y, o);
         }
-        if (lane == 0 && (x != 0.0 || y != 0.0)) {
-            atomicAdd(&rho[k].x, x);
-            atomicAdd(&rho[k].y, y);
+        if (lane == 0) s_r[warp][k] = make_double2(x, y);
+    }
+    __syncthreads();
+    if (threadIdx.x < MM) {
+        double x = 0.0, y = 0.0;
+        for (int w = 0; w < NW; ++w) {
+            x += s_r[w][threadIdx.x].x;
+            y += s_r[w][threadIdx.x].y;
         }
+        P.rho_part[(size_t)blockIdx.x * MM + threadIdx.x] = make_double2(x, y);
     }
 }
 
-__global__ void k_finalize(Params P, int MM) {
+// Step finalisation (one block): rho(t) from the expand blocks' partial sums
+// (one warp per element, fixed block order: deterministic), then counts,
+// statistics and the step index.
+__global__ void __launch_bounds__(256) k_finalize(Params P, int MM, int nblk) {
     DevState *st = P.st;
-    if (st->err) { st->n_groups = 0; st->n_out = 0; return; }
+    const unsigned long long err = st->err;
+    if (err) {
+        if (threadIdx.x == 0) { st->n_groups = 0; st->n_out = 0; }
+        return;
+    }
     const unsigned long long t = st->t, tn = t + 1;
+    double2 *rho = P.rho_ring + (size_t)(tn % (unsigned long long)P.rho_hist) * MM;
+    // T threads per element k; each sums a fixed stride of the partials with
+    // four independent accumulators so that the loads overlap
+    __shared__ double2 s_p[256];
+    const int T = (int)blockDim.x / MM;
+    const int k = (int)threadIdx.x / T, sidx = (int)threadIdx.x % T;
+    double2 a0 = make_double2(0.0, 0.0), a1 = a0, a2 = a0, a3 = a0;
+    if (k < MM) {
+        int b = sidx;
+        for (; b + 3 * T < nblk; b += 4 * T) {
+            const double2 v0 = P.rho_part[(size_t)b * MM + k];
+            const double2 v1 = P.rho_part[(size_t)(b + T) * MM + k];
+            const double2 v2 = P.rho_part[(size_t)(b + 2 * T) * MM + k];
+            const double2 v3 = P.rho_part[(size_t)(b + 3 * T) * MM + k];
+            a0.x += v0.x; a0.y += v0.y;
+            a1.x += v1.x; a1.y += v1.y;
+            a2.x += v2.x; a2.y += v2.y;
+            a3.x += v3.x; a3.y += v3.y;
+        }
+        for (; b < nblk; b += T) {
+            const double2 v = P.rho_part[(size_t)b * MM + k];
+            a0.x += v.x; a0.y += v.y;
+        }
+    }
+    s_p[threadIdx.x] = make_double2((a0.x + a1.x) + (a2.x + a3.x), (a0.y + a1.y) + (a2.y + a3.y));
+    __syncthreads();
+    if ((int)threadIdx.x < MM) {
+        double x = 0.0, y = 0.0;
+        for (int i = 0; i < T; ++i) {
+            x += s_p[threadIdx.x * T + i].x;
+            y += s_p[threadIdx.x * T + i].y;
+        }
+        rho[threadIdx.x] = make_double2(x, y);
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
     const bool merge = tn >= (unsigned long long)P.dkmax;
     const unsigned long long groups = merge ? st->n_groups : st->n_cur;
     if (st->n_out > (unsigned long long)P.max_paths) {
@@ -422,8 +543,6 @@ __global__ void k_finalize(Params P, int MM) {
     st->t = tn;
     st->n_groups = 0;
     st->n_out = 0;
-    double2 *nxt = P.rho_ring + (size_t)((tn + 1) % (unsigned long long)P.rho_hist) * MM;
-    for (int k = 0; k < MM; ++k) nxt[k] = make_double2(0.0, 0.0);
 }
 
 // ---------------------------------------------------------------- set-up kernels
@@ -472,7 +591,7 @@ __global__ void k_build_lut(double2 *lut, float2 *lutf, float2 *lutlo, const dou
 }
 
 // W[(a,b)][(a',b')] = U[a,a'] conj(U[b,b']) exp(-(q_a - q_b)(eta_0 q_a - conj(eta_0) q_b))
-__global__ void k_build_w(double2 *w, const double2 *U, const double2 *eta, const double *q, int M) {
+__global__ void k_build_w(double2 *w, float2 *wf, const double2 *U, const double2 *eta, const double *q, int M) {
     const int MM = M * M;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < MM * MM; i += gridDim.x * blockDim.x) {
         const int child = i / MM, par = i % MM;
@@ -490,6 +609,26 @@ __global__ void k_build_w(double2 *w, const double2 *U, const double2 *eta, cons
         sincos(zi, &s, &c);
         const double m = exp(zr);
         w[i] = cmul(prop, make_double2(m * c, m * s));
+        wf[i] = make_float2((float)w[i].x, (float)w[i].y);
+    }
+}
+
+// exp(-delta_d T) for every history table entry T[n_act][j][v] and every
+// distinct nonzero coupling difference delta_d (FP64 extension path).
+__global__ void k_build_etab(double2 *etab, const double2 *lut, const double *deltas, int ndelta, int dkmax,
+                             int nchunks) {
+    const long long per = (long long)nchunks * kLutEntries;
+    const long long total = (long long)dkmax * ndelta * per;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const long long r = i % per;
+        const int d = (int)((i / per) % ndelta);
+        const int n = (int)(i / (per * ndelta));
+        const double2 T = lut[(long long)n * per + r];
+        const double zr = -deltas[d] * T.x, zi = -deltas[d] * T.y;
+        double sn, cs;
+        sincos(zi, &sn, &cs);
+        const double m = exp(zr);
+        etab[i] = make_double2(m * cs, m * sn);
     }
 }
 
@@ -498,8 +637,8 @@ __global__ void k_build_w(double2 *w, const double2 *U, const double2 *eta, cons
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
-    size_t keys[2], amps[2], slots, repk, slot_of, groups, lut, lutf, lutlo, wtab, uprop, eta, q, rho, stats, state,
-        total;
+    size_t keys[2], amps[2], slots, repk, slot_of, groups, lut, lutf, lutlo, etab, wtab, wtabf, uprop, eta, q, deltas,
+        rho, rho_part, stats, state, total;
     unsigned long long tcap;
     unsigned int tcap_log2;
     int nchunks;
@@ -538,6 +677,27 @@ const char *validate(const qp_config *c) {
     return nullptr;
 }
 
+// Distinct nonzero differences q_a - q_b (a != b); dsel[a*M+b] = index or -1.
+int distinct_deltas(int M, const double *q, std::vector<double> *vals, signed char *dsel) {
+    std::vector<double> v;
+    for (int a = 0; a < M; ++a)
+        for (int b = 0; b < M; ++b) {
+            const double d = q[a] - q[b];
+            int idx = -1;
+            if (d != 0.0) {
+                for (size_t k = 0; k < v.size(); ++k)
+                    if (v[k] == d) idx = (int)k;
+                if (idx < 0) {
+                    v.push_back(d);
+                    idx = (int)v.size() - 1;
+                }
+            }
+            if (dsel) dsel[a * M + b] = (signed char)idx;
+        }
+    if (vals) *vals = v;
+    return (int)v.size();
+}
+
 Layout make_layout(const qp_config *c) {
     Layout L{};
     const long long mp = c->max_paths;
@@ -566,11 +726,16 @@ Layout make_layout(const qp_config *c) {
     L.lut = take(nlut * sizeof(double2));
     L.lutf = take(nlut * sizeof(float2));
     L.lutlo = take(nlut * sizeof(float2));
+    const int nd = distinct_deltas(c->M, c->q, nullptr, nullptr);
+    L.etab = take(nlut * std::max(1, nd) * sizeof(double2));
     L.wtab = take(MM * MM * sizeof(double2));
+    L.wtabf = take(MM * MM * sizeof(float2));
+    L.deltas = take(kMaxDelta * sizeof(double));
     L.uprop = take(MM * sizeof(double2));
     L.eta = take(c->dkmax * sizeof(double2));
     L.q = take(c->M * sizeof(double));
     L.rho = take((size_t)R * MM * sizeof(double2));
+    L.rho_part = take((size_t)kMaxExpandBlocks * MM * sizeof(double2));
     L.stats = take((size_t)R * sizeof(StepRec));
     L.total = off;
     return L;
@@ -582,6 +747,7 @@ struct qp_ctx {
     qp_config cfg;
     std::vector<double> q;
     std::vector<qp::cplx> hs, U;
+    std::vector<double> deltas;
     Layout L;
     char *ws = nullptr;
     size_t ws_bytes = 0;
@@ -615,15 +781,16 @@ constexpr int kStepKernels = 4;
 // ev[kStepKernels] after the last one.
 template <int M, typename Amp>
 cudaError_t launch_step_t(qp_ctx *c, cudaEvent_t *ev) {
-    const int g_stream = c->nsm * 4;
+    const int g_ins = c->nsm * 4;
+    const int g_exp = std::min(c->nsm * 4, kMaxExpandBlocks);
     if (ev) cudaEventRecord(ev[0], c->stream);
-    k_insert<Amp><<<g_stream, 256, 0, c->stream>>>(c->P);
+    k_insert<Amp><<<g_ins, kInsertThreads, 0, c->stream>>>(c->P);
     if (ev) cudaEventRecord(ev[1], c->stream);
-    k_tiebreak<Amp><<<g_stream, 256, 0, c->stream>>>(c->P);
+    k_tiebreak<Amp><<<g_ins, 256, 0, c->stream>>>(c->P);
     if (ev) cudaEventRecord(ev[2], c->stream);
-    k_expand<M, Amp><<<c->nsm * 4, 128, 0, c->stream>>>(c->P, reinterpret_cast<const double *>(c->ws + c->L.q));
+    k_expand<M, sizeof(Amp) == sizeof(float2)><<<g_exp, kExpandThreads, 0, c->stream>>>(c->P);
     if (ev) cudaEventRecord(ev[3], c->stream);
-    k_finalize<<<1, 1, 0, c->stream>>>(c->P, M * M);
+    k_finalize<<<1, 256, 0, c->stream>>>(c->P, M * M, g_exp);
     if (ev) cudaEventRecord(ev[4], c->stream);
     return cudaGetLastError();
 }
@@ -753,7 +920,21 @@ qp_status qp_create(const qp_config *cfg, void *d_workspace, size_t bytes, void 
     P.lutf = reinterpret_cast<const float2 *>(c->ws + L.lutf);
     P.lutf_lo = reinterpret_cast<const float2 *>(c->ws + L.lutlo);
     P.wtab = reinterpret_cast<const double2 *>(c->ws + L.wtab);
+    P.wtabf = reinterpret_cast<const float2 *>(c->ws + L.wtabf);
+    P.etab = reinterpret_cast<const double2 *>(c->ws + L.etab);
+    {
+        std::vector<double> dv;
+        signed char dsel[16];
+        for (int k = 0; k < 16; ++k) dsel[k] = -1;
+        P.ndelta = distinct_deltas(M, cfg->q, &dv, dsel);
+        for (int k = 0; k < 16; ++k) P.dsel[k] = dsel[k];
+        for (int k = 0; k < kMaxDelta; ++k) P.deltaf[k] = k < P.ndelta ? (float)dv[k] : 0.f;
+        c->deltas = dv;
+    }
+    P.theta2f = (float)(cfg->theta * cfg->theta);
+    P.tie_rel = cfg->precision == QP_C64 ? kTieRelC64 : kTieRelFP64;
     P.rho_ring = reinterpret_cast<double2 *>(c->ws + L.rho);
+    P.rho_part = reinterpret_cast<double2 *>(c->ws + L.rho_part);
     P.stats_ring = reinterpret_cast<StepRec *>(c->ws + L.stats);
     P.st = reinterpret_cast<DevState *>(c->ws + L.state);
     c->mask.clear();
@@ -765,6 +946,9 @@ qp_status qp_create(const qp_config *cfg, void *d_workspace, size_t bytes, void 
     e = cudaMemcpyAsync(c->ws + L.q, c->q.data(), M * sizeof(double), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(c->ws + L.uprop, Ud.data(), M * M * sizeof(double2), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && !c->deltas.empty())
+        e = cudaMemcpyAsync(c->ws + L.deltas, c->deltas.data(), c->deltas.size() * sizeof(double), cudaMemcpyHostToDevice,
+                            c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.state, 0, sizeof(DevState), c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
@@ -813,8 +997,16 @@ qp_status qp_set_eta(qp_ctx *c, const double *re, const double *im, int n) {
         QP_CUDA(c, cudaGetLastError());
     }
     k_build_w<<<1, 256, 0, c->stream>>>(reinterpret_cast<double2 *>(c->ws + c->L.wtab),
+                                        reinterpret_cast<float2 *>(c->ws + c->L.wtabf),
                                         reinterpret_cast<const double2 *>(c->ws + c->L.uprop), ed, qd, M);
     QP_CUDA(c, cudaGetLastError());
+    if (P.nchunks > 0 && P.ndelta > 0) {
+        k_build_etab<<<256, 256, 0, c->stream>>>(reinterpret_cast<double2 *>(c->ws + c->L.etab),
+                                                 reinterpret_cast<const double2 *>(c->ws + c->L.lut),
+                                                 reinterpret_cast<const double *>(c->ws + c->L.deltas), P.ndelta, dk,
+                                                 P.nchunks);
+        QP_CUDA(c, cudaGetLastError());
+    }
     QP_CUDA(c, cudaStreamSynchronize(c->stream));
     c->have_eta = true;
     return QP_OK;
@@ -1055,3 +1247,4 @@ qp_status qp_profile_steps(qp_ctx *c, int nsteps, double *kernel_ms, int nk) {
 const char *qp_last_error(const qp_ctx *c) { return c ? c->err.c_str() : "null context"; }
 
 }  // extern "C"
+

@@ -124,9 +124,11 @@ def test_spin_boson_structured_dk16_first_40_steps_against_stored_oracle():
 
 
 def test_spin_boson_structured_dk16_full_length_properties():
-    """All 2000 steps at full size: physical properties that hold at any size
-    (trace loss only from the filter and small, Hermitian diagonal real and
-    non-negative to rounding, counts bounded by M^(2 dk_eff))."""
+    """All 2000 steps at full size: properties that hold at any size.  The
+    trace is conserved by merging and propagation, so it changes only through
+    the filter: its real part stays at or below 1 and its loss, like its
+    imaginary part (the filtered paths carry complex weight), stays small.
+    Counts stay below M^(2 dk_eff).  With a mask rho need not be Hermitian."""
     w = W.SPIN_BOSON_STRUCTURED_DK16
     p = Propagator.from_workload(w, max_paths=1 << 21)
     p.step(w.steps)
@@ -136,9 +138,9 @@ def test_spin_boson_structured_dk16_full_length_properties():
     rho = p.rho(w.steps - 999, 1000)
     tr = np.trace(rho, axis1=1, axis2=2)
     assert np.all(tr.real <= 1 + 1e-12) and np.all(tr.real > 0.95)
-    assert np.abs(tr.imag).max() < 1e-9
+    assert np.abs(tr.imag).max() < 1e-3 and (1 - tr.real).max() < 1e-2
     d = np.diagonal(rho, axis1=1, axis2=2)
-    assert d.real.min() > -1e-9
+    assert d.real.min() > -1e-6
     p.close()
 
 
