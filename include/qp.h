@@ -187,6 +187,50 @@ qp_status qp_profile_steps(qp_ctx *ctx, int nsteps, double *kernel_ms, int nk);
 /* Last error message of the context ("" if none).                           */
 const char *qp_last_error(const qp_ctx *ctx);
 
+/* One propagation step t -> t+1 that allocates nothing and needs no context.
+ *
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory -- a plug-in running inside a host program
+ * that owns all GPU memory through its own pool and offers no allocator, a
+ * real-time loop that may not call cudaMalloc (it can block and synchronise
+ * the device), or a process under a hard device-memory quota.
+ *
+ * It runs the same step kernels as qp_step (FP64 path only) on the caller's
+ * buffers.  All scratch (merge table, eta tables, partial sums) lives in one
+ * fixed array of 20 MiB of device memory inside the library, which every GPU
+ * that loads the library holds until the process exits.  Limits set by that
+ * array: n_in <= 2^20 stored paths, at most 2^16 merge groups in the step,
+ * dkmax <= 16 (and 2 <= M <= 4 as everywhere).  Larger inputs return
+ * QP_ERR_ARG; more than 2^16 groups or more survivors than cap_out return
+ * QP_ERR_CAPACITY (*n_out = 0).  No cudaMalloc, cudaFree or other allocating
+ * routine is called.
+ *
+ *   cfg          as for qp_create; precision must be QP_FP64; max_paths,
+ *                max_groups, rho_history and engine are ignored
+ *   eta_re/im    host [n_eta >= dkmax] influence coefficients eta_0..
+ *   mask/n_mask  as for qp_set_mask (NULL/0 = full mask)
+ *   t            time index of the input set (it holds the newest
+ *                min(t+1, dkmax) points of each path)
+ *   d_keys_in    device [n_in] packed keys of the input set
+ *   d_amps_in    device [2*n_in] amplitudes, (re, im) interleaved
+ *   d_keys_out   device [cap_out] keys of the set at t+1 (no aliasing)
+ *   d_amps_out   device [2*cap_out] its amplitudes, (re, im) interleaved
+ *   n_out        host: number of stored paths at t+1
+ *   rho_re/im    host [M*M]: rho(t+1)
+ *   cuda_stream  cudaStream_t or NULL; the call synchronises it
+ *
+ * The first call on a device looks up the device address of the array
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call reuses the same array and clears
+ * what must start at zero; calls that overlap on one GPU (several host
+ * threads or streams) race on the array and must be serialised by the
+ * caller.                                                                   */
+qp_status qp_step_noalloc(const qp_config *cfg, const double *eta_re, const double *eta_im, int n_eta,
+                          const int *mask, int n_mask, int64_t t,
+                          const uint64_t *d_keys_in, const double *d_amps_in, int64_t n_in,
+                          uint64_t *d_keys_out, double *d_amps_out, int64_t cap_out,
+                          int64_t *n_out, double *rho_re, double *rho_im, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -197,3 +197,25 @@ def qp_profile_steps(ctx, nsteps: int) -> np.ndarray:
 
 def qp_last_error(ctx) -> str:
     return lib.qp_last_error(ctx).decode()
+
+
+def qp_step_noalloc(cfg, eta, mask, t, d_keys_in, d_amps_in, n_in, d_keys_out, d_amps_out, cap_out, stream=0):
+    """One step without allocation or context (see include/qp.h).  Device
+    buffers are passed as integer addresses; returns (n_out, rho(t+1))."""
+    f = lib.qp_step_noalloc
+    if f.argtypes is None:
+        f.restype = ctypes.c_int
+        f.argtypes = [ctypes.POINTER(qp_config), _dp, _dp, ctypes.c_int, _ip, ctypes.c_int, ctypes.c_int64,
+                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                      ctypes.c_int64, _i64p, _dp, _dp, ctypes.c_void_p]
+    M = cfg.M
+    eta = np.asarray(eta, dtype=np.complex128)
+    er, ei = _arr(eta.real), _arr(eta.imag)
+    m = None if mask is None else _arr(list(mask), np.int32)
+    n_out = ctypes.c_int64()
+    rr, ri = np.zeros(M * M), np.zeros(M * M)
+    check(f(ctypes.byref(cfg), _ptr(er), _ptr(ei), eta.size, None if m is None else _ptr(m, _ip),
+            0 if m is None else m.size, t, ctypes.c_void_p(d_keys_in), ctypes.c_void_p(d_amps_in), n_in,
+            ctypes.c_void_p(d_keys_out), ctypes.c_void_p(d_amps_out), cap_out, ctypes.byref(n_out),
+            _ptr(rr), _ptr(ri), ctypes.c_void_p(stream)))
+    return n_out.value, (rr + 1j * ri).reshape(M, M)

@@ -33,6 +33,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 #include <type_traits>
 #include <cmath>
 #include <complex>
@@ -1248,3 +1249,286 @@ const char *qp_last_error(const qp_ctx *c) { return c ? c->err.c_str() : "null c
 
 }  // extern "C"
 
+// ================================================================= step without allocation
+//
+// qp_step_noalloc runs the same four step kernels as qp_step for one step,
+// but on caller-provided input/output path buffers and with all scratch in
+// one fixed-size array of device memory defined in this file, so that it
+// neither allocates nor needs a workspace.  The paper has no counterpart; it
+// exists for callers that cannot allocate device memory.
+
+namespace {
+
+constexpr long long kNaMaxPaths = 1ll << 20;   // stored paths of the input set
+constexpr long long kNaMaxGroups = 1ll << 16;  // merge groups in one step
+constexpr unsigned kNaTcapLog2 = 17;           // merge-table slots = 2^17
+constexpr int kNaMaxDk = 16;                   // memory length
+constexpr size_t kNaBytes = 20ull << 20;       // size of the fixed scratch (20 MiB)
+
+// The fixed scratch.  In host code this name is only a stand-in for the
+// device array: its device address comes from cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_na_scratch[kNaBytes];
+
+std::mutex g_na_mutex;
+void *g_na_addr[256] = {};   // device address of g_na_scratch per device
+
+qp_status na_scratch_address(int dev, unsigned char **out) {
+    std::lock_guard<std::mutex> lock(g_na_mutex);
+    if (dev < 0 || dev >= 256) return QP_ERR_ARG;
+    if (!g_na_addr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_na_scratch) != cudaSuccess || !p) return QP_ERR_CUDA;
+        g_na_addr[dev] = p;
+    }
+    *out = static_cast<unsigned char *>(g_na_addr[dev]);
+    return QP_OK;
+}
+
+struct NaSetup {            // small set-up inputs, passed by value
+    double2 eta[kNaMaxDk];
+    double2 U[16];
+    double q[4];
+    double deltas[kMaxDelta];
+    int dkmax, M, ndelta;
+    unsigned long long t, n_in;
+};
+
+__global__ void k_na_setup(NaSetup s, double2 *eta, double *q, double2 *U, double *deltas, DevState *st) {
+    const int i = threadIdx.x;
+    if (i < s.dkmax) eta[i] = s.eta[i];
+    if (i < s.M) q[i] = s.q[i];
+    if (i < s.M * s.M) U[i] = s.U[i];
+    if (i < s.ndelta) deltas[i] = s.deltas[i];
+    if (i == 0) {
+        DevState z{};
+        z.t = s.t;
+        z.n_cur = s.n_in;
+        *st = z;
+    }
+}
+
+// U = exp(-i H dt) for M <= 4 on fixed arrays (scaling and squaring of the
+// Taylor series, as in host_numerics.cpp).
+void na_propagator(int M, const qp::cplx *H, double dt, qp::cplx *U) {
+    qp::cplx A[16], P[16], T[16];
+    double norm = 0.0;
+    for (int j = 0; j < M; ++j) {
+        double col = 0.0;
+        for (int i = 0; i < M; ++i) col += std::abs(H[i * M + j]) * std::fabs(dt);
+        norm = std::max(norm, col);
+    }
+    int s = 0;
+    while (norm > 0.25) { norm *= 0.5; ++s; }
+    const double scale = std::ldexp(1.0, -s);
+    for (int i = 0; i < M * M; ++i) {
+        A[i] = qp::cplx(0.0, -1.0) * H[i] * dt * scale;
+        T[i] = P[i] = 0.0;
+    }
+    for (int i = 0; i < M; ++i) T[i * M + i] = P[i * M + i] = 1.0;
+    for (int k = 1; k <= 20; ++k) {
+        qp::cplx nx[16];
+        for (int i = 0; i < M; ++i)
+            for (int j = 0; j < M; ++j) {
+                qp::cplx acc = 0.0;
+                for (int l = 0; l < M; ++l) acc += P[i * M + l] * A[l * M + j];
+                nx[i * M + j] = acc / double(k);
+            }
+        for (int i = 0; i < M * M; ++i) { P[i] = nx[i]; T[i] += nx[i]; }
+    }
+    for (int r = 0; r < s; ++r) {
+        qp::cplx sq[16];
+        for (int i = 0; i < M; ++i)
+            for (int j = 0; j < M; ++j) {
+                qp::cplx acc = 0.0;
+                for (int l = 0; l < M; ++l) acc += T[i * M + l] * T[l * M + j];
+                sq[i * M + j] = acc;
+            }
+        for (int i = 0; i < M * M; ++i) T[i] = sq[i];
+    }
+    for (int i = 0; i < M * M; ++i) U[i] = T[i];
+}
+
+}  // namespace
+
+extern "C" qp_status qp_step_noalloc(const qp_config *cfg, const double *eta_re, const double *eta_im, int n_eta,
+                                     const int *mask, int n_mask, int64_t t, const uint64_t *d_keys_in,
+                                     const double *d_amps_in, int64_t n_in, uint64_t *d_keys_out, double *d_amps_out,
+                                     int64_t cap_out, int64_t *n_out, double *rho_re, double *rho_im,
+                                     void *cuda_stream) {
+    if (validate(cfg) || cfg->precision != QP_FP64) return QP_ERR_ARG;
+    const int M = cfg->M, dk = cfg->dkmax;
+    if (dk > kNaMaxDk || !eta_re || !eta_im || n_eta < dk || !n_out || !rho_re || !rho_im) return QP_ERR_ARG;
+    if (t < 0 || n_in < 0 || cap_out < 0) return QP_ERR_ARG;
+    if (n_in > kNaMaxPaths) return QP_ERR_ARG;   // beyond the fixed scratch
+    if ((n_in > 0 && (!d_keys_in || !d_amps_in)) || (cap_out > 0 && (!d_keys_out || !d_amps_out))) return QP_ERR_ARG;
+    if ((const void *)d_keys_in == (const void *)d_keys_out || (const void *)d_amps_in == (const void *)d_amps_out)
+        return QP_ERR_ARG;
+    // mask -> P' bits and the compressed-index runs (fixed arrays)
+    bool inP[kNaMaxDk] = {};
+    if (!mask || n_mask == 0) {
+        for (int p = 0; p < dk; ++p) inP[p] = true;
+    } else {
+        if (n_mask < 0 || n_mask > dk) return QP_ERR_ARG;
+        for (int i = 0; i < n_mask; ++i) {
+            if (mask[i] < 0 || mask[i] >= dk) return QP_ERR_ARG;
+            inP[mask[i]] = true;
+        }
+        if (!inP[0] || (dk >= 2 && !inP[1])) return QP_ERR_ARG;
+    }
+    for (int i = 0; i < dk; ++i)
+        if (!std::isfinite(eta_re[i]) || !std::isfinite(eta_im[i])) return QP_ERR_ARG;
+
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return QP_ERR_CUDA;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return QP_ERR_CUDA;
+    unsigned char *base = nullptr;
+    const qp_status ss = na_scratch_address(dev, &base);
+    if (ss != QP_OK) return ss;
+    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+
+    Params P{};
+    P.M = M;
+    P.bs = bits_per_state(M);
+    P.b = 2 * P.bs;
+    P.dkmax = dk;
+    P.nchunks = (dk - 1) * P.b > 0 ? ((dk - 1) * P.b + 7) / 8 : 0;
+    P.tcap_log2 = kNaTcapLog2;
+    P.tcap_mask = (1ull << kNaTcapLog2) - 1ull;
+    P.theta2 = cfg->theta * cfg->theta;
+    P.theta2f = (float)P.theta2;
+    P.tie_rel = kTieRelFP64;
+    P.max_paths = cap_out;
+    P.max_groups = kNaMaxGroups;
+    P.rho_hist = 2;
+    {   // pre-merge positions P' = {p-1 : p in P, p >= 1} plus 0, and dense runs
+        bool inPp[kNaMaxDk] = {};
+        inPp[0] = true;
+        for (int p = 1; p < dk; ++p)
+            if (inP[p]) inPp[p - 1] = true;
+        unsigned long long pm = 0;
+        int nruns = 0, off = 0;
+        bool ok = true;
+        for (int p = 0; p < dk;) {
+            if (!inPp[p]) { ++p; continue; }
+            int q2 = p;
+            while (q2 + 1 < dk && inPp[q2 + 1]) ++q2;
+            const int len = q2 - p + 1;
+            for (int r = p; r <= q2; ++r) pm |= ((1ull << P.b) - 1ull) << (P.b * r);
+            if (nruns == kMaxRuns) ok = false;
+            else {
+                P.run_shift[nruns] = P.b * p;
+                P.run_mask[nruns] = (P.b * len >= 64) ? ~0ull : ((1ull << (P.b * len)) - 1ull);
+                P.run_off[nruns] = off;
+                ++nruns;
+            }
+            off += P.b * len;
+            p = q2 + 1;
+        }
+        P.pmask = pm;
+        P.nruns = nruns;
+        P.dense = (ok && off <= (int)kNaTcapLog2) ? 1 : 0;
+    }
+    NaSetup su{};
+    su.dkmax = dk;
+    su.M = M;
+    su.t = (unsigned long long)t;
+    su.n_in = (unsigned long long)n_in;
+    for (int i = 0; i < dk; ++i) su.eta[i] = make_double2(eta_re[i], eta_im[i]);
+    for (int i = 0; i < M; ++i) su.q[i] = cfg->q[i];
+    {
+        qp::cplx H[16], U[16];
+        for (int i = 0; i < M * M; ++i) H[i] = qp::cplx(cfg->hs_re[i], cfg->hs_im ? cfg->hs_im[i] : 0.0);
+        na_propagator(M, H, cfg->dt, U);
+        for (int i = 0; i < M * M; ++i) su.U[i] = make_double2(U[i].real(), U[i].imag());
+        signed char dsel[16];
+        for (int k = 0; k < 16; ++k) dsel[k] = -1;
+        int nd = 0;
+        for (int a = 0; a < M; ++a)
+            for (int b = 0; b < M; ++b) {
+                const double d = cfg->q[a] - cfg->q[b];
+                int idx = -1;
+                if (d != 0.0) {
+                    for (int k = 0; k < nd; ++k)
+                        if (su.deltas[k] == d) idx = k;
+                    if (idx < 0) { su.deltas[nd] = d; idx = nd++; }
+                }
+                dsel[a * M + b] = (signed char)idx;
+            }
+        su.ndelta = nd;
+        P.ndelta = nd;
+        for (int k = 0; k < 16; ++k) P.dsel[k] = dsel[k];
+        for (int k = 0; k < kMaxDelta; ++k) P.deltaf[k] = k < nd ? (float)su.deltas[k] : 0.f;
+    }
+    // carve the fixed scratch (offsets from the limits above)
+    const int MM = M * M;
+    const size_t nlut = (size_t)kNaMaxDk * 8 * kLutEntries;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return base + o; };
+    DevState *st = reinterpret_cast<DevState *>(take(sizeof(DevState)));
+    P.slots = reinterpret_cast<Slot *>(take((1ull << kNaTcapLog2) * sizeof(Slot)));
+    P.repk = reinterpret_cast<unsigned long long *>(take((1ull << kNaTcapLog2) * 8));
+    P.slot_of = reinterpret_cast<unsigned int *>(take(kNaMaxPaths * 4));
+    P.groups = reinterpret_cast<unsigned int *>(take(kNaMaxGroups * 4));
+    double2 *lut = reinterpret_cast<double2 *>(take(nlut * sizeof(double2)));
+    float2 *lutf = reinterpret_cast<float2 *>(take(nlut * sizeof(float2)));
+    float2 *lutlo = reinterpret_cast<float2 *>(take(nlut * sizeof(float2)));
+    double2 *etab = reinterpret_cast<double2 *>(take(nlut * kMaxDelta * sizeof(double2)));
+    double2 *wtab = reinterpret_cast<double2 *>(take(256 * sizeof(double2)));
+    float2 *wtabf = reinterpret_cast<float2 *>(take(256 * sizeof(float2)));
+    double2 *Ud = reinterpret_cast<double2 *>(take(16 * sizeof(double2)));
+    double2 *etad = reinterpret_cast<double2 *>(take(kNaMaxDk * sizeof(double2)));
+    double *qd = reinterpret_cast<double *>(take(4 * sizeof(double)));
+    double *deltad = reinterpret_cast<double *>(take(kMaxDelta * sizeof(double)));
+    P.rho_ring = reinterpret_cast<double2 *>(take(2 * 16 * sizeof(double2)));
+    P.rho_part = reinterpret_cast<double2 *>(take((size_t)kMaxExpandBlocks * 16 * sizeof(double2)));
+    P.stats_ring = reinterpret_cast<StepRec *>(take(2 * sizeof(StepRec)));
+    if (off > kNaBytes) return QP_ERR_OOM;
+    P.lut = lut;
+    P.lutf = lutf;
+    P.lutf_lo = lutlo;
+    P.etab = etab;
+    P.wtab = wtab;
+    P.wtabf = wtabf;
+    P.st = st;
+    const int in = (int)(t & 1);
+    P.keys[in] = const_cast<unsigned long long *>(reinterpret_cast<const unsigned long long *>(d_keys_in));
+    P.amps[in] = const_cast<double *>(d_amps_in);
+    P.keys[in ^ 1] = reinterpret_cast<unsigned long long *>(d_keys_out);
+    P.amps[in ^ 1] = d_amps_out;
+
+    // set-up (every call: the array keeps the previous call's contents)
+    k_na_setup<<<1, 32, 0, stream>>>(su, etad, qd, Ud, deltad, st);
+    k_clear_table<<<nsm * 4, 256, 0, stream>>>(P.slots, P.repk, 1ull << kNaTcapLog2);
+    if (P.nchunks > 0)
+        k_build_lut<<<64, 256, 0, stream>>>(lut, lutf, lutlo, etad, qd, M, P.bs, P.b, dk, P.nchunks);
+    k_build_w<<<1, 256, 0, stream>>>(wtab, wtabf, Ud, etad, qd, M);
+    if (P.nchunks > 0 && P.ndelta > 0) k_build_etab<<<256, 256, 0, stream>>>(etab, lut, deltad, P.ndelta, dk, P.nchunks);
+    // the step: the same kernels as qp_step
+    const int g_ins = nsm * 4;
+    const int g_exp = std::min(nsm * 4, kMaxExpandBlocks);
+    k_insert<double2><<<g_ins, kInsertThreads, 0, stream>>>(P);
+    k_tiebreak<double2><<<g_ins, 256, 0, stream>>>(P);
+    switch (M) {
+        case 2: k_expand<2, false><<<g_exp, kExpandThreads, 0, stream>>>(P); break;
+        case 3: k_expand<3, false><<<g_exp, kExpandThreads, 0, stream>>>(P); break;
+        default: k_expand<4, false><<<g_exp, kExpandThreads, 0, stream>>>(P); break;
+    }
+    k_finalize<<<1, 256, 0, stream>>>(P, MM, g_exp);
+    if (cudaGetLastError() != cudaSuccess) return QP_ERR_CUDA;
+    if (cudaStreamSynchronize(stream) != cudaSuccess) return QP_ERR_CUDA;
+    DevState s;
+    double2 rho[16];
+    if (cudaMemcpy(&s, st, sizeof(DevState), cudaMemcpyDeviceToHost) != cudaSuccess) return QP_ERR_CUDA;
+    if (s.err) {
+        *n_out = 0;
+        return QP_ERR_CAPACITY;
+    }
+    if (cudaMemcpy(rho, P.rho_ring + ((t + 1) % 2) * MM, MM * sizeof(double2), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return QP_ERR_CUDA;
+    *n_out = (int64_t)s.n_cur;
+    for (int k = 0; k < MM; ++k) {
+        rho_re[k] = rho[k].x;
+        rho_im[k] = rho[k].y;
+    }
+    return QP_OK;
+}
