@@ -51,11 +51,13 @@ constexpr unsigned long long kEmpty = ~0ull;
 constexpr unsigned int kNoSlot = 0xffffffffu;
 constexpr int kMaxRuns = 8;
 constexpr int kMaxProbe = 64;
-constexpr unsigned int kErrPaths = 1u, kErrGroups = 2u, kErrProbe = 4u;
+constexpr unsigned int kErrPaths = 1u, kErrGroups = 2u, kErrProbe = 4u, kErrTimeout = 8u;
 constexpr int kLutEntries = 256;
 constexpr int kInsertThreads = 256;
 constexpr int kExpandThreads = 128;
 constexpr int kMaxExpandBlocks = 2048;
+constexpr int kPersistThreads = 256;
+constexpr long long kBarrierCycles = 4000000000ll;  // ~2 s at 2 GHz: a grid barrier gives up after this
 constexpr int kMaxDelta = 12;
 constexpr double kTieRelFP64 = 1e-12;  // weights equal to this relative width are ties (R4)
 constexpr double kTieRelC64 = 1e-5;    // same, at complex64 resolution
@@ -66,14 +68,18 @@ struct __align__(32) Slot {
     double sre, sim;           // FP64 group sum
 };
 
-struct __align__(64) DevState {
-    unsigned long long t;        // time index of the stored set Omega(t)
-    unsigned long long n_cur;    // stored paths in buffer (t & 1)
-    unsigned long long n_groups; // groups claimed in the current step
-    unsigned long long n_out;    // children appended in the current step
-    unsigned int err;            // error bits, sticky until qp_set_rho0
+struct __align__(128) DevState {
+    unsigned long long t;             // time index of the stored set Omega(t)
+    unsigned long long n_cur;         // stored paths in buffer (t & 1)
+    unsigned long long cnt_groups[3]; // step t' uses [t' % 3]: merge groups claimed
+    unsigned long long cnt_out[3];    // step t' uses [t' % 3]: survivors appended
+    unsigned int err;                 // error bits, sticky until qp_set_rho0
     unsigned int pad;
-    unsigned long long err_t;    // step at which the error was raised
+    unsigned long long err_t;         // step at which the error was raised
+    unsigned int bar_count;           // grid barrier of the persistent kernel: arrivals
+    unsigned int pad1[31];
+    unsigned int bar_gen;             // generation (own cache line)
+    unsigned int pad2[31];
 };
 
 struct StepRec { long long t, groups, extended, kept; };
@@ -117,9 +123,11 @@ struct Params {
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 
-__device__ __forceinline__ double2 load_amp(const double2 *p, unsigned long long i) { return p[i]; }
+// Path data and merge-table fields are written by other blocks of the same
+// persistent kernel, so they are read through L2 (ld.global.cg), never L1.
+__device__ __forceinline__ double2 load_amp(const double2 *p, unsigned long long i) { return __ldcg(p + i); }
 __device__ __forceinline__ double2 load_amp(const float2 *p, unsigned long long i) {
-    float2 v = p[i];
+    const float2 v = __ldcg(p + i);
     return make_double2(v.x, v.y);
 }
 
@@ -183,24 +191,23 @@ __device__ __forceinline__ Append block_append(unsigned cnt, unsigned long long 
 
 // ---------------------------------------------------------------- pre-merge
 
-template <typename Amp>
-__global__ void __launch_bounds__(kInsertThreads) k_insert(Params P) {
+// Pass 1 over the stored set Omega(t) (n paths): claim the group slot of the
+// masked key, add the amplitude into the group sum, raise the group maximum
+// of |amp|^2.  Newly claimed slots are appended to the group list.
+template <typename Amp, int NT>
+__device__ __forceinline__ void phase_insert(const Params &P, unsigned long long t, unsigned long long n,
+                                             unsigned long long *cnt_groups) {
     DevState *st = P.st;
-    if (st->err) return;
-    const unsigned long long t = st->t, tn = t + 1;
-    if (tn < (unsigned long long)P.dkmax) return;   // window not full: no merge
-    const unsigned long long n = st->n_cur;
     const unsigned long long *keys = P.keys[t & 1];
     const Amp *amps = static_cast<const Amp *>(P.amps[t & 1]);
-    const unsigned long long stride = (unsigned long long)gridDim.x * kInsertThreads;
-    for (unsigned long long base = blockIdx.x * (unsigned long long)kInsertThreads; base < n; base += stride) {
+    const unsigned long long stride = (unsigned long long)gridDim.x * NT;
+    for (unsigned long long base = blockIdx.x * (unsigned long long)NT; base < n; base += stride) {
         const unsigned long long i = base + threadIdx.x;
         bool claimed = false, found = false;
         unsigned long long h = 0;
-        double2 a = make_double2(0.0, 0.0);
         if (i < n) {
-            const unsigned long long key = keys[i];
-            a = load_amp(amps, i);
+            const unsigned long long key = __ldcg(keys + i);
+            const double2 a = load_amp(amps, i);
             const unsigned long long mk = key & P.pmask;
             h = table_index(P, mk);
             for (int probe = 0; probe < kMaxProbe; ++probe) {
@@ -224,7 +231,7 @@ __global__ void __launch_bounds__(kInsertThreads) k_insert(Params P) {
                 raise_err(st, kErrProbe);
             }
         }
-        const Append ap = block_append<kInsertThreads>(claimed ? 1u : 0u, &st->n_groups);
+        const Append ap = block_append<NT>(claimed ? 1u : 0u, cnt_groups);
         if (claimed) {
             const unsigned long long g = ap.base + ap.excl;
             if (g < (unsigned long long)P.max_groups) P.groups[g] = (unsigned int)h;
@@ -233,24 +240,39 @@ __global__ void __launch_bounds__(kInsertThreads) k_insert(Params P) {
     }
 }
 
+// Pass 2: paths whose |amp|^2 lies within the tie window of the group maximum
+// compete for the representative with atomicMin on the packed key.
+template <typename Amp, int NT>
+__device__ __forceinline__ void phase_tiebreak(const Params &P, unsigned long long t, unsigned long long n) {
+    const unsigned long long *keys = P.keys[t & 1];
+    const Amp *amps = static_cast<const Amp *>(P.amps[t & 1]);
+    const unsigned long long stride = (unsigned long long)gridDim.x * NT;
+    for (unsigned long long i = blockIdx.x * (unsigned long long)NT + threadIdx.x; i < n; i += stride) {
+        const unsigned int h = __ldcg(P.slot_of + i);
+        if (h == kNoSlot) continue;
+        const double2 a = load_amp(amps, i);
+        const double w2 = a.x * a.x + a.y * a.y;
+        const double wm = __longlong_as_double((long long)__ldcg(&P.slots[h].wmax));
+        if (w2 >= (1.0 - P.tie_rel) * wm) atomicMin(&P.repk[h], __ldcg(keys + i));
+    }
+}
+
 template <typename Amp>
-__global__ void __launch_bounds__(256) k_tiebreak(Params P) {
+__global__ void __launch_bounds__(kInsertThreads) k_insert(Params P) {
+    DevState *st = P.st;
+    if (st->err) return;
+    const unsigned long long t = st->t, tn = t + 1;
+    if (tn < (unsigned long long)P.dkmax) return;   // window not full: no merge
+    phase_insert<Amp, kInsertThreads>(P, t, st->n_cur, &st->cnt_groups[tn % 3]);
+}
+
+template <typename Amp>
+__global__ void __launch_bounds__(kInsertThreads) k_tiebreak(Params P) {
     DevState *st = P.st;
     if (st->err) return;
     const unsigned long long t = st->t, tn = t + 1;
     if (tn < (unsigned long long)P.dkmax) return;
-    const unsigned long long n = st->n_cur;
-    const unsigned long long *keys = P.keys[t & 1];
-    const Amp *amps = static_cast<const Amp *>(P.amps[t & 1]);
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n; i += stride) {
-        const unsigned int h = P.slot_of[i];
-        if (h == kNoSlot) continue;
-        const double2 a = load_amp(amps, i);
-        const double w2 = a.x * a.x + a.y * a.y;
-        const double wm = __longlong_as_double((long long)P.slots[h].wmax);
-        if (w2 >= (1.0 - P.tie_rel) * wm) atomicMin(&P.repk[h], keys[i]);
-    }
+    phase_tiebreak<Amp, kInsertThreads>(P, t, st->n_cur);
 }
 
 // ---------------------------------------------------------------- extension
@@ -378,17 +400,18 @@ struct Expander {
     }
 };
 
-template <int M, bool C64>
-__global__ void __launch_bounds__(kExpandThreads) k_expand(Params P) {
+// Extension of n groups (merge steps) or n stored paths (while the window
+// fills) to their children; survivors appended through *cnt_out; this
+// block's partial sum of rho(t+1) written to part[blockIdx.x].
+template <int M, bool C64, int NT>
+__device__ __forceinline__ void phase_expand(const Params &P, unsigned long long t, unsigned long long n, bool merge,
+                                             unsigned long long *cnt_out, double2 *part) {
     using X = Expander<M, C64>;
     using AmpT = typename X::AmpT;
     constexpr int MM = M * M;
-    constexpr int NW = kExpandThreads / 32;
+    constexpr int NW = NT / 32;
     DevState *st = P.st;
-    if (st->err) return;
-    const unsigned long long t = st->t, tn = t + 1;
-    const bool merge = tn >= (unsigned long long)P.dkmax;
-    const unsigned long long n = merge ? st->n_groups : st->n_cur;
+    const unsigned long long tn = t + 1;
     const int n_act = (int)min(tn, (unsigned long long)P.dkmax);
     const int L_child = (int)min(tn + 1, (unsigned long long)P.dkmax);
     const unsigned long long wmask = (P.b * L_child >= 64) ? ~0ull : ((1ull << (P.b * L_child)) - 1ull);
@@ -400,7 +423,7 @@ __global__ void __launch_bounds__(kExpandThreads) k_expand(Params P) {
     __shared__ double2 s_w[MM * MM];
     __shared__ float2 s_wf[MM * MM];
     __shared__ double2 s_r[NW][MM];
-    for (int i = threadIdx.x; i < MM * MM; i += blockDim.x) {
+    for (int i = threadIdx.x; i < MM * MM; i += NT) {
         s_w[i] = P.wtab[i];
         s_wf[i] = P.wtabf[i];
     }
@@ -413,8 +436,8 @@ __global__ void __launch_bounds__(kExpandThreads) k_expand(Params P) {
         rcmp[k].x = rcmp[k].y = 0;
     }
 
-    const unsigned long long stride = (unsigned long long)gridDim.x * kExpandThreads;
-    for (unsigned long long base = blockIdx.x * (unsigned long long)kExpandThreads; base < n; base += stride) {
+    const unsigned long long stride = (unsigned long long)gridDim.x * NT;
+    for (unsigned long long base = blockIdx.x * (unsigned long long)NT; base < n; base += stride) {
         const unsigned long long g = base + threadIdx.x;
         unsigned keepbits = 0;
         AmpT camp[MM];
@@ -422,9 +445,9 @@ __global__ void __launch_bounds__(kExpandThreads) k_expand(Params P) {
         if (g < n) {
             double2 S;
             if (merge) {
-                const unsigned int h = P.groups[g];
-                rep = P.repk[h];
-                S = make_double2(P.slots[h].sre, P.slots[h].sim);
+                const unsigned int h = __ldcg(P.groups + g);
+                rep = __ldcg(P.repk + h);
+                S = __ldcg(reinterpret_cast<const double2 *>(&P.slots[h].sre));
                 Slot fresh;
                 fresh.mk = kEmpty;
                 fresh.wmax = 0ull;
@@ -433,13 +456,13 @@ __global__ void __launch_bounds__(kExpandThreads) k_expand(Params P) {
                 P.slots[h] = fresh;
                 P.repk[h] = kEmpty;
             } else {
-                rep = keys_in[g];
+                rep = __ldcg(keys_in + g);
                 S = load_amp(amps_in, g);
             }
             keepbits = X::children(P, n_act, rep, S, s_w, s_wf, camp, racc, rcmp);
         }
         const unsigned cnt = __popc(keepbits);
-        const Append ap = block_append<kExpandThreads>(cnt, &st->n_out);
+        const Append ap = block_append<NT>(cnt, cnt_out);
         if (ap.total && ap.base + ap.total > (unsigned long long)P.max_paths) {
             if (threadIdx.x == 0) raise_err(st, kErrPaths);
         } else if (cnt) {
@@ -456,8 +479,7 @@ __global__ void __launch_bounds__(kExpandThreads) k_expand(Params P) {
             }
         }
     }
-    // rho(t): per-block partial sums (warp shuffles, then across warps); the
-    // finalize kernel adds the partials in block order (deterministic)
+    // this block's partial sum of rho(t+1): warp shuffles, then across warps
     const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < MM; ++k) {
@@ -476,46 +498,41 @@ __global__ void __launch_bounds__(kExpandThreads) k_expand(Params P) {
             x += s_r[w][threadIdx.x].x;
             y += s_r[w][threadIdx.x].y;
         }
-        P.rho_part[(size_t)blockIdx.x * MM + threadIdx.x] = make_double2(x, y);
+        part[(size_t)blockIdx.x * MM + threadIdx.x] = make_double2(x, y);
     }
+    __syncthreads();
 }
 
-// Step finalisation (one block): rho(t) from the expand blocks' partial sums
-// (one warp per element, fixed block order: deterministic), then counts,
-// statistics and the step index.
-__global__ void __launch_bounds__(256) k_finalize(Params P, int MM, int nblk) {
-    DevState *st = P.st;
-    const unsigned long long err = st->err;
-    if (err) {
-        if (threadIdx.x == 0) { st->n_groups = 0; st->n_out = 0; }
-        return;
-    }
-    const unsigned long long t = st->t, tn = t + 1;
+// One block: rho(tn) from the nblk partial sums in block order (deterministic)
+// and the step's statistics.  Thread 0 returns true.
+__device__ __forceinline__ void phase_finalize(const Params &P, unsigned long long tn, unsigned long long groups,
+                                               unsigned long long n_out, const double2 *part, int nblk, int MM) {
+    __shared__ double2 s_p[1024];
     double2 *rho = P.rho_ring + (size_t)(tn % (unsigned long long)P.rho_hist) * MM;
-    // T threads per element k; each sums a fixed stride of the partials with
-    // four independent accumulators so that the loads overlap
-    __shared__ double2 s_p[256];
-    const int T = (int)blockDim.x / MM;
+    // T threads per element k sum a fixed stride of the partials with four
+    // independent accumulators so that the loads overlap
+    const int T = min((int)blockDim.x, 1024) / MM;
     const int k = (int)threadIdx.x / T, sidx = (int)threadIdx.x % T;
     double2 a0 = make_double2(0.0, 0.0), a1 = a0, a2 = a0, a3 = a0;
-    if (k < MM) {
+    if (k < MM && threadIdx.x < 1024) {
         int b = sidx;
         for (; b + 3 * T < nblk; b += 4 * T) {
-            const double2 v0 = P.rho_part[(size_t)b * MM + k];
-            const double2 v1 = P.rho_part[(size_t)(b + T) * MM + k];
-            const double2 v2 = P.rho_part[(size_t)(b + 2 * T) * MM + k];
-            const double2 v3 = P.rho_part[(size_t)(b + 3 * T) * MM + k];
+            const double2 v0 = __ldcg(part + (size_t)b * MM + k);
+            const double2 v1 = __ldcg(part + (size_t)(b + T) * MM + k);
+            const double2 v2 = __ldcg(part + (size_t)(b + 2 * T) * MM + k);
+            const double2 v3 = __ldcg(part + (size_t)(b + 3 * T) * MM + k);
             a0.x += v0.x; a0.y += v0.y;
             a1.x += v1.x; a1.y += v1.y;
             a2.x += v2.x; a2.y += v2.y;
             a3.x += v3.x; a3.y += v3.y;
         }
         for (; b < nblk; b += T) {
-            const double2 v = P.rho_part[(size_t)b * MM + k];
+            const double2 v = __ldcg(part + (size_t)b * MM + k);
             a0.x += v.x; a0.y += v.y;
         }
     }
-    s_p[threadIdx.x] = make_double2((a0.x + a1.x) + (a2.x + a3.x), (a0.y + a1.y) + (a2.y + a3.y));
+    if (threadIdx.x < 1024)
+        s_p[threadIdx.x] = make_double2((a0.x + a1.x) + (a2.x + a3.x), (a0.y + a1.y) + (a2.y + a3.y));
     __syncthreads();
     if ((int)threadIdx.x < MM) {
         double x = 0.0, y = 0.0;
@@ -525,25 +542,136 @@ __global__ void __launch_bounds__(256) k_finalize(Params P, int MM, int nblk) {
         }
         rho[threadIdx.x] = make_double2(x, y);
     }
-    __syncthreads();
-    if (threadIdx.x != 0) return;
-    const bool merge = tn >= (unsigned long long)P.dkmax;
-    const unsigned long long groups = merge ? st->n_groups : st->n_cur;
-    if (st->n_out > (unsigned long long)P.max_paths) {
-        st->err |= kErrPaths;
-        st->err_t = tn;
-        return;
+    if (threadIdx.x == 0) {
+        StepRec r;
+        r.t = (long long)tn;
+        r.groups = (long long)groups;
+        r.extended = (long long)groups * MM;
+        r.kept = (long long)n_out;
+        P.stats_ring[tn % (unsigned long long)P.rho_hist] = r;
     }
-    StepRec r;
-    r.t = (long long)tn;
-    r.groups = (long long)groups;
-    r.extended = (long long)groups * MM;
-    r.kept = (long long)st->n_out;
-    P.stats_ring[tn % (unsigned long long)P.rho_hist] = r;
-    st->n_cur = st->n_out;
+    __syncthreads();
+}
+
+__device__ __forceinline__ double2 *rho_part_of(const Params &P, unsigned long long tn, int MM) {
+    return P.rho_part + (size_t)(tn & 1) * kMaxExpandBlocks * MM;
+}
+
+template <int M, bool C64>
+__global__ void __launch_bounds__(kExpandThreads) k_expand(Params P) {
+    DevState *st = P.st;
+    if (st->err) return;
+    const unsigned long long t = st->t, tn = t + 1;
+    const bool merge = tn >= (unsigned long long)P.dkmax;
+    const unsigned long long n = merge ? st->cnt_groups[tn % 3] : st->n_cur;
+    phase_expand<M, C64, kExpandThreads>(P, t, n, merge, &st->cnt_out[tn % 3], rho_part_of(P, tn, M * M));
+}
+
+// Step finalisation of the multi-kernel path (one block).
+__global__ void __launch_bounds__(256) k_finalize(Params P, int MM, int nblk) {
+    DevState *st = P.st;
+    if (st->err) return;
+    const unsigned long long t = st->t, tn = t + 1;
+    const bool merge = tn >= (unsigned long long)P.dkmax;
+    const unsigned long long groups = merge ? st->cnt_groups[tn % 3] : st->n_cur;
+    const unsigned long long n_out = st->cnt_out[tn % 3];
+    __syncthreads();
+    phase_finalize(P, tn, groups, n_out, rho_part_of(P, tn, MM), nblk, MM);
+    if (threadIdx.x != 0) return;
+    st->n_cur = n_out;
     st->t = tn;
-    st->n_groups = 0;
-    st->n_out = 0;
+    st->cnt_groups[(tn + 1) % 3] = 0;   // counters of the next step
+    st->cnt_out[(tn + 1) % 3] = 0;
+}
+
+// Grid-wide barrier of the persistent kernel (all blocks are co-resident: the
+// kernel is launched cooperatively).  The wait is bounded: after
+// kBarrierCycles, or as soon as another block has raised an error, the block
+// stops waiting and the timeout is recorded.  Returns the error bits.
+__device__ __forceinline__ unsigned grid_barrier(DevState *st) {
+    __shared__ unsigned s_err;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *vgen = &st->bar_gen;
+        volatile unsigned *verr = &st->err;
+        const unsigned g = *vgen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(&st->bar_count, 1u);
+        if (arrived == gridDim.x - 1) {
+            st->bar_count = 0;
+            __threadfence();
+            atomicAdd(&st->bar_gen, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (*vgen == g) {
+                if (*verr) break;
+                if (clock64() - t0 > kBarrierCycles) {
+                    atomicOr(&st->err, kErrTimeout);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        s_err = *verr;
+    }
+    __syncthreads();
+    return s_err;
+}
+
+// All steps of one qp_step call in one cooperative launch.  Per step: insert
+// | tiebreak | expand, separated by grid barriers (only expand while the
+// window fills).  Block 0 finalises step t' at the start of step t'+1 (and
+// the last step after the loop) from values every block already holds.
+// Counter sets rotate mod 3 so that no counter is reset while a block may
+// still read it.
+template <int M, bool C64>
+__global__ void __launch_bounds__(kPersistThreads) k_step_persistent(Params P, int nsteps) {
+    constexpr int MM = M * M;
+    using Amp = typename Expander<M, C64>::AmpT;
+    DevState *st = P.st;
+    const int nblk = (int)gridDim.x;
+    unsigned err = *(volatile unsigned *)&st->err;
+    unsigned long long t = st->t;
+    unsigned long long n_in = st->n_cur;
+    unsigned long long prev_groups = 0, prev_out = 0;
+    int done = 0;
+    for (int s = 0; s < nsteps && !err; ++s) {
+        const unsigned long long tn = t + 1;
+        const int cs = (int)(tn % 3);
+        const bool merge = tn >= (unsigned long long)P.dkmax;
+        if (blockIdx.x == 0) {
+            if (threadIdx.x == 0) {
+                st->cnt_groups[(tn + 1) % 3] = 0;   // last used two steps ago
+                st->cnt_out[(tn + 1) % 3] = 0;
+            }
+            if (s > 0) phase_finalize(P, t, prev_groups, prev_out, rho_part_of(P, t, MM), nblk, MM);
+        }
+        if (merge) {
+            phase_insert<Amp, kPersistThreads>(P, t, n_in, &st->cnt_groups[cs]);
+            err = grid_barrier(st);
+            if (err) break;
+            phase_tiebreak<Amp, kPersistThreads>(P, t, n_in);
+            err = grid_barrier(st);
+            if (err) break;
+        }
+        const unsigned long long ng = merge ? __ldcg(&st->cnt_groups[cs]) : n_in;
+        phase_expand<M, C64, kPersistThreads>(P, t, ng, merge, &st->cnt_out[cs], rho_part_of(P, tn, MM));
+        err = grid_barrier(st);
+        if (err) break;
+        prev_groups = ng;
+        prev_out = __ldcg(&st->cnt_out[cs]);
+        n_in = prev_out;
+        t = tn;
+        ++done;
+    }
+    if (blockIdx.x == 0) {
+        if (done > 0) phase_finalize(P, t, prev_groups, prev_out, rho_part_of(P, t, MM), nblk, MM);
+        if (threadIdx.x == 0 && done > 0) {
+            st->n_cur = n_in;
+            st->t = t;
+        }
+    }
 }
 
 // ---------------------------------------------------------------- set-up kernels
@@ -736,7 +864,7 @@ Layout make_layout(const qp_config *c) {
     L.eta = take(c->dkmax * sizeof(double2));
     L.q = take(c->M * sizeof(double));
     L.rho = take((size_t)R * MM * sizeof(double2));
-    L.rho_part = take((size_t)kMaxExpandBlocks * MM * sizeof(double2));
+    L.rho_part = take((size_t)2 * kMaxExpandBlocks * MM * sizeof(double2));   // by step parity
     L.stats = take((size_t)R * sizeof(StepRec));
     L.total = off;
     return L;
@@ -757,6 +885,8 @@ struct qp_ctx {
     Params P{};
     bool have_eta = false, have_state = false, failed = false;
     std::vector<int> mask;
+    int persist_grid = 0;              // blocks of the cooperative persistent kernel (0 = not usable)
+    bool use_persistent = true;
     cudaGraphExec_t graph = nullptr;
     bool graph_dirty = true;
     bool use_graph = true;
@@ -802,6 +932,40 @@ cudaError_t launch_step(qp_ctx *c, cudaEvent_t *ev = nullptr) {
         case 2: return c64 ? launch_step_t<2, float2>(c, ev) : launch_step_t<2, double2>(c, ev);
         case 3: return c64 ? launch_step_t<3, float2>(c, ev) : launch_step_t<3, double2>(c, ev);
         default: return c64 ? launch_step_t<4, float2>(c, ev) : launch_step_t<4, double2>(c, ev);
+    }
+}
+
+template <int M, bool C64>
+cudaError_t launch_persistent_t(qp_ctx *c, int nsteps) {
+    void *args[] = {(void *)&c->P, (void *)&nsteps};
+    return cudaLaunchCooperativeKernel((const void *)k_step_persistent<M, C64>, dim3(c->persist_grid),
+                                       dim3(kPersistThreads), args, 0, c->stream);
+}
+
+cudaError_t launch_persistent(qp_ctx *c, int nsteps) {
+    const bool c64 = c->cfg.precision == QP_C64;
+    switch (c->cfg.M) {
+        case 2: return c64 ? launch_persistent_t<2, true>(c, nsteps) : launch_persistent_t<2, false>(c, nsteps);
+        case 3: return c64 ? launch_persistent_t<3, true>(c, nsteps) : launch_persistent_t<3, false>(c, nsteps);
+        default: return c64 ? launch_persistent_t<4, true>(c, nsteps) : launch_persistent_t<4, false>(c, nsteps);
+    }
+}
+
+// Blocks of the persistent kernel: all must be co-resident (cooperative
+// launch), at most kMaxExpandBlocks (rho partial buffer).
+template <int M, bool C64>
+int persistent_grid_t(int nsm) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_persistent<M, C64>, kPersistThreads, 0) != cudaSuccess)
+        return 0;
+    return std::min(std::max(0, nb) * nsm, kMaxExpandBlocks);
+}
+
+int persistent_grid(int M, bool c64, int nsm) {
+    switch (M) {
+        case 2: return c64 ? persistent_grid_t<2, true>(nsm) : persistent_grid_t<2, false>(nsm);
+        case 3: return c64 ? persistent_grid_t<3, true>(nsm) : persistent_grid_t<3, false>(nsm);
+        default: return c64 ? persistent_grid_t<4, true>(nsm) : persistent_grid_t<4, false>(nsm);
     }
 }
 
@@ -896,6 +1060,18 @@ qp_status qp_create(const qp_config *cfg, void *d_workspace, size_t bytes, void 
     if (e != cudaSuccess) {
         delete c;
         return QP_ERR_CUDA;
+    }
+    {
+        int coop = 0;
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->device);
+        c->persist_grid = coop ? persistent_grid(M, cfg->precision == QP_C64, c->nsm) : 0;
+        if (const char *bps = getenv("QP_PERSIST_BLOCKS_PER_SM")) {   // launch-shape override (tuning)
+            const int want = atoi(bps) * c->nsm;
+            if (want > 0 && want < c->persist_grid) c->persist_grid = want;
+        }
+        // default: the CUDA graph of the four step kernels (faster than the
+        // persistent kernel's grid barriers when one step is launched at a time)
+        c->use_persistent = c->persist_grid > 0 && getenv("QP_PERSISTENT") != nullptr;
     }
     Params &P = c->P;
     P.M = M;
@@ -1088,6 +1264,11 @@ qp_status qp_step(qp_ctx *c, int nsteps) {
     if (!c->have_state) return fail(c, QP_ERR_STATE, "qp_set_rho0 must come before qp_step");
     if (c->failed) return fail(c, QP_ERR_STATE, "context holds a device error; call qp_set_rho0");
     if (nsteps == 0) return QP_OK;
+    if (c->use_persistent) {
+        const cudaError_t e = launch_persistent(c, nsteps);
+        if (e != cudaSuccess) return fail(c, QP_ERR_CUDA, std::string("persistent launch: ") + cudaGetErrorString(e));
+        return QP_OK;
+    }
     if (c->use_graph) {
         if (c->graph_dirty || !c->graph) {
             if (c->graph) {
@@ -1124,6 +1305,9 @@ static qp_status read_state(qp_ctx *c, DevState *s) {
         if (s->err & kErrPaths) what += " path buffer (max_paths)";
         if (s->err & kErrGroups) what += " merge groups (max_groups)";
         if (s->err & kErrProbe) what += " merge table probe limit";
+        if (s->err & kErrTimeout)
+            return fail(c, QP_ERR_TIMEOUT, "a grid barrier of the persistent step kernel timed out at step " +
+                                               std::to_string(s->t + 1));
         return fail(c, QP_ERR_CAPACITY, "capacity exceeded at step " + std::to_string(s->t + 1) + ":" + what);
     }
     return QP_OK;
@@ -1480,7 +1664,7 @@ extern "C" qp_status qp_step_noalloc(const qp_config *cfg, const double *eta_re,
     double *qd = reinterpret_cast<double *>(take(4 * sizeof(double)));
     double *deltad = reinterpret_cast<double *>(take(kMaxDelta * sizeof(double)));
     P.rho_ring = reinterpret_cast<double2 *>(take(2 * 16 * sizeof(double2)));
-    P.rho_part = reinterpret_cast<double2 *>(take((size_t)kMaxExpandBlocks * 16 * sizeof(double2)));
+    P.rho_part = reinterpret_cast<double2 *>(take((size_t)2 * kMaxExpandBlocks * 16 * sizeof(double2)));
     P.stats_ring = reinterpret_cast<StepRec *>(take(2 * sizeof(StepRec)));
     if (off > kNaBytes) return QP_ERR_OOM;
     P.lut = lut;
