@@ -217,6 +217,63 @@ def run_ours(args, rank, world, precision):
     return res
 
 
+def run_batched_sweep(n_inst=64, reps=3):
+    """The resonance sweep (n_inst instances of the 8-step model) as one
+    batched context in complex64, autotuned, each trajectory (all steps) one
+    timed qp_step call after an L2 flush; against the plain FP64 path running
+    the instances one after another.  Returns the summary object."""
+    import torch
+    from paper_2506_03127_gb300 import Propagator, batch_from_workloads
+
+    ws = W.resonance_sweep(n_inst)
+    w0 = ws[0]
+    T = w0.steps
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    p = batch_from_workloads(ws, precision="c64", max_paths=1 << 23, rho_history=max(4096, T + 1))
+    p.step(w0.dkmax + 2)
+    best, tune_ms = p.autotune(trial_steps=4, use_cache=False)
+    times = []
+    for _ in range(reps):
+        p.set_rho0(w0.rho0_array())
+        with torch.cuda.stream(p.stream):
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(p.stream)
+        p.step(T)
+        e1.record(p.stream)
+        p.sync()
+        times.append(e0.elapsed_time(e1))
+    ext = float(sum(r[2] for r in p.stats(1, T)))
+    rho_b = p.rho(0, T + 1)
+    counts = p.instance_counts(T)
+    p.close()
+    t_b = float(np.median(times))
+    # plain FP64 path, one instance at a time
+    t_s, ext_s, err = 0.0, 0.0, 0.0
+    for i, w in enumerate(ws):
+        q = Propagator.from_workload(w, precision="fp64", max_paths=1 << 18)
+        with torch.cuda.stream(q.stream):
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(q.stream)
+        q.step(T)
+        e1.record(q.stream)
+        q.sync()
+        t_s += e0.elapsed_time(e1)
+        ext_s += float(sum(r[2] for r in q.stats(1, T)))
+        err = max(err, float(np.abs(q.rho(0, T + 1) - rho_b[:, i]).max()))
+        q.close()
+    return {"workload": f"resonance_sweep{n_inst}", "instances": n_inst, "steps": T, "theta": w0.theta,
+            "value": ext / (t_b / 1e3), "unit": "paths/s", "ms_per_trajectory": t_b, "precision": "c64",
+            "launch": "one qp_step call for all steps (tuned: %s)" % ("persistent kernel" if best.mode else
+                                                                    "CUDA graphs of %d steps" % best.graph_steps),
+            "tuning": best.as_dict(), "l2": "flushed before each timed trajectory",
+            "kept_per_instance": {"min": int(counts.min()), "max": int(counts.max())},
+            "fp64_one_by_one": {"value": ext_s / (t_s / 1e3), "ms_total": t_s},
+            "speedup_vs_fp64_one_by_one": (ext / (t_b / 1e3)) / (ext_s / (t_s / 1e3)),
+            "rho_max_abs_err_vs_fp64": err}
+
+
 def cpu_baseline(w, steps_total=60, timed_from=None):
     """Oracle (FP64 CPU, as it stands) on a bounded sample of the workload:
     propagate from t = 0 and time the steps after the window is full."""
@@ -250,6 +307,7 @@ def main():
     ap.add_argument("--t0", type=int, default=T0_DEFAULT)
     ap.add_argument("--max-paths", type=int, default=1 << 21)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-sweep measurement")
     args = ap.parse_args()
     assert args.warmup >= 3, "at least 3 warm-up steps"
 
@@ -334,6 +392,8 @@ def main():
             "vs_fp64_gpu": {"fp64_value": fp64_value, "fp64_ms_per_step": ref["t_ms"] / args.steps,
                             "speedup": value / fp64_value, "rho_max_abs_err": rho_err,
                             "rho_err_steps": n, "fp64_roofline": ref["roof"], "fp64_e2e": ref["e2e"]}}
+    if not args.no_batched and world == 1:
+        line["batched_sweep"] = run_batched_sweep()
     if not args.no_cpu_baseline and world == 1:
         v, sample = cpu_baseline(W.SPIN_BOSON_STRUCTURED_DK16 if args.workload == "spin_boson_structured_dk16"
                                  else WORKLOADS[args.workload])

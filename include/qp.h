@@ -83,6 +83,12 @@ typedef struct {
     int64_t max_paths;     /* capacity of each stored-path buffer, entries          */
     int64_t max_groups;    /* capacity of the merge table, groups (0 = max_paths)   */
     int rho_history;       /* rho(t) slots kept on the device, ring (0 = 4096)      */
+    int n_inst;            /* independent instances propagated together (0 or 1 =
+                              one problem; at most 128).  All instances share M,
+                              q, H_S, dt, dkmax, mask and theta; each has its own
+                              eta (qp_set_eta_instance).  The instance index is
+                              stored above the path bits of the key, so
+                              b*dkmax + ceil(log2 n_inst) <= 64.               */
 } qp_config;
 
 /* Spectral density J(w) = (pi/2) ohmic_alpha w exp(-w/ohmic_wc)
@@ -102,6 +108,19 @@ typedef struct {
     int64_t extended;      /* children generated, groups * M^2               */
     int64_t kept;          /* children surviving the filter = stored paths   */
 } qp_step_stats;
+
+/* Launch shape and table size of the step (qp_set_tuning / qp_autotune). */
+enum { QP_LAUNCH_GRAPH = 0,        /* CUDA graph of the four step kernels        */
+       QP_LAUNCH_PERSISTENT = 1 }; /* one cooperative kernel for all steps of a
+                                      qp_step call, grid barriers between phases */
+typedef struct {
+    int mode;                  /* QP_LAUNCH_*                                     */
+    int insert_blocks_per_sm;  /* pre-merge kernels (graph mode)                 */
+    int expand_blocks_per_sm;  /* extension kernel (graph mode)                  */
+    int persistent_blocks;     /* grid of the persistent kernel                  */
+    int graph_steps;           /* steps captured per CUDA graph launch           */
+    int table_log2;            /* active merge-table slots = 2^table_log2        */
+} qp_tuning;
 
 typedef struct qp_ctx qp_ctx;
 
@@ -141,6 +160,10 @@ qp_status qp_eta_from_bath(const qp_bath *bath, double dt, int n, double *eta_re
  * device tables of the history sum and of propagator x new-point influence. */
 qp_status qp_set_eta(qp_ctx *ctx, const double *eta_re, const double *eta_im, int n);
 
+/* eta of one instance of a batched context (after qp_set_eta, which sets
+ * every instance).  inst in [0, n_inst).                                    */
+qp_status qp_set_eta_instance(qp_ctx *ctx, int inst, const double *eta_re, const double *eta_im, int n);
+
 /* MACGIC mask P: the window positions at time t (0 = newest) on which paths
  * must agree to merge (Sec. 2.1).  Must contain 0, and 1 when dkmax >= 2;
  * positions in [0, dkmax).  The pre-merge uses P' = {p-1 : p in P, p >= 1}
@@ -165,10 +188,15 @@ qp_status qp_sync(qp_ctx *ctx);
 qp_status qp_current(qp_ctx *ctx, int64_t *t, int64_t *n_paths);
 
 /* rho(t) for count consecutive steps t0 .. t0+count-1 (synchronises).  Each
- * step must be among the last rho_history steps.  re/im: [count*M*M].      */
+ * step must be among the last rho_history steps.  re/im:
+ * [count][n_inst][M*M] (n_inst = 1 for a single problem).                  */
 qp_status qp_read_rho(qp_ctx *ctx, int64_t t0, int count, double *rho_re, double *rho_im);
 
-/* Per-step path counts for steps t0 .. t0+count-1 (1 <= t, synchronises).   */
+/* Stored paths of each instance after step t: kept[n_inst] (synchronises). */
+qp_status qp_read_instance_counts(qp_ctx *ctx, int64_t t, int64_t *kept);
+
+/* Per-step path counts for steps t0 .. t0+count-1 (1 <= t, synchronises);
+ * totals over all instances.                                               */
 qp_status qp_read_stats(qp_ctx *ctx, int64_t t0, int count, qp_step_stats *out);
 
 /* Copy the stored path set Omega(t) to host arrays: keys[cap] packed keys,
@@ -183,6 +211,30 @@ qp_status qp_export_paths(qp_ctx *ctx, uint64_t *keys, double *amps, int64_t cap
  * insert, 1 merge tie-break, 2 extension/filter/rho, 3 step finalisation.
  * nk = length of kernel_ms (at most 4 entries are written).               */
 qp_status qp_profile_steps(qp_ctx *ctx, int nsteps, double *kernel_ms, int nk);
+
+/* Current launch shape and table size.                                      */
+qp_status qp_get_tuning(qp_ctx *ctx, qp_tuning *out);
+
+/* Set the launch shape and table size (validated against the device: the
+ * persistent grid must be co-resident, the table at most the workspace's).  */
+qp_status qp_set_tuning(qp_ctx *ctx, const qp_tuning *t);
+
+/* Autotuner: time trial_steps steps for each candidate launch shape and
+ * table size (graph mode with 2/4/8 blocks per SM for the pre-merge and
+ * extension kernels and, for hashed tables, smaller tables; persistent mode
+ * with 1/2/4 blocks per SM) and keep the fastest.  The propagation advances
+ * by (trial_steps + 1) steps per candidate.  Results are cached per problem
+ * bucket (M, dkmax, n_inst, precision, mask, filter on/off, log2 of the path
+ * count); with use_cache the cached choice is applied without trials
+ * (*best_ms_per_step = -1 then).  best / best_ms_per_step may be NULL.    */
+qp_status qp_autotune(qp_ctx *ctx, int trial_steps, int use_cache, qp_tuning *best, double *best_ms_per_step);
+
+/* Test hook for the bounded waits of the persistent kernel: corrupts the grid
+ * barrier's arrival count so that the next persistent launch cannot complete
+ * its first barrier; every block gives up after about two seconds, the step
+ * is not applied and the next synchronising call returns QP_ERR_TIMEOUT.
+ * qp_set_rho0 restores a usable context.                                    */
+qp_status qp_test_stall_barrier(qp_ctx *ctx);
 
 /* Last error message of the context ("" if none).                           */
 const char *qp_last_error(const qp_ctx *ctx);

@@ -12,7 +12,7 @@ import importlib
 
 import numpy as np
 
-__all__ = ["abi", "Propagator", "eta_from_bath"]
+__all__ = ["abi", "Propagator", "eta_from_bath", "batch_from_workloads"]
 
 
 def _abi():
@@ -36,17 +36,18 @@ class Propagator:
     """One propagation context: owns a device workspace tensor and a stream."""
 
     def __init__(self, M, dkmax, dt, q, hs, theta=0.0, precision="fp64", engine="auto",
-                 max_paths=1 << 20, max_groups=0, rho_history=4096, device=None, stream=None):
+                 max_paths=1 << 20, max_groups=0, rho_history=4096, device=None, stream=None, n_inst=1):
         import torch
         from . import abi
         if not torch.cuda.is_available():
             raise RuntimeError("Propagator needs a CUDA device")
         self.M = M
         self.dkmax = dkmax
+        self.n_inst = n_inst
         prec = {"fp64": abi.QP_FP64, "c64": abi.QP_C64}[precision]
         eng = {"auto": abi.QP_ENGINE_AUTO, "hash": abi.QP_ENGINE_HASH, "stream": abi.QP_ENGINE_STREAM}[engine]
         self._cfg, self._keep = abi.make_config(M, dkmax, dt, q, hs, theta, prec, eng, max_paths, max_groups,
-                                                rho_history)
+                                                rho_history, n_inst)
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
@@ -81,7 +82,26 @@ class Propagator:
         return _abi().qp_current(self.ctx)
 
     def rho(self, t0, count=1):
-        return _abi().qp_read_rho(self.ctx, t0, count, self.M)
+        """rho(t0..t0+count-1): (count, M, M), or (count, n_inst, M, M) for a batch."""
+        return _abi().qp_read_rho(self.ctx, t0, count, self.M, self.n_inst)
+
+    def set_eta_instance(self, inst, eta):
+        _abi().qp_set_eta_instance(self.ctx, inst, eta)
+
+    def instance_counts(self, t):
+        return _abi().qp_read_instance_counts(self.ctx, t, self.n_inst)
+
+    def tuning(self):
+        return _abi().qp_get_tuning(self.ctx)
+
+    def set_tuning(self, **kw):
+        t = _abi().qp_get_tuning(self.ctx)
+        for k, v in kw.items():
+            setattr(t, k, v)
+        _abi().qp_set_tuning(self.ctx, t)
+
+    def autotune(self, trial_steps=8, use_cache=True):
+        return _abi().qp_autotune(self.ctx, trial_steps, use_cache)
 
     def stats(self, t0, count=1):
         return _abi().qp_read_stats(self.ctx, t0, count)
@@ -105,3 +125,21 @@ class Propagator:
             self.close()
         except Exception:
             pass
+
+
+def batch_from_workloads(ws, precision="c64", max_paths=1 << 22, **kw):
+    """One batched Propagator over instances that differ only in their bath
+    (e.g. workloads.resonance_sweep): eta per instance from libqp."""
+    w0 = ws[0]
+    for w in ws[1:]:
+        if (w.M, w.q, w.hs, w.dt, w.dkmax, w.mask, w.theta, w.rho0) != (w0.M, w0.q, w0.hs, w0.dt, w0.dkmax, w0.mask,
+                                                                         w0.theta, w0.rho0):
+            raise ValueError("batched instances must share everything but the bath")
+    p = Propagator(w0.M, w0.dkmax, w0.dt, w0.q, w0.hs_array(), w0.theta, precision, "auto", max_paths,
+                   n_inst=len(ws), **kw)
+    p.set_eta(eta_from_bath(w0.bath, w0.dt, w0.dkmax))
+    for i, w in enumerate(ws):
+        p.set_eta_instance(i, eta_from_bath(w.bath, w.dt, w.dkmax))
+    p.set_mask(w0.mask)
+    p.set_rho0(w0.rho0_array())
+    return p

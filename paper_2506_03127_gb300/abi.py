@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_PKG, "libqp.so")
 QP_OK, QP_ERR_ARG, QP_ERR_OOM, QP_ERR_CUDA, QP_ERR_CAPACITY, QP_ERR_TIMEOUT, QP_ERR_STATE = range(7)
 QP_FP64, QP_C64 = 0, 1
 QP_ENGINE_AUTO, QP_ENGINE_HASH, QP_ENGINE_STREAM = 0, 1, 2
+QP_LAUNCH_GRAPH, QP_LAUNCH_PERSISTENT = 0, 1
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int)
@@ -28,7 +29,16 @@ class qp_config(ctypes.Structure):
     _fields_ = [("M", ctypes.c_int), ("dkmax", ctypes.c_int), ("dt", ctypes.c_double),
                 ("q", _dp), ("hs_re", _dp), ("hs_im", _dp),
                 ("precision", ctypes.c_int), ("engine", ctypes.c_int), ("theta", ctypes.c_double),
-                ("max_paths", ctypes.c_int64), ("max_groups", ctypes.c_int64), ("rho_history", ctypes.c_int)]
+                ("max_paths", ctypes.c_int64), ("max_groups", ctypes.c_int64), ("rho_history", ctypes.c_int),
+                ("n_inst", ctypes.c_int)]
+
+
+class qp_tuning(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int), ("insert_blocks_per_sm", ctypes.c_int), ("expand_blocks_per_sm", ctypes.c_int),
+                ("persistent_blocks", ctypes.c_int), ("graph_steps", ctypes.c_int), ("table_log2", ctypes.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class qp_bath(ctypes.Structure):
@@ -70,6 +80,12 @@ def _load():
                                          ctypes.POINTER(qp_step_stats)]),
         "qp_export_paths": (ctypes.c_int, [ctypes.c_void_p, _u64p, _dp, ctypes.c_int64, _i64p]),
         "qp_profile_steps": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _dp, ctypes.c_int]),
+        "qp_set_eta_instance": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _dp, _dp, ctypes.c_int]),
+        "qp_read_instance_counts": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, _i64p]),
+        "qp_get_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+        "qp_set_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+        "qp_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, _dp]),
+        "qp_test_stall_barrier": (ctypes.c_int, [ctypes.c_void_p]),
         "qp_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     }
     for name, (res, args) in sig.items():
@@ -97,14 +113,14 @@ def check(status, ctx=None):
 
 
 def make_config(M, dkmax, dt, q, hs, theta=0.0, precision=QP_FP64, engine=QP_ENGINE_AUTO,
-                max_paths=1 << 20, max_groups=0, rho_history=4096):
+                max_paths=1 << 20, max_groups=0, rho_history=4096, n_inst=1):
     """qp_config plus the numpy arrays it points into (keep both alive)."""
     q = _arr(q)
     hs = np.asarray(hs, dtype=np.complex128)
     hre, him = _arr(hs.real), _arr(hs.imag)
     cfg = qp_config(M=M, dkmax=dkmax, dt=dt, q=_ptr(q), hs_re=_ptr(hre), hs_im=_ptr(him),
                     precision=precision, engine=engine, theta=theta, max_paths=max_paths,
-                    max_groups=max_groups, rho_history=rho_history)
+                    max_groups=max_groups, rho_history=rho_history, n_inst=n_inst)
     return cfg, (q, hre, him)
 
 
@@ -167,10 +183,45 @@ def qp_current(ctx):
     return t.value, n.value
 
 
-def qp_read_rho(ctx, t0: int, count: int, M: int) -> np.ndarray:
-    re, im = np.zeros(count * M * M), np.zeros(count * M * M)
+def qp_read_rho(ctx, t0: int, count: int, M: int, n_inst: int = 1) -> np.ndarray:
+    """rho(t0 .. t0+count-1): shape (count, M, M), or (count, n_inst, M, M) for a batch."""
+    re, im = np.zeros(count * n_inst * M * M), np.zeros(count * n_inst * M * M)
     check(lib.qp_read_rho(ctx, t0, count, _ptr(re), _ptr(im)), ctx)
-    return (re + 1j * im).reshape(count, M, M)
+    r = (re + 1j * im)
+    return r.reshape(count, M, M) if n_inst == 1 else r.reshape(count, n_inst, M, M)
+
+
+def qp_set_eta_instance(ctx, inst: int, eta):
+    eta = np.asarray(eta, dtype=np.complex128)
+    re, im = _arr(eta.real), _arr(eta.imag)
+    check(lib.qp_set_eta_instance(ctx, inst, _ptr(re), _ptr(im), eta.size), ctx)
+
+
+def qp_read_instance_counts(ctx, t: int, n_inst: int) -> np.ndarray:
+    kept = np.zeros(n_inst, dtype=np.int64)
+    check(lib.qp_read_instance_counts(ctx, t, _ptr(kept, _i64p)), ctx)
+    return kept
+
+
+def qp_get_tuning(ctx) -> qp_tuning:
+    t = qp_tuning()
+    check(lib.qp_get_tuning(ctx, ctypes.byref(t)), ctx)
+    return t
+
+
+def qp_set_tuning(ctx, t: qp_tuning):
+    check(lib.qp_set_tuning(ctx, ctypes.byref(t)), ctx)
+
+
+def qp_autotune(ctx, trial_steps: int = 8, use_cache: bool = True):
+    t = qp_tuning()
+    ms = ctypes.c_double()
+    check(lib.qp_autotune(ctx, trial_steps, 1 if use_cache else 0, ctypes.byref(t), ctypes.byref(ms)), ctx)
+    return t, ms.value
+
+
+def qp_test_stall_barrier(ctx):
+    check(lib.qp_test_stall_barrier(ctx), ctx)
 
 
 def qp_read_stats(ctx, t0: int, count: int):

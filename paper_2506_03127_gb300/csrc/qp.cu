@@ -33,6 +33,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <map>
 #include <mutex>
 #include <type_traits>
 #include <cmath>
@@ -57,6 +58,7 @@ constexpr int kInsertThreads = 256;
 constexpr int kExpandThreads = 128;
 constexpr int kMaxExpandBlocks = 2048;
 constexpr int kPersistThreads = 256;
+constexpr int kMaxInst = 128;                      // instances of one batched context
 constexpr long long kBarrierCycles = 4000000000ll;  // ~2 s at 2 GHz: a grid barrier gives up after this
 constexpr int kMaxDelta = 12;
 constexpr double kTieRelFP64 = 1e-12;  // weights equal to this relative width are ties (R4)
@@ -115,8 +117,15 @@ struct Params {
     signed char dsel[16];              // child k -> delta index, -1 when q_a == q_b
     float theta2f;
     double tie_rel;                    // relative window of equal weights (R4)
-    double2 *rho_ring;                 // [rho_hist][M*M]
-    double2 *rho_part;                 // [expand blocks][M*M] per-block partial sums of rho(t)
+    double2 *rho_ring;                 // [rho_hist][n_inst][M*M]
+    double2 *rho_part;                 // [2 (step parity)][kMaxExpandBlocks][n_inst][M*M + 1] per-block partials
+                                       // of rho(t) per instance; element M*M holds the survivor count
+    long long *inst_kept;              // [rho_hist][n_inst] stored paths per instance after each step
+    unsigned int *fin_count;           // blocks of k_finalize that are done (last one updates the state)
+    int n_inst;                        // independent instances (1 = single problem)
+    int inst_shift;                    // key bit where the instance index starts (b * dkmax)
+    unsigned long long instmask;       // key bits of the instance index
+    size_t lut_stride, etab_stride;    // per-instance strides of the history / exp tables (entries)
     StepRec *stats_ring;               // [rho_hist]
     DevState *st;
 };
@@ -325,16 +334,15 @@ struct Expander {
         s.y = ty;
     }
 
-    static __device__ __forceinline__ unsigned children(const Params &P, int n_act, unsigned long long rep, double2 S,
-                                                        const double2 *s_w, const float2 *s_wf, AmpT *v,
-                                                        AccT *racc, AccT *rcmp) {
+    static __device__ __forceinline__ unsigned children(const Params &P, int n_act, int inst, unsigned long long rep,
+                                                        double2 S, const double2 *w, const float2 *wf, AmpT *v) {
         const unsigned c0 = (unsigned)(rep & ((1u << P.b) - 1u));
         const int pidx = (int)(c0 & ((1u << P.bs) - 1u)) * M + (int)(c0 >> P.bs);
         unsigned keep = 0;
         if constexpr (C64) {
             float2 Ed[ND];
             if (P.ndelta) {
-                const size_t off = (size_t)(n_act - 1) * P.nchunks * kLutEntries;
+                const size_t off = (size_t)inst * P.lut_stride + (size_t)(n_act - 1) * P.nchunks * kLutEntries;
                 float sx = 0.f, sy = 0.f, cx = 0.f, cy = 0.f, lx = 0.f, ly = 0.f;
                 for (int j = 0; j < P.nchunks; ++j) {
                     const size_t idx = off + (size_t)j * kLutEntries + key_byte(rep, j);
@@ -363,19 +371,16 @@ struct Expander {
             const float2 Sf = make_float2((float)S.x, (float)S.y);
 #pragma unroll
             for (int k = 0; k < MM; ++k) {
-                float2 a = cmulf(Sf, s_wf[k * MM + pidx]);
+                float2 a = cmulf(Sf, wf[k * MM + pidx]);
                 const int d = P.dsel[k];
                 if (d >= 0) a = cmulf(a, pick(Ed, d));
                 v[k] = a;
-                if (a.x * a.x + a.y * a.y >= P.theta2f) {
-                    keep |= 1u << k;
-                    kahan_add(racc[k], rcmp[k], a);
-                }
+                if (a.x * a.x + a.y * a.y >= P.theta2f) keep |= 1u << k;
             }
         } else {
             double2 Ed[ND];
             const size_t dstride = (size_t)P.nchunks * kLutEntries;
-            const double2 *et = P.etab + (size_t)(n_act - 1) * P.ndelta * dstride;
+            const double2 *et = P.etab + (size_t)inst * P.etab_stride + (size_t)(n_act - 1) * P.ndelta * dstride;
 #pragma unroll
             for (int d = 0; d < ND; ++d) {
                 if (d >= P.ndelta) break;
@@ -385,15 +390,11 @@ struct Expander {
             }
 #pragma unroll
             for (int k = 0; k < MM; ++k) {
-                double2 a = cmul(S, s_w[k * MM + pidx]);
+                double2 a = cmul(S, w[k * MM + pidx]);
                 const int d = P.dsel[k];
                 if (d >= 0) a = cmul(a, pick(Ed, d));
                 v[k] = a;
-                if (a.x * a.x + a.y * a.y >= P.theta2) {
-                    keep |= 1u << k;
-                    racc[k].x += a.x;
-                    racc[k].y += a.y;
-                }
+                if (a.x * a.x + a.y * a.y >= P.theta2) keep |= 1u << k;
             }
         }
         return keep;
@@ -401,9 +402,13 @@ struct Expander {
 };
 
 // Extension of n groups (merge steps) or n stored paths (while the window
-// fills) to their children; survivors appended through *cnt_out; this
-// block's partial sum of rho(t+1) written to part[blockIdx.x].
-template <int M, bool C64, int NT>
+// fills) to their children; survivors appended through *cnt_out.  This
+// block's partial sums of rho(t+1) (and its survivor count) per instance go
+// to part[blockIdx.x][inst][0 .. M*M].  Single problems accumulate in
+// registers (FP64, or FP32 + Kahan on the C64 path); batches accumulate per
+// instance in shared memory (FP64 atomics; dynamic shared memory of
+// n_inst * (M*M + 1) double2).
+template <int M, bool C64, int NT, bool BATCH>
 __device__ __forceinline__ void phase_expand(const Params &P, unsigned long long t, unsigned long long n, bool merge,
                                              unsigned long long *cnt_out, double2 *part) {
     using X = Expander<M, C64>;
@@ -423,18 +428,24 @@ __device__ __forceinline__ void phase_expand(const Params &P, unsigned long long
     __shared__ double2 s_w[MM * MM];
     __shared__ float2 s_wf[MM * MM];
     __shared__ double2 s_r[NW][MM];
-    for (int i = threadIdx.x; i < MM * MM; i += NT) {
-        s_w[i] = P.wtab[i];
-        s_wf[i] = P.wtabf[i];
+    extern __shared__ double2 s_acc[];   // BATCH: [n_inst][MM + 1]
+    if constexpr (BATCH) {
+        for (int i = threadIdx.x; i < P.n_inst * (MM + 1); i += NT) s_acc[i] = make_double2(0.0, 0.0);
+    } else {
+        for (int i = threadIdx.x; i < MM * MM; i += NT) {
+            s_w[i] = P.wtab[i];
+            s_wf[i] = P.wtabf[i];
+        }
     }
     __syncthreads();
 
-    typename X::AccT racc[MM], rcmp[MM];
+    typename X::AccT racc[BATCH ? 1 : MM], rcmp[BATCH ? 1 : MM];
 #pragma unroll
-    for (int k = 0; k < MM; ++k) {
+    for (int k = 0; k < (BATCH ? 1 : MM); ++k) {
         racc[k].x = racc[k].y = 0;
         rcmp[k].x = rcmp[k].y = 0;
     }
+    unsigned long long block_kept = 0;
 
     const unsigned long long stride = (unsigned long long)gridDim.x * NT;
     for (unsigned long long base = blockIdx.x * (unsigned long long)NT; base < n; base += stride) {
@@ -442,6 +453,7 @@ __device__ __forceinline__ void phase_expand(const Params &P, unsigned long long
         unsigned keepbits = 0;
         AmpT camp[MM];
         unsigned long long rep = 0;
+        int inst = 0;
         if (g < n) {
             double2 S;
             if (merge) {
@@ -459,125 +471,175 @@ __device__ __forceinline__ void phase_expand(const Params &P, unsigned long long
                 rep = __ldcg(keys_in + g);
                 S = load_amp(amps_in, g);
             }
-            keepbits = X::children(P, n_act, rep, S, s_w, s_wf, camp, racc, rcmp);
+            if constexpr (BATCH) {
+                inst = (int)(rep >> P.inst_shift);
+                keepbits = X::children(P, n_act, inst, rep, S, P.wtab + (size_t)inst * MM * MM,
+                                       P.wtabf + (size_t)inst * MM * MM, camp);
+                double2 *acc = s_acc + (size_t)inst * (MM + 1);
+#pragma unroll
+                for (int k = 0; k < MM; ++k)
+                    if (keepbits & (1u << k)) {
+                        atomicAdd(&acc[k].x, (double)camp[k].x);
+                        atomicAdd(&acc[k].y, (double)camp[k].y);
+                    }
+                if (keepbits) atomicAdd(&acc[MM].x, (double)__popc(keepbits));
+            } else {
+                keepbits = X::children(P, n_act, 0, rep, S, s_w, s_wf, camp);
+#pragma unroll
+                for (int k = 0; k < MM; ++k)
+                    if (keepbits & (1u << k)) {
+                        if constexpr (C64) {
+                            X::kahan_add(racc[k], rcmp[k], camp[k]);
+                        } else {
+                            racc[k].x += camp[k].x;
+                            racc[k].y += camp[k].y;
+                        }
+                    }
+            }
         }
         const unsigned cnt = __popc(keepbits);
         const Append ap = block_append<NT>(cnt, cnt_out);
+        block_kept += ap.total;
         if (ap.total && ap.base + ap.total > (unsigned long long)P.max_paths) {
             if (threadIdx.x == 0) raise_err(st, kErrPaths);
         } else if (cnt) {
             unsigned long long o = ap.base + ap.excl;
             const unsigned long long shifted = rep << P.b;
+            const unsigned long long ibits = rep & P.instmask;
 #pragma unroll
             for (int k = 0; k < MM; ++k) {
                 if (keepbits & (1u << k)) {
                     const unsigned long long code = (unsigned long long)((k / M) | ((k % M) << P.bs));
-                    keys_out[o] = (shifted | code) & wmask;
+                    keys_out[o] = ((shifted | code) & wmask) | ibits;
                     amps_out[o] = camp[k];
                     ++o;
                 }
             }
         }
     }
-    // this block's partial sum of rho(t+1): warp shuffles, then across warps
-    const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+    double2 *mine = part + (size_t)blockIdx.x * P.n_inst * (MM + 1);
+    if constexpr (BATCH) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < P.n_inst * (MM + 1); i += NT) mine[i] = s_acc[i];
+    } else {
+        // this block's partial sums: warp shuffles, then across warps
+        const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int k = 0; k < MM; ++k) {
-        double x = (double)racc[k].x - (double)rcmp[k].x, y = (double)racc[k].y - (double)rcmp[k].y;
+        for (int k = 0; k < MM; ++k) {
+            double x = (double)racc[k].x - (double)rcmp[k].x, y = (double)racc[k].y - (double)rcmp[k].y;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            x += __shfl_down_sync(0xffffffffu, x, o);
-            y += __shfl_down_sync(0xffffffffu, y, o);
+            for (int o = 16; o > 0; o >>= 1) {
+                x += __shfl_down_sync(0xffffffffu, x, o);
+                y += __shfl_down_sync(0xffffffffu, y, o);
+            }
+            if (lane == 0) s_r[warp][k] = make_double2(x, y);
         }
-        if (lane == 0) s_r[warp][k] = make_double2(x, y);
-    }
-    __syncthreads();
-    if (threadIdx.x < MM) {
-        double x = 0.0, y = 0.0;
-        for (int w = 0; w < NW; ++w) {
-            x += s_r[w][threadIdx.x].x;
-            y += s_r[w][threadIdx.x].y;
+        __syncthreads();
+        if (threadIdx.x < MM) {
+            double x = 0.0, y = 0.0;
+            for (int w = 0; w < NW; ++w) {
+                x += s_r[w][threadIdx.x].x;
+                y += s_r[w][threadIdx.x].y;
+            }
+            mine[threadIdx.x] = make_double2(x, y);
         }
-        part[(size_t)blockIdx.x * MM + threadIdx.x] = make_double2(x, y);
+        if (threadIdx.x == 0) mine[MM] = make_double2((double)block_kept, 0.0);
     }
     __syncthreads();
 }
 
-// One block: rho(tn) from the nblk partial sums in block order (deterministic)
-// and the step's statistics.  Thread 0 returns true.
-__device__ __forceinline__ void phase_finalize(const Params &P, unsigned long long tn, unsigned long long groups,
-                                               unsigned long long n_out, const double2 *part, int nblk, int MM) {
-    __shared__ double2 s_p[1024];
-    double2 *rho = P.rho_ring + (size_t)(tn % (unsigned long long)P.rho_hist) * MM;
+// One block, one instance: rho(tn) of the instance and its survivor count
+// from the nblk per-block partials, summed in block order (deterministic).
+__device__ __forceinline__ void phase_finalize(const Params &P, unsigned long long tn, int inst, const double2 *part,
+                                               int nblk, int MM) {
+    __shared__ double2 s_p[256];
+    const int MM1 = MM + 1;
+    const size_t pstride = (size_t)P.n_inst * MM1;
+    const double2 *src = part + (size_t)inst * MM1;
     // T threads per element k sum a fixed stride of the partials with four
     // independent accumulators so that the loads overlap
-    const int T = min((int)blockDim.x, 1024) / MM;
+    const int T = min((int)blockDim.x, 256) / MM1;
     const int k = (int)threadIdx.x / T, sidx = (int)threadIdx.x % T;
     double2 a0 = make_double2(0.0, 0.0), a1 = a0, a2 = a0, a3 = a0;
-    if (k < MM && threadIdx.x < 1024) {
+    if (k < MM1 && threadIdx.x < 256) {
         int b = sidx;
         for (; b + 3 * T < nblk; b += 4 * T) {
-            const double2 v0 = __ldcg(part + (size_t)b * MM + k);
-            const double2 v1 = __ldcg(part + (size_t)(b + T) * MM + k);
-            const double2 v2 = __ldcg(part + (size_t)(b + 2 * T) * MM + k);
-            const double2 v3 = __ldcg(part + (size_t)(b + 3 * T) * MM + k);
+            const double2 v0 = __ldcg(src + (size_t)b * pstride + k);
+            const double2 v1 = __ldcg(src + (size_t)(b + T) * pstride + k);
+            const double2 v2 = __ldcg(src + (size_t)(b + 2 * T) * pstride + k);
+            const double2 v3 = __ldcg(src + (size_t)(b + 3 * T) * pstride + k);
             a0.x += v0.x; a0.y += v0.y;
             a1.x += v1.x; a1.y += v1.y;
             a2.x += v2.x; a2.y += v2.y;
             a3.x += v3.x; a3.y += v3.y;
         }
         for (; b < nblk; b += T) {
-            const double2 v = __ldcg(part + (size_t)b * MM + k);
+            const double2 v = __ldcg(src + (size_t)b * pstride + k);
             a0.x += v.x; a0.y += v.y;
         }
     }
-    if (threadIdx.x < 1024)
+    if (threadIdx.x < 256)
         s_p[threadIdx.x] = make_double2((a0.x + a1.x) + (a2.x + a3.x), (a0.y + a1.y) + (a2.y + a3.y));
     __syncthreads();
-    if ((int)threadIdx.x < MM) {
+    if ((int)threadIdx.x < MM1) {
         double x = 0.0, y = 0.0;
         for (int i = 0; i < T; ++i) {
             x += s_p[threadIdx.x * T + i].x;
             y += s_p[threadIdx.x * T + i].y;
         }
-        rho[threadIdx.x] = make_double2(x, y);
-    }
-    if (threadIdx.x == 0) {
-        StepRec r;
-        r.t = (long long)tn;
-        r.groups = (long long)groups;
-        r.extended = (long long)groups * MM;
-        r.kept = (long long)n_out;
-        P.stats_ring[tn % (unsigned long long)P.rho_hist] = r;
+        const size_t slot = (size_t)(tn % (unsigned long long)P.rho_hist);
+        if ((int)threadIdx.x < MM)
+            P.rho_ring[(slot * P.n_inst + inst) * MM + threadIdx.x] = make_double2(x, y);
+        else
+            P.inst_kept[slot * P.n_inst + inst] = (long long)(x + 0.5);
     }
     __syncthreads();
 }
 
-__device__ __forceinline__ double2 *rho_part_of(const Params &P, unsigned long long tn, int MM) {
-    return P.rho_part + (size_t)(tn & 1) * kMaxExpandBlocks * MM;
+__device__ __forceinline__ void write_step_totals(const Params &P, unsigned long long tn, unsigned long long groups,
+                                                  unsigned long long n_out, int MM) {
+    StepRec r;
+    r.t = (long long)tn;
+    r.groups = (long long)groups;
+    r.extended = (long long)groups * MM;
+    r.kept = (long long)n_out;
+    P.stats_ring[tn % (unsigned long long)P.rho_hist] = r;
 }
 
-template <int M, bool C64>
+__device__ __forceinline__ double2 *rho_part_of(const Params &P, unsigned long long tn, int MM) {
+    return P.rho_part + (size_t)(tn & 1) * kMaxExpandBlocks * P.n_inst * (MM + 1);
+}
+
+template <int M, bool C64, bool BATCH>
 __global__ void __launch_bounds__(kExpandThreads) k_expand(Params P) {
     DevState *st = P.st;
     if (st->err) return;
     const unsigned long long t = st->t, tn = t + 1;
     const bool merge = tn >= (unsigned long long)P.dkmax;
     const unsigned long long n = merge ? st->cnt_groups[tn % 3] : st->n_cur;
-    phase_expand<M, C64, kExpandThreads>(P, t, n, merge, &st->cnt_out[tn % 3], rho_part_of(P, tn, M * M));
+    phase_expand<M, C64, kExpandThreads, BATCH>(P, t, n, merge, &st->cnt_out[tn % 3], rho_part_of(P, tn, M * M));
 }
 
-// Step finalisation of the multi-kernel path (one block).
+// Step finalisation of the multi-kernel path: block i finalises instance i;
+// the last block to finish publishes the step (counts, t, next counters).
 __global__ void __launch_bounds__(256) k_finalize(Params P, int MM, int nblk) {
     DevState *st = P.st;
+    __shared__ bool s_last;
     if (st->err) return;
     const unsigned long long t = st->t, tn = t + 1;
+    for (int inst = blockIdx.x; inst < P.n_inst; inst += gridDim.x)
+        phase_finalize(P, tn, inst, rho_part_of(P, tn, MM), nblk, MM);
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(P.fin_count, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last || threadIdx.x != 0) return;
+    *P.fin_count = 0;
     const bool merge = tn >= (unsigned long long)P.dkmax;
     const unsigned long long groups = merge ? st->cnt_groups[tn % 3] : st->n_cur;
     const unsigned long long n_out = st->cnt_out[tn % 3];
-    __syncthreads();
-    phase_finalize(P, tn, groups, n_out, rho_part_of(P, tn, MM), nblk, MM);
-    if (threadIdx.x != 0) return;
+    write_step_totals(P, tn, groups, n_out, MM);
     st->n_cur = n_out;
     st->t = tn;
     st->cnt_groups[(tn + 1) % 3] = 0;   // counters of the next step
@@ -621,11 +683,12 @@ __device__ __forceinline__ unsigned grid_barrier(DevState *st) {
 
 // All steps of one qp_step call in one cooperative launch.  Per step: insert
 // | tiebreak | expand, separated by grid barriers (only expand while the
-// window fills).  Block 0 finalises step t' at the start of step t'+1 (and
-// the last step after the loop) from values every block already holds.
+// window fills).  Step t' is finalised at the start of step t'+1 (and the
+// last step after the loop) from values every block already holds: block b
+// finalises instances b, b + gridDim.x, ...; block 0 writes the totals.
 // Counter sets rotate mod 3 so that no counter is reset while a block may
 // still read it.
-template <int M, bool C64>
+template <int M, bool C64, bool BATCH>
 __global__ void __launch_bounds__(kPersistThreads) k_step_persistent(Params P, int nsteps) {
     constexpr int MM = M * M;
     using Amp = typename Expander<M, C64>::AmpT;
@@ -640,13 +703,14 @@ __global__ void __launch_bounds__(kPersistThreads) k_step_persistent(Params P, i
         const unsigned long long tn = t + 1;
         const int cs = (int)(tn % 3);
         const bool merge = tn >= (unsigned long long)P.dkmax;
-        if (blockIdx.x == 0) {
-            if (threadIdx.x == 0) {
-                st->cnt_groups[(tn + 1) % 3] = 0;   // last used two steps ago
-                st->cnt_out[(tn + 1) % 3] = 0;
-            }
-            if (s > 0) phase_finalize(P, t, prev_groups, prev_out, rho_part_of(P, t, MM), nblk, MM);
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            st->cnt_groups[(tn + 1) % 3] = 0;   // last used two steps ago
+            st->cnt_out[(tn + 1) % 3] = 0;
+            if (s > 0) write_step_totals(P, t, prev_groups, prev_out, MM);
         }
+        if (s > 0)
+            for (int inst = blockIdx.x; inst < P.n_inst; inst += nblk)
+                phase_finalize(P, t, inst, rho_part_of(P, t, MM), nblk, MM);
         if (merge) {
             phase_insert<Amp, kPersistThreads>(P, t, n_in, &st->cnt_groups[cs]);
             err = grid_barrier(st);
@@ -656,7 +720,7 @@ __global__ void __launch_bounds__(kPersistThreads) k_step_persistent(Params P, i
             if (err) break;
         }
         const unsigned long long ng = merge ? __ldcg(&st->cnt_groups[cs]) : n_in;
-        phase_expand<M, C64, kPersistThreads>(P, t, ng, merge, &st->cnt_out[cs], rho_part_of(P, tn, MM));
+        phase_expand<M, C64, kPersistThreads, BATCH>(P, t, ng, merge, &st->cnt_out[cs], rho_part_of(P, tn, MM));
         err = grid_barrier(st);
         if (err) break;
         prev_groups = ng;
@@ -665,9 +729,11 @@ __global__ void __launch_bounds__(kPersistThreads) k_step_persistent(Params P, i
         t = tn;
         ++done;
     }
-    if (blockIdx.x == 0) {
-        if (done > 0) phase_finalize(P, t, prev_groups, prev_out, rho_part_of(P, t, MM), nblk, MM);
-        if (threadIdx.x == 0 && done > 0) {
+    if (done > 0) {
+        for (int inst = blockIdx.x; inst < P.n_inst; inst += nblk)
+            phase_finalize(P, t, inst, rho_part_of(P, t, MM), nblk, MM);
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            write_step_totals(P, t, prev_groups, prev_out, MM);
             st->n_cur = n_in;
             st->t = t;
         }
@@ -767,7 +833,9 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
     size_t keys[2], amps[2], slots, repk, slot_of, groups, lut, lutf, lutlo, etab, wtab, wtabf, uprop, eta, q, deltas,
-        rho, rho_part, stats, state, total;
+        rho, rho_part, stats, inst_kept, fin_count, state, total;
+    size_t nlut;           // history-table entries of one instance
+    int nd;                // distinct nonzero coupling differences
     unsigned long long tcap;
     unsigned int tcap_log2;
     int nchunks;
@@ -777,6 +845,12 @@ int bits_per_state(int M) {
     int bs = 1;
     while ((1 << bs) < M) ++bs;
     return bs;
+}
+
+int inst_bits(int n_inst) {
+    int ib = 0;
+    while ((1 << ib) < n_inst) ++ib;
+    return ib;
 }
 
 const char *validate(const qp_config *c) {
@@ -794,6 +868,8 @@ const char *validate(const qp_config *c) {
     if (c->max_groups < 0 || c->max_groups > (int64_t(1) << 30)) return "max_groups out of range";
     if (c->max_groups == 0 && c->max_paths > (int64_t(1) << 30)) return "set max_groups (<= 2^30) for max_paths > 2^30";
     if (c->rho_history < 0 || c->rho_history > (1 << 24)) return "rho_history out of range";
+    if (c->n_inst < 0 || c->n_inst > kMaxInst) return "n_inst out of range (0..128)";
+    if (b * c->dkmax + inst_bits(c->n_inst) > 64) return "b*dkmax plus the instance index exceed the 64-bit key";
     for (int i = 0; i < c->M; ++i)
         if (!std::isfinite(c->q[i])) return "q must be finite";
     for (int i = 0; i < c->M * c->M; ++i) {
@@ -851,21 +927,26 @@ Layout make_layout(const qp_config *c) {
     L.repk = take(L.tcap * 8);
     L.slot_of = take(mp * 4);
     L.groups = take(mg * 4);
+    const int NI = std::max(1, c->n_inst);
     const size_t nlut = (size_t)c->dkmax * std::max(1, L.nchunks) * kLutEntries;
-    L.lut = take(nlut * sizeof(double2));
-    L.lutf = take(nlut * sizeof(float2));
-    L.lutlo = take(nlut * sizeof(float2));
+    L.nlut = nlut;
+    L.lut = take(NI * nlut * sizeof(double2));
+    L.lutf = take(NI * nlut * sizeof(float2));
+    L.lutlo = take(NI * nlut * sizeof(float2));
     const int nd = distinct_deltas(c->M, c->q, nullptr, nullptr);
-    L.etab = take(nlut * std::max(1, nd) * sizeof(double2));
-    L.wtab = take(MM * MM * sizeof(double2));
-    L.wtabf = take(MM * MM * sizeof(float2));
+    L.nd = nd;
+    L.etab = take(NI * nlut * std::max(1, nd) * sizeof(double2));
+    L.wtab = take((size_t)NI * MM * MM * sizeof(double2));
+    L.wtabf = take((size_t)NI * MM * MM * sizeof(float2));
     L.deltas = take(kMaxDelta * sizeof(double));
     L.uprop = take(MM * sizeof(double2));
-    L.eta = take(c->dkmax * sizeof(double2));
+    L.eta = take((size_t)NI * c->dkmax * sizeof(double2));
     L.q = take(c->M * sizeof(double));
-    L.rho = take((size_t)R * MM * sizeof(double2));
-    L.rho_part = take((size_t)2 * kMaxExpandBlocks * MM * sizeof(double2));   // by step parity
+    L.rho = take((size_t)R * NI * MM * sizeof(double2));
+    L.rho_part = take((size_t)2 * kMaxExpandBlocks * NI * (MM + 1) * sizeof(double2));   // by step parity
     L.stats = take((size_t)R * sizeof(StepRec));
+    L.inst_kept = take((size_t)R * NI * sizeof(long long));
+    L.fin_count = take(sizeof(unsigned int));
     L.total = off;
     return L;
 }
@@ -886,7 +967,11 @@ struct qp_ctx {
     bool have_eta = false, have_state = false, failed = false;
     std::vector<int> mask;
     int persist_grid = 0;              // blocks of the cooperative persistent kernel (0 = not usable)
+    int persist_max = 0;               // co-resident limit of that kernel
     bool use_persistent = true;
+    int bps_ins = 4, bps_exp = 4;      // blocks per SM of the pre-merge and extension kernels
+    int graph_steps = 1;               // steps captured per CUDA graph
+    cudaGraphExec_t graph1 = nullptr;  // one-step graph for remainders
     cudaGraphExec_t graph = nullptr;
     bool graph_dirty = true;
     bool use_graph = true;
@@ -910,18 +995,28 @@ constexpr int kStepKernels = 4;
 
 // Launch one step; if ev is given, record ev[k] before kernel k and
 // ev[kStepKernels] after the last one.
+size_t batch_smem(const qp_ctx *c) {
+    const int MM = c->cfg.M * c->cfg.M;
+    return c->P.n_inst > 1 ? (size_t)c->P.n_inst * (MM + 1) * sizeof(double2) : 0;
+}
+
 template <int M, typename Amp>
 cudaError_t launch_step_t(qp_ctx *c, cudaEvent_t *ev) {
-    const int g_ins = c->nsm * 4;
-    const int g_exp = std::min(c->nsm * 4, kMaxExpandBlocks);
+    constexpr bool C64 = sizeof(Amp) == sizeof(float2);
+    const int g_ins = c->nsm * c->bps_ins;
+    const int g_exp = std::min(c->nsm * c->bps_exp, kMaxExpandBlocks);
+    const size_t sm = batch_smem(c);
     if (ev) cudaEventRecord(ev[0], c->stream);
     k_insert<Amp><<<g_ins, kInsertThreads, 0, c->stream>>>(c->P);
     if (ev) cudaEventRecord(ev[1], c->stream);
-    k_tiebreak<Amp><<<g_ins, 256, 0, c->stream>>>(c->P);
+    k_tiebreak<Amp><<<g_ins, kInsertThreads, 0, c->stream>>>(c->P);
     if (ev) cudaEventRecord(ev[2], c->stream);
-    k_expand<M, sizeof(Amp) == sizeof(float2)><<<g_exp, kExpandThreads, 0, c->stream>>>(c->P);
+    if (c->P.n_inst > 1)
+        k_expand<M, C64, true><<<g_exp, kExpandThreads, sm, c->stream>>>(c->P);
+    else
+        k_expand<M, C64, false><<<g_exp, kExpandThreads, 0, c->stream>>>(c->P);
     if (ev) cudaEventRecord(ev[3], c->stream);
-    k_finalize<<<1, 256, 0, c->stream>>>(c->P, M * M, g_exp);
+    k_finalize<<<std::max(1, std::min(c->P.n_inst, 1024)), 256, 0, c->stream>>>(c->P, M * M, g_exp);
     if (ev) cudaEventRecord(ev[4], c->stream);
     return cudaGetLastError();
 }
@@ -938,7 +1033,10 @@ cudaError_t launch_step(qp_ctx *c, cudaEvent_t *ev = nullptr) {
 template <int M, bool C64>
 cudaError_t launch_persistent_t(qp_ctx *c, int nsteps) {
     void *args[] = {(void *)&c->P, (void *)&nsteps};
-    return cudaLaunchCooperativeKernel((const void *)k_step_persistent<M, C64>, dim3(c->persist_grid),
+    if (c->P.n_inst > 1)
+        return cudaLaunchCooperativeKernel((const void *)k_step_persistent<M, C64, true>, dim3(c->persist_grid),
+                                           dim3(kPersistThreads), args, batch_smem(c), c->stream);
+    return cudaLaunchCooperativeKernel((const void *)k_step_persistent<M, C64, false>, dim3(c->persist_grid),
                                        dim3(kPersistThreads), args, 0, c->stream);
 }
 
@@ -954,18 +1052,37 @@ cudaError_t launch_persistent(qp_ctx *c, int nsteps) {
 // Blocks of the persistent kernel: all must be co-resident (cooperative
 // launch), at most kMaxExpandBlocks (rho partial buffer).
 template <int M, bool C64>
-int persistent_grid_t(int nsm) {
+int persistent_grid_t(int nsm, bool batch, size_t smem) {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_persistent<M, C64>, kPersistThreads, 0) != cudaSuccess)
-        return 0;
+    cudaError_t e = batch ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_persistent<M, C64, true>,
+                                                                          kPersistThreads, smem)
+                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_persistent<M, C64, false>,
+                                                                          kPersistThreads, 0);
+    if (e != cudaSuccess) return 0;
     return std::min(std::max(0, nb) * nsm, kMaxExpandBlocks);
 }
 
-int persistent_grid(int M, bool c64, int nsm) {
+// Batched kernels keep per-instance rho accumulators in dynamic shared memory.
+template <int M, bool C64>
+void allow_batch_smem_t(size_t smem) {
+    if (smem <= 48 * 1024) return;
+    cudaFuncSetAttribute(k_expand<M, C64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_step_persistent<M, C64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+void allow_batch_smem(int M, bool c64, size_t smem) {
     switch (M) {
-        case 2: return c64 ? persistent_grid_t<2, true>(nsm) : persistent_grid_t<2, false>(nsm);
-        case 3: return c64 ? persistent_grid_t<3, true>(nsm) : persistent_grid_t<3, false>(nsm);
-        default: return c64 ? persistent_grid_t<4, true>(nsm) : persistent_grid_t<4, false>(nsm);
+        case 2: c64 ? allow_batch_smem_t<2, true>(smem) : allow_batch_smem_t<2, false>(smem); break;
+        case 3: c64 ? allow_batch_smem_t<3, true>(smem) : allow_batch_smem_t<3, false>(smem); break;
+        default: c64 ? allow_batch_smem_t<4, true>(smem) : allow_batch_smem_t<4, false>(smem); break;
+    }
+}
+
+int persistent_grid(int M, bool c64, int nsm, bool batch, size_t smem) {
+    switch (M) {
+        case 2: return c64 ? persistent_grid_t<2, true>(nsm, batch, smem) : persistent_grid_t<2, false>(nsm, batch, smem);
+        case 3: return c64 ? persistent_grid_t<3, true>(nsm, batch, smem) : persistent_grid_t<3, false>(nsm, batch, smem);
+        default: return c64 ? persistent_grid_t<4, true>(nsm, batch, smem) : persistent_grid_t<4, false>(nsm, batch, smem);
     }
 }
 
@@ -983,8 +1100,9 @@ void set_mask_params(qp_ctx *c) {
             Pp.push_back(p);
             pm |= ((1ull << b) - 1ull) << (b * p);
         }
-    P.pmask = pm;
-    // dense index: compress the runs of consecutive P' positions
+    P.pmask = pm | P.instmask;   // paths of different instances never merge
+    // dense index: compress the runs of consecutive P' positions (then the
+    // instance index)
     int nruns = 0, off = 0;
     bool ok = true;
     for (size_t i = 0; i < Pp.size();) {
@@ -999,8 +1117,19 @@ void set_mask_params(qp_ctx *c) {
         ++nruns;
         i = j + 1;
     }
+    if (P.n_inst > 1) {
+        if (nruns == kMaxRuns) ok = false;
+        else {
+            const int ib = inst_bits(P.n_inst);
+            P.run_shift[nruns] = P.inst_shift;
+            P.run_mask[nruns] = (1ull << ib) - 1ull;
+            P.run_off[nruns] = off;
+            off += ib;
+            ++nruns;
+        }
+    }
     P.nruns = nruns;
-    P.dense = (ok && off <= (int)c->L.tcap_log2) ? 1 : 0;
+    P.dense = (ok && off <= (int)P.tcap_log2) ? 1 : 0;
 }
 
 }  // namespace
@@ -1064,10 +1193,14 @@ qp_status qp_create(const qp_config *cfg, void *d_workspace, size_t bytes, void 
     {
         int coop = 0;
         cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->device);
-        c->persist_grid = coop ? persistent_grid(M, cfg->precision == QP_C64, c->nsm) : 0;
+        const int NI = std::max(1, cfg->n_inst);
+        const size_t smem = NI > 1 ? (size_t)NI * (M * M + 1) * sizeof(double2) : 0;
+        if (NI > 1) allow_batch_smem(M, cfg->precision == QP_C64, smem);
+        c->persist_max = coop ? persistent_grid(M, cfg->precision == QP_C64, c->nsm, NI > 1, smem) : 0;
+        c->persist_grid = std::min(c->persist_max, 2 * c->nsm);
         if (const char *bps = getenv("QP_PERSIST_BLOCKS_PER_SM")) {   // launch-shape override (tuning)
             const int want = atoi(bps) * c->nsm;
-            if (want > 0 && want < c->persist_grid) c->persist_grid = want;
+            if (want > 0 && want <= c->persist_max) c->persist_grid = want;
         }
         // default: the CUDA graph of the four step kernels (faster than the
         // persistent kernel's grid barriers when one step is launched at a time)
@@ -1112,6 +1245,13 @@ qp_status qp_create(const qp_config *cfg, void *d_workspace, size_t bytes, void 
     P.tie_rel = cfg->precision == QP_C64 ? kTieRelC64 : kTieRelFP64;
     P.rho_ring = reinterpret_cast<double2 *>(c->ws + L.rho);
     P.rho_part = reinterpret_cast<double2 *>(c->ws + L.rho_part);
+    P.inst_kept = reinterpret_cast<long long *>(c->ws + L.inst_kept);
+    P.fin_count = reinterpret_cast<unsigned int *>(c->ws + L.fin_count);
+    P.n_inst = std::max(1, cfg->n_inst);
+    P.inst_shift = P.b * cfg->dkmax;
+    P.instmask = P.n_inst > 1 ? (((1ull << inst_bits(P.n_inst)) - 1ull) << P.inst_shift) : 0ull;
+    P.lut_stride = L.nlut;
+    P.etab_stride = L.nlut * (size_t)std::max(1, L.nd);
     P.stats_ring = reinterpret_cast<StepRec *>(c->ws + L.stats);
     P.st = reinterpret_cast<DevState *>(c->ws + L.state);
     c->mask.clear();
@@ -1127,6 +1267,7 @@ qp_status qp_create(const qp_config *cfg, void *d_workspace, size_t bytes, void 
         e = cudaMemcpyAsync(c->ws + L.deltas, c->deltas.data(), c->deltas.size() * sizeof(double), cudaMemcpyHostToDevice,
                             c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.state, 0, sizeof(DevState), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.fin_count, 0, sizeof(unsigned int), c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         delete c;
@@ -1139,6 +1280,7 @@ qp_status qp_create(const qp_config *cfg, void *d_workspace, size_t bytes, void 
 void qp_destroy(qp_ctx *ctx) {
     if (!ctx) return;
     if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+    if (ctx->graph1) cudaGraphExecDestroy(ctx->graph1);
     delete ctx;
 }
 
@@ -1153,40 +1295,55 @@ qp_status qp_eta_from_bath(const qp_bath *bath, double dt, int n, double *eta_re
     return QP_OK;
 }
 
-qp_status qp_set_eta(qp_ctx *c, const double *re, const double *im, int n) {
-    if (!c) return QP_ERR_ARG;
-    if (!re || !im || n < c->cfg.dkmax) return fail(c, QP_ERR_ARG, "need dkmax influence coefficients");
-    const int dk = c->cfg.dkmax, M = c->cfg.M;
+static qp_status set_eta_one(qp_ctx *c, int inst, const double *re, const double *im) {
+    const int dk = c->cfg.dkmax, M = c->cfg.M, MM = M * M;
     std::vector<double2> e(dk);
     for (int i = 0; i < dk; ++i) {
         if (!std::isfinite(re[i]) || !std::isfinite(im[i])) return fail(c, QP_ERR_ARG, "eta must be finite");
         e[i] = make_double2(re[i], im[i]);
     }
-    QP_CUDA(c, cudaMemcpyAsync(c->ws + c->L.eta, e.data(), dk * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
     const Params &P = c->P;
+    double2 *ed = reinterpret_cast<double2 *>(c->ws + c->L.eta) + (size_t)inst * dk;
+    QP_CUDA(c, cudaMemcpyAsync(ed, e.data(), dk * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
     const double *qd = reinterpret_cast<const double *>(c->ws + c->L.q);
-    const double2 *ed = reinterpret_cast<const double2 *>(c->ws + c->L.eta);
+    double2 *lut = reinterpret_cast<double2 *>(c->ws + c->L.lut) + (size_t)inst * P.lut_stride;
     if (P.nchunks > 0) {
-        k_build_lut<<<64, 256, 0, c->stream>>>(reinterpret_cast<double2 *>(c->ws + c->L.lut),
-                                               reinterpret_cast<float2 *>(c->ws + c->L.lutf),
-                                               reinterpret_cast<float2 *>(c->ws + c->L.lutlo), ed, qd, M, P.bs, P.b,
-                                               dk, P.nchunks);
+        k_build_lut<<<64, 256, 0, c->stream>>>(lut, reinterpret_cast<float2 *>(c->ws + c->L.lutf) + inst * P.lut_stride,
+                                               reinterpret_cast<float2 *>(c->ws + c->L.lutlo) + inst * P.lut_stride, ed,
+                                               qd, M, P.bs, P.b, dk, P.nchunks);
         QP_CUDA(c, cudaGetLastError());
     }
-    k_build_w<<<1, 256, 0, c->stream>>>(reinterpret_cast<double2 *>(c->ws + c->L.wtab),
-                                        reinterpret_cast<float2 *>(c->ws + c->L.wtabf),
+    k_build_w<<<1, 256, 0, c->stream>>>(reinterpret_cast<double2 *>(c->ws + c->L.wtab) + (size_t)inst * MM * MM,
+                                        reinterpret_cast<float2 *>(c->ws + c->L.wtabf) + (size_t)inst * MM * MM,
                                         reinterpret_cast<const double2 *>(c->ws + c->L.uprop), ed, qd, M);
     QP_CUDA(c, cudaGetLastError());
     if (P.nchunks > 0 && P.ndelta > 0) {
-        k_build_etab<<<256, 256, 0, c->stream>>>(reinterpret_cast<double2 *>(c->ws + c->L.etab),
-                                                 reinterpret_cast<const double2 *>(c->ws + c->L.lut),
-                                                 reinterpret_cast<const double *>(c->ws + c->L.deltas), P.ndelta, dk,
-                                                 P.nchunks);
+        k_build_etab<<<256, 256, 0, c->stream>>>(reinterpret_cast<double2 *>(c->ws + c->L.etab) + inst * P.etab_stride,
+                                                 lut, reinterpret_cast<const double *>(c->ws + c->L.deltas), P.ndelta,
+                                                 dk, P.nchunks);
         QP_CUDA(c, cudaGetLastError());
     }
     QP_CUDA(c, cudaStreamSynchronize(c->stream));
+    return QP_OK;
+}
+
+qp_status qp_set_eta(qp_ctx *c, const double *re, const double *im, int n) {
+    if (!c) return QP_ERR_ARG;
+    if (!re || !im || n < c->cfg.dkmax) return fail(c, QP_ERR_ARG, "need dkmax influence coefficients");
+    for (int inst = 0; inst < c->P.n_inst; ++inst) {
+        const qp_status st = set_eta_one(c, inst, re, im);
+        if (st != QP_OK) return st;
+    }
     c->have_eta = true;
     return QP_OK;
+}
+
+qp_status qp_set_eta_instance(qp_ctx *c, int inst, const double *re, const double *im, int n) {
+    if (!c) return QP_ERR_ARG;
+    if (inst < 0 || inst >= c->P.n_inst) return fail(c, QP_ERR_ARG, "instance index out of range");
+    if (!re || !im || n < c->cfg.dkmax) return fail(c, QP_ERR_ARG, "need dkmax influence coefficients");
+    if (!c->have_eta) return fail(c, QP_ERR_STATE, "qp_set_eta (all instances) must come first");
+    return set_eta_one(c, inst, re, im);
 }
 
 qp_status qp_set_mask(qp_ctx *c, const int *positions, int n) {
@@ -1217,36 +1374,47 @@ qp_status qp_set_rho0(qp_ctx *c, const double *re, const double *im) {
     if (!c) return QP_ERR_ARG;
     if (!re) return fail(c, QP_ERR_ARG, "rho0 required");
     if (!c->have_eta) return fail(c, QP_ERR_STATE, "qp_set_eta must come before qp_set_rho0");
-    const int M = c->cfg.M, MM = M * M;
+    const int M = c->cfg.M, MM = M * M, NI = c->P.n_inst;
     const int bs = c->P.bs;
     std::vector<unsigned long long> keys;
-    std::vector<double2> amps, rho(MM);
+    std::vector<double2> amps, rho((size_t)NI * MM);
     for (int a = 0; a < M; ++a)
         for (int b = 0; b < M; ++b) {
             const double x = re[a * M + b], y = im ? im[a * M + b] : 0.0;
             if (!std::isfinite(x) || !std::isfinite(y)) return fail(c, QP_ERR_ARG, "rho0 must be finite");
-            rho[a * M + b] = make_double2(x, y);
-            if (x != 0.0 || y != 0.0) {
-                keys.push_back((unsigned long long)(a | (b << bs)));
-                amps.push_back(make_double2(x, y));
-            }
+            for (int i = 0; i < NI; ++i) rho[(size_t)i * MM + a * M + b] = make_double2(x, y);
         }
+    long long nnz = 0;
+    for (int i = 0; i < NI; ++i)
+        for (int a = 0; a < M; ++a)
+            for (int b = 0; b < M; ++b) {
+                const double2 v = rho[(size_t)i * MM + a * M + b];
+                if (v.x != 0.0 || v.y != 0.0) {
+                    const unsigned long long ib = NI > 1 ? ((unsigned long long)i << c->P.inst_shift) : 0ull;
+                    keys.push_back(ib | (unsigned long long)(a | (b << bs)));
+                    amps.push_back(v);
+                    if (i == 0) ++nnz;
+                }
+            }
     if ((int64_t)keys.size() > c->cfg.max_paths) return fail(c, QP_ERR_CAPACITY, "rho0 exceeds max_paths");
     const size_t n = keys.size();
     QP_CUDA(c, cudaMemcpyAsync(c->P.keys[0], keys.data(), n * 8, cudaMemcpyHostToDevice, c->stream));
+    std::vector<float2> af;
     if (c->cfg.precision == QP_C64) {
-        std::vector<float2> af(n);
+        af.resize(n);
         for (size_t i = 0; i < n; ++i) af[i] = make_float2((float)amps[i].x, (float)amps[i].y);
         QP_CUDA(c, cudaMemcpyAsync(c->P.amps[0], af.data(), n * sizeof(float2), cudaMemcpyHostToDevice, c->stream));
-        QP_CUDA(c, cudaStreamSynchronize(c->stream));
     } else {
         QP_CUDA(c, cudaMemcpyAsync(c->P.amps[0], amps.data(), n * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
     }
     DevState s{};
     s.n_cur = n;
     QP_CUDA(c, cudaMemcpyAsync(c->P.st, &s, sizeof(DevState), cudaMemcpyHostToDevice, c->stream));
-    QP_CUDA(c, cudaMemcpyAsync(c->P.rho_ring, rho.data(), MM * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
-    QP_CUDA(c, cudaMemsetAsync(c->P.rho_ring + MM, 0, MM * sizeof(double2), c->stream));
+    QP_CUDA(c, cudaMemcpyAsync(c->P.rho_ring, rho.data(), (size_t)NI * MM * sizeof(double2), cudaMemcpyHostToDevice,
+                               c->stream));
+    std::vector<long long> kept0(NI, nnz);
+    QP_CUDA(c, cudaMemcpyAsync(c->P.inst_kept, kept0.data(), NI * sizeof(long long), cudaMemcpyHostToDevice, c->stream));
+    QP_CUDA(c, cudaMemsetAsync(c->P.fin_count, 0, sizeof(unsigned int), c->stream));
     StepRec r0{0, 0, 0, (long long)n};
     QP_CUDA(c, cudaMemcpyAsync(c->P.stats_ring, &r0, sizeof(StepRec), cudaMemcpyHostToDevice, c->stream));
     k_clear_table<<<c->nsm * 4, 256, 0, c->stream>>>(c->P.slots, c->P.repk, c->L.tcap);
@@ -1255,6 +1423,24 @@ qp_status qp_set_rho0(qp_ctx *c, const double *re, const double *im) {
     c->have_state = true;
     c->failed = false;
     c->err.clear();
+    return QP_OK;
+}
+
+static qp_status capture_graph(qp_ctx *c, int steps, cudaGraphExec_t *out) {
+    if (*out) {
+        cudaGraphExecDestroy(*out);
+        *out = nullptr;
+    }
+    cudaGraph_t g;
+    QP_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t le = cudaSuccess;
+    for (int s = 0; s < steps && le == cudaSuccess; ++s) le = launch_step(c);
+    cudaError_t ce = cudaStreamEndCapture(c->stream, &g);
+    if (le != cudaSuccess) return fail(c, QP_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(le));
+    if (ce != cudaSuccess) return fail(c, QP_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(ce));
+    cudaError_t ie = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) return fail(c, QP_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(ie));
     return QP_OK;
 }
 
@@ -1270,23 +1456,19 @@ qp_status qp_step(qp_ctx *c, int nsteps) {
         return QP_OK;
     }
     if (c->use_graph) {
-        if (c->graph_dirty || !c->graph) {
-            if (c->graph) {
-                cudaGraphExecDestroy(c->graph);
-                c->graph = nullptr;
+        if (c->graph_dirty || !c->graph1 || (c->graph_steps > 1 && !c->graph)) {
+            qp_status st = capture_graph(c, 1, &c->graph1);
+            if (st != QP_OK) return st;
+            if (c->graph_steps > 1) {
+                st = capture_graph(c, c->graph_steps, &c->graph);
+                if (st != QP_OK) return st;
             }
-            cudaGraph_t g;
-            QP_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-            cudaError_t le = launch_step(c);
-            cudaError_t ce = cudaStreamEndCapture(c->stream, &g);
-            if (le != cudaSuccess) return fail(c, QP_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(le));
-            if (ce != cudaSuccess) return fail(c, QP_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(ce));
-            cudaError_t ie = cudaGraphInstantiate(&c->graph, g, 0);
-            cudaGraphDestroy(g);
-            if (ie != cudaSuccess) return fail(c, QP_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(ie));
             c->graph_dirty = false;
         }
-        for (int s = 0; s < nsteps; ++s) QP_CUDA(c, cudaGraphLaunch(c->graph, c->stream));
+        int left = nsteps;
+        if (c->graph_steps > 1)
+            for (; left >= c->graph_steps; left -= c->graph_steps) QP_CUDA(c, cudaGraphLaunch(c->graph, c->stream));
+        for (; left > 0; --left) QP_CUDA(c, cudaGraphLaunch(c->graph1, c->stream));
     } else {
         for (int s = 0; s < nsteps; ++s) {
             cudaError_t e = launch_step(c);
@@ -1338,18 +1520,35 @@ qp_status qp_read_rho(qp_ctx *c, int64_t t0, int count, double *re, double *im) 
     if (r != QP_OK) return r;
     const int64_t R = c->cfg.rho_history, tc = (int64_t)s.t;
     if (t0 < 0 || t0 + count - 1 > tc || t0 <= tc - R) return fail(c, QP_ERR_ARG, "step outside the kept rho history");
-    const int MM = c->cfg.M * c->cfg.M;
-    std::vector<double2> buf(MM);
+    const size_t per = (size_t)c->P.n_inst * c->cfg.M * c->cfg.M;
+    std::vector<double2> buf(per);
     for (int k = 0; k < count; ++k) {
         const int64_t t = t0 + k;
-        QP_CUDA(c, cudaMemcpyAsync(buf.data(), c->P.rho_ring + (size_t)(t % R) * MM, MM * sizeof(double2),
+        QP_CUDA(c, cudaMemcpyAsync(buf.data(), c->P.rho_ring + (size_t)(t % R) * per, per * sizeof(double2),
                                    cudaMemcpyDeviceToHost, c->stream));
         QP_CUDA(c, cudaStreamSynchronize(c->stream));
-        for (int i = 0; i < MM; ++i) {
-            re[(size_t)k * MM + i] = buf[i].x;
-            im[(size_t)k * MM + i] = buf[i].y;
+        for (size_t i = 0; i < per; ++i) {
+            re[(size_t)k * per + i] = buf[i].x;
+            im[(size_t)k * per + i] = buf[i].y;
         }
     }
+    return QP_OK;
+}
+
+qp_status qp_read_instance_counts(qp_ctx *c, int64_t t, int64_t *kept) {
+    if (!c) return QP_ERR_ARG;
+    if (!kept) return fail(c, QP_ERR_ARG, "bad output");
+    if (!c->have_state) return fail(c, QP_ERR_STATE, "no state");
+    DevState s;
+    qp_status r = read_state(c, &s);
+    if (r != QP_OK) return r;
+    const int64_t R = c->cfg.rho_history, tc = (int64_t)s.t;
+    if (t < 0 || t > tc || t <= tc - R) return fail(c, QP_ERR_ARG, "step outside the kept history");
+    std::vector<long long> buf(c->P.n_inst);
+    QP_CUDA(c, cudaMemcpyAsync(buf.data(), c->P.inst_kept + (size_t)(t % R) * c->P.n_inst,
+                               c->P.n_inst * sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
+    QP_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (int i = 0; i < c->P.n_inst; ++i) kept[i] = buf[i];
     return QP_OK;
 }
 
@@ -1429,6 +1628,152 @@ qp_status qp_profile_steps(qp_ctx *c, int nsteps, double *kernel_ms, int nk) {
     return read_state(c, &ds);
 }
 
+qp_status qp_get_tuning(qp_ctx *c, qp_tuning *out) {
+    if (!c || !out) return QP_ERR_ARG;
+    out->mode = c->use_persistent ? QP_LAUNCH_PERSISTENT : QP_LAUNCH_GRAPH;
+    out->insert_blocks_per_sm = c->bps_ins;
+    out->expand_blocks_per_sm = c->bps_exp;
+    out->persistent_blocks = c->persist_grid;
+    out->graph_steps = c->graph_steps;
+    out->table_log2 = (int)c->P.tcap_log2;
+    return QP_OK;
+}
+
+qp_status qp_set_tuning(qp_ctx *c, const qp_tuning *t) {
+    if (!c || !t) return QP_ERR_ARG;
+    if (t->mode != QP_LAUNCH_GRAPH && t->mode != QP_LAUNCH_PERSISTENT) return fail(c, QP_ERR_ARG, "unknown mode");
+    if (t->mode == QP_LAUNCH_PERSISTENT && c->persist_max <= 0)
+        return fail(c, QP_ERR_ARG, "cooperative launch not available on this device");
+    if (t->insert_blocks_per_sm < 1 || t->insert_blocks_per_sm > 32 || t->expand_blocks_per_sm < 1 ||
+        c->nsm * t->expand_blocks_per_sm > kMaxExpandBlocks)
+        return fail(c, QP_ERR_ARG, "blocks per SM out of range");
+    if (t->mode == QP_LAUNCH_PERSISTENT && (t->persistent_blocks < 1 || t->persistent_blocks > c->persist_max))
+        return fail(c, QP_ERR_ARG, "persistent blocks out of range (co-residency limit)");
+    if (t->graph_steps < 1 || t->graph_steps > 1024) return fail(c, QP_ERR_ARG, "graph_steps out of range");
+    if (t->table_log2 < 4 || t->table_log2 > (int)c->L.tcap_log2)
+        return fail(c, QP_ERR_ARG, "table_log2 out of range (at most the workspace's table)");
+    c->use_persistent = t->mode == QP_LAUNCH_PERSISTENT;
+    c->bps_ins = t->insert_blocks_per_sm;
+    c->bps_exp = t->expand_blocks_per_sm;
+    if (c->use_persistent) c->persist_grid = t->persistent_blocks;
+    c->graph_steps = t->graph_steps;
+    c->P.tcap_log2 = (unsigned)t->table_log2;
+    c->P.tcap_mask = (1ull << t->table_log2) - 1ull;
+    set_mask_params(c);   // the direct-index decision depends on the table size
+    c->graph_dirty = true;
+    return QP_OK;
+}
+
+namespace {
+std::mutex g_tune_mutex;
+std::map<std::string, qp_tuning> g_tune_cache;   // problem bucket -> best tuning
+
+std::string tune_key(qp_ctx *c, long long n_paths) {
+    int lg = 0;
+    while ((1ll << lg) < std::max(1ll, n_paths)) ++lg;
+    char buf[256];
+    snprintf(buf, sizeof(buf), "M%d dk%d ni%d p%d th%d pm%llx n2^%d sm%d", c->cfg.M, c->cfg.dkmax, c->P.n_inst,
+             c->cfg.precision, c->cfg.theta > 0.0 ? 1 : 0, c->P.pmask, lg, c->nsm);
+    return buf;
+}
+}  // namespace
+
+qp_status qp_autotune(qp_ctx *c, int trial_steps, int use_cache, qp_tuning *best, double *best_ms_per_step) {
+    if (!c) return QP_ERR_ARG;
+    if (trial_steps < 1 || trial_steps > 10000) return fail(c, QP_ERR_ARG, "trial_steps out of range");
+    if (!c->have_state) return fail(c, QP_ERR_STATE, "qp_set_rho0 must come before qp_autotune");
+    if (c->failed) return fail(c, QP_ERR_STATE, "context holds a device error; call qp_set_rho0");
+    int64_t t0 = 0, n0 = 0;
+    qp_status st = qp_current(c, &t0, &n0);
+    if (st != QP_OK) return st;
+    const std::string key = tune_key(c, n0);
+    if (use_cache) {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            st = qp_set_tuning(c, &it->second);
+            if (st == QP_OK) {
+                if (best) *best = it->second;
+                if (best_ms_per_step) *best_ms_per_step = -1.0;   // taken from the cache, not measured now
+            }
+            return st;
+        }
+    }
+    // candidates: the step-kernel graph with several launch shapes and table
+    // sizes, and the persistent kernel with several grid sizes
+    std::vector<qp_tuning> cand;
+    const int tl = (int)c->L.tcap_log2;
+    std::vector<int> tables{tl};
+    if (!c->P.dense)   // hashed tables: smaller tables trade probes for locality
+        for (int d = 1; d <= 2; ++d) {
+            long long need = 2;
+            while (need < 2 * std::max<long long>(n0, 1)) need <<= 1;
+            if ((1ll << (tl - d)) >= need) tables.push_back(tl - d);
+        }
+    const int gs = 8;
+    for (int tb : tables)
+        for (int bi : {2, 4, 8})
+            for (int be : {2, 4, 8}) {
+                if (c->nsm * be > kMaxExpandBlocks) continue;
+                cand.push_back(qp_tuning{QP_LAUNCH_GRAPH, bi, be, c->persist_grid, gs, tb});
+            }
+    if (c->persist_max > 0)
+        for (int pb : {1, 2, 4}) {
+            const int blocks = std::min(c->persist_max, pb * c->nsm);
+            cand.push_back(qp_tuning{QP_LAUNCH_PERSISTENT, 4, 4, blocks, gs, tl});
+        }
+    qp_tuning save;
+    qp_get_tuning(c, &save);
+    cudaEvent_t e0, e1;
+    QP_CUDA(c, cudaEventCreate(&e0));
+    QP_CUDA(c, cudaEventCreate(&e1));
+    double best_ms = 1e300;
+    qp_tuning bt = save;
+    for (const qp_tuning &cd : cand) {
+        if (qp_set_tuning(c, &cd) != QP_OK) continue;
+        if ((st = qp_step(c, 1)) != QP_OK) break;   // warm-up (captures the graphs)
+        cudaEventRecord(e0, c->stream);
+        if ((st = qp_step(c, trial_steps)) != QP_OK) break;
+        cudaEventRecord(e1, c->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) { st = fail(c, QP_ERR_CUDA, "autotune sync"); break; }
+        DevState ds;
+        if ((st = read_state(c, &ds)) != QP_OK) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms / trial_steps < best_ms) {
+            best_ms = ms / trial_steps;
+            bt = cd;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != QP_OK) {
+        qp_set_tuning(c, &save);
+        return st;
+    }
+    st = qp_set_tuning(c, &bt);
+    if (st != QP_OK) return st;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        g_tune_cache[key] = bt;
+    }
+    if (best) *best = bt;
+    if (best_ms_per_step) *best_ms_per_step = best_ms;
+    return QP_OK;
+}
+
+qp_status qp_test_stall_barrier(qp_ctx *c) {
+    if (!c) return QP_ERR_ARG;
+    if (!c->have_state) return fail(c, QP_ERR_STATE, "no state");
+    // an arrival count that the last block can never complete: the next
+    // persistent launch waits at its first grid barrier until the bounded
+    // wait gives up
+    const unsigned int poison = 0x40000000u;
+    QP_CUDA(c, cudaMemcpyAsync(&c->P.st->bar_count, &poison, sizeof(poison), cudaMemcpyHostToDevice, c->stream));
+    QP_CUDA(c, cudaStreamSynchronize(c->stream));
+    return QP_OK;
+}
+
 const char *qp_last_error(const qp_ctx *c) { return c ? c->err.c_str() : "null context"; }
 
 }  // extern "C"
@@ -1477,8 +1822,10 @@ struct NaSetup {            // small set-up inputs, passed by value
     unsigned long long t, n_in;
 };
 
-__global__ void k_na_setup(NaSetup s, double2 *eta, double *q, double2 *U, double *deltas, DevState *st) {
+__global__ void k_na_setup(NaSetup s, double2 *eta, double *q, double2 *U, double *deltas, DevState *st,
+                           unsigned int *fin_count) {
     const int i = threadIdx.x;
+    if (i == 0) *fin_count = 0;
     if (i < s.dkmax) eta[i] = s.eta[i];
     if (i < s.M) q[i] = s.q[i];
     if (i < s.M * s.M) U[i] = s.U[i];
@@ -1584,7 +1931,10 @@ extern "C" qp_status qp_step_noalloc(const qp_config *cfg, const double *eta_re,
     P.max_paths = cap_out;
     P.max_groups = kNaMaxGroups;
     P.rho_hist = 2;
-    {   // pre-merge positions P' = {p-1 : p in P, p >= 1} plus 0, and dense runs
+    P.n_inst = 1;
+    P.inst_shift = P.b * dk;
+    P.instmask = 0ull;
+    {   // pre-merge positions P'' = {p-1 : p in P, p >= 1} plus 0, and dense runs
         bool inPp[kNaMaxDk] = {};
         inPp[0] = true;
         for (int p = 1; p < dk; ++p)
@@ -1666,6 +2016,8 @@ extern "C" qp_status qp_step_noalloc(const qp_config *cfg, const double *eta_re,
     P.rho_ring = reinterpret_cast<double2 *>(take(2 * 16 * sizeof(double2)));
     P.rho_part = reinterpret_cast<double2 *>(take((size_t)2 * kMaxExpandBlocks * 16 * sizeof(double2)));
     P.stats_ring = reinterpret_cast<StepRec *>(take(2 * sizeof(StepRec)));
+    P.inst_kept = reinterpret_cast<long long *>(take(2 * sizeof(long long)));
+    P.fin_count = reinterpret_cast<unsigned int *>(take(sizeof(unsigned int)));
     if (off > kNaBytes) return QP_ERR_OOM;
     P.lut = lut;
     P.lutf = lutf;
@@ -1681,7 +2033,7 @@ extern "C" qp_status qp_step_noalloc(const qp_config *cfg, const double *eta_re,
     P.amps[in ^ 1] = d_amps_out;
 
     // set-up (every call: the array keeps the previous call's contents)
-    k_na_setup<<<1, 32, 0, stream>>>(su, etad, qd, Ud, deltad, st);
+    k_na_setup<<<1, 32, 0, stream>>>(su, etad, qd, Ud, deltad, st, P.fin_count);
     k_clear_table<<<nsm * 4, 256, 0, stream>>>(P.slots, P.repk, 1ull << kNaTcapLog2);
     if (P.nchunks > 0)
         k_build_lut<<<64, 256, 0, stream>>>(lut, lutf, lutlo, etad, qd, M, P.bs, P.b, dk, P.nchunks);
@@ -1693,9 +2045,9 @@ extern "C" qp_status qp_step_noalloc(const qp_config *cfg, const double *eta_re,
     k_insert<double2><<<g_ins, kInsertThreads, 0, stream>>>(P);
     k_tiebreak<double2><<<g_ins, 256, 0, stream>>>(P);
     switch (M) {
-        case 2: k_expand<2, false><<<g_exp, kExpandThreads, 0, stream>>>(P); break;
-        case 3: k_expand<3, false><<<g_exp, kExpandThreads, 0, stream>>>(P); break;
-        default: k_expand<4, false><<<g_exp, kExpandThreads, 0, stream>>>(P); break;
+        case 2: k_expand<2, false, false><<<g_exp, kExpandThreads, 0, stream>>>(P); break;
+        case 3: k_expand<3, false, false><<<g_exp, kExpandThreads, 0, stream>>>(P); break;
+        default: k_expand<4, false, false><<<g_exp, kExpandThreads, 0, stream>>>(P); break;
     }
     k_finalize<<<1, 256, 0, stream>>>(P, MM, g_exp);
     if (cudaGetLastError() != cudaSuccess) return QP_ERR_CUDA;
