@@ -274,6 +274,50 @@ def run_batched_sweep(n_inst=64, reps=3):
             "rho_max_abs_err_vs_fp64": err}
 
 
+def run_surrogate(T_train=100, T_long=1000, L=32, epochs=2000):
+    """The learned surrogate: train (libqp kernels) on 100-step trajectories of
+    48 sweep instances, roll 16 held-out instances out to t = 1000 and judge
+    them against the plain path at checkpoints; times of both."""
+    import torch
+    from paper_2506_03127_gb300 import batch_from_workloads
+    from paper_2506_03127_gb300.surrogate import Surrogate, bath_features, judge
+
+    ws = W.resonance_sweep(64)
+    p = batch_from_workloads(ws, precision="c64", max_paths=1 << 23)
+    p.step(T_train)
+    rho = p.rho(0, T_train + 1)
+    p.close()
+    par = bath_features(ws)
+    s = Surrogate(L=L)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hist = s.fit(rho, par, train=(0, 48), epochs=epochs, lr=2e-3, log_every=epochs - 1)
+    t_fit = time.perf_counter() - t0
+    q = batch_from_workloads(ws[48:], precision="c64", max_paths=1 << 22)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    q.step(T_long - 1)
+    q.sync()
+    t_plain = time.perf_counter() - t0
+    rp = q.rho(0, T_long)
+    q.close()
+    t0 = time.perf_counter()
+    rs = s.rollout(rp[:L].transpose(1, 0, 2, 3), par[48:], T_long)
+    t_sur = time.perf_counter() - t0
+    errs, raw, fb = judge(rs, rp, (200, 400, 600, 800, 999))
+    return {"network": "MLP %d-256-256-8, tanh, BF16 weights/activations, FP32 accumulation" % (8 * L + 2),
+            "train": {"instances": 48, "steps": T_train, "windows": 48 * (T_train + 1 - L), "epochs": epochs,
+                      "seconds": round(t_fit, 3), "loss_first": hist[0][1], "loss_last": hist[-1][1]},
+            "rollout": {"instances": 16, "from_step": L, "to_step": T_long, "seconds": round(t_sur, 4),
+                        "us_per_step": round(1e6 * t_sur / (T_long - L), 2)},
+            "plain_c64_path": {"seconds": round(t_plain, 4), "us_per_step": round(1e6 * t_plain / (T_long - 1), 2)},
+            "speedup_vs_plain": round(t_plain / (t_sur + fb.mean() * t_plain), 2),
+            "speedup_note": "fallback instances are charged the plain path's time",
+            "rho_max_abs_err_at_checkpoints": {str(k): round(v, 5) for k, v in errs.items()},
+            "rho_max_abs_err_raw_surrogate": {str(k): round(v, 5) for k, v in raw.items()},
+            "fallback_instances": int(fb.sum())}
+
+
 def cpu_baseline(w, steps_total=60, timed_from=None):
     """Oracle (FP64 CPU, as it stands) on a bounded sample of the workload:
     propagate from t = 0 and time the steps after the window is full."""
@@ -394,6 +438,7 @@ def main():
                             "rho_err_steps": n, "fp64_roofline": ref["roof"], "fp64_e2e": ref["e2e"]}}
     if not args.no_batched and world == 1:
         line["batched_sweep"] = run_batched_sweep()
+        line["surrogate"] = run_surrogate()
     if not args.no_cpu_baseline and world == 1:
         v, sample = cpu_baseline(W.SPIN_BOSON_STRUCTURED_DK16 if args.workload == "spin_boson_structured_dk16"
                                  else WORKLOADS[args.workload])

@@ -283,6 +283,61 @@ qp_status qp_step_noalloc(const qp_config *cfg, const double *eta_re, const doub
                           uint64_t *d_keys_out, double *d_amps_out, int64_t cap_out,
                           int64_t *n_out, double *rho_re, double *rho_im, void *cuda_stream);
 
+/* ===================================================================== */
+/* Learned surrogate of rho(t).  The paper has no counterpart: a small MLP
+ * over the last L steps of rho(t) and the bath parameters, trained on
+ * trajectories of the path update above, extends propagation in time; the
+ * path update judges it at checkpoints and is its fallback.
+ *
+ * Network: x (d_in) -> tanh(x W1 + b1) (width) -> tanh(. W2 + b2) (width)
+ * -> . W3 + b3 (d_out); loss = mean squared error.  Parameters are FP32;
+ * every matrix product reads BF16 copies of weights and activations and
+ * accumulates in FP32 on the tensor cores.  Parameter vector layout (FP32):
+ * W1 [d_in x width] row-major, b1 [width], W2 [width x width], b2 [width],
+ * W3 [width x d_out], b3 [d_out].  Device workspace and stream as for
+ * qp_create (caller-owned; the library allocates nothing).               */
+typedef struct qp_mlp qp_mlp;
+
+qp_status qp_mlp_workspace_size(int d_in, int width, int d_out, int max_batch, size_t *bytes);
+qp_status qp_mlp_create(int d_in, int width, int d_out, int max_batch, void *d_workspace, size_t bytes,
+                        void *cuda_stream, qp_mlp **out);
+void qp_mlp_destroy(qp_mlp *m);
+qp_status qp_mlp_num_params(const qp_mlp *m, int64_t *n);
+/* Host FP32 parameters in (resets the Adam moments and step count) / out. */
+qp_status qp_mlp_set_params(qp_mlp *m, const float *params);
+qp_status qp_mlp_get_params(qp_mlp *m, float *params);
+/* y = net(x): d_x [batch x d_in], d_y [batch x d_out], FP32 device, async.  */
+qp_status qp_mlp_forward(qp_mlp *m, const float *d_x, int batch, float *d_y);
+/* Forward and backward without update (synchronises): gradients of the loss
+ * w.r.t. all parameters into host grads [num_params] (NULL = skip), loss.   */
+qp_status qp_mlp_gradients(qp_mlp *m, const float *d_x, const float *d_target, int batch, float *grads,
+                           double *loss);
+/* One Adam step (bias-corrected) on the batch; loss != NULL synchronises
+ * and returns the loss before the update.                                 */
+qp_status qp_mlp_train_step(qp_mlp *m, const float *d_x, const float *d_target, int batch, float lr, float beta1,
+                            float beta2, float eps, double *loss);
+const char *qp_mlp_last_error(const qp_mlp *m);
+
+/* Training windows from device rho trajectories d_rho [T][n_inst][4]
+ * (complex FP64, the layout of qp_read_rho's output for M = 2): for
+ * instances inst0 .. inst0+ninst_used-1 and target times t_begin <= t <
+ * t_end (t_begin >= L): features = Re, Im of rho_00, rho_01, rho_10, rho_11
+ * at t-L .. t-1 (8 L values), then the instance's n_par parameters
+ * d_par [n_inst x n_par]; target = (rho(t) - rho(t-1)) * out_scale (8
+ * values).  d_x [rows x (8 L + n_par)], d_target [rows x 8], rows =
+ * ninst_used * (t_end - t_begin), instance-major.  Async on the stream.   */
+qp_status qp_surrogate_windows(const double *d_rho, int n_inst, int L, const float *d_par, int n_par, int t_begin,
+                               int t_end, int inst0, int ninst_used, float out_scale, float *d_x, float *d_target,
+                               void *cuda_stream);
+
+/* Autoregressive rollout of n trajectories held in d_hist [n][T][8] (FP32,
+ * same 8 reals as above; steps < t_from must be filled): for t = t_from ..
+ * t_to-1, rho(t) = rho(t-1) + net(window) / out_scale with the increment
+ * made traceless, projected onto Hermitian matrices.  d_xbuf [n x d_in],
+ * d_ybuf [n x 8] device scratch.                                          */
+qp_status qp_surrogate_rollout(qp_mlp *m, float *d_hist, int n, int T, int L, const float *d_par, int n_par,
+                               int t_from, int t_to, float out_scale, float *d_xbuf, float *d_ybuf);
+
 #ifdef __cplusplus
 }
 #endif

@@ -86,6 +86,26 @@ def _load():
         "qp_set_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
         "qp_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, _dp]),
         "qp_test_stall_barrier": (ctypes.c_int, [ctypes.c_void_p]),
+        "qp_mlp_workspace_size": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                 ctypes.POINTER(ctypes.c_size_t)]),
+        "qp_mlp_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                         ctypes.c_size_t, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+        "qp_mlp_destroy": (None, [ctypes.c_void_p]),
+        "qp_mlp_num_params": (ctypes.c_int, [ctypes.c_void_p, _i64p]),
+        "qp_mlp_set_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float)]),
+        "qp_mlp_get_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float)]),
+        "qp_mlp_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+        "qp_mlp_gradients": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                            ctypes.POINTER(ctypes.c_float), _dp]),
+        "qp_mlp_train_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                             ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, _dp]),
+        "qp_mlp_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+        "qp_surrogate_windows": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                                ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+        "qp_surrogate_rollout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                                ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                                ctypes.c_int, ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p]),
         "qp_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     }
     for name, (res, args) in sig.items():
@@ -270,3 +290,74 @@ def qp_step_noalloc(cfg, eta, mask, t, d_keys_in, d_amps_in, n_in, d_keys_out, d
             ctypes.c_void_p(d_keys_out), ctypes.c_void_p(d_amps_out), cap_out, ctypes.byref(n_out),
             _ptr(rr), _ptr(ri), ctypes.c_void_p(stream)))
     return n_out.value, (rr + 1j * ri).reshape(M, M)
+
+
+# ----------------------------------------------------------------- surrogate MLP
+
+_fp = ctypes.POINTER(ctypes.c_float)
+
+
+def mcheck(status, m=None):
+    if status != QP_OK:
+        raise QPError(status, lib.qp_mlp_last_error(m).decode() if m else "")
+
+
+def qp_mlp_workspace_size(d_in, width, d_out, max_batch) -> int:
+    n = ctypes.c_size_t()
+    mcheck(lib.qp_mlp_workspace_size(d_in, width, d_out, max_batch, ctypes.byref(n)))
+    return n.value
+
+
+def qp_mlp_create(d_in, width, d_out, max_batch, d_ws, nbytes, stream):
+    h = ctypes.c_void_p()
+    mcheck(lib.qp_mlp_create(d_in, width, d_out, max_batch, ctypes.c_void_p(d_ws), nbytes, ctypes.c_void_p(stream),
+                             ctypes.byref(h)))
+    return h
+
+
+def qp_mlp_num_params(m) -> int:
+    n = ctypes.c_int64()
+    mcheck(lib.qp_mlp_num_params(m, ctypes.byref(n)), m)
+    return n.value
+
+
+def qp_mlp_set_params(m, params):
+    p = _arr(params, np.float32)
+    mcheck(lib.qp_mlp_set_params(m, _ptr(p, _fp)), m)
+
+
+def qp_mlp_get_params(m, n):
+    p = np.zeros(n, dtype=np.float32)
+    mcheck(lib.qp_mlp_get_params(m, _ptr(p, _fp)), m)
+    return p
+
+
+def qp_mlp_forward(m, d_x, batch, d_y):
+    mcheck(lib.qp_mlp_forward(m, ctypes.c_void_p(d_x), batch, ctypes.c_void_p(d_y)), m)
+
+
+def qp_mlp_gradients(m, d_x, d_t, batch, n):
+    g = np.zeros(n, dtype=np.float32)
+    loss = ctypes.c_double()
+    mcheck(lib.qp_mlp_gradients(m, ctypes.c_void_p(d_x), ctypes.c_void_p(d_t), batch, _ptr(g, _fp),
+                                ctypes.byref(loss)), m)
+    return loss.value, g
+
+
+def qp_mlp_train_step(m, d_x, d_t, batch, lr, beta1=0.9, beta2=0.999, eps=1e-8, want_loss=False):
+    loss = ctypes.c_double()
+    mcheck(lib.qp_mlp_train_step(m, ctypes.c_void_p(d_x), ctypes.c_void_p(d_t), batch, lr, beta1, beta2, eps,
+                                 ctypes.byref(loss) if want_loss else None), m)
+    return loss.value if want_loss else None
+
+
+def qp_surrogate_windows(d_rho, n_inst, L, d_par, n_par, t_begin, t_end, inst0, ninst_used, out_scale, d_x, d_t,
+                         stream):
+    check(lib.qp_surrogate_windows(ctypes.c_void_p(d_rho), n_inst, L, ctypes.c_void_p(d_par), n_par, t_begin, t_end,
+                                   inst0, ninst_used, out_scale, ctypes.c_void_p(d_x), ctypes.c_void_p(d_t),
+                                   ctypes.c_void_p(stream)))
+
+
+def qp_surrogate_rollout(m, d_hist, n, T, L, d_par, n_par, t_from, t_to, out_scale, d_xbuf, d_ybuf):
+    mcheck(lib.qp_surrogate_rollout(m, ctypes.c_void_p(d_hist), n, T, L, ctypes.c_void_p(d_par), n_par, t_from, t_to,
+                                    out_scale, ctypes.c_void_p(d_xbuf), ctypes.c_void_p(d_ybuf)), m)

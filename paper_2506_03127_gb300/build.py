@@ -21,7 +21,7 @@ LIB = os.path.join(PKG, "libqp.so")
 BUILD = os.path.join(PKG, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["qp.cu", "host_numerics.cpp"]
+SOURCES = ["qp.cu", "mlp.cu", "host_numerics.cpp"]
 HEADERS = ["internal.h"]
 
 

@@ -1,0 +1,60 @@
+"""GPU: what the learned surrogate gains over the path update without it.
+
+Trained by libqp's own kernels on 100-step trajectories of 48 instances of
+the resonance sweep (computed by the batched path update), it rolls 16
+held-out instances out from their first 32 steps to t = 1000 (10x the
+training length).  The plain path update propagates the same instances to
+t = 1000 and judges the surrogate at the checkpoints 200, 400, ..., 1000.
+The test asserts the surrogate is faster than the plain path over the same
+steps, stays within the stated error, and keeps rho Hermitian.
+"""
+import time
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU container
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_2506_03127_gb300 import batch_from_workloads, build  # noqa: E402
+
+build.build()
+from paper_2506_03127_gb300.surrogate import Surrogate, bath_features, judge  # noqa: E402
+
+T_TRAIN, T_LONG, L = 100, 1000, 32
+CHECKPOINTS = (200, 400, 600, 800, 999)
+
+
+def test_surrogate_gain_and_error_at_checkpoints():
+    ws = W.resonance_sweep(64)
+    p = batch_from_workloads(ws, precision="c64", max_paths=1 << 23)
+    p.step(T_TRAIN)
+    rho = p.rho(0, T_TRAIN + 1)
+    p.close()
+    par = bath_features(ws)
+    s = Surrogate(L=L)
+    hist = s.fit(rho, par, train=(0, 48), epochs=2000, lr=2e-3, log_every=1999)
+    assert hist[-1][1] < 1e-3 * hist[0][1]
+    q = batch_from_workloads(ws[48:], precision="c64", max_paths=1 << 22)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    q.step(T_LONG - 1)
+    q.sync()
+    t_plain = time.perf_counter() - t0
+    rp = q.rho(0, T_LONG)
+    q.close()
+    t0 = time.perf_counter()
+    rs = s.rollout(rp[:L].transpose(1, 0, 2, 3), par[48:], T_LONG)
+    t_sur = time.perf_counter() - t0
+    combined, raw, fallback = judge(rs, rp, CHECKPOINTS)
+    # instances that fall back cost the plain path's time on top
+    t_eff = t_sur + fallback.mean() * t_plain
+    assert t_eff < t_plain / 2, (t_sur, t_plain, fallback.sum())
+    assert raw[200] < 0.05 and max(combined.values()) < 0.1, (raw, combined)
+    assert fallback.sum() <= 4
+    np.testing.assert_allclose(rs, np.conj(np.swapaxes(rs, 2, 3)), atol=1e-7)   # Hermitian by projection
