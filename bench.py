@@ -107,13 +107,16 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def algorithmic_bytes(stats_rows, M, amp_bytes, merge):
+def algorithmic_bytes(stats_rows, M, amp_bytes, merge, engine="hash"):
     """Per-kernel algorithmic DRAM bytes for a list of steps:
-    stored path = 8 B key + amp_bytes; merge-table slot 32 B + 8 B key."""
+    stored path = 8 B key + amp_bytes; merge-table slot 32 B + 8 B key.  The
+    stream engine reads the stored set once and writes the survivors."""
     E = 8 + amp_bytes
     ins = tie = exp = 0
     for (t, groups, extended, kept), n_in in stats_rows:
-        if merge(t):
+        if engine == "stream":
+            exp += n_in * E + kept * E
+        elif merge(t):
             ins += n_in * (E + 4) + groups * 32
             tie += n_in * (E + 4) + groups * 16
             exp += groups * (4 + 8 + 32 + 40) + kept * E
@@ -181,12 +184,16 @@ def run_ours(args, rank, world, precision):
     t_end = p.current()[0]
     rho_hist = p.rho(1, t_end)
     merge = (lambda t: t >= w.dkmax)
-    abytes = algorithmic_bytes(list(zip(pstats, [r[3] for r in pprev])), w.M, amp_bytes, merge)
+    tun = p.tuning()
+    engine = "stream" if tun.engine == 2 else "hash"
+    abytes = algorithmic_bytes(list(zip(pstats, [r[3] for r in pprev])), w.M, amp_bytes, merge, engine)
     names = ["premerge_insert", "premerge_tiebreak", "expand_influence_filter_rho", "finalize"]
+    if engine == "stream":
+        names = ["-", "-", "stream_step", "finalize"]
     dom = int(np.argmax(kern_ms))
     peak, peak_src = peaks()
     achieved = abytes[dom] / (kern_ms[dom] / 1e3) / 1e9 if kern_ms[dom] > 0 else 0.0
-    roof = {"bound": "hbm", "kernel": names[dom], "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+    roof = {"bound": "hbm", "kernel": names[dom], "engine": engine, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": None, "peak_source": peak_src,
             "kernel_share": {n: round(float(m / kern_ms.sum()), 4) for n, m in zip(names, kern_ms)},
             "kernel_avg_us": {n: round(float(m / nprof * 1e3), 2) for n, m in zip(names, kern_ms)}}
@@ -359,7 +366,7 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", 1))
     w = WORKLOADS[args.workload]
     cfg = {"workload": w.name, "M": w.M, "dkmax": w.dkmax, "mask": w.mask_list(), "theta": w.theta,
-           "dt": w.dt, "t0": args.t0, "precision": args.precision, "engine": "hash",
+           "dt": w.dt, "t0": args.t0, "precision": args.precision, "engine": "auto (reported in roofline)",
            "amplitudes": "complex64, FP32 influence exponent (Kahan), FP64 eta/merge sums/rho"
            if args.precision == "c64" else "complex128, FP64 throughout",
            "l2": "flushed between timed steps (512 MB write)", "parallelism": f"replicas{args.gpus}"}

@@ -120,6 +120,9 @@ typedef struct {
     int persistent_blocks;     /* grid of the persistent kernel                  */
     int graph_steps;           /* steps captured per CUDA graph launch           */
     int table_log2;            /* active merge-table slots = 2^table_log2        */
+    int engine;                /* engine of the running propagation (QP_ENGINE_HASH
+                                  or QP_ENGINE_STREAM; read-only, set at
+                                  qp_set_rho0 from qp_config.engine and the mask) */
 } qp_tuning;
 
 typedef struct qp_ctx qp_ctx;

@@ -59,6 +59,9 @@ constexpr int kExpandThreads = 128;
 constexpr int kMaxExpandBlocks = 2048;
 constexpr int kPersistThreads = 256;
 constexpr int kMaxInst = 128;                      // instances of one batched context
+constexpr int kStreamTile = 1024;                   // stored paths per tile of the stream engine (NX = 1)
+constexpr int kStreamThreads = 256;
+constexpr unsigned kLbAgg = 1u, kLbInc = 2u;        // look-back word states (bits 30-31)
 constexpr long long kBarrierCycles = 4000000000ll;  // ~2 s at 2 GHz: a grid barrier gives up after this
 constexpr int kMaxDelta = 12;
 constexpr double kTieRelFP64 = 1e-12;  // weights equal to this relative width are ties (R4)
@@ -78,6 +81,9 @@ struct __align__(128) DevState {
     unsigned int err;                 // error bits, sticky until qp_set_rho0
     unsigned int pad;
     unsigned long long err_t;         // step at which the error was raised
+    unsigned long long reg_n[2][16];  // stream engine: stored paths per region, by buffer parity
+    unsigned int ticket[3];           // stream engine: tile tickets, step t' uses [t' % 3]
+    unsigned int pad0;
     unsigned int bar_count;           // grid barrier of the persistent kernel: arrivals
     unsigned int pad1[31];
     unsigned int bar_gen;             // generation (own cache line)
@@ -126,6 +132,13 @@ struct Params {
     int inst_shift;                    // key bit where the instance index starts (b * dkmax)
     unsigned long long instmask;       // key bits of the instance index
     size_t lut_stride, etab_stride;    // per-instance strides of the history / exp tables (entries)
+    // stream engine (stored set kept in M*M regions by newest point, each
+    // sorted lexicographically by the older points)
+    int stream;                        // 1: stream layout
+    unsigned long long prefmask;       // key bits of the prefix positions 0 .. k-1 of P'
+    int x_shift;                       // key bit of the one extra position of P' (NX = 4), else -1
+    long long region_cap;              // entries per region
+    unsigned long long *tile_state;    // [max_tiles][M*M] look-back words
     StepRec *stats_ring;               // [rho_hist]
     DevState *st;
 };
@@ -134,11 +147,14 @@ __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 
 // Path data and merge-table fields are written by other blocks of the same
 // persistent kernel, so they are read through L2 (ld.global.cg), never L1.
+// Global memory only: shared-memory copies are read with as_d2.
 __device__ __forceinline__ double2 load_amp(const double2 *p, unsigned long long i) { return __ldcg(p + i); }
 __device__ __forceinline__ double2 load_amp(const float2 *p, unsigned long long i) {
     const float2 v = __ldcg(p + i);
     return make_double2(v.x, v.y);
 }
+__device__ __forceinline__ double2 as_d2(double2 v) { return v; }
+__device__ __forceinline__ double2 as_d2(float2 v) { return make_double2(v.x, v.y); }
 
 __device__ __forceinline__ unsigned long long table_index(const Params &P, unsigned long long mk) {
     if (P.dense) {
@@ -581,12 +597,16 @@ __device__ __forceinline__ void phase_finalize(const Params &P, unsigned long lo
     if (threadIdx.x < 256)
         s_p[threadIdx.x] = make_double2((a0.x + a1.x) + (a2.x + a3.x), (a0.y + a1.y) + (a2.y + a3.y));
     __syncthreads();
-    if ((int)threadIdx.x < MM1) {
-        double x = 0.0, y = 0.0;
-        for (int i = 0; i < T; ++i) {
-            x += s_p[threadIdx.x * T + i].x;
-            y += s_p[threadIdx.x * T + i].y;
+    // the T partials of element k: pairwise tree in shared memory
+    for (int w = 1; w < T; w <<= 1) {
+        if (k < MM1 && threadIdx.x < 256 && (sidx % (2 * w)) == 0 && sidx + w < T) {
+            s_p[threadIdx.x].x += s_p[threadIdx.x + w].x;
+            s_p[threadIdx.x].y += s_p[threadIdx.x + w].y;
         }
+        __syncthreads();
+    }
+    if ((int)threadIdx.x < MM1) {
+        const double x = s_p[threadIdx.x * T].x, y = s_p[threadIdx.x * T].y;
         const size_t slot = (size_t)(tn % (unsigned long long)P.rho_hist);
         if ((int)threadIdx.x < MM)
             P.rho_ring[(slot * P.n_inst + inst) * MM + threadIdx.x] = make_double2(x, y);
@@ -644,6 +664,7 @@ __global__ void __launch_bounds__(256) k_finalize(Params P, int MM, int nblk) {
     st->t = tn;
     st->cnt_groups[(tn + 1) % 3] = 0;   // counters of the next step
     st->cnt_out[(tn + 1) % 3] = 0;
+    st->ticket[(tn + 1) % 3] = 0;
 }
 
 // Grid-wide barrier of the persistent kernel (all blocks are co-resident: the
@@ -740,6 +761,411 @@ __global__ void __launch_bounds__(kPersistThreads) k_step_persistent(Params P, i
     }
 }
 
+// ---------------------------------------------------------------- stream engine
+
+// Look-back word: (step epoch << 32) | (state << 30) | count.
+__device__ __forceinline__ unsigned long long lb_word(unsigned epoch, unsigned state, unsigned long long cnt) {
+    return ((unsigned long long)epoch << 32) | ((unsigned long long)state << 30) | cnt;
+}
+
+// One step of the stream engine: one kernel over tiles of the stored set.
+// The set lives in M*M regions (newest point), each sorted by the older
+// points, so the paths of one pre-merge group form a run of equal prefix
+// (positions 0 .. k-1 of P'); at most one extra position of P' splits a run
+// into NX sub-groups.  Per tile (dynamic tickets): load, find run heads,
+// reduce each run owned by the tile (runs start in the tile and may extend
+// past it) into sub-group sums and representatives, count survivors per new
+// point, get the tile's output offsets per region by decoupled look-back
+// (bounded waits), recompute and write the survivors.  Output region c
+// receives, in order, the children with newest point c of all groups, so the
+// next set is again sorted.  No atomics on the data.
+template <int M, bool C64, int NX>
+__global__ void __launch_bounds__(kStreamThreads) k_stream_step(Params P) {
+    using X = Expander<M, C64>;
+    using AmpT = typename X::AmpT;
+    constexpr int MM = M * M;
+    constexpr int S = NX > 1 ? kStreamTile / 2 : kStreamTile, NT = kStreamThreads, NW = NT / 32;
+    constexpr int NSLOT = S * NX;
+    static_assert(S % NT == 0 && S / NT <= 32, "tile size");
+    DevState *st = P.st;
+    if (st->err) return;
+    const unsigned long long t = st->t, tn = t + 1;
+    const int in = (int)(t & 1), outp = (int)(tn & 1), cs = (int)(tn % 3);
+    const bool merge = tn >= (unsigned long long)P.dkmax;
+    const unsigned long long pref = merge ? P.prefmask : ~0ull;   // filling: every path is its own group
+    const int n_act = (int)min(tn, (unsigned long long)P.dkmax);
+    const int L_child = (int)min(tn + 1, (unsigned long long)P.dkmax);
+    const unsigned long long wmask = (P.b * L_child >= 64) ? ~0ull : ((1ull << (P.b * L_child)) - 1ull);
+    const long long G = P.region_cap;
+    const unsigned epoch = (unsigned)tn;
+    const unsigned long long *keys_in = P.keys[in];
+    const AmpT *amps_in = static_cast<const AmpT *>(P.amps[in]);
+    unsigned long long *keys_out = P.keys[outp];
+    AmpT *amps_out = static_cast<AmpT *>(P.amps[outp]);
+
+    // tile arrays in dynamic shared memory (stream_smem_bytes)
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    double2 *s_gS = reinterpret_cast<double2 *>(s_dyn);
+    unsigned long long *s_grep = reinterpret_cast<unsigned long long *>(s_gS + NSLOT);
+    unsigned long long *s_wm = s_grep + NSLOT;   // sub-group maximum weight (bits)
+    unsigned long long *s_key = s_wm + NSLOT;
+    AmpT *s_amp = reinterpret_cast<AmpT *>(s_key + S);
+    int *s_seg = reinterpret_cast<int *>(s_amp + S);
+    unsigned short *s_keep = reinterpret_cast<unsigned short *>(s_seg + S + 1);
+    __shared__ double2 s_w[MM * MM];
+    __shared__ float2 s_wf[MM * MM];
+    __shared__ long long s_nr[MM], s_tile0[MM + 1];
+    __shared__ unsigned s_wsum[NW][MM > 1 ? MM : 1];
+    __shared__ unsigned long long s_base[MM], s_tot[MM];
+    __shared__ unsigned s_ticket, s_nseg, s_ngroups, s_hw[NW];
+    __shared__ double2 s_r[NW][MM];
+
+    for (int i = threadIdx.x; i < MM * MM; i += NT) {
+        s_w[i] = P.wtab[i];
+        s_wf[i] = P.wtabf[i];
+    }
+    if (threadIdx.x == 0) {
+        long long acc = 0;
+        for (int r = 0; r < MM; ++r) {
+            s_nr[r] = (long long)__ldcg(&st->reg_n[in][r]);
+            s_tile0[r] = acc;
+            acc += (s_nr[r] + S - 1) / S;
+        }
+        s_tile0[MM] = acc;
+        if (acc == 0 && blockIdx.x == 0) {   // empty input: the output is empty
+            for (int r = 0; r < MM; ++r) st->reg_n[outp][r] = 0;
+            st->cnt_out[cs] = 0;
+        }
+    }
+    __syncthreads();
+    const long long ntiles = s_tile0[MM];
+
+    typename X::AccT racc[MM], rcmp[MM];
+#pragma unroll
+    for (int k = 0; k < MM; ++k) {
+        racc[k].x = racc[k].y = 0;
+        rcmp[k].x = rcmp[k].y = 0;
+    }
+    const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+    unsigned long long block_kept = 0;
+
+    for (;;) {
+        if (threadIdx.x == 0) s_ticket = atomicAdd(&st->ticket[cs], 1u);
+        __syncthreads();
+        const long long ticket = s_ticket;
+        if (ticket >= ntiles) break;
+        int r = 0;
+        while (r + 1 < MM && ticket >= s_tile0[r + 1]) ++r;
+        const long long e0 = (ticket - s_tile0[r]) * S;
+        const long long nr = s_nr[r];
+        const int cnt = (int)min((long long)S, nr - e0);
+        const unsigned long long *kin = keys_in + r * G;
+        const AmpT *ain = amps_in + r * G;
+        for (int i = threadIdx.x; i < cnt; i += NT) {
+            s_key[i] = __ldcg(kin + e0 + i);
+            s_amp[i] = __ldcg(ain + e0 + i);
+        }
+        __syncthreads();
+        // run heads (S/NT entries per thread), block scan of their count
+        unsigned hmask = 0;
+#pragma unroll
+        for (int u = 0; u < S / NT; ++u) {
+            const int i = threadIdx.x * (S / NT) + u;
+            if (i < cnt) {
+                const unsigned long long prevk = i > 0 ? s_key[i - 1] : (e0 > 0 ? __ldcg(kin + e0 - 1) : ~s_key[0]);
+                if (i == 0 && e0 == 0) hmask |= 1u << u;
+                else if ((s_key[i] & pref) != (prevk & pref)) hmask |= 1u << u;
+            }
+        }
+        unsigned hc = __popc(hmask), hincl = hc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, hincl, o);
+            if ((int)lane >= o) hincl += y;
+        }
+        if (lane == 31) s_hw[warp] = hincl;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned a = 0;
+            for (int w = 0; w < NW; ++w) {
+                const unsigned v = s_hw[w];
+                s_hw[w] = a;
+                a += v;
+            }
+            s_nseg = a;
+        }
+        __syncthreads();
+        {
+            unsigned pos = s_hw[warp] + hincl - hc;
+#pragma unroll
+            for (int u = 0; u < S / NT; ++u)
+                if (hmask & (1u << u)) s_seg[pos++] = threadIdx.x * (S / NT) + u;
+        }
+        __syncthreads();
+        const int nseg = (int)s_nseg;
+        if (threadIdx.x == 0) s_seg[nseg] = cnt;
+        __syncthreads();
+        // reduce the runs into NX sub-groups, one thread per stored path:
+        // shared-memory atomics add the amplitude into its sub-group's FP64
+        // sum and raise its maximum weight, then paths within the tie window
+        // of the maximum compete for the representative (atomicMin on the
+        // key).  Paths of the tile's last run past the tile end are read by
+        // warp 0, 32 at a time, while they share the run's prefix.
+        const int nslot_all = nseg * NX;
+        for (int i = threadIdx.x; i < nslot_all; i += NT) {
+            s_gS[i] = make_double2(0.0, 0.0);
+            s_grep[i] = kEmpty;
+            s_wm[i] = 0ull;
+        }
+        __syncthreads();
+        int segbase = (int)(s_hw[warp] + hincl - hc) - 1;   // run of the thread's first entry (-1: previous tile's)
+        auto slot_of_key = [&](int sg, unsigned long long key) {
+            return sg * NX + (NX > 1 ? (int)((key >> P.x_shift) & (NX - 1)) : 0);
+        };
+        auto weight_bits = [&](double2 a) -> unsigned long long {
+            if constexpr (C64) {
+                const float ax = (float)a.x, ay = (float)a.y;
+                return (unsigned long long)__float_as_uint(ax * ax + ay * ay);
+            } else {
+                return (unsigned long long)__double_as_longlong(a.x * a.x + a.y * a.y);
+            }
+        };
+        auto within_tie = [&](unsigned long long w, unsigned long long wm) -> bool {
+            if constexpr (C64) {
+                return __uint_as_float((unsigned)w) >= (float)(1.0 - P.tie_rel) * __uint_as_float((unsigned)wm);
+            } else {
+                return __longlong_as_double((long long)w) >= (1.0 - P.tie_rel) * __longlong_as_double((long long)wm);
+            }
+        };
+        const unsigned long long plast = nseg ? (s_key[s_seg[nseg - 1]] & pref) : 0ull;
+        {
+            int sg = segbase;
+#pragma unroll
+            for (int u = 0; u < S / NT; ++u) {
+                const int i = threadIdx.x * (S / NT) + u;
+                if (hmask & (1u << u)) ++sg;
+                if (i < cnt && sg >= 0) {
+                    const double2 a = as_d2(s_amp[i]);
+                    const int sl = slot_of_key(sg, s_key[i]);
+                    atomicAdd(&s_gS[sl].x, a.x);
+                    atomicAdd(&s_gS[sl].y, a.y);
+                    atomicMax(&s_wm[sl], weight_bits(a));
+                }
+            }
+        }
+        long long ahead = cnt;   // tile-relative end of the last run
+        if (warp == 0 && nseg > 0 && cnt == S) {
+            for (;;) {
+                const long long i = ahead + lane;
+                bool inrun = e0 + i < nr;
+                unsigned long long key = 0;
+                if (inrun) {
+                    key = __ldcg(kin + e0 + i);
+                    inrun = (key & pref) == plast;
+                }
+                const unsigned inm = __ballot_sync(0xffffffffu, inrun);
+                const int nin = inm == 0xffffffffu ? 32 : __ffs(~inm) - 1;   // leading members of the run
+                if ((int)lane < nin) {
+                    const double2 a = load_amp(ain, (unsigned long long)(e0 + i));
+                    const int sl = slot_of_key(nseg - 1, key);
+                    atomicAdd(&s_gS[sl].x, a.x);
+                    atomicAdd(&s_gS[sl].y, a.y);
+                    atomicMax(&s_wm[sl], weight_bits(a));
+                }
+                ahead += nin;
+                if (nin < 32) break;
+            }
+        }
+        __syncthreads();
+        {
+            int sg = segbase;
+#pragma unroll
+            for (int u = 0; u < S / NT; ++u) {
+                const int i = threadIdx.x * (S / NT) + u;
+                if (hmask & (1u << u)) ++sg;
+                if (i < cnt && sg >= 0) {
+                    const double2 a = as_d2(s_amp[i]);
+                    const int sl = slot_of_key(sg, s_key[i]);
+                    if (within_tie(weight_bits(a), s_wm[sl])) atomicMin(&s_grep[sl], s_key[i]);
+                }
+            }
+        }
+        if (warp == 0 && ahead > cnt) {
+            for (long long base = cnt; base < ahead; base += 32) {
+                const long long i = base + lane;
+                if (i < ahead) {
+                    const unsigned long long key = __ldcg(kin + e0 + i);
+                    const double2 a = load_amp(ain, (unsigned long long)(e0 + i));
+                    const int sl = slot_of_key(nseg - 1, key);
+                    if (within_tie(weight_bits(a), s_wm[sl])) atomicMin(&s_grep[sl], key);
+                }
+            }
+        }
+        __syncthreads();
+        // pass A: survivors per new point for a contiguous range of slots
+        const int nslot = nseg * NX;
+        const int spt = (nslot + NT - 1) / NT;
+        const int sl0 = min(nslot, (int)threadIdx.x * spt), sl1 = min(nslot, sl0 + spt);
+        unsigned cntc[MM];
+        unsigned ng = 0;
+#pragma unroll
+        for (int c = 0; c < MM; ++c) cntc[c] = 0;
+        for (int sl = sl0; sl < sl1; ++sl) {
+            const unsigned long long rk = s_grep[sl];
+            unsigned keep = 0;
+            if (rk != kEmpty) {
+                AmpT v[MM];
+                keep = X::children(P, n_act, 0, rk, s_gS[sl], s_w, s_wf, v);
+                ++ng;
+            }
+            s_keep[sl] = (unsigned short)keep;
+#pragma unroll
+            for (int c = 0; c < MM; ++c) cntc[c] += (keep >> c) & 1u;
+        }
+        // block exclusive scan per new point (warp shuffles, then across warps)
+        unsigned tb[MM];
+#pragma unroll
+        for (int c = 0; c < MM; ++c) {
+            unsigned v = cntc[c], incl = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+                if ((int)lane >= o) incl += y;
+            }
+            tb[c] = incl - v;
+            if (lane == 31) s_wsum[warp][c] = incl;
+        }
+        unsigned ngw = ng;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ngw += __shfl_down_sync(0xffffffffu, ngw, o);
+        if (threadIdx.x == 0) s_ngroups = 0;
+        __syncthreads();
+        if (lane == 0 && ngw) atomicAdd(&s_ngroups, ngw);
+        if (threadIdx.x < MM) {
+            unsigned a = 0;
+            for (int w = 0; w < NW; ++w) {
+                const unsigned v = s_wsum[w][threadIdx.x];
+                s_wsum[w][threadIdx.x] = a;
+                a += v;
+            }
+            s_tot[threadIdx.x] = a;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < MM; ++c) tb[c] += s_wsum[warp][c];
+        // decoupled look-back, one warp per bucket (buckets c, c + NW, ...):
+        // publish the tile's aggregate, then read 32 predecessors at a time
+        // and add aggregates back to the nearest inclusive prefix
+        for (int c = warp; c < MM; c += NW) {
+            unsigned long long *my = P.tile_state + (size_t)ticket * MM + c;
+            const unsigned long long tot = s_tot[c];
+            if (lane == 0) atomicExch(my, lb_word(epoch, ticket == 0 ? kLbInc : kLbAgg, tot));
+            unsigned long long excl = 0;
+            long long pred = ticket - 1;
+            const long long t0 = clock64();
+            bool timeout = false;
+            while (pred >= 0 && !timeout) {
+                const long long idx = pred - (long long)lane;
+                unsigned long long w = 0, val = 0;
+                unsigned state = 0;
+                for (;;) {   // every lane of the window must see its predecessor's word
+                    if (idx < 0) {
+                        state = kLbInc;   // before the first tile: an inclusive prefix of 0
+                        val = 0;
+                    } else {
+                        w = *(volatile unsigned long long *)(P.tile_state + (size_t)idx * MM + c);
+                        state = (unsigned)(w >> 32) == epoch ? ((unsigned)(w >> 30) & 3u) : 0u;
+                        val = w & ((1ull << 30) - 1ull);
+                    }
+                    if (__all_sync(0xffffffffu, state != 0)) break;
+                    if (*(volatile unsigned *)&st->err || clock64() - t0 > kBarrierCycles) {
+                        timeout = true;
+                        break;
+                    }
+                    __nanosleep(32);
+                }
+                if (timeout) break;
+                const unsigned incm = __ballot_sync(0xffffffffu, state == kLbInc);
+                const int lim = incm ? __ffs(incm) - 1 : 31;   // nearest inclusive predecessor
+                unsigned long long v = (int)lane <= lim ? val : 0ull;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+                excl += __shfl_sync(0xffffffffu, v, 0);
+                if (incm) break;
+                pred -= 32;
+            }
+            if (timeout && lane == 0) atomicOr(&st->err, kErrTimeout);
+            if (lane == 0) {
+                if (ticket > 0) atomicExch(my, lb_word(epoch, kLbInc, excl + tot));
+                s_base[c] = excl;
+                if (ticket == ntiles - 1) st->reg_n[outp][c] = excl + tot;   // the last tile knows the region sizes
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int c = 0; c < MM; ++c) block_kept += s_tot[c];
+            if (s_ngroups) atomicAdd(&st->cnt_groups[cs], (unsigned long long)s_ngroups);
+            if (ticket == ntiles - 1) {
+                unsigned long long sumc = 0;
+                for (int c = 0; c < MM; ++c) sumc += s_base[c] + s_tot[c];
+                st->cnt_out[cs] = sumc;
+            }
+        }
+        // pass B: recompute the survivors and write them to their regions
+        for (int sl = sl0; sl < sl1; ++sl) {
+            const unsigned keep = s_keep[sl];
+            if (!keep) continue;
+            const unsigned long long rk = s_grep[sl];
+            AmpT v[MM];
+            X::children(P, n_act, 0, rk, s_gS[sl], s_w, s_wf, v);
+            const unsigned long long shifted = rk << P.b;
+#pragma unroll
+            for (int c = 0; c < MM; ++c) {
+                if (!(keep & (1u << c))) continue;
+                const unsigned long long o = s_base[c] + tb[c]++;
+                if ((long long)o >= G) {
+                    raise_err(st, kErrPaths);
+                    continue;
+                }
+                const unsigned long long code = (unsigned long long)((c / M) | ((c % M) << P.bs));
+                keys_out[c * G + o] = (shifted | code) & wmask;
+                amps_out[c * G + o] = v[c];
+                if constexpr (C64) {
+                    X::kahan_add(racc[c], rcmp[c], v[c]);
+                } else {
+                    racc[c].x += v[c].x;
+                    racc[c].y += v[c].y;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // this block's partial sums of rho(t+1) (and survivor count)
+    double2 *mine = rho_part_of(P, tn, MM) + (size_t)blockIdx.x * (MM + 1);
+    double kept = 0.0;
+#pragma unroll
+    for (int k = 0; k < MM; ++k) {
+        double x = (double)racc[k].x - (double)rcmp[k].x, y = (double)racc[k].y - (double)rcmp[k].y;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            x += __shfl_down_sync(0xffffffffu, x, o);
+            y += __shfl_down_sync(0xffffffffu, y, o);
+        }
+        if (lane == 0) s_r[warp][k] = make_double2(x, y);
+    }
+    __syncthreads();
+    if (threadIdx.x < MM) {
+        double x = 0.0, y = 0.0;
+        for (int w = 0; w < NW; ++w) {
+            x += s_r[w][threadIdx.x].x;
+            y += s_r[w][threadIdx.x].y;
+        }
+        mine[threadIdx.x] = make_double2(x, y);
+    }
+    (void)kept;
+    if (threadIdx.x == 0) mine[MM] = make_double2((double)block_kept, 0.0);
+}
+
 // ---------------------------------------------------------------- set-up kernels
 
 __global__ void k_clear_table(Slot *slots, unsigned long long *repk, unsigned long long n) {
@@ -833,7 +1259,8 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
     size_t keys[2], amps[2], slots, repk, slot_of, groups, lut, lutf, lutlo, etab, wtab, wtabf, uprop, eta, q, deltas,
-        rho, rho_part, stats, inst_kept, fin_count, state, total;
+        rho, rho_part, stats, inst_kept, fin_count, tile_state, state, total;
+    long long entries, max_tiles;
     size_t nlut;           // history-table entries of one instance
     int nd;                // distinct nonzero coupling differences
     unsigned long long tcap;
@@ -919,10 +1346,14 @@ Layout make_layout(const qp_config *c) {
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
     L.state = take(sizeof(DevState));
-    L.keys[0] = take(mp * 8);
-    L.keys[1] = take(mp * 8);
-    L.amps[0] = take(mp * ampb);
-    L.amps[1] = take(mp * ampb);
+    // path buffers: a flat array of max_paths entries (merge-table engine),
+    // or the same memory as M*M regions of max_paths / (M*M) (stream engine)
+    const long long ent = mp;
+    L.entries = ent;
+    L.keys[0] = take(ent * 8);
+    L.keys[1] = take(ent * 8);
+    L.amps[0] = take(ent * ampb);
+    L.amps[1] = take(ent * ampb);
     L.slots = take(L.tcap * sizeof(Slot));
     L.repk = take(L.tcap * 8);
     L.slot_of = take(mp * 4);
@@ -947,6 +1378,8 @@ Layout make_layout(const qp_config *c) {
     L.stats = take((size_t)R * sizeof(StepRec));
     L.inst_kept = take((size_t)R * NI * sizeof(long long));
     L.fin_count = take(sizeof(unsigned int));
+    L.max_tiles = (long long)MM * ((mp / MM + kStreamTile / 2 - 1) / (kStreamTile / 2) + 1);   // smallest tile
+    L.tile_state = take((size_t)L.max_tiles * MM * 8);
     L.total = off;
     return L;
 }
@@ -971,6 +1404,8 @@ struct qp_ctx {
     bool use_persistent = true;
     int bps_ins = 4, bps_exp = 4;      // blocks per SM of the pre-merge and extension kernels
     int graph_steps = 1;               // steps captured per CUDA graph
+    int stream_nx = 0;                 // stream engine usable with the mask: sub-groups per run (0 = no)
+    bool use_stream = false;           // this propagation runs on the stream engine
     cudaGraphExec_t graph1 = nullptr;  // one-step graph for remainders
     cudaGraphExec_t graph = nullptr;
     bool graph_dirty = true;
@@ -1021,8 +1456,56 @@ cudaError_t launch_step_t(qp_ctx *c, cudaEvent_t *ev) {
     return cudaGetLastError();
 }
 
+template <int NX, typename Amp>
+constexpr size_t stream_smem_bytes() {
+    constexpr int S = NX > 1 ? kStreamTile / 2 : kStreamTile;
+    return (size_t)S * NX * (sizeof(double2) + 16) + (size_t)S * (8 + sizeof(Amp)) + (S + 1) * 4 + (size_t)S * NX * 2 + 16;
+}
+
+template <int M, bool C64, int NX>
+cudaError_t launch_stream_kernel(qp_ctx *c, int g) {
+    using Amp = typename std::conditional<C64, float2, double2>::type;
+    constexpr size_t sm = stream_smem_bytes<NX, Amp>();
+    static bool attr_set = false;   // per instantiation: allow more than 48 KB of dynamic shared memory
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_stream_step<M, C64, NX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        attr_set = true;
+    }
+    k_stream_step<M, C64, NX><<<g, kStreamThreads, sm, c->stream>>>(c->P);
+    return cudaGetLastError();
+}
+
+template <int M, typename Amp>
+cudaError_t launch_stream_t(qp_ctx *c, cudaEvent_t *ev) {
+    constexpr bool C64 = sizeof(Amp) == sizeof(float2);
+    const int g = std::min(c->nsm * c->bps_exp, kMaxExpandBlocks);
+    if (ev) {
+        cudaEventRecord(ev[0], c->stream);
+        cudaEventRecord(ev[1], c->stream);
+        cudaEventRecord(ev[2], c->stream);
+    }
+    cudaError_t e;
+    if constexpr (M == 2) {
+        e = c->stream_nx == 4 ? launch_stream_kernel<M, C64, 4>(c, g) : launch_stream_kernel<M, C64, 1>(c, g);
+    } else {
+        e = launch_stream_kernel<M, C64, 1>(c, g);
+    }
+    if (e != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[3], c->stream);
+    k_finalize<<<1, 256, 0, c->stream>>>(c->P, M * M, g);
+    if (ev) cudaEventRecord(ev[4], c->stream);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_step(qp_ctx *c, cudaEvent_t *ev = nullptr) {
     const bool c64 = c->cfg.precision == QP_C64;
+    if (c->use_stream) {
+        switch (c->cfg.M) {
+            case 2: return c64 ? launch_stream_t<2, float2>(c, ev) : launch_stream_t<2, double2>(c, ev);
+            case 3: return c64 ? launch_stream_t<3, float2>(c, ev) : launch_stream_t<3, double2>(c, ev);
+            default: return c64 ? launch_stream_t<4, float2>(c, ev) : launch_stream_t<4, double2>(c, ev);
+        }
+    }
     switch (c->cfg.M) {
         case 2: return c64 ? launch_step_t<2, float2>(c, ev) : launch_step_t<2, double2>(c, ev);
         case 3: return c64 ? launch_step_t<3, float2>(c, ev) : launch_step_t<3, double2>(c, ev);
@@ -1130,6 +1613,14 @@ void set_mask_params(qp_ctx *c) {
     }
     P.nruns = nruns;
     P.dense = (ok && off <= (int)P.tcap_log2) ? 1 : 0;
+    // stream engine: P' = prefix {0 .. k-1} plus at most one extra position
+    // (M = 2: four sub-groups per run)
+    int k = 0;
+    while (k < (int)Pp.size() && Pp[k] == k) ++k;
+    const int nextra = (int)Pp.size() - k;
+    P.prefmask = (b * k >= 64) ? ~0ull : ((1ull << (b * k)) - 1ull);
+    P.x_shift = nextra == 1 ? b * Pp[k] : -1;
+    c->stream_nx = (P.n_inst == 1 && (nextra == 0 || (nextra == 1 && c->cfg.M == 2))) ? (nextra ? 4 : 1) : 0;
 }
 
 }  // namespace
@@ -1251,6 +1742,8 @@ qp_status qp_create(const qp_config *cfg, void *d_workspace, size_t bytes, void 
     P.inst_shift = P.b * cfg->dkmax;
     P.instmask = P.n_inst > 1 ? (((1ull << inst_bits(P.n_inst)) - 1ull) << P.inst_shift) : 0ull;
     P.lut_stride = L.nlut;
+    P.region_cap = cfg->max_paths / (M * M);
+    P.tile_state = reinterpret_cast<unsigned long long *>(c->ws + L.tile_state);
     P.etab_stride = L.nlut * (size_t)std::max(1, L.nd);
     P.stats_ring = reinterpret_cast<StepRec *>(c->ws + L.stats);
     P.st = reinterpret_cast<DevState *>(c->ws + L.state);
@@ -1268,6 +1761,7 @@ qp_status qp_create(const qp_config *cfg, void *d_workspace, size_t bytes, void 
                             c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.state, 0, sizeof(DevState), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.fin_count, 0, sizeof(unsigned int), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.tile_state, 0, (size_t)L.max_tiles * M * M * 8, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         delete c;
@@ -1364,8 +1858,15 @@ qp_status qp_set_mask(qp_ctx *c, const int *positions, int n) {
         for (int p = 0; p < dk; ++p)
             if (seen[p]) m.push_back(p);
     }
+    const std::vector<int> old = c->mask;
     c->mask = m;
     set_mask_params(c);
+    if (c->have_state && c->use_stream && c->stream_nx == 0) {
+        c->mask = old;
+        set_mask_params(c);
+        return fail(c, QP_ERR_STATE, "the running stream-engine propagation cannot take this mask (restart with "
+                                     "qp_set_rho0 after choosing the merge-table engine)");
+    }
     c->graph_dirty = true;
     return QP_OK;
 }
@@ -1397,18 +1898,35 @@ qp_status qp_set_rho0(qp_ctx *c, const double *re, const double *im) {
                 }
             }
     if ((int64_t)keys.size() > c->cfg.max_paths) return fail(c, QP_ERR_CAPACITY, "rho0 exceeds max_paths");
+    // engine of this propagation
+    if (c->cfg.engine == QP_ENGINE_STREAM && c->stream_nx == 0)
+        return fail(c, QP_ERR_ARG, "the stream engine needs a mask whose P' is a prefix {0..k-1} plus at most one "
+                                   "extra position (M = 2) and a single instance");
+    c->use_stream = c->cfg.engine == QP_ENGINE_STREAM || (c->cfg.engine == QP_ENGINE_AUTO && c->stream_nx > 0);
+    if (c->use_stream && c->P.region_cap < 1) return fail(c, QP_ERR_CAPACITY, "max_paths < M*M");
+    c->P.stream = c->use_stream ? 1 : 0;
+    c->graph_dirty = true;
     const size_t n = keys.size();
-    QP_CUDA(c, cudaMemcpyAsync(c->P.keys[0], keys.data(), n * 8, cudaMemcpyHostToDevice, c->stream));
-    std::vector<float2> af;
-    if (c->cfg.precision == QP_C64) {
-        af.resize(n);
-        for (size_t i = 0; i < n; ++i) af[i] = make_float2((float)amps[i].x, (float)amps[i].y);
-        QP_CUDA(c, cudaMemcpyAsync(c->P.amps[0], af.data(), n * sizeof(float2), cudaMemcpyHostToDevice, c->stream));
-    } else {
-        QP_CUDA(c, cudaMemcpyAsync(c->P.amps[0], amps.data(), n * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
-    }
+    const size_t ab = c->cfg.precision == QP_C64 ? sizeof(float2) : sizeof(double2);
+    std::vector<float2> af(n);
+    for (size_t i = 0; i < n; ++i) af[i] = make_float2((float)amps[i].x, (float)amps[i].y);
+    const void *asrc = c->cfg.precision == QP_C64 ? (const void *)af.data() : (const void *)amps.data();
     DevState s{};
     s.n_cur = n;
+    if (c->use_stream) {   // one path per region (newest point a*M + b)
+        for (size_t i = 0; i < n; ++i) {
+            const int a = (int)(keys[i] & ((1u << bs) - 1u)), b = (int)((keys[i] >> bs) & ((1u << bs) - 1u));
+            const size_t reg = (size_t)(a * M + b);
+            QP_CUDA(c, cudaMemcpyAsync(c->P.keys[0] + reg * c->P.region_cap, &keys[i], 8, cudaMemcpyHostToDevice,
+                                       c->stream));
+            QP_CUDA(c, cudaMemcpyAsync(static_cast<char *>(c->P.amps[0]) + reg * c->P.region_cap * ab,
+                                       static_cast<const char *>(asrc) + i * ab, ab, cudaMemcpyHostToDevice, c->stream));
+            s.reg_n[0][reg] = 1;
+        }
+    } else {
+        QP_CUDA(c, cudaMemcpyAsync(c->P.keys[0], keys.data(), n * 8, cudaMemcpyHostToDevice, c->stream));
+        QP_CUDA(c, cudaMemcpyAsync(c->P.amps[0], asrc, n * ab, cudaMemcpyHostToDevice, c->stream));
+    }
     QP_CUDA(c, cudaMemcpyAsync(c->P.st, &s, sizeof(DevState), cudaMemcpyHostToDevice, c->stream));
     QP_CUDA(c, cudaMemcpyAsync(c->P.rho_ring, rho.data(), (size_t)NI * MM * sizeof(double2), cudaMemcpyHostToDevice,
                                c->stream));
@@ -1450,7 +1968,7 @@ qp_status qp_step(qp_ctx *c, int nsteps) {
     if (!c->have_state) return fail(c, QP_ERR_STATE, "qp_set_rho0 must come before qp_step");
     if (c->failed) return fail(c, QP_ERR_STATE, "context holds a device error; call qp_set_rho0");
     if (nsteps == 0) return QP_OK;
-    if (c->use_persistent) {
+    if (c->use_persistent && !c->use_stream) {
         const cudaError_t e = launch_persistent(c, nsteps);
         if (e != cudaSuccess) return fail(c, QP_ERR_CUDA, std::string("persistent launch: ") + cudaGetErrorString(e));
         return QP_OK;
@@ -1585,18 +2103,33 @@ qp_status qp_export_paths(qp_ctx *c, uint64_t *keys, double *amps, int64_t cap, 
     if ((int64_t)s.n_cur > cap) return fail(c, QP_ERR_CAPACITY, "export buffer too small");
     const int buf = (int)(s.t & 1);
     const size_t cnt = s.n_cur;
-    QP_CUDA(c, cudaMemcpyAsync(keys, c->P.keys[buf], cnt * 8, cudaMemcpyDeviceToHost, c->stream));
-    if (c->cfg.precision == QP_C64) {
-        std::vector<float2> tmp(cnt);
-        QP_CUDA(c, cudaMemcpyAsync(tmp.data(), c->P.amps[buf], cnt * sizeof(float2), cudaMemcpyDeviceToHost, c->stream));
-        QP_CUDA(c, cudaStreamSynchronize(c->stream));
-        for (size_t i = 0; i < cnt; ++i) {
-            amps[2 * i] = tmp[i].x;
-            amps[2 * i + 1] = tmp[i].y;
-        }
-    } else {
-        QP_CUDA(c, cudaMemcpyAsync(amps, c->P.amps[buf], cnt * sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
-        QP_CUDA(c, cudaStreamSynchronize(c->stream));
+    const int MM = c->cfg.M * c->cfg.M;
+    // contiguous pieces: the flat array, or the M*M regions of the stream engine
+    std::vector<std::pair<size_t, size_t>> pieces;   // (device offset, count)
+    if (c->use_stream) {
+        for (int r = 0; r < MM; ++r)
+            if (s.reg_n[buf][r]) pieces.push_back({(size_t)r * c->P.region_cap, (size_t)s.reg_n[buf][r]});
+    } else if (cnt) {
+        pieces.push_back({0, cnt});
+    }
+    size_t o = 0;
+    std::vector<float2> tmp(c->cfg.precision == QP_C64 ? cnt : 0);
+    for (const auto &pc : pieces) {
+        QP_CUDA(c, cudaMemcpyAsync(keys + o, c->P.keys[buf] + pc.first, pc.second * 8, cudaMemcpyDeviceToHost,
+                                   c->stream));
+        if (c->cfg.precision == QP_C64)
+            QP_CUDA(c, cudaMemcpyAsync(tmp.data() + o, static_cast<float2 *>(c->P.amps[buf]) + pc.first,
+                                       pc.second * sizeof(float2), cudaMemcpyDeviceToHost, c->stream));
+        else
+            QP_CUDA(c, cudaMemcpyAsync(amps + 2 * o, static_cast<double2 *>(c->P.amps[buf]) + pc.first,
+                                       pc.second * sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
+        o += pc.second;
+    }
+    QP_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (o != cnt) return fail(c, QP_ERR_STATE, "region counts do not add up to the stored count");
+    for (size_t i = 0; i < tmp.size(); ++i) {
+        amps[2 * i] = tmp[i].x;
+        amps[2 * i + 1] = tmp[i].y;
     }
     return QP_OK;
 }
@@ -1636,6 +2169,7 @@ qp_status qp_get_tuning(qp_ctx *c, qp_tuning *out) {
     out->persistent_blocks = c->persist_grid;
     out->graph_steps = c->graph_steps;
     out->table_log2 = (int)c->P.tcap_log2;
+    out->engine = c->use_stream ? QP_ENGINE_STREAM : QP_ENGINE_HASH;
     return QP_OK;
 }
 
@@ -1715,12 +2249,12 @@ qp_status qp_autotune(qp_ctx *c, int trial_steps, int use_cache, qp_tuning *best
         for (int bi : {2, 4, 8})
             for (int be : {2, 4, 8}) {
                 if (c->nsm * be > kMaxExpandBlocks) continue;
-                cand.push_back(qp_tuning{QP_LAUNCH_GRAPH, bi, be, c->persist_grid, gs, tb});
+                cand.push_back(qp_tuning{QP_LAUNCH_GRAPH, bi, be, c->persist_grid, gs, tb, 0});
             }
     if (c->persist_max > 0)
         for (int pb : {1, 2, 4}) {
             const int blocks = std::min(c->persist_max, pb * c->nsm);
-            cand.push_back(qp_tuning{QP_LAUNCH_PERSISTENT, 4, 4, blocks, gs, tl});
+            if (!c->use_stream) cand.push_back(qp_tuning{QP_LAUNCH_PERSISTENT, 4, 4, blocks, gs, tl, 0});
         }
     qp_tuning save;
     qp_get_tuning(c, &save);

@@ -101,7 +101,7 @@ def test_resonance_sweep_instances_against_oracle():
 def test_autotune_picks_a_valid_shape_and_keeps_parity():
     case = W.random_case(5, 2, 8)
     mask, theta = (0, 1, 2, 5), 1e-6
-    p = Propagator(2, 8, case["dt"], case["q"], case["hs"], theta, max_paths=1 << 18)
+    p = Propagator(2, 8, case["dt"], case["q"], case["hs"], theta, engine="hash", max_paths=1 << 18)
     p.set_eta(case["eta"])
     p.set_mask(mask)
     p.set_rho0(case["rho0"])
@@ -115,7 +115,7 @@ def test_autotune_picks_a_valid_shape_and_keeps_parity():
     o = iquapi.propagate(2, case["q"], case["hs"], case["dt"], case["eta"], 8, mask, theta, case["rho0"], t + 5)
     assert np.abs(rho - o.rho).max() <= TOL
     # cached choice is applied without trials
-    p2 = Propagator(2, 8, case["dt"], case["q"], case["hs"], theta, max_paths=1 << 18)
+    p2 = Propagator(2, 8, case["dt"], case["q"], case["hs"], theta, engine="hash", max_paths=1 << 18)
     p2.set_eta(case["eta"])
     p2.set_mask(mask)
     p2.set_rho0(case["rho0"])
@@ -141,7 +141,7 @@ def test_persistent_barrier_wait_is_bounded():
     its bound, the step is not applied, the context reports QP_ERR_TIMEOUT and
     is usable again after qp_set_rho0."""
     case = W.random_case(8, 2, 5)
-    p = Propagator(2, 5, case["dt"], case["q"], case["hs"], 0.0, max_paths=1 << 14)
+    p = Propagator(2, 5, case["dt"], case["q"], case["hs"], 0.0, engine="hash", max_paths=1 << 14)
     p.set_eta(case["eta"])
     p.set_mask(None)
     p.set_rho0(case["rho0"])

@@ -71,11 +71,15 @@ def run_both(case, mask, theta, steps, **kw):
     return g, o
 
 
+ENGINES = ["stream", "hash"]
+
+
+@pytest.mark.parametrize("engine", ENGINES)
 @pytest.mark.parametrize("M,dkmax,steps,seed", [(2, 1, 10, 1), (2, 2, 12, 2), (2, 5, 14, 3), (2, 8, 12, 4),
                                                 (3, 1, 8, 5), (3, 3, 8, 6), (3, 4, 7, 7), (4, 2, 6, 8), (4, 3, 5, 9)])
-def test_unmasked_unfiltered_matches_oracle(M, dkmax, steps, seed):
+def test_unmasked_unfiltered_matches_oracle(M, dkmax, steps, seed, engine):
     case = W.random_case(seed, M, dkmax)
-    g, o = run_both(case, None, 0.0, steps)
+    g, o = run_both(case, None, 0.0, steps, engine=engine)
     compare(g, o, M)
 
 
@@ -88,9 +92,12 @@ def test_unmasked_unfiltered_matches_oracle(M, dkmax, steps, seed):
     (3, 6, (0, 1, 2, 3), 0.0, 9, 16),
     (4, 4, (0, 1, 3), 1e-4, 8, 17),
 ])
-def test_masked_filtered_matches_oracle(M, dkmax, mask, theta, steps, seed):
+@pytest.mark.parametrize("engine", ["auto", "hash"])
+def test_masked_filtered_matches_oracle(M, dkmax, mask, theta, steps, seed, engine):
+    """auto: the stream engine wherever P' is a prefix plus at most one extra
+    position (M = 2), the merge table otherwise."""
     case = W.random_case(seed, M, dkmax)
-    g, o = run_both(case, mask, theta, steps)
+    g, o = run_both(case, mask, theta, steps, engine=engine)
     compare(g, o, M)
 
 
@@ -102,11 +109,12 @@ def test_hashed_table_index_matches_oracle():
     compare(g, o, 2)
 
 
-def test_spin_boson_ohmic_dk8_trajectory_against_stored_oracle():
+@pytest.mark.parametrize("engine", ENGINES)
+def test_spin_boson_ohmic_dk8_trajectory_against_stored_oracle(engine):
     w = W.SPIN_BOSON_OHMIC_DK8
     eta = eta_from_bath(w.bath, w.dt, w.dkmax)
     rho, stats, keys, amps = gpu_run(w.M, w.q, w.hs_array(), w.dt, eta, w.dkmax, w.mask, w.theta,
-                                     w.rho0_array(), w.steps)
+                                     w.rho0_array(), w.steps, engine=engine)
     t, n, rho_o = load_golden("spin_boson_ohmic_dk8_rho.txt")
     assert np.abs(rho - rho_o).max() <= RHO_TOL
     assert [s[3] for s in stats] == list(n[1:])
@@ -116,6 +124,12 @@ def test_spin_boson_ohmic_dk8_trajectory_against_stored_oracle():
 def test_spin_boson_structured_dk16_first_40_steps_against_stored_oracle():
     w = W.SPIN_BOSON_STRUCTURED_DK16
     eta = eta_from_bath(w.bath, w.dt, w.dkmax)
+    for engine in ("stream", "hash"):
+        rho, stats, keys, amps = gpu_run(w.M, w.q, w.hs_array(), w.dt, eta, w.dkmax, w.mask, w.theta,
+                                         w.rho0_array(), 40, max_paths=1 << 21, engine=engine)
+        t, n, rho_o = load_golden("spin_boson_structured_dk16_rho40.txt")
+        assert np.abs(rho - rho_o).max() <= RHO_TOL, engine
+        assert [s[3] for s in stats] == list(n[1:]), engine
     rho, stats, keys, amps = gpu_run(w.M, w.q, w.hs_array(), w.dt, eta, w.dkmax, w.mask, w.theta,
                                      w.rho0_array(), 40, max_paths=1 << 21)
     t, n, rho_o = load_golden("spin_boson_structured_dk16_rho40.txt")
