@@ -123,6 +123,10 @@ typedef struct {
     int engine;                /* engine of the running propagation (QP_ENGINE_HASH
                                   or QP_ENGINE_STREAM; read-only, set at
                                   qp_set_rho0 from qp_config.engine and the mask) */
+    int stream_tile;           /* stream engine: stored paths per tile, 256, 512
+                                  or 1024 (0 in qp_set_tuning: unchanged); its
+                                  grid is min(expand_blocks_per_sm, co-resident
+                                  blocks per SM) blocks per SM               */
 } qp_tuning;
 
 typedef struct qp_ctx qp_ctx;

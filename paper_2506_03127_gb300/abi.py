@@ -36,7 +36,7 @@ class qp_config(ctypes.Structure):
 class qp_tuning(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int), ("insert_blocks_per_sm", ctypes.c_int), ("expand_blocks_per_sm", ctypes.c_int),
                 ("persistent_blocks", ctypes.c_int), ("graph_steps", ctypes.c_int), ("table_log2", ctypes.c_int),
-                ("engine", ctypes.c_int)]
+                ("engine", ctypes.c_int), ("stream_tile", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -59,7 +59,7 @@ constexpr int kExpandThreads = 128;
 constexpr int kMaxExpandBlocks = 2048;
 constexpr int kPersistThreads = 256;
 constexpr int kMaxInst = 128;                      // instances of one batched context
-constexpr int kStreamTile = 1024;                   // stored paths per tile of the stream engine (NX = 1)
+constexpr int kStreamMinTile = 256;                 // smallest stream tile (256, 512 or 1024 stored paths)
 constexpr int kStreamThreads = 256;
 constexpr unsigned kLbAgg = 1u, kLbInc = 2u;        // look-back word states (bits 30-31)
 constexpr long long kBarrierCycles = 4000000000ll;  // ~2 s at 2 GHz: a grid barrier gives up after this
@@ -155,6 +155,28 @@ __device__ __forceinline__ double2 load_amp(const float2 *p, unsigned long long 
 }
 __device__ __forceinline__ double2 as_d2(double2 v) { return v; }
 __device__ __forceinline__ double2 as_d2(float2 v) { return make_double2(v.x, v.y); }
+
+// float -> double by IEEE-754 fields (exact): a normal number keeps its sign
+// and 23 fraction bits, its exponent is rebiased by 1023 - 127; zeros keep
+// their sign.  Subnormals, infinities and NaNs take the conversion
+// instruction.  Keeps the widening of FP32 amplitudes off the FP64 pipe.
+__device__ __forceinline__ double f2d_exact(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xffu;
+    const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+    if (e == 0u) {
+        if ((u & 0x7fffffu) == 0u) return __longlong_as_double((long long)sign);
+        return (double)f;
+    }
+    if (e == 0xffu) return (double)f;
+    const unsigned long long bits = sign | ((unsigned long long)(e + 896u) << 52) |
+                                    ((unsigned long long)(u & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)bits);
+}
+__device__ __forceinline__ double to_d(double v) { return v; }
+__device__ __forceinline__ double to_d(float v) { return f2d_exact(v); }
+__device__ __forceinline__ float2 to_f2(float2 v) { return v; }
+__device__ __forceinline__ float2 to_f2(double2 v) { return make_float2((float)v.x, (float)v.y); }
 
 __device__ __forceinline__ unsigned long long table_index(const Params &P, unsigned long long mk) {
     if (P.dense) {
@@ -350,8 +372,11 @@ struct Expander {
         s.y = ty;
     }
 
+    // S: the group's merge sum (FP64), or on the C64 path already rounded to
+    // FP32 (float2)
+    template <typename SumT>
     static __device__ __forceinline__ unsigned children(const Params &P, int n_act, int inst, unsigned long long rep,
-                                                        double2 S, const double2 *w, const float2 *wf, AmpT *v) {
+                                                        SumT S, const double2 *w, const float2 *wf, AmpT *v) {
         const unsigned c0 = (unsigned)(rep & ((1u << P.b) - 1u));
         const int pidx = (int)(c0 & ((1u << P.bs) - 1u)) * M + (int)(c0 >> P.bs);
         unsigned keep = 0;
@@ -384,7 +409,7 @@ struct Expander {
                     Ed[d] = make_float2(m * cs, m * sn);
                 }
             }
-            const float2 Sf = make_float2((float)S.x, (float)S.y);
+            const float2 Sf = to_f2(S);
 #pragma unroll
             for (int k = 0; k < MM; ++k) {
                 float2 a = cmulf(Sf, wf[k * MM + pidx]);
@@ -626,6 +651,23 @@ __device__ __forceinline__ void write_step_totals(const Params &P, unsigned long
     P.stats_ring[tn % (unsigned long long)P.rho_hist] = r;
 }
 
+// Publishes step tn (one thread, after every block of the step is done):
+// totals, the new count and time, and zeroed counters of the next step.
+// Counters are read through L2: other blocks of the same kernel may have
+// written them.
+__device__ __forceinline__ void publish_step(const Params &P, DevState *st, unsigned long long tn, int MM) {
+    *P.fin_count = 0;
+    const bool merge = tn >= (unsigned long long)P.dkmax;
+    const unsigned long long groups = merge ? __ldcg(&st->cnt_groups[tn % 3]) : __ldcg(&st->n_cur);
+    const unsigned long long n_out = __ldcg(&st->cnt_out[tn % 3]);
+    write_step_totals(P, tn, groups, n_out, MM);
+    st->n_cur = n_out;
+    st->t = tn;
+    st->cnt_groups[(tn + 1) % 3] = 0;   // counters of the next step
+    st->cnt_out[(tn + 1) % 3] = 0;
+    st->ticket[(tn + 1) % 3] = 0;
+}
+
 __device__ __forceinline__ double2 *rho_part_of(const Params &P, unsigned long long tn, int MM) {
     return P.rho_part + (size_t)(tn & 1) * kMaxExpandBlocks * P.n_inst * (MM + 1);
 }
@@ -655,16 +697,7 @@ __global__ void __launch_bounds__(256) k_finalize(Params P, int MM, int nblk) {
     }
     __syncthreads();
     if (!s_last || threadIdx.x != 0) return;
-    *P.fin_count = 0;
-    const bool merge = tn >= (unsigned long long)P.dkmax;
-    const unsigned long long groups = merge ? st->cnt_groups[tn % 3] : st->n_cur;
-    const unsigned long long n_out = st->cnt_out[tn % 3];
-    write_step_totals(P, tn, groups, n_out, MM);
-    st->n_cur = n_out;
-    st->t = tn;
-    st->cnt_groups[(tn + 1) % 3] = 0;   // counters of the next step
-    st->cnt_out[(tn + 1) % 3] = 0;
-    st->ticket[(tn + 1) % 3] = 0;
+    publish_step(P, st, tn, MM);
 }
 
 // Grid-wide barrier of the persistent kernel (all blocks are co-resident: the
@@ -778,13 +811,16 @@ __device__ __forceinline__ unsigned long long lb_word(unsigned epoch, unsigned s
 // point, get the tile's output offsets per region by decoupled look-back
 // (bounded waits), recompute and write the survivors.  Output region c
 // receives, in order, the children with newest point c of all groups, so the
-// next set is again sorted.  No atomics on the data.
-template <int M, bool C64, int NX>
+// next set is again sorted.  No atomics on the data.  The last block to
+// finish sums the blocks' partials of rho(t+1) and publishes the step.
+template <int M, bool C64, int NX, int S>
 __global__ void __launch_bounds__(kStreamThreads) k_stream_step(Params P) {
     using X = Expander<M, C64>;
     using AmpT = typename X::AmpT;
+    // weight |a|^2 as ordered bits: FP32 on the C64 path, FP64 otherwise
+    using WT = typename std::conditional<C64, unsigned, unsigned long long>::type;
     constexpr int MM = M * M;
-    constexpr int S = NX > 1 ? kStreamTile / 2 : kStreamTile, NT = kStreamThreads, NW = NT / 32;
+    constexpr int NT = kStreamThreads, NW = NT / 32;
     constexpr int NSLOT = S * NX;
     static_assert(S % NT == 0 && S / NT <= 32, "tile size");
     DevState *st = P.st;
@@ -807,8 +843,8 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream_step(Params P) {
     extern __shared__ __align__(16) unsigned char s_dyn[];
     double2 *s_gS = reinterpret_cast<double2 *>(s_dyn);
     unsigned long long *s_grep = reinterpret_cast<unsigned long long *>(s_gS + NSLOT);
-    unsigned long long *s_wm = s_grep + NSLOT;   // sub-group maximum weight (bits)
-    unsigned long long *s_key = s_wm + NSLOT;
+    WT *s_wm = reinterpret_cast<WT *>(s_grep + NSLOT);   // sub-group maximum weight (bits)
+    unsigned long long *s_key = s_grep + 2 * NSLOT;
     AmpT *s_amp = reinterpret_cast<AmpT *>(s_key + S);
     int *s_seg = reinterpret_cast<int *>(s_amp + S);
     unsigned short *s_keep = reinterpret_cast<unsigned short *>(s_seg + S + 1);
@@ -819,6 +855,9 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream_step(Params P) {
     __shared__ unsigned long long s_base[MM], s_tot[MM];
     __shared__ unsigned s_ticket, s_nseg, s_ngroups, s_hw[NW];
     __shared__ double2 s_r[NW][MM];
+    __shared__ bool s_last;
+    const double tie_d = 1.0 - P.tie_rel;   // R4 window, once per thread
+    const float tie_f = (float)tie_d;
 
     for (int i = threadIdx.x; i < MM * MM; i += NT) {
         s_w[i] = P.wtab[i];
@@ -915,27 +954,20 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream_step(Params P) {
         for (int i = threadIdx.x; i < nslot_all; i += NT) {
             s_gS[i] = make_double2(0.0, 0.0);
             s_grep[i] = kEmpty;
-            s_wm[i] = 0ull;
+            s_wm[i] = 0;
         }
         __syncthreads();
         int segbase = (int)(s_hw[warp] + hincl - hc) - 1;   // run of the thread's first entry (-1: previous tile's)
         auto slot_of_key = [&](int sg, unsigned long long key) {
             return sg * NX + (NX > 1 ? (int)((key >> P.x_shift) & (NX - 1)) : 0);
         };
-        auto weight_bits = [&](double2 a) -> unsigned long long {
-            if constexpr (C64) {
-                const float ax = (float)a.x, ay = (float)a.y;
-                return (unsigned long long)__float_as_uint(ax * ax + ay * ay);
-            } else {
-                return (unsigned long long)__double_as_longlong(a.x * a.x + a.y * a.y);
-            }
+        auto weight_bits = [&](AmpT a) -> WT {
+            if constexpr (C64) return __float_as_uint(a.x * a.x + a.y * a.y);
+            else return (unsigned long long)__double_as_longlong(a.x * a.x + a.y * a.y);
         };
-        auto within_tie = [&](unsigned long long w, unsigned long long wm) -> bool {
-            if constexpr (C64) {
-                return __uint_as_float((unsigned)w) >= (float)(1.0 - P.tie_rel) * __uint_as_float((unsigned)wm);
-            } else {
-                return __longlong_as_double((long long)w) >= (1.0 - P.tie_rel) * __longlong_as_double((long long)wm);
-            }
+        auto within_tie = [&](WT w, WT wm) -> bool {
+            if constexpr (C64) return __uint_as_float(w) >= tie_f * __uint_as_float(wm);
+            else return __longlong_as_double((long long)w) >= tie_d * __longlong_as_double((long long)wm);
         };
         const unsigned long long plast = nseg ? (s_key[s_seg[nseg - 1]] & pref) : 0ull;
         {
@@ -945,10 +977,10 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream_step(Params P) {
                 const int i = threadIdx.x * (S / NT) + u;
                 if (hmask & (1u << u)) ++sg;
                 if (i < cnt && sg >= 0) {
-                    const double2 a = as_d2(s_amp[i]);
+                    const AmpT a = s_amp[i];
                     const int sl = slot_of_key(sg, s_key[i]);
-                    atomicAdd(&s_gS[sl].x, a.x);
-                    atomicAdd(&s_gS[sl].y, a.y);
+                    atomicAdd(&s_gS[sl].x, to_d(a.x));
+                    atomicAdd(&s_gS[sl].y, to_d(a.y));
                     atomicMax(&s_wm[sl], weight_bits(a));
                 }
             }
@@ -966,10 +998,10 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream_step(Params P) {
                 const unsigned inm = __ballot_sync(0xffffffffu, inrun);
                 const int nin = inm == 0xffffffffu ? 32 : __ffs(~inm) - 1;   // leading members of the run
                 if ((int)lane < nin) {
-                    const double2 a = load_amp(ain, (unsigned long long)(e0 + i));
+                    const AmpT a = __ldcg(ain + e0 + i);
                     const int sl = slot_of_key(nseg - 1, key);
-                    atomicAdd(&s_gS[sl].x, a.x);
-                    atomicAdd(&s_gS[sl].y, a.y);
+                    atomicAdd(&s_gS[sl].x, to_d(a.x));
+                    atomicAdd(&s_gS[sl].y, to_d(a.y));
                     atomicMax(&s_wm[sl], weight_bits(a));
                 }
                 ahead += nin;
@@ -984,9 +1016,8 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream_step(Params P) {
                 const int i = threadIdx.x * (S / NT) + u;
                 if (hmask & (1u << u)) ++sg;
                 if (i < cnt && sg >= 0) {
-                    const double2 a = as_d2(s_amp[i]);
                     const int sl = slot_of_key(sg, s_key[i]);
-                    if (within_tie(weight_bits(a), s_wm[sl])) atomicMin(&s_grep[sl], s_key[i]);
+                    if (within_tie(weight_bits(s_amp[i]), s_wm[sl])) atomicMin(&s_grep[sl], s_key[i]);
                 }
             }
         }
@@ -995,7 +1026,7 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream_step(Params P) {
                 const long long i = base + lane;
                 if (i < ahead) {
                     const unsigned long long key = __ldcg(kin + e0 + i);
-                    const double2 a = load_amp(ain, (unsigned long long)(e0 + i));
+                    const AmpT a = __ldcg(ain + e0 + i);
                     const int sl = slot_of_key(nseg - 1, key);
                     if (within_tie(weight_bits(a), s_wm[sl])) atomicMin(&s_grep[sl], key);
                 }
@@ -1010,12 +1041,20 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream_step(Params P) {
         unsigned ng = 0;
 #pragma unroll
         for (int c = 0; c < MM; ++c) cntc[c] = 0;
+        // C64: each sum is rounded to FP32 once, kept in its slot for pass B
+        float2 *s_gSf = reinterpret_cast<float2 *>(s_gS);   // slot sl at [2 * sl]
         for (int sl = sl0; sl < sl1; ++sl) {
             const unsigned long long rk = s_grep[sl];
             unsigned keep = 0;
             if (rk != kEmpty) {
                 AmpT v[MM];
-                keep = X::children(P, n_act, 0, rk, s_gS[sl], s_w, s_wf, v);
+                if constexpr (C64) {
+                    const float2 Sf = to_f2(s_gS[sl]);
+                    s_gSf[2 * sl] = Sf;
+                    keep = X::children(P, n_act, 0, rk, Sf, s_w, s_wf, v);
+                } else {
+                    keep = X::children(P, n_act, 0, rk, s_gS[sl], s_w, s_wf, v);
+                }
                 ++ng;
             }
             s_keep[sl] = (unsigned short)keep;
@@ -1063,8 +1102,8 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream_step(Params P) {
             unsigned long long excl = 0;
             long long pred = ticket - 1;
             const long long t0 = clock64();
-            bool timeout = false;
-            while (pred >= 0 && !timeout) {
+            bool timeout = false, abort = false;   // abort: another block raised an error
+            while (pred >= 0 && !timeout && !abort) {
                 const long long idx = pred - (long long)lane;
                 unsigned long long w = 0, val = 0;
                 unsigned state = 0;
@@ -1078,13 +1117,17 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream_step(Params P) {
                         val = w & ((1ull << 30) - 1ull);
                     }
                     if (__all_sync(0xffffffffu, state != 0)) break;
-                    if (*(volatile unsigned *)&st->err || clock64() - t0 > kBarrierCycles) {
+                    if (*(volatile unsigned *)&st->err) {
+                        abort = true;
+                        break;
+                    }
+                    if (clock64() - t0 > kBarrierCycles) {
                         timeout = true;
                         break;
                     }
                     __nanosleep(32);
                 }
-                if (timeout) break;
+                if (timeout || abort) break;
                 const unsigned incm = __ballot_sync(0xffffffffu, state == kLbInc);
                 const int lim = incm ? __ffs(incm) - 1 : 31;   // nearest inclusive predecessor
                 unsigned long long v = (int)lane <= lim ? val : 0ull;
@@ -1117,7 +1160,8 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream_step(Params P) {
             if (!keep) continue;
             const unsigned long long rk = s_grep[sl];
             AmpT v[MM];
-            X::children(P, n_act, 0, rk, s_gS[sl], s_w, s_wf, v);
+            if constexpr (C64) X::children(P, n_act, 0, rk, s_gSf[2 * sl], s_w, s_wf, v);
+            else X::children(P, n_act, 0, rk, s_gS[sl], s_w, s_wf, v);
             const unsigned long long shifted = rk << P.b;
 #pragma unroll
             for (int c = 0; c < MM; ++c) {
@@ -1164,6 +1208,22 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream_step(Params P) {
     }
     (void)kept;
     if (threadIdx.x == 0) mine[MM] = make_double2((double)block_kept, 0.0);
+    // last block done: rho(t+1) from the partials in block order, then the
+    // step is published (no separate finalisation kernel)
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(P.fin_count, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (__ldcg(&st->err)) {   // a failed step is not published
+        if (threadIdx.x == 0) *P.fin_count = 0;
+        return;
+    }
+    phase_finalize(P, tn, 0, rho_part_of(P, tn, MM), gridDim.x, MM);
+    if (threadIdx.x == 0) publish_step(P, st, tn, MM);
 }
 
 // ---------------------------------------------------------------- set-up kernels
@@ -1378,7 +1438,7 @@ Layout make_layout(const qp_config *c) {
     L.stats = take((size_t)R * sizeof(StepRec));
     L.inst_kept = take((size_t)R * NI * sizeof(long long));
     L.fin_count = take(sizeof(unsigned int));
-    L.max_tiles = (long long)MM * ((mp / MM + kStreamTile / 2 - 1) / (kStreamTile / 2) + 1);   // smallest tile
+    L.max_tiles = (long long)MM * ((mp / MM + kStreamMinTile - 1) / kStreamMinTile + 1);   // smallest tile
     L.tile_state = take((size_t)L.max_tiles * MM * 8);
     L.total = off;
     return L;
@@ -1405,6 +1465,7 @@ struct qp_ctx {
     int bps_ins = 4, bps_exp = 4;      // blocks per SM of the pre-merge and extension kernels
     int graph_steps = 1;               // steps captured per CUDA graph
     int stream_nx = 0;                 // stream engine usable with the mask: sub-groups per run (0 = no)
+    int stream_tile = 1024;            // stored paths per tile of the stream engine
     bool use_stream = false;           // this propagation runs on the stream engine
     cudaGraphExec_t graph1 = nullptr;  // one-step graph for remainders
     cudaGraphExec_t graph = nullptr;
@@ -1456,29 +1517,51 @@ cudaError_t launch_step_t(qp_ctx *c, cudaEvent_t *ev) {
     return cudaGetLastError();
 }
 
-template <int NX, typename Amp>
+// Dynamic shared memory of a stream tile of S stored paths: per slot
+// (S * NX) the FP64 sum, the representative and the maximum weight; per path
+// the key and amplitude; run heads; survivor bits per slot.
+template <int NX, typename Amp, int S>
 constexpr size_t stream_smem_bytes() {
-    constexpr int S = NX > 1 ? kStreamTile / 2 : kStreamTile;
     return (size_t)S * NX * (sizeof(double2) + 16) + (size_t)S * (8 + sizeof(Amp)) + (S + 1) * 4 + (size_t)S * NX * 2 + 16;
 }
 
-template <int M, bool C64, int NX>
-cudaError_t launch_stream_kernel(qp_ctx *c, int g) {
+// Grid of the stream kernel: every block resident (tiles are taken by
+// ticket, so blocks beyond the co-resident count would only start after a
+// first wave), at most blocks_per_sm per SM and kMaxExpandBlocks in all.
+template <int M, bool C64, int NX, int S>
+cudaError_t launch_stream_kernel(qp_ctx *c, int blocks_per_sm) {
     using Amp = typename std::conditional<C64, float2, double2>::type;
-    constexpr size_t sm = stream_smem_bytes<NX, Amp>();
-    static bool attr_set = false;   // per instantiation: allow more than 48 KB of dynamic shared memory
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_stream_step<M, C64, NX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        attr_set = true;
+    constexpr size_t sm = stream_smem_bytes<NX, Amp, S>();
+    static int resident = 0;   // per instantiation (one device per process is assumed for the attribute)
+    if (resident == 0) {
+        cudaError_t e = cudaFuncSetAttribute(k_stream_step<M, C64, NX, S>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        int nb = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stream_step<M, C64, NX, S>, kStreamThreads, sm);
+        if (e != cudaSuccess) return e;
+        if (nb < 1) return cudaErrorInvalidConfiguration;
+        resident = nb;
     }
-    k_stream_step<M, C64, NX><<<g, kStreamThreads, sm, c->stream>>>(c->P);
+    const int g = std::min(c->nsm * std::min(blocks_per_sm, resident), kMaxExpandBlocks);
+    k_stream_step<M, C64, NX, S><<<g, kStreamThreads, sm, c->stream>>>(c->P);
     return cudaGetLastError();
 }
 
+template <int M, bool C64, int NX>
+cudaError_t launch_stream_tile(qp_ctx *c) {
+    switch (c->stream_tile) {
+        case 256: return launch_stream_kernel<M, C64, NX, 256>(c, c->bps_exp);
+        case 1024: return launch_stream_kernel<M, C64, NX, 1024>(c, c->bps_exp);
+        default: return launch_stream_kernel<M, C64, NX, 512>(c, c->bps_exp);
+    }
+}
+
+// One step of the stream engine: a single kernel (events 2 -> 3 bracket it;
+// the other intervals of the per-kernel profile are empty).
 template <int M, typename Amp>
 cudaError_t launch_stream_t(qp_ctx *c, cudaEvent_t *ev) {
     constexpr bool C64 = sizeof(Amp) == sizeof(float2);
-    const int g = std::min(c->nsm * c->bps_exp, kMaxExpandBlocks);
     if (ev) {
         cudaEventRecord(ev[0], c->stream);
         cudaEventRecord(ev[1], c->stream);
@@ -1486,14 +1569,15 @@ cudaError_t launch_stream_t(qp_ctx *c, cudaEvent_t *ev) {
     }
     cudaError_t e;
     if constexpr (M == 2) {
-        e = c->stream_nx == 4 ? launch_stream_kernel<M, C64, 4>(c, g) : launch_stream_kernel<M, C64, 1>(c, g);
+        e = c->stream_nx == 4 ? launch_stream_tile<M, C64, 4>(c) : launch_stream_tile<M, C64, 1>(c);
     } else {
-        e = launch_stream_kernel<M, C64, 1>(c, g);
+        e = launch_stream_tile<M, C64, 1>(c);
     }
     if (e != cudaSuccess) return e;
-    if (ev) cudaEventRecord(ev[3], c->stream);
-    k_finalize<<<1, 256, 0, c->stream>>>(c->P, M * M, g);
-    if (ev) cudaEventRecord(ev[4], c->stream);
+    if (ev) {
+        cudaEventRecord(ev[3], c->stream);
+        cudaEventRecord(ev[4], c->stream);
+    }
     return cudaGetLastError();
 }
 
@@ -1933,6 +2017,9 @@ qp_status qp_set_rho0(qp_ctx *c, const double *re, const double *im) {
     std::vector<long long> kept0(NI, nnz);
     QP_CUDA(c, cudaMemcpyAsync(c->P.inst_kept, kept0.data(), NI * sizeof(long long), cudaMemcpyHostToDevice, c->stream));
     QP_CUDA(c, cudaMemsetAsync(c->P.fin_count, 0, sizeof(unsigned int), c->stream));
+    // look-back words are tagged with the step number, which restarts at 0:
+    // words of an earlier propagation must not pass for this one's
+    QP_CUDA(c, cudaMemsetAsync(c->P.tile_state, 0, (size_t)c->L.max_tiles * M * M * 8, c->stream));
     StepRec r0{0, 0, 0, (long long)n};
     QP_CUDA(c, cudaMemcpyAsync(c->P.stats_ring, &r0, sizeof(StepRec), cudaMemcpyHostToDevice, c->stream));
     k_clear_table<<<c->nsm * 4, 256, 0, c->stream>>>(c->P.slots, c->P.repk, c->L.tcap);
@@ -2005,8 +2092,8 @@ static qp_status read_state(qp_ctx *c, DevState *s) {
         if (s->err & kErrPaths) what += " path buffer (max_paths)";
         if (s->err & kErrGroups) what += " merge groups (max_groups)";
         if (s->err & kErrProbe) what += " merge table probe limit";
-        if (s->err & kErrTimeout)
-            return fail(c, QP_ERR_TIMEOUT, "a grid barrier of the persistent step kernel timed out at step " +
+        if (what.empty())   // only a bounded wait gave up: a grid barrier or a look-back
+            return fail(c, QP_ERR_TIMEOUT, "a bounded device wait (grid barrier or tile look-back) timed out at step " +
                                                std::to_string(s->t + 1));
         return fail(c, QP_ERR_CAPACITY, "capacity exceeded at step " + std::to_string(s->t + 1) + ":" + what);
     }
@@ -2170,6 +2257,7 @@ qp_status qp_get_tuning(qp_ctx *c, qp_tuning *out) {
     out->graph_steps = c->graph_steps;
     out->table_log2 = (int)c->P.tcap_log2;
     out->engine = c->use_stream ? QP_ENGINE_STREAM : QP_ENGINE_HASH;
+    out->stream_tile = c->stream_tile;
     return QP_OK;
 }
 
@@ -2186,6 +2274,9 @@ qp_status qp_set_tuning(qp_ctx *c, const qp_tuning *t) {
     if (t->graph_steps < 1 || t->graph_steps > 1024) return fail(c, QP_ERR_ARG, "graph_steps out of range");
     if (t->table_log2 < 4 || t->table_log2 > (int)c->L.tcap_log2)
         return fail(c, QP_ERR_ARG, "table_log2 out of range (at most the workspace's table)");
+    if (t->stream_tile != 0 && t->stream_tile != 256 && t->stream_tile != 512 && t->stream_tile != 1024)
+        return fail(c, QP_ERR_ARG, "stream_tile must be 0 (unchanged), 256, 512 or 1024");
+    if (t->stream_tile) c->stream_tile = t->stream_tile;
     c->use_persistent = t->mode == QP_LAUNCH_PERSISTENT;
     c->bps_ins = t->insert_blocks_per_sm;
     c->bps_exp = t->expand_blocks_per_sm;
@@ -2245,17 +2336,25 @@ qp_status qp_autotune(qp_ctx *c, int trial_steps, int use_cache, qp_tuning *best
             if ((1ll << (tl - d)) >= need) tables.push_back(tl - d);
         }
     const int gs = 8;
-    for (int tb : tables)
-        for (int bi : {2, 4, 8})
-            for (int be : {2, 4, 8}) {
+    if (c->use_stream) {   // one kernel per step: tile size and blocks per SM
+        for (int tile : {256, 512, 1024})
+            for (int be : {1, 2, 4, 8}) {
                 if (c->nsm * be > kMaxExpandBlocks) continue;
-                cand.push_back(qp_tuning{QP_LAUNCH_GRAPH, bi, be, c->persist_grid, gs, tb, 0});
+                cand.push_back(qp_tuning{QP_LAUNCH_GRAPH, c->bps_ins, be, c->persist_grid, gs, tl, 0, tile});
             }
-    if (c->persist_max > 0)
-        for (int pb : {1, 2, 4}) {
-            const int blocks = std::min(c->persist_max, pb * c->nsm);
-            if (!c->use_stream) cand.push_back(qp_tuning{QP_LAUNCH_PERSISTENT, 4, 4, blocks, gs, tl, 0});
-        }
+    } else {
+        for (int tb : tables)
+            for (int bi : {2, 4, 8})
+                for (int be : {2, 4, 8}) {
+                    if (c->nsm * be > kMaxExpandBlocks) continue;
+                    cand.push_back(qp_tuning{QP_LAUNCH_GRAPH, bi, be, c->persist_grid, gs, tb, 0, 0});
+                }
+        if (c->persist_max > 0)
+            for (int pb : {1, 2, 4}) {
+                const int blocks = std::min(c->persist_max, pb * c->nsm);
+                cand.push_back(qp_tuning{QP_LAUNCH_PERSISTENT, 4, 4, blocks, gs, tl, 0, 0});
+            }
+    }
     qp_tuning save;
     qp_get_tuning(c, &save);
     cudaEvent_t e0, e1;

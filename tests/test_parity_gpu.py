@@ -137,6 +137,31 @@ def test_spin_boson_structured_dk16_first_40_steps_against_stored_oracle():
     assert [s[3] for s in stats] == list(n[1:])
 
 
+@pytest.mark.parametrize("precision", ["fp64", "c64"])
+def test_stream_engine_rerun_and_launch_shapes_agree(precision):
+    """Look-back words carry the step number, which restarts with every
+    qp_set_rho0: a second propagation on the same context, and the same
+    propagation with every tile size and grid, give the same survivor counts
+    and rho (group sums are FP64 atomics, so rho only up to rounding)."""
+    w = W.SPIN_BOSON_STRUCTURED_DK16
+    p = Propagator.from_workload(w, precision=precision, engine="stream", max_paths=1 << 21)
+    runs = []
+    for tile, bps in [(512, 4), (512, 4), (256, 2), (1024, 1), (512, 8)]:
+        p.set_rho0(w.rho0_array())
+        p.set_tuning(stream_tile=tile, expand_blocks_per_sm=bps)
+        p.step(60)
+        p.sync()
+        runs.append((p.rho(0, 61), [s[3] for s in p.stats(1, 60)]))
+    tol = 1e-12 if precision == "fp64" else 1e-6
+    for rho, kept in runs[1:]:
+        assert kept == runs[0][1]
+        assert np.abs(rho - runs[0][0]).max() <= tol
+    if precision == "fp64":
+        t, n, rho_o = load_golden("spin_boson_structured_dk16_rho40.txt")
+        assert np.abs(runs[-1][0][:41] - rho_o).max() <= RHO_TOL
+    p.close()
+
+
 def test_spin_boson_structured_dk16_full_length_properties():
     """All 2000 steps at full size: properties that hold at any size.  The
     trace is conserved by merging and propagation, so it changes only through
