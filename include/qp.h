@@ -63,12 +63,19 @@ enum { QP_FP64 = 0,       /* complex128 amplitudes, FP64 everywhere */
        QP_C64 = 1 };      /* complex64 amplitudes, FP32 influence exponent
                              with compensated sums; FP64 eta, merge sums, rho */
 
-enum { QP_ENGINE_AUTO = 0,    /* library picks                                 */
+enum { QP_ENGINE_AUTO = 0,    /* library picks: the stream engine where the
+                                 mask allows it (single problems), else the
+                                 merge table; the workspace holds both        */
        QP_ENGINE_HASH = 1,    /* device open-addressing table keyed by the
-                                 masked key (any mask)                          */
+                                 masked key (any mask, batches)                 */
        QP_ENGINE_STREAM = 2   /* order-preserving stream: groups stay
                                  contiguous, merge = segmented reduction
-                                 (masks whose P' is a prefix {0..k-1})         */ };
+                                 (single problems; masks whose P' is a prefix
+                                 {0..k-1}, for M = 2 plus one more position).
+                                 Stored paths live in M*M regions of
+                                 max_paths / (M*M) entries, by newest point.
+                                 The workspace holds no merge table: about
+                                 2 * (8 + amplitude bytes) per path.          */ };
 
 typedef struct {
     int M;                 /* number of system states (DVR points), 2..4            */

@@ -60,6 +60,7 @@ constexpr int kMaxExpandBlocks = 2048;
 constexpr int kPersistThreads = 256;
 constexpr int kMaxInst = 128;                      // instances of one batched context
 constexpr int kStreamMinTile = 256;                 // smallest stream tile (256, 512 or 1024 stored paths)
+constexpr size_t kMaxStreamLut = 32 * 1024;         // history tables staged in shared memory up to this size
 constexpr int kStreamThreads = 256;
 constexpr unsigned kLbAgg = 1u, kLbInc = 2u;        // look-back word states (bits 30-31)
 constexpr long long kBarrierCycles = 4000000000ll;  // ~2 s at 2 GHz: a grid barrier gives up after this
@@ -147,14 +148,12 @@ __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 
 // Path data and merge-table fields are written by other blocks of the same
 // persistent kernel, so they are read through L2 (ld.global.cg), never L1.
-// Global memory only: shared-memory copies are read with as_d2.
+// Global memory only (never a shared-memory pointer).
 __device__ __forceinline__ double2 load_amp(const double2 *p, unsigned long long i) { return __ldcg(p + i); }
 __device__ __forceinline__ double2 load_amp(const float2 *p, unsigned long long i) {
     const float2 v = __ldcg(p + i);
     return make_double2(v.x, v.y);
 }
-__device__ __forceinline__ double2 as_d2(double2 v) { return v; }
-__device__ __forceinline__ double2 as_d2(float2 v) { return make_double2(v.x, v.y); }
 
 // float -> double by IEEE-754 fields (exact): a normal number keeps its sign
 // and 23 fraction bits, its exponent is rebiased by 1023 - 127; zeros keep
@@ -343,6 +342,22 @@ __device__ __forceinline__ unsigned key_byte(unsigned long long k, int j) { retu
 // read from tables of exp(-delta T) (no transcendental per group).
 // C64: H is summed in FP32 with Kahan compensation over the per-byte terms
 // (each stored as an FP32 hi + lo pair), then exp/sincos in FP32.
+// History tables of one instance at one window length, in global or shared
+// memory: FP32 hi/lo parts of the per-byte history terms, [chunk][256] each
+// (C64 path), or exp(-delta_d T), [delta][chunk][256] (FP64 path).
+struct Tab {
+    const float2 *hi, *lo;
+    const double2 *et;
+};
+__device__ __forceinline__ Tab tab_global(const Params &P, int n_act, int inst) {
+    const size_t row = (size_t)(n_act - 1) * P.nchunks * kLutEntries;
+    Tab t;
+    t.hi = P.lutf + (size_t)inst * P.lut_stride + row;
+    t.lo = P.lutf_lo + (size_t)inst * P.lut_stride + row;
+    t.et = P.etab + (size_t)inst * P.etab_stride + (size_t)P.ndelta * row;
+    return t;
+}
+
 template <int M, bool C64>
 struct Expander {
     static constexpr int MM = M * M;
@@ -377,18 +392,24 @@ struct Expander {
     template <typename SumT>
     static __device__ __forceinline__ unsigned children(const Params &P, int n_act, int inst, unsigned long long rep,
                                                         SumT S, const double2 *w, const float2 *wf, AmpT *v) {
+        return children_tab(P, tab_global(P, n_act, inst), rep, S, w, wf, v);
+    }
+
+    // the same with the history tables given (tb: global or shared memory)
+    template <typename SumT>
+    static __device__ __forceinline__ unsigned children_tab(const Params &P, const Tab &tb, unsigned long long rep,
+                                                            SumT S, const double2 *w, const float2 *wf, AmpT *v) {
         const unsigned c0 = (unsigned)(rep & ((1u << P.b) - 1u));
         const int pidx = (int)(c0 & ((1u << P.bs) - 1u)) * M + (int)(c0 >> P.bs);
         unsigned keep = 0;
         if constexpr (C64) {
             float2 Ed[ND];
             if (P.ndelta) {
-                const size_t off = (size_t)inst * P.lut_stride + (size_t)(n_act - 1) * P.nchunks * kLutEntries;
                 float sx = 0.f, sy = 0.f, cx = 0.f, cy = 0.f, lx = 0.f, ly = 0.f;
                 for (int j = 0; j < P.nchunks; ++j) {
-                    const size_t idx = off + (size_t)j * kLutEntries + key_byte(rep, j);
-                    const float2 hi = __ldg(&P.lutf[idx]);
-                    const float2 lo = __ldg(&P.lutf_lo[idx]);
+                    const int idx = j * kLutEntries + (int)key_byte(rep, j);
+                    const float2 hi = tb.hi[idx];
+                    const float2 lo = tb.lo[idx];
                     const float yx = hi.x - cx, tx = sx + yx;
                     cx = (tx - sx) - yx;
                     sx = tx;
@@ -420,13 +441,12 @@ struct Expander {
             }
         } else {
             double2 Ed[ND];
-            const size_t dstride = (size_t)P.nchunks * kLutEntries;
-            const double2 *et = P.etab + (size_t)inst * P.etab_stride + (size_t)(n_act - 1) * P.ndelta * dstride;
+            const int dstride = P.nchunks * kLutEntries;
 #pragma unroll
             for (int d = 0; d < ND; ++d) {
                 if (d >= P.ndelta) break;
                 double2 e = make_double2(1.0, 0.0);
-                for (int j = 0; j < P.nchunks; ++j) e = cmul(e, __ldg(&et[d * dstride + (size_t)j * kLutEntries + key_byte(rep, j)]));
+                for (int j = 0; j < P.nchunks; ++j) e = cmul(e, tb.et[d * dstride + j * kLutEntries + (int)key_byte(rep, j)]);
                 Ed[d] = e;
             }
 #pragma unroll
@@ -801,28 +821,77 @@ __device__ __forceinline__ unsigned long long lb_word(unsigned epoch, unsigned s
     return ((unsigned long long)epoch << 32) | ((unsigned long long)state << 30) | cnt;
 }
 
+// Dynamic shared memory of the stream kernel for a tile of S stored paths
+// (16-byte aligned arrays).  A tile holds at most NG = S + NX - 1 groups: every
+// group has a member in the tile, except sub-groups of the tile's last run
+// whose members all lie past the tile end (at most NX - 1 of them).
+//   gS    [NG] FP64 group sums          grep [NG] representative keys
+//   wm    [NG] maximum weight (bits)    key/amp [S] the tile's stored paths
+//   stage [NSTG][M*M] children amplitudes of the first NSTG groups (S/2
+//         for M = 2, S/3 otherwise) between the two passes (tiles usually
+//         hold fewer groups; later ones are recomputed in pass B)
+//   seg   [S+1] run heads               xm/sb [S]/[S+1] sub-group bits and
+//   keep  [NG] survivor bits                 slot bases per run (NX > 1)
+// followed at run time by the history tables when they are staged.
+template <int M, bool C64, int NX, int S>
+struct StreamLayout {
+    using AmpT = typename std::conditional<C64, float2, double2>::type;
+    using WT = typename std::conditional<C64, unsigned, unsigned long long>::type;
+    static constexpr int MM = M * M;
+    static constexpr int NG = S + NX - 1;
+    static constexpr size_t a16(size_t x) { return (x + 15) & ~(size_t)15; }
+    static constexpr int NSTG = M == 2 ? S / 2 : S / 3;
+    static constexpr bool stage = (size_t)NSTG * MM * sizeof(AmpT) <= 64 * 1024;
+    static constexpr size_t gS = 0;
+    static constexpr size_t grep = gS + a16((size_t)NG * sizeof(double2));
+    static constexpr size_t wm = grep + a16((size_t)NG * 8);
+    static constexpr size_t key = wm + a16((size_t)NG * sizeof(WT));
+    static constexpr size_t amp = key + a16((size_t)S * 8);
+    static constexpr size_t stg = amp + a16((size_t)S * sizeof(AmpT));
+    static constexpr size_t seg = stg + (stage ? a16((size_t)NSTG * MM * sizeof(AmpT)) : 0);
+    static constexpr size_t xm = seg + a16((size_t)(S + 1) * 4);
+    static constexpr size_t sb = xm + (NX > 1 ? a16((size_t)S * 4) : 0);
+    static constexpr size_t keep = sb + (NX > 1 ? a16((size_t)(S + 1) * 4) : 0);
+    static constexpr size_t lut = keep + a16((size_t)NG * 2);
+    static constexpr size_t bytes = lut;   // + staged history tables (run time)
+};
+
+// Relaxed GPU-scope load of a word other blocks publish (no L1, no
+// hoisting; independent loads stay in flight together).
+__device__ __forceinline__ unsigned long long ld_relaxed_gpu(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
 // One step of the stream engine: one kernel over tiles of the stored set.
 // The set lives in M*M regions (newest point), each sorted by the older
 // points, so the paths of one pre-merge group form a run of equal prefix
 // (positions 0 .. k-1 of P'); at most one extra position of P' splits a run
-// into NX sub-groups.  Per tile (dynamic tickets): load, find run heads,
-// reduce each run owned by the tile (runs start in the tile and may extend
-// past it) into sub-group sums and representatives, count survivors per new
-// point, get the tile's output offsets per region by decoupled look-back
-// (bounded waits), recompute and write the survivors.  Output region c
-// receives, in order, the children with newest point c of all groups, so the
-// next set is again sorted.  No atomics on the data.  The last block to
-// finish sums the blocks' partials of rho(t+1) and publishes the step.
+// into NX sub-groups.  Per tile (dynamic tickets): load (and prefetch the 32
+// paths past the tile end), find run heads; for NX > 1 give each sub-group
+// present a compact slot; sum each group in FP64 and elect its
+// representative (runs start in the tile and may extend past it); compute
+// the children of every group once, keep them in shared memory, count the
+// survivors per new point and accumulate rho(t+1); get the tile's output
+// offsets per region by a decoupled look-back (one warp, a window of
+// 32 * LB_K predecessors per round, bounded waits); write the survivors.
+// Output region c receives, in order, the children with newest point c of
+// all groups, so the next set is again sorted.  No atomics on the data.  The
+// last block to finish sums the blocks' partials of rho(t+1) and publishes
+// the step.  lut_smem: the history tables of this window length are copied
+// into shared memory once per block.
 template <int M, bool C64, int NX, int S>
-__global__ void __launch_bounds__(kStreamThreads) k_stream_step(Params P) {
+__global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 2 : 1)
+    k_stream_step(Params P, int lut_smem) {
     using X = Expander<M, C64>;
+    using Lay = StreamLayout<M, C64, NX, S>;
     using AmpT = typename X::AmpT;
-    // weight |a|^2 as ordered bits: FP32 on the C64 path, FP64 otherwise
-    using WT = typename std::conditional<C64, unsigned, unsigned long long>::type;
+    using WT = typename Lay::WT;   // weight |a|^2 as ordered bits: FP32 (C64) or FP64
     constexpr int MM = M * M;
-    constexpr int NT = kStreamThreads, NW = NT / 32;
-    constexpr int NSLOT = S * NX;
-    static_assert(S % NT == 0 && S / NT <= 32, "tile size");
+    constexpr int NT = kStreamThreads, NW = NT / 32, EPT = S / NT;
+    constexpr int NG = Lay::NG;
+    static_assert(S % NT == 0 && EPT <= 32, "tile size");
     DevState *st = P.st;
     if (st->err) return;
     const unsigned long long t = st->t, tn = t + 1;
@@ -839,29 +908,51 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream_step(Params P) {
     unsigned long long *keys_out = P.keys[outp];
     AmpT *amps_out = static_cast<AmpT *>(P.amps[outp]);
 
-    // tile arrays in dynamic shared memory (stream_smem_bytes)
     extern __shared__ __align__(16) unsigned char s_dyn[];
-    double2 *s_gS = reinterpret_cast<double2 *>(s_dyn);
-    unsigned long long *s_grep = reinterpret_cast<unsigned long long *>(s_gS + NSLOT);
-    WT *s_wm = reinterpret_cast<WT *>(s_grep + NSLOT);   // sub-group maximum weight (bits)
-    unsigned long long *s_key = s_grep + 2 * NSLOT;
-    AmpT *s_amp = reinterpret_cast<AmpT *>(s_key + S);
-    int *s_seg = reinterpret_cast<int *>(s_amp + S);
-    unsigned short *s_keep = reinterpret_cast<unsigned short *>(s_seg + S + 1);
-    __shared__ double2 s_w[MM * MM];
+    double2 *s_gS = reinterpret_cast<double2 *>(s_dyn + Lay::gS);
+    unsigned long long *s_grep = reinterpret_cast<unsigned long long *>(s_dyn + Lay::grep);
+    WT *s_wm = reinterpret_cast<WT *>(s_dyn + Lay::wm);
+    unsigned long long *s_key = reinterpret_cast<unsigned long long *>(s_dyn + Lay::key);
+    AmpT *s_amp = reinterpret_cast<AmpT *>(s_dyn + Lay::amp);
+    AmpT *s_stg = reinterpret_cast<AmpT *>(s_dyn + Lay::stg);
+    int *s_seg = reinterpret_cast<int *>(s_dyn + Lay::seg);
+    unsigned *s_xm = reinterpret_cast<unsigned *>(s_dyn + Lay::xm);
+    int *s_sb = reinterpret_cast<int *>(s_dyn + Lay::sb);
+    unsigned short *s_keep = reinterpret_cast<unsigned short *>(s_dyn + Lay::keep);
+    __shared__ double2 s_w[C64 ? 1 : MM * MM];   // FP64 weights (FP64 path only)
     __shared__ float2 s_wf[MM * MM];
     __shared__ long long s_nr[MM], s_tile0[MM + 1];
-    __shared__ unsigned s_wsum[NW][MM > 1 ? MM : 1];
-    __shared__ unsigned long long s_base[MM], s_tot[MM];
-    __shared__ unsigned s_ticket, s_nseg, s_ngroups, s_hw[NW];
+    __shared__ unsigned s_wsum[NW][MM];
+    __shared__ unsigned long long s_base[MM], s_tot[MM], s_kprev, s_ra_key[32];
+    __shared__ AmpT s_ra_amp[32];
+    __shared__ unsigned s_ra_n;   // prefetched paths past the tile end
+    __shared__ unsigned s_ticket, s_nseg, s_ng, s_hw[NW];
     __shared__ double2 s_r[NW][MM];
     __shared__ bool s_last;
     const double tie_d = 1.0 - P.tie_rel;   // R4 window, once per thread
     const float tie_f = (float)tie_d;
 
+    // weights and the history tables of this window length
     for (int i = threadIdx.x; i < MM * MM; i += NT) {
-        s_w[i] = P.wtab[i];
+        if constexpr (!C64) s_w[i] = P.wtab[i];
         s_wf[i] = P.wtabf[i];
+    }
+    Tab tab = tab_global(P, n_act, 0);
+    if (lut_smem && P.ndelta) {
+        const int n = P.nchunks * kLutEntries;
+        if constexpr (C64) {
+            float2 *hi = reinterpret_cast<float2 *>(s_dyn + Lay::lut), *lo = hi + n;
+            for (int i = threadIdx.x; i < n; i += NT) {
+                hi[i] = __ldg(tab.hi + i);
+                lo[i] = __ldg(tab.lo + i);
+            }
+            tab.hi = hi;
+            tab.lo = lo;
+        } else {
+            double2 *et = reinterpret_cast<double2 *>(s_dyn + Lay::lut);
+            for (int i = threadIdx.x; i < n * P.ndelta; i += NT) et[i] = __ldg(tab.et + i);
+            tab.et = et;
+        }
     }
     if (threadIdx.x == 0) {
         long long acc = 0;
@@ -879,14 +970,30 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream_step(Params P) {
     __syncthreads();
     const long long ntiles = s_tile0[MM];
 
-    typename X::AccT racc[MM], rcmp[MM];
+    // rho(t+1) accumulators of this thread: FP64, or on the C64 path FP32
+    // with a Kahan compensation term (M = 2; for M >= 3 plain FP32 sums, to
+    // stay within the register budget of two blocks per SM), widened to
+    // FP64 once at the end
+    constexpr bool kKahan = C64 && M == 2;
+    typename X::AccT racc[MM], rcmp[kKahan ? MM : 1];
 #pragma unroll
     for (int k = 0; k < MM; ++k) {
         racc[k].x = racc[k].y = 0;
-        rcmp[k].x = rcmp[k].y = 0;
+        if constexpr (kKahan) rcmp[k].x = rcmp[k].y = 0;
     }
     const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
     unsigned long long block_kept = 0;
+    auto weight_bits = [&](AmpT a) -> WT {
+        if constexpr (C64) return __float_as_uint(a.x * a.x + a.y * a.y);
+        else return (unsigned long long)__double_as_longlong(a.x * a.x + a.y * a.y);
+    };
+    auto within_tie = [&](WT w, WT wm) -> bool {
+        if constexpr (C64) return __uint_as_float(w) >= tie_f * __uint_as_float(wm);
+        else return __longlong_as_double((long long)w) >= tie_d * __longlong_as_double((long long)wm);
+    };
+    auto xval = [&](unsigned long long key) -> unsigned {
+        return NX > 1 ? (unsigned)((key >> P.x_shift) & (NX - 1)) : 0u;
+    };
 
     for (;;) {
         if (threadIdx.x == 0) s_ticket = atomicAdd(&st->ticket[cs], 1u);
@@ -900,23 +1007,43 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream_step(Params P) {
         const int cnt = (int)min((long long)S, nr - e0);
         const unsigned long long *kin = keys_in + r * G;
         const AmpT *ain = amps_in + r * G;
+        // load the tile; warp 0 prefetches the 32 paths past its end (the
+        // last run may continue there), thread 0 the key before it; slots of
+        // the previous tile are free (the loop ends with a barrier)
         for (int i = threadIdx.x; i < cnt; i += NT) {
             s_key[i] = __ldcg(kin + e0 + i);
             s_amp[i] = __ldcg(ain + e0 + i);
         }
+        if (warp == 0) {
+            const bool ok = cnt == S && e0 + S + lane < nr;
+            if (ok) {
+                s_ra_key[lane] = __ldcg(kin + e0 + S + lane);
+                s_ra_amp[lane] = __ldcg(ain + e0 + S + lane);
+            }
+            const unsigned okm = __ballot_sync(0xffffffffu, ok);
+            if (lane == 0) s_ra_n = __popc(okm);   // a prefix of the 32 lanes
+        }
+        if (threadIdx.x == 0) s_kprev = e0 > 0 ? __ldcg(kin + e0 - 1) : 0ull;
+        for (int i = threadIdx.x; i < NG; i += NT) {
+            s_gS[i] = make_double2(0.0, 0.0);
+            s_grep[i] = kEmpty;
+            s_wm[i] = 0;
+        }
+        if constexpr (NX > 1)
+            for (int i = threadIdx.x; i < S; i += NT) s_xm[i] = 0u;
         __syncthreads();
-        // run heads (S/NT entries per thread), block scan of their count
+        // run heads (EPT consecutive entries per thread), block scan of their count
         unsigned hmask = 0;
 #pragma unroll
-        for (int u = 0; u < S / NT; ++u) {
-            const int i = threadIdx.x * (S / NT) + u;
+        for (int u = 0; u < EPT; ++u) {
+            const int i = threadIdx.x * EPT + u;
             if (i < cnt) {
-                const unsigned long long prevk = i > 0 ? s_key[i - 1] : (e0 > 0 ? __ldcg(kin + e0 - 1) : ~s_key[0]);
                 if (i == 0 && e0 == 0) hmask |= 1u << u;
-                else if ((s_key[i] & pref) != (prevk & pref)) hmask |= 1u << u;
+                else if ((s_key[i] & pref) != ((i > 0 ? s_key[i - 1] : s_kprev) & pref)) hmask |= 1u << u;
             }
         }
-        unsigned hc = __popc(hmask), hincl = hc;
+        const unsigned hc = __popc(hmask);
+        unsigned hincl = hc;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const unsigned y = __shfl_up_sync(0xffffffffu, hincl, o);
@@ -934,132 +1061,225 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream_step(Params P) {
             s_nseg = a;
         }
         __syncthreads();
-        {
-            unsigned pos = s_hw[warp] + hincl - hc;
-#pragma unroll
-            for (int u = 0; u < S / NT; ++u)
-                if (hmask & (1u << u)) s_seg[pos++] = threadIdx.x * (S / NT) + u;
-        }
-        __syncthreads();
         const int nseg = (int)s_nseg;
-        if (threadIdx.x == 0) s_seg[nseg] = cnt;
-        __syncthreads();
-        // reduce the runs into NX sub-groups, one thread per stored path:
-        // shared-memory atomics add the amplitude into its sub-group's FP64
-        // sum and raise its maximum weight, then paths within the tie window
-        // of the maximum compete for the representative (atomicMin on the
-        // key).  Paths of the tile's last run past the tile end are read by
-        // warp 0, 32 at a time, while they share the run's prefix.
-        const int nslot_all = nseg * NX;
-        for (int i = threadIdx.x; i < nslot_all; i += NT) {
-            s_gS[i] = make_double2(0.0, 0.0);
-            s_grep[i] = kEmpty;
-            s_wm[i] = 0;
+        const int segbase = (int)(s_hw[warp] + hincl - hc) - 1;   // run of the entry before the thread's first
+        {
+            int pos = segbase + 1;
+#pragma unroll
+            for (int u = 0; u < EPT; ++u)
+                if (hmask & (1u << u)) s_seg[pos++] = threadIdx.x * EPT + u;
         }
         __syncthreads();
-        int segbase = (int)(s_hw[warp] + hincl - hc) - 1;   // run of the thread's first entry (-1: previous tile's)
-        auto slot_of_key = [&](int sg, unsigned long long key) {
-            return sg * NX + (NX > 1 ? (int)((key >> P.x_shift) & (NX - 1)) : 0);
-        };
-        auto weight_bits = [&](AmpT a) -> WT {
-            if constexpr (C64) return __float_as_uint(a.x * a.x + a.y * a.y);
-            else return (unsigned long long)__double_as_longlong(a.x * a.x + a.y * a.y);
-        };
-        auto within_tie = [&](WT w, WT wm) -> bool {
-            if constexpr (C64) return __uint_as_float(w) >= tie_f * __uint_as_float(wm);
-            else return __longlong_as_double((long long)w) >= tie_d * __longlong_as_double((long long)wm);
-        };
+        // extent of the tile's last run past the tile end (warp 0): members
+        // share its prefix; the first 32 come from the prefetch.  For NX > 1
+        // the sub-group bits of every run are collected.
         const unsigned long long plast = nseg ? (s_key[s_seg[nseg - 1]] & pref) : 0ull;
-        {
+        long long ahead = cnt;   // tile-relative end of the last run
+        if constexpr (NX > 1) {
             int sg = segbase;
 #pragma unroll
-            for (int u = 0; u < S / NT; ++u) {
-                const int i = threadIdx.x * (S / NT) + u;
+            for (int u = 0; u < EPT; ++u) {
+                const int i = threadIdx.x * EPT + u;
                 if (hmask & (1u << u)) ++sg;
-                if (i < cnt && sg >= 0) {
-                    const AmpT a = s_amp[i];
-                    const int sl = slot_of_key(sg, s_key[i]);
-                    atomicAdd(&s_gS[sl].x, to_d(a.x));
-                    atomicAdd(&s_gS[sl].y, to_d(a.y));
-                    atomicMax(&s_wm[sl], weight_bits(a));
-                }
+                if (i < cnt && sg >= 0) atomicOr(&s_xm[sg], 1u << xval(s_key[i]));
             }
         }
-        long long ahead = cnt;   // tile-relative end of the last run
         if (warp == 0 && nseg > 0 && cnt == S) {
-            for (;;) {
-                const long long i = ahead + lane;
-                bool inrun = e0 + i < nr;
-                unsigned long long key = 0;
-                if (inrun) {
-                    key = __ldcg(kin + e0 + i);
-                    inrun = (key & pref) == plast;
+            unsigned long long key = s_ra_key[lane];
+            bool inrun = lane < s_ra_n && (key & pref) == plast;
+            for (int round = 0;; ++round) {
+                if (round > 0) {
+                    const long long i = e0 + ahead + lane;
+                    inrun = i < nr;
+                    if (inrun) {
+                        key = __ldcg(kin + i);
+                        inrun = (key & pref) == plast;
+                    }
                 }
                 const unsigned inm = __ballot_sync(0xffffffffu, inrun);
                 const int nin = inm == 0xffffffffu ? 32 : __ffs(~inm) - 1;   // leading members of the run
-                if ((int)lane < nin) {
-                    const AmpT a = __ldcg(ain + e0 + i);
-                    const int sl = slot_of_key(nseg - 1, key);
-                    atomicAdd(&s_gS[sl].x, to_d(a.x));
-                    atomicAdd(&s_gS[sl].y, to_d(a.y));
-                    atomicMax(&s_wm[sl], weight_bits(a));
-                }
+                if constexpr (NX > 1)
+                    if ((int)lane < nin) atomicOr(&s_xm[nseg - 1], 1u << xval(key));
                 ahead += nin;
                 if (nin < 32) break;
             }
         }
         __syncthreads();
-        {
-            int sg = segbase;
+        // compact slots: sub-groups of run sg are slots sb[sg] + rank of x
+        int ngroups = nseg;
+        if constexpr (NX > 1) {
+            // EPT runs per thread: thread-local sum, warp scan, across warps
+            unsigned loc[EPT];
+            unsigned lsum = 0;
 #pragma unroll
-            for (int u = 0; u < S / NT; ++u) {
-                const int i = threadIdx.x * (S / NT) + u;
+            for (int u = 0; u < EPT; ++u) {
+                const int g = threadIdx.x * EPT + u;
+                loc[u] = g < nseg ? (unsigned)__popc(s_xm[g]) : 0u;
+                lsum += loc[u];
+            }
+            unsigned inc = lsum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
+                if ((int)lane >= o) inc += y;
+            }
+            if (lane == 31) s_wsum[warp][0] = inc;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                unsigned a = 0;
+                for (int w = 0; w < NW; ++w) {
+                    const unsigned v = s_wsum[w][0];
+                    s_wsum[w][0] = a;
+                    a += v;
+                }
+                s_ng = a;
+            }
+            __syncthreads();
+            unsigned pos = s_wsum[warp][0] + inc - lsum;
+#pragma unroll
+            for (int u = 0; u < EPT; ++u) {
+                const int g = threadIdx.x * EPT + u;
+                if (g < nseg) s_sb[g] = (int)pos;
+                pos += loc[u];
+            }
+            ngroups = (int)s_ng;
+            __syncthreads();
+        }
+        auto slot_of = [&](int sg, unsigned long long key) -> int {
+            if constexpr (NX > 1) {
+                const unsigned m = s_xm[sg];
+                return s_sb[sg] + __popc(m & ((1u << xval(key)) - 1u));
+            } else {
+                return sg;
+            }
+        };
+        // pass 1: group sums (FP64) and maximum weights; consecutive entries
+        // of a thread in the same slot are combined before the atomics
+        {
+            int sg = segbase, cur = -1;
+            double ax = 0.0, ay = 0.0;
+            WT wmx = 0;
+#pragma unroll
+            for (int u = 0; u < EPT; ++u) {
+                const int i = threadIdx.x * EPT + u;
                 if (hmask & (1u << u)) ++sg;
                 if (i < cnt && sg >= 0) {
-                    const int sl = slot_of_key(sg, s_key[i]);
-                    if (within_tie(weight_bits(s_amp[i]), s_wm[sl])) atomicMin(&s_grep[sl], s_key[i]);
+                    const AmpT a = s_amp[i];
+                    const int sl = slot_of(sg, s_key[i]);
+                    const WT wb = weight_bits(a);
+                    if (sl != cur) {
+                        if (cur >= 0) {
+                            atomicAdd(&s_gS[cur].x, ax);
+                            atomicAdd(&s_gS[cur].y, ay);
+                            atomicMax(&s_wm[cur], wmx);
+                        }
+                        cur = sl;   // the slot's local sum starts at its first member
+                        ax = to_d(a.x);
+                        ay = to_d(a.y);
+                        wmx = wb;
+                    } else {
+                        ax += to_d(a.x);
+                        ay += to_d(a.y);
+                        wmx = wb > wmx ? wb : wmx;
+                    }
                 }
             }
+            if (cur >= 0) {
+                atomicAdd(&s_gS[cur].x, ax);
+                atomicAdd(&s_gS[cur].y, ay);
+                atomicMax(&s_wm[cur], wmx);
+            }
+        }
+        if (warp == 0 && ahead > cnt) {   // members of the last run past the tile end
+            for (long long base = cnt; base < ahead; base += 32) {
+                const long long i = base + lane;
+                if (i < ahead) {
+                    unsigned long long key;
+                    AmpT a;
+                    if (base == cnt) {
+                        key = s_ra_key[lane];
+                        a = s_ra_amp[lane];
+                    } else {
+                        key = __ldcg(kin + e0 + i);
+                        a = __ldcg(ain + e0 + i);
+                    }
+                    const int sl = slot_of(nseg - 1, key);
+                    atomicAdd(&s_gS[sl].x, to_d(a.x));
+                    atomicAdd(&s_gS[sl].y, to_d(a.y));
+                    atomicMax(&s_wm[sl], weight_bits(a));
+                }
+            }
+        }
+        __syncthreads();
+        // pass 2: paths within the tie window of their group's maximum compete
+        // for the representative (smallest key)
+        {
+            int sg = segbase, cur = -1;
+            unsigned long long kmin = kEmpty;
+#pragma unroll
+            for (int u = 0; u < EPT; ++u) {
+                const int i = threadIdx.x * EPT + u;
+                if (hmask & (1u << u)) ++sg;
+                if (i < cnt && sg >= 0) {
+                    const unsigned long long key = s_key[i];
+                    const int sl = slot_of(sg, key);
+                    if (sl != cur) {
+                        if (cur >= 0 && kmin != kEmpty) atomicMin(&s_grep[cur], kmin);
+                        cur = sl;
+                        kmin = kEmpty;
+                    }
+                    if (within_tie(weight_bits(s_amp[i]), s_wm[sl]) && key < kmin) kmin = key;
+                }
+            }
+            if (cur >= 0 && kmin != kEmpty) atomicMin(&s_grep[cur], kmin);
         }
         if (warp == 0 && ahead > cnt) {
             for (long long base = cnt; base < ahead; base += 32) {
                 const long long i = base + lane;
                 if (i < ahead) {
-                    const unsigned long long key = __ldcg(kin + e0 + i);
-                    const AmpT a = __ldcg(ain + e0 + i);
-                    const int sl = slot_of_key(nseg - 1, key);
+                    unsigned long long key;
+                    AmpT a;
+                    if (base == cnt) {
+                        key = s_ra_key[lane];
+                        a = s_ra_amp[lane];
+                    } else {
+                        key = __ldcg(kin + e0 + i);
+                        a = __ldcg(ain + e0 + i);
+                    }
+                    const int sl = slot_of(nseg - 1, key);
                     if (within_tie(weight_bits(a), s_wm[sl])) atomicMin(&s_grep[sl], key);
                 }
             }
         }
         __syncthreads();
-        // pass A: survivors per new point for a contiguous range of slots
-        const int nslot = nseg * NX;
-        const int spt = (nslot + NT - 1) / NT;
-        const int sl0 = min(nslot, (int)threadIdx.x * spt), sl1 = min(nslot, sl0 + spt);
+        // pass A: children of a contiguous range of groups per thread, once;
+        // survivors counted per new point, amplitudes kept in shared memory
+        // for pass B (the first NSTG groups)
+        const int gpt = (ngroups + NT - 1) / NT;
+        const int g0 = min(ngroups, (int)threadIdx.x * gpt), g1 = min(ngroups, g0 + gpt);
         unsigned cntc[MM];
-        unsigned ng = 0;
 #pragma unroll
         for (int c = 0; c < MM; ++c) cntc[c] = 0;
-        // C64: each sum is rounded to FP32 once, kept in its slot for pass B
-        float2 *s_gSf = reinterpret_cast<float2 *>(s_gS);   // slot sl at [2 * sl]
-        for (int sl = sl0; sl < sl1; ++sl) {
-            const unsigned long long rk = s_grep[sl];
+        for (int g = g0; g < g1; ++g) {
+            const unsigned long long rk = s_grep[g];
             unsigned keep = 0;
+            AmpT v[MM];
             if (rk != kEmpty) {
-                AmpT v[MM];
                 if constexpr (C64) {
-                    const float2 Sf = to_f2(s_gS[sl]);
-                    s_gSf[2 * sl] = Sf;
-                    keep = X::children(P, n_act, 0, rk, Sf, s_w, s_wf, v);
+                    const float2 Sf = to_f2(s_gS[g]);
+                    reinterpret_cast<float2 *>(s_gS)[2 * g] = Sf;   // for pass B, if not staged
+                    keep = X::children_tab(P, tab, rk, Sf, s_w, s_wf, v);
                 } else {
-                    keep = X::children(P, n_act, 0, rk, s_gS[sl], s_w, s_wf, v);
+                    keep = X::children_tab(P, tab, rk, s_gS[g], s_w, s_wf, v);
                 }
-                ++ng;
             }
-            s_keep[sl] = (unsigned short)keep;
+            s_keep[g] = (unsigned short)keep;
 #pragma unroll
-            for (int c = 0; c < MM; ++c) cntc[c] += (keep >> c) & 1u;
+            for (int c = 0; c < MM; ++c) {
+                if (!(keep & (1u << c))) continue;
+                ++cntc[c];
+                if (Lay::stage && g < Lay::NSTG) s_stg[g * MM + c] = v[c];
+            }
         }
         // block exclusive scan per new point (warp shuffles, then across warps)
         unsigned tb[MM];
@@ -1074,12 +1294,7 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream_step(Params P) {
             tb[c] = incl - v;
             if (lane == 31) s_wsum[warp][c] = incl;
         }
-        unsigned ngw = ng;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) ngw += __shfl_down_sync(0xffffffffu, ngw, o);
-        if (threadIdx.x == 0) s_ngroups = 0;
         __syncthreads();
-        if (lane == 0 && ngw) atomicAdd(&s_ngroups, ngw);
         if (threadIdx.x < MM) {
             unsigned a = 0;
             for (int w = 0; w < NW; ++w) {
@@ -1094,7 +1309,8 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream_step(Params P) {
         for (int c = 0; c < MM; ++c) tb[c] += s_wsum[warp][c];
         // decoupled look-back, one warp per bucket (buckets c, c + NW, ...):
         // publish the tile's aggregate, then read 32 predecessors at a time
-        // and add aggregates back to the nearest inclusive prefix
+        // (relaxed GPU-scope loads, bounded waits) and add aggregates back to
+        // the nearest inclusive prefix
         for (int c = warp; c < MM; c += NW) {
             unsigned long long *my = P.tile_state + (size_t)ticket * MM + c;
             const unsigned long long tot = s_tot[c];
@@ -1103,16 +1319,16 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream_step(Params P) {
             long long pred = ticket - 1;
             const long long t0 = clock64();
             bool timeout = false, abort = false;   // abort: another block raised an error
-            while (pred >= 0 && !timeout && !abort) {
+            while (pred >= 0) {
                 const long long idx = pred - (long long)lane;
-                unsigned long long w = 0, val = 0;
                 unsigned state = 0;
+                unsigned long long val = 0;
                 for (;;) {   // every lane of the window must see its predecessor's word
                     if (idx < 0) {
                         state = kLbInc;   // before the first tile: an inclusive prefix of 0
                         val = 0;
                     } else {
-                        w = *(volatile unsigned long long *)(P.tile_state + (size_t)idx * MM + c);
+                        const unsigned long long w = ld_relaxed_gpu(P.tile_state + (size_t)idx * MM + c);
                         state = (unsigned)(w >> 32) == epoch ? ((unsigned)(w >> 30) & 3u) : 0u;
                         val = w & ((1ull << 30) - 1ull);
                     }
@@ -1147,21 +1363,28 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream_step(Params P) {
         __syncthreads();
         if (threadIdx.x == 0) {
             for (int c = 0; c < MM; ++c) block_kept += s_tot[c];
-            if (s_ngroups) atomicAdd(&st->cnt_groups[cs], (unsigned long long)s_ngroups);
+            if (ngroups) atomicAdd(&st->cnt_groups[cs], (unsigned long long)ngroups);
             if (ticket == ntiles - 1) {
                 unsigned long long sumc = 0;
                 for (int c = 0; c < MM; ++c) sumc += s_base[c] + s_tot[c];
                 st->cnt_out[cs] = sumc;
             }
         }
-        // pass B: recompute the survivors and write them to their regions
-        for (int sl = sl0; sl < sl1; ++sl) {
-            const unsigned keep = s_keep[sl];
+        // pass B: write the survivors to their regions
+        for (int g = g0; g < g1; ++g) {
+            const unsigned keep = s_keep[g];
             if (!keep) continue;
-            const unsigned long long rk = s_grep[sl];
+            const unsigned long long rk = s_grep[g];
             AmpT v[MM];
-            if constexpr (C64) X::children(P, n_act, 0, rk, s_gSf[2 * sl], s_w, s_wf, v);
-            else X::children(P, n_act, 0, rk, s_gS[sl], s_w, s_wf, v);
+            if (Lay::stage && g < Lay::NSTG) {
+#pragma unroll
+                for (int c = 0; c < MM; ++c)
+                    if (keep & (1u << c)) v[c] = s_stg[g * MM + c];
+            } else if constexpr (C64) {
+                X::children_tab(P, tab, rk, reinterpret_cast<const float2 *>(s_gS)[2 * g], s_w, s_wf, v);
+            } else {
+                X::children_tab(P, tab, rk, s_gS[g], s_w, s_wf, v);
+            }
             const unsigned long long shifted = rk << P.b;
 #pragma unroll
             for (int c = 0; c < MM; ++c) {
@@ -1174,7 +1397,7 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream_step(Params P) {
                 const unsigned long long code = (unsigned long long)((c / M) | ((c % M) << P.bs));
                 keys_out[c * G + o] = (shifted | code) & wmask;
                 amps_out[c * G + o] = v[c];
-                if constexpr (C64) {
+                if constexpr (kKahan) {
                     X::kahan_add(racc[c], rcmp[c], v[c]);
                 } else {
                     racc[c].x += v[c].x;
@@ -1186,10 +1409,13 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream_step(Params P) {
     }
     // this block's partial sums of rho(t+1) (and survivor count)
     double2 *mine = rho_part_of(P, tn, MM) + (size_t)blockIdx.x * (MM + 1);
-    double kept = 0.0;
 #pragma unroll
     for (int k = 0; k < MM; ++k) {
-        double x = (double)racc[k].x - (double)rcmp[k].x, y = (double)racc[k].y - (double)rcmp[k].y;
+        double x = (double)racc[k].x, y = (double)racc[k].y;
+        if constexpr (kKahan) {
+            x -= (double)rcmp[k].x;
+            y -= (double)rcmp[k].y;
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             x += __shfl_down_sync(0xffffffffu, x, o);
@@ -1206,7 +1432,6 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream_step(Params P) {
         }
         mine[threadIdx.x] = make_double2(x, y);
     }
-    (void)kept;
     if (threadIdx.x == 0) mine[MM] = make_double2((double)block_kept, 0.0);
     // last block done: rho(t+1) from the partials in block order, then the
     // step is published (no separate finalisation kernel)
@@ -1393,7 +1618,11 @@ int distinct_deltas(int M, const double *q, std::vector<double> *vals, signed ch
 Layout make_layout(const qp_config *c) {
     Layout L{};
     const long long mp = c->max_paths;
-    const long long mg = c->max_groups ? c->max_groups : c->max_paths;
+    // the stream engine, when asked for explicitly, never uses the merge
+    // table or the group arrays: they shrink to a token size, leaving the
+    // memory to the path buffers (about 2 * (8 + amplitude) bytes per path)
+    const bool stream_only = c->engine == QP_ENGINE_STREAM;
+    const long long mg = stream_only ? 1 : (c->max_groups ? c->max_groups : c->max_paths);
     const size_t ampb = c->precision == QP_C64 ? sizeof(float2) : sizeof(double2);
     unsigned int lg = 4;
     while ((1ull << lg) < 2ull * (unsigned long long)mg) ++lg;
@@ -1416,7 +1645,7 @@ Layout make_layout(const qp_config *c) {
     L.amps[1] = take(ent * ampb);
     L.slots = take(L.tcap * sizeof(Slot));
     L.repk = take(L.tcap * 8);
-    L.slot_of = take(mp * 4);
+    L.slot_of = take(stream_only ? 4 : mp * 4);
     L.groups = take(mg * 4);
     const int NI = std::max(1, c->n_inst);
     const size_t nlut = (size_t)c->dkmax * std::max(1, L.nchunks) * kLutEntries;
@@ -1466,6 +1695,9 @@ struct qp_ctx {
     int graph_steps = 1;               // steps captured per CUDA graph
     int stream_nx = 0;                 // stream engine usable with the mask: sub-groups per run (0 = no)
     int stream_tile = 1024;            // stored paths per tile of the stream engine
+    const void *scache_fn = nullptr;   // stream kernel launched last, its dynamic shared memory and
+    size_t scache_smem = 0;            // co-resident blocks per SM
+    int scache_res = 0;
     bool use_stream = false;           // this propagation runs on the stream engine
     cudaGraphExec_t graph1 = nullptr;  // one-step graph for remainders
     cudaGraphExec_t graph = nullptr;
@@ -1517,12 +1749,13 @@ cudaError_t launch_step_t(qp_ctx *c, cudaEvent_t *ev) {
     return cudaGetLastError();
 }
 
-// Dynamic shared memory of a stream tile of S stored paths: per slot
-// (S * NX) the FP64 sum, the representative and the maximum weight; per path
-// the key and amplitude; run heads; survivor bits per slot.
-template <int NX, typename Amp, int S>
-constexpr size_t stream_smem_bytes() {
-    return (size_t)S * NX * (sizeof(double2) + 16) + (size_t)S * (8 + sizeof(Amp)) + (S + 1) * 4 + (size_t)S * NX * 2 + 16;
+// History tables of one window length staged in the stream kernel's shared
+// memory when they take at most kMaxStreamLut bytes (0: read from global).
+size_t stream_lut_bytes(const qp_ctx *c, bool c64) {
+    if (c->P.ndelta == 0) return 0;
+    const size_t n = (size_t)c->P.nchunks * kLutEntries;
+    const size_t b = c64 ? 2 * n * sizeof(float2) : (size_t)c->P.ndelta * n * sizeof(double2);
+    return b <= kMaxStreamLut ? b : 0;
 }
 
 // Grid of the stream kernel: every block resident (tiles are taken by
@@ -1530,21 +1763,26 @@ constexpr size_t stream_smem_bytes() {
 // first wave), at most blocks_per_sm per SM and kMaxExpandBlocks in all.
 template <int M, bool C64, int NX, int S>
 cudaError_t launch_stream_kernel(qp_ctx *c, int blocks_per_sm) {
-    using Amp = typename std::conditional<C64, float2, double2>::type;
-    constexpr size_t sm = stream_smem_bytes<NX, Amp, S>();
-    static int resident = 0;   // per instantiation (one device per process is assumed for the attribute)
-    if (resident == 0) {
-        cudaError_t e = cudaFuncSetAttribute(k_stream_step<M, C64, NX, S>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    using Lay = StreamLayout<M, C64, NX, S>;
+    const void *fn = (const void *)k_stream_step<M, C64, NX, S>;
+    const size_t lutb = stream_lut_bytes(c, C64);
+    const size_t sm = Lay::bytes + lutb;
+    if (c->scache_fn != fn || c->scache_smem != sm) {
+        // the attribute is a property of the function: set it to the most
+        // any context may ask for, so that contexts do not undo each other
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(Lay::bytes + kMaxStreamLut));
         if (e != cudaSuccess) return e;
         int nb = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stream_step<M, C64, NX, S>, kStreamThreads, sm);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kStreamThreads, sm);
         if (e != cudaSuccess) return e;
         if (nb < 1) return cudaErrorInvalidConfiguration;
-        resident = nb;
+        c->scache_fn = fn;
+        c->scache_smem = sm;
+        c->scache_res = nb;
     }
-    const int g = std::min(c->nsm * std::min(blocks_per_sm, resident), kMaxExpandBlocks);
-    k_stream_step<M, C64, NX, S><<<g, kStreamThreads, sm, c->stream>>>(c->P);
+    const int g = std::min(c->nsm * std::min(blocks_per_sm, c->scache_res), kMaxExpandBlocks);
+    k_stream_step<M, C64, NX, S><<<g, kStreamThreads, sm, c->stream>>>(c->P, lutb ? 1 : 0);
     return cudaGetLastError();
 }
 

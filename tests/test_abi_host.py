@@ -51,6 +51,18 @@ def test_workspace_size_grows_with_capacity():
     assert abi.qp_workspace_size(c2) > abi.qp_workspace_size(c1) > 0
 
 
+@pytest.mark.parametrize("precision,amp_bytes", [(abi.QP_C64, 8), (abi.QP_FP64, 16)])
+def test_stream_only_workspace_holds_little_beyond_the_path_buffers(precision, amp_bytes):
+    """With the stream engine asked for, the merge table is not allocated:
+    per path, two buffers of key + amplitude and a small look-back share."""
+    n = 1 << 22
+    cs, ks = _cfg(max_paths=n, precision=precision, engine=abi.QP_ENGINE_STREAM)
+    ca, ka = _cfg(max_paths=n, precision=precision, engine=abi.QP_ENGINE_AUTO)
+    ws, wa = abi.qp_workspace_size(cs), abi.qp_workspace_size(ca)
+    assert 2 * (8 + amp_bytes) * n <= ws <= (2 * (8 + amp_bytes) + 1) * n
+    assert wa > ws + 16 * n   # AUTO keeps the merge table as well
+
+
 @pytest.mark.parametrize("bad", [dict(M=1), dict(M=5), dict(dkmax=0), dict(M=2, dkmax=33), dict(M=3, q=[1, 0, -1],
                                  hs=np.eye(3), dkmax=17), dict(dt=-1.0), dict(theta=-1.0), dict(max_paths=0),
                                  dict(hs=np.array([[0, 0.5], [0.2, 0]])), dict(precision=7), dict(engine=9)])
