@@ -38,6 +38,7 @@ WORKLOADS = {
     "spin_boson_ohmic_dk8": W.SPIN_BOSON_OHMIC_DK8,
     "chain3_structured_dk12": W.CHAIN3_STRUCTURED_DK12,
     "tls_ohmic_full_dk14": W.TLS_OHMIC_FULL_DK14,
+    "tls_ohmic_full_dk13": W.tls_ohmic_full(13),
 }
 METRIC = "extended paths/s"
 T0_DEFAULT = 100
@@ -136,6 +137,10 @@ def run_ours(args, rank, world, precision):
     p = Propagator.from_workload(w, precision=precision, engine=args.engine, max_paths=args.max_paths)
     p.step(args.t0)
     p.sync()
+    # the library's autotuner picks the launch shape (tile size, blocks per
+    # SM) on the running propagation; it advances it by a few steps
+    tuning, _ = p.autotune(trial_steps=8, use_cache=True)
+    p.sync()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=f"cuda:{dev}")
     for _ in range(args.warmup):
         p.step(1)
@@ -218,7 +223,7 @@ def run_ours(args, rank, world, precision):
     d2h = w.M * w.M * 16 + 64
     p.close()
 
-    res = dict(ext=extended, t_ms=t_ms, wall=wall1 - wall0, e2e=e2e_ext / (e1 - e0), roof=roof,
+    res = dict(ext=extended, t_ms=t_ms, wall=wall1 - wall0, e2e=e2e_ext / (e1 - e0), roof=roof, tuning=tuning.as_dict(),
                clocks=clocks.summary(), h2d=h2d, d2h=d2h, step_ms=step_ms, stats=stats,
                kernels_per_step=1 if engine == "stream" else 4, rho=rho_hist)
     return res
@@ -325,6 +330,25 @@ def run_surrogate(T_train=100, T_long=1000, L=32, epochs=2000):
             "fallback_instances": int(fb.sum())}
 
 
+def run_more_config(name, t0, steps, max_paths, warmup=3):
+    """Another workload of the benchmark set, same measurement as the
+    headline (c64, autotuned, L2 flushed between timed steps) with the plain
+    FP64 GPU path on the same trajectory for the speed and rho comparison."""
+    a = argparse.Namespace(workload=name, t0=t0, steps=steps, warmup=warmup, max_paths=max_paths, engine="auto")
+    w = WORKLOADS[name]
+    res = run_ours(a, 0, 1, "c64")
+    ref = run_ours(a, 0, 1, "fp64")
+    n = min(len(res["rho"]), len(ref["rho"]))
+    v, vf = res["ext"] / (res["t_ms"] / 1e3), ref["ext"] / (ref["t_ms"] / 1e3)
+    return {"workload": name, "M": w.M, "dkmax": w.dkmax, "mask": w.mask_list(), "theta": w.theta, "t0": t0,
+            "steps": steps, "value": v, "unit": "paths/s", "ms_per_step": res["t_ms"] / steps,
+            "paths_kept_last": int(res["stats"][-1][3]), "roofline": res["roof"], "tuning": res["tuning"],
+            "clocks": res["clocks"], "fp64_gpu": {"value": vf, "ms_per_step": ref["t_ms"] / steps,
+                                                  "roofline": ref["roof"]},
+            "speedup_vs_fp64_gpu": v / vf, "rho_max_abs_err_vs_fp64": float(np.abs(res["rho"][:n] - ref["rho"][:n]).max()),
+            "rho_err_steps": n}
+
+
 def cpu_baseline(w, steps_total=60, timed_from=None):
     """Oracle (FP64 CPU, as it stands) on a bounded sample of the workload:
     propagate from t = 0 and time the steps after the window is full."""
@@ -360,6 +384,8 @@ def main():
     ap.add_argument("--max-paths", type=int, default=1 << 21)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-sweep measurement")
+    ap.add_argument("--no-more-configs", action="store_true",
+                    help="skip the three-level chain and full-memory TLS measurements")
     args = ap.parse_args()
     assert args.warmup >= 3, "at least 3 warm-up steps"
 
@@ -444,6 +470,10 @@ def main():
             "vs_fp64_gpu": {"fp64_value": fp64_value, "fp64_ms_per_step": ref["t_ms"] / args.steps,
                             "speedup": value / fp64_value, "rho_max_abs_err": rho_err,
                             "rho_err_steps": n, "fp64_roofline": ref["roof"], "fp64_e2e": ref["e2e"]}}
+    line["config"]["tuning"] = res["tuning"]
+    if not args.no_more_configs and world == 1:
+        line["more_configs"] = [run_more_config("chain3_structured_dk12", 40, 50, 1 << 26),
+                                run_more_config("tls_ohmic_full_dk13", 13, 10, 1 << 27)]
     if not args.no_batched and world == 1:
         line["batched_sweep"] = run_batched_sweep()
         line["surrogate"] = run_surrogate()
