@@ -250,6 +250,14 @@ qp_status qp_autotune(qp_ctx *ctx, int trial_steps, int use_cache, qp_tuning *be
  * qp_set_rho0 restores a usable context.                                    */
 qp_status qp_test_stall_barrier(qp_ctx *ctx);
 
+/* Test hook: out[i] = in[i] widened from FP32 to FP64 exactly as the step
+ * kernels widen FP32 amplitudes and partial sums before FP64 arithmetic
+ * (IEEE-754 field arithmetic in integer registers, all classes: zeros,
+ * subnormals, normals, infinities, NaNs).  in, out: device pointers, n
+ * entries (0 <= n <= 2^31); asynchronous on stream (NULL = default stream).
+ * QP_ERR_ARG for bad arguments, QP_ERR_CUDA if the launch fails.            */
+qp_status qp_test_widen(const float *in, double *out, int64_t n, void *stream);
+
 /* Last error message of the context ("" if none).                           */
 const char *qp_last_error(const qp_ctx *ctx);
 

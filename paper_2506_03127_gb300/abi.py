@@ -87,6 +87,7 @@ def _load():
         "qp_set_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
         "qp_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, _dp]),
         "qp_test_stall_barrier": (ctypes.c_int, [ctypes.c_void_p]),
+        "qp_test_widen": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
         "qp_mlp_workspace_size": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                  ctypes.POINTER(ctypes.c_size_t)]),
         "qp_mlp_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
@@ -243,6 +244,11 @@ def qp_autotune(ctx, trial_steps: int = 8, use_cache: bool = True):
 
 def qp_test_stall_barrier(ctx):
     check(lib.qp_test_stall_barrier(ctx), ctx)
+
+
+def qp_test_widen(in_ptr: int, out_ptr: int, n: int, stream: int = 0):
+    """Device FP32 -> FP64 widening of the step kernels over n entries."""
+    check(lib.qp_test_widen(in_ptr, out_ptr, n, stream), None)
 
 
 def qp_read_stats(ctx, t0: int, count: int):

@@ -155,21 +155,24 @@ __device__ __forceinline__ double2 load_amp(const float2 *p, unsigned long long 
     return make_double2(v.x, v.y);
 }
 
-// float -> double by IEEE-754 fields (exact): a normal number keeps its sign
-// and 23 fraction bits, its exponent is rebiased by 1023 - 127; zeros keep
-// their sign.  Subnormals, infinities and NaNs take the conversion
-// instruction.  Keeps the widening of FP32 amplitudes off the FP64 pipe.
+// float -> double by IEEE-754 fields, exactly, with integer operations only
+// (keeps the widening of FP32 values off the FP64 pipe): the sign is kept;
+// a normal number keeps its 23 fraction bits (shifted up by 29) and its
+// exponent rebiased by 1023 - 127; a subnormal m * 2^-149 is normalised at
+// its leading one k (exponent k - 149); infinities and NaNs keep the all-ones
+// exponent and the shifted fraction; zeros stay zeros.
 __device__ __forceinline__ double f2d_exact(float f) {
     const unsigned u = __float_as_uint(f);
-    const unsigned e = (u >> 23) & 0xffu;
-    const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
-    if (e == 0u) {
-        if ((u & 0x7fffffu) == 0u) return __longlong_as_double((long long)sign);
-        return (double)f;
+    const unsigned e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+    unsigned long long bits = (unsigned long long)(u >> 31) << 63;
+    if (e == 0xffu) {
+        bits |= (0x7ffull << 52) | ((unsigned long long)m << 29);
+    } else if (e != 0u) {
+        bits |= ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)m << 29);
+    } else if (m != 0u) {
+        const int k = 31 - __clz((int)m);   // 0 .. 22
+        bits |= ((unsigned long long)(k + 874) << 52) | (((unsigned long long)m << (52 - k)) & 0xfffffffffffffull);
     }
-    if (e == 0xffu) return (double)f;
-    const unsigned long long bits = sign | ((unsigned long long)(e + 896u) << 52) |
-                                    ((unsigned long long)(u & 0x7fffffu) << 29);
     return __longlong_as_double((long long)bits);
 }
 __device__ __forceinline__ double to_d(double v) { return v; }
@@ -462,6 +465,55 @@ struct Expander {
     }
 };
 
+// Block partial of the threads' rho accumulators into out[0 .. MM): per
+// component the thread's value is hi + lo.  C64 (FP32 sum and compensation):
+// each warp reduces with error-free additions (TwoSum, every rounding error
+// carried into the lo part) and widens to FP64 once, in lane 0, so that the
+// reduction stays off the FP64 pipe (1/64 of the FP32 rate on this part);
+// FP64 accumulators (lo unused) reduce with FP64 shuffles.  Warps are summed
+// in FP64, in warp order.  s_r: [NW][MM] scratch; every thread of the block
+// calls it.
+template <int MM, int NW, bool C64>
+__device__ __forceinline__ void block_rho_partial(const typename std::conditional<C64, float2, double2>::type *hi,
+                                                  const float2 *lo, double2 (*s_r)[MM], double2 *out) {
+    const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < MM; ++k) {
+        if constexpr (C64) {
+            float sx = hi[k].x, ex = lo[k].x, sy = hi[k].y, ey = lo[k].y;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float bx = __shfl_down_sync(0xffffffffu, sx, o), fx = __shfl_down_sync(0xffffffffu, ex, o);
+                const float by = __shfl_down_sync(0xffffffffu, sy, o), fy = __shfl_down_sync(0xffffffffu, ey, o);
+                const float tx = sx + bx, vx = tx - sx;
+                ex += fx + ((sx - (tx - vx)) + (bx - vx));
+                sx = tx;
+                const float ty = sy + by, vy = ty - sy;
+                ey += fy + ((sy - (ty - vy)) + (by - vy));
+                sy = ty;
+            }
+            if (lane == 0) s_r[warp][k] = make_double2(f2d_exact(sx) + f2d_exact(ex), f2d_exact(sy) + f2d_exact(ey));
+        } else {
+            double x = hi[k].x, y = hi[k].y;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                x += __shfl_down_sync(0xffffffffu, x, o);
+                y += __shfl_down_sync(0xffffffffu, y, o);
+            }
+            if (lane == 0) s_r[warp][k] = make_double2(x, y);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < MM) {
+        double x = 0.0, y = 0.0;
+        for (int w = 0; w < NW; ++w) {
+            x += s_r[w][threadIdx.x].x;
+            y += s_r[w][threadIdx.x].y;
+        }
+        out[threadIdx.x] = make_double2(x, y);
+    }
+}
+
 // Extension of n groups (merge steps) or n stored paths (while the window
 // fills) to their children; survivors appended through *cnt_out.  This
 // block's partial sums of rho(t+1) (and its survivor count) per instance go
@@ -583,27 +635,14 @@ __device__ __forceinline__ void phase_expand(const Params &P, unsigned long long
         __syncthreads();
         for (int i = threadIdx.x; i < P.n_inst * (MM + 1); i += NT) mine[i] = s_acc[i];
     } else {
-        // this block's partial sums: warp shuffles, then across warps
-        const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+        // this block's partial sums
+        float2 lo[MM];
 #pragma unroll
         for (int k = 0; k < MM; ++k) {
-            double x = (double)racc[k].x - (double)rcmp[k].x, y = (double)racc[k].y - (double)rcmp[k].y;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                x += __shfl_down_sync(0xffffffffu, x, o);
-                y += __shfl_down_sync(0xffffffffu, y, o);
-            }
-            if (lane == 0) s_r[warp][k] = make_double2(x, y);
+            if constexpr (C64) lo[k] = make_float2(-rcmp[k].x, -rcmp[k].y);
+            else lo[k] = make_float2(0.f, 0.f);
         }
-        __syncthreads();
-        if (threadIdx.x < MM) {
-            double x = 0.0, y = 0.0;
-            for (int w = 0; w < NW; ++w) {
-                x += s_r[w][threadIdx.x].x;
-                y += s_r[w][threadIdx.x].y;
-            }
-            mine[threadIdx.x] = make_double2(x, y);
-        }
+        block_rho_partial<MM, NW, C64>(racc, lo, s_r, mine);
         if (threadIdx.x == 0) mine[MM] = make_double2((double)block_kept, 0.0);
     }
     __syncthreads();
@@ -929,6 +968,7 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
     __shared__ unsigned s_ticket, s_nseg, s_ng, s_hw[NW];
     __shared__ double2 s_r[NW][MM];
     __shared__ bool s_last;
+    __shared__ int s_any;   // the block processed a tile
     const double tie_d = 1.0 - P.tie_rel;   // R4 window, once per thread
     const float tie_f = (float)tie_d;
 
@@ -955,6 +995,7 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
         }
     }
     if (threadIdx.x == 0) {
+        s_any = 0;
         long long acc = 0;
         for (int r = 0; r < MM; ++r) {
             s_nr[r] = (long long)__ldcg(&st->reg_n[in][r]);
@@ -1000,6 +1041,7 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
         __syncthreads();
         const long long ticket = s_ticket;
         if (ticket >= ntiles) break;
+        if (threadIdx.x == 0) s_any = 1;
         int r = 0;
         while (r + 1 < MM && ticket >= s_tile0[r + 1]) ++r;
         const long long e0 = (ticket - s_tile0[r]) * S;
@@ -1407,30 +1449,22 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
         }
         __syncthreads();
     }
-    // this block's partial sums of rho(t+1) (and survivor count)
+    // this block's partial sums of rho(t+1) (and survivor count); a block
+    // that processed no tile has zeros (block_kept is block-uniform: thread
+    // 0 holds it, the loop ended with a barrier)
     double2 *mine = rho_part_of(P, tn, MM) + (size_t)blockIdx.x * (MM + 1);
-#pragma unroll
-    for (int k = 0; k < MM; ++k) {
-        double x = (double)racc[k].x, y = (double)racc[k].y;
-        if constexpr (kKahan) {
-            x -= (double)rcmp[k].x;
-            y -= (double)rcmp[k].y;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            x += __shfl_down_sync(0xffffffffu, x, o);
-            y += __shfl_down_sync(0xffffffffu, y, o);
-        }
-        if (lane == 0) s_r[warp][k] = make_double2(x, y);
-    }
+    if (threadIdx.x == 0) s_any = block_kept > 0 || s_any;
     __syncthreads();
-    if (threadIdx.x < MM) {
-        double x = 0.0, y = 0.0;
-        for (int w = 0; w < NW; ++w) {
-            x += s_r[w][threadIdx.x].x;
-            y += s_r[w][threadIdx.x].y;
+    if (s_any) {
+        float2 lo[MM];
+#pragma unroll
+        for (int k = 0; k < MM; ++k) {
+            if constexpr (kKahan) lo[k] = make_float2(-rcmp[k].x, -rcmp[k].y);
+            else lo[k] = make_float2(0.f, 0.f);
         }
-        mine[threadIdx.x] = make_double2(x, y);
+        block_rho_partial<MM, NW, C64>(racc, lo, s_r, mine);
+    } else if (threadIdx.x < MM) {
+        mine[threadIdx.x] = make_double2(0.0, 0.0);
     }
     if (threadIdx.x == 0) mine[MM] = make_double2((double)block_kept, 0.0);
     // last block done: rho(t+1) from the partials in block order, then the
@@ -1449,6 +1483,12 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
     }
     phase_finalize(P, tn, 0, rho_part_of(P, tn, MM), gridDim.x, MM);
     if (threadIdx.x == 0) publish_step(P, st, tn, MM);
+}
+
+// The kernels' FP32 -> FP64 widening over an array (test hook).
+__global__ void k_widen(const float *in, double *out, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = f2d_exact(in[i]);
 }
 
 // ---------------------------------------------------------------- set-up kernels
@@ -2646,6 +2686,14 @@ qp_status qp_test_stall_barrier(qp_ctx *c) {
 }
 
 const char *qp_last_error(const qp_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+qp_status qp_test_widen(const float *in, double *out, int64_t n, void *stream) {
+    if (n < 0 || (n > 0 && (!in || !out)) || n > (int64_t)1 << 31) return QP_ERR_ARG;
+    if (n == 0) return QP_OK;
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 65535);
+    k_widen<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(in, out, n);
+    return cudaGetLastError() == cudaSuccess ? QP_OK : QP_ERR_CUDA;
+}
 
 }  // extern "C"
 

@@ -222,3 +222,27 @@ def test_invalid_mask_rejected():
         p.step(1)                  # no rho0 yet
     assert e.value.status == abi.QP_ERR_STATE
     p.close()
+
+
+def test_device_widening_is_exact_for_every_float_class():
+    """The FP32 -> FP64 widening the step kernels apply (integer field
+    arithmetic) equals IEEE conversion bit for bit: signed zeros, every
+    subnormal leading-one position, normals over the whole exponent range,
+    the largest float, infinities; NaNs stay NaNs."""
+    rng = np.random.default_rng(7)
+    bits = [0, 0x80000000, 1, 0x80000001, 0x007FFFFF, 0x807FFFFF, 0x00400000, 0x00000100, 0x00800000,
+            0x7F7FFFFF, 0xFF7FFFFF, 0x7F800000, 0xFF800000, 0x7FC00000, 0x7F800001, 0x3F800000, 0xBF800000]
+    bits += [1 << k for k in range(23)] + [(1 << k) | 0x80000000 for k in range(23)]
+    x = np.concatenate([np.array(bits, dtype=np.uint32),
+                        rng.integers(0, 2 ** 32, size=200000, dtype=np.uint64).astype(np.uint32)]).view(np.float32)
+    xin = torch.from_numpy(x.copy()).cuda()
+    out = torch.empty(x.size, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    abi.qp_test_widen(xin.data_ptr(), out.data_ptr(), x.size, 0)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    with np.errstate(invalid="ignore"):   # signalling NaNs among the random patterns
+        ref = x.astype(np.float64)
+    nan = np.isnan(ref)
+    assert np.array_equal(np.isnan(got), nan)
+    assert np.array_equal(got[~nan].view(np.uint64), ref[~nan].view(np.uint64))
