@@ -39,6 +39,8 @@ WORKLOADS = {
     "chain3_structured_dk12": W.CHAIN3_STRUCTURED_DK12,
     "tls_ohmic_full_dk14": W.TLS_OHMIC_FULL_DK14,
     "tls_ohmic_full_dk13": W.tls_ohmic_full(13),
+    "tls_ohmic_full_dk15": W.tls_ohmic_full(15),
+    "tls_ohmic_full_dk16": W.tls_ohmic_full(16),
 }
 METRIC = "extended paths/s"
 T0_DEFAULT = 100
@@ -138,8 +140,19 @@ def run_ours(args, rank, world, precision):
     p.step(args.t0)
     p.sync()
     # the library's autotuner picks the launch shape (tile size, blocks per
-    # SM) on the running propagation; it advances it by a few steps
-    tuning, _ = p.autotune(trial_steps=8, use_cache=True)
+    # SM) on the running propagation; it advances it by a few steps.  A shape
+    # given on the command line is used as is (profiling runs pin it: the
+    # autotuner's timings are not meaningful under a profiler)
+    if getattr(args, "stream_tile", None) or getattr(args, "blocks_per_sm", None):
+        kw = {}
+        if args.stream_tile:
+            kw["stream_tile"] = args.stream_tile
+        if args.blocks_per_sm:
+            kw["expand_blocks_per_sm"] = args.blocks_per_sm
+        p.set_tuning(**kw)
+        tuning = p.tuning()
+    else:
+        tuning, _ = p.autotune(trial_steps=8, use_cache=True)
     p.sync()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=f"cuda:{dev}")
     for _ in range(args.warmup):
@@ -193,15 +206,24 @@ def run_ours(args, rank, world, precision):
     engine = "stream" if tun.engine == 2 else "hash"
     abytes = algorithmic_bytes(list(zip(pstats, [r[3] for r in pprev])), w.M, amp_bytes, merge, engine)
     names = ["premerge_insert", "premerge_tiebreak", "expand_influence_filter_rho", "finalize"]
-    if engine == "stream":
-        names = ["-", "-", "stream_step", "-"]   # one kernel per step (finalised by its last block)
-    dom = int(np.argmax(kern_ms))
     peak, peak_src = peaks()
-    achieved = abytes[dom] / (kern_ms[dom] / 1e3) / 1e9 if kern_ms[dom] > 0 else 0.0
-    roof = {"bound": "hbm", "kernel": names[dom], "engine": engine, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+    regular_cfg = engine == "stream" and w.theta == 0.0 and w.M == 2
+    if engine == "stream":
+        # one step = the regular map kernel (launched where regular steps are
+        # possible: M = 2, no filter) and the tile kernel, one of which does
+        # the step; both are timed together as the step's kernel
+        names = ["stream_regular", "-", "stream_tile", "-"]
+        step_ms = kern_ms[0] + kern_ms[2]
+        kname = "stream_step (regular map + tile kernel)" if regular_cfg else "stream_step (tile kernel)"
+        achieved = abytes[2] / (step_ms / 1e3) / 1e9 if step_ms > 0 else 0.0
+    else:
+        dom = int(np.argmax(kern_ms))
+        kname = names[dom]
+        achieved = abytes[dom] / (kern_ms[dom] / 1e3) / 1e9 if kern_ms[dom] > 0 else 0.0
+    roof = {"bound": "hbm", "kernel": kname, "engine": engine, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": None, "peak_source": peak_src,
-            "kernel_share": {n: round(float(m / kern_ms.sum()), 4) for n, m in zip(names, kern_ms)},
-            "kernel_avg_us": {n: round(float(m / nprof * 1e3), 2) for n, m in zip(names, kern_ms)}}
+            "kernel_share": {n: round(float(m / kern_ms.sum()), 4) for n, m in zip(names, kern_ms) if n != "-"},
+            "kernel_avg_us": {n: round(float(m / nprof * 1e3), 2) for n, m in zip(names, kern_ms) if n != "-"}}
 
     # end to end through the public API from host inputs: set eta/mask/rho0
     # from host arrays, then per step qp_step + read rho(t) back to the host
@@ -225,7 +247,7 @@ def run_ours(args, rank, world, precision):
 
     res = dict(ext=extended, t_ms=t_ms, wall=wall1 - wall0, e2e=e2e_ext / (e1 - e0), roof=roof, tuning=tuning.as_dict(),
                clocks=clocks.summary(), h2d=h2d, d2h=d2h, step_ms=step_ms, stats=stats,
-               kernels_per_step=1 if engine == "stream" else 4, rho=rho_hist)
+               kernels_per_step=(2 if regular_cfg else 1) if engine == "stream" else 4, rho=rho_hist)
     return res
 
 
@@ -330,23 +352,29 @@ def run_surrogate(T_train=100, T_long=1000, L=32, epochs=2000):
             "fallback_instances": int(fb.sum())}
 
 
-def run_more_config(name, t0, steps, max_paths, warmup=3):
+def run_more_config(name, t0, steps, max_paths, warmup=3, engine="auto", fp64=True):
     """Another workload of the benchmark set, same measurement as the
-    headline (c64, autotuned, L2 flushed between timed steps) with the plain
-    FP64 GPU path on the same trajectory for the speed and rho comparison."""
-    a = argparse.Namespace(workload=name, t0=t0, steps=steps, warmup=warmup, max_paths=max_paths, engine="auto")
+    headline (c64, autotuned, L2 flushed between timed steps) with, if fp64,
+    the plain FP64 GPU path on the same trajectory for the speed and rho
+    comparison."""
+    a = argparse.Namespace(workload=name, t0=t0, steps=steps, warmup=warmup, max_paths=max_paths, engine=engine,
+                           stream_tile=None, blocks_per_sm=None)
     w = WORKLOADS[name]
     res = run_ours(a, 0, 1, "c64")
-    ref = run_ours(a, 0, 1, "fp64")
-    n = min(len(res["rho"]), len(ref["rho"]))
-    v, vf = res["ext"] / (res["t_ms"] / 1e3), ref["ext"] / (ref["t_ms"] / 1e3)
-    return {"workload": name, "M": w.M, "dkmax": w.dkmax, "mask": w.mask_list(), "theta": w.theta, "t0": t0,
-            "steps": steps, "value": v, "unit": "paths/s", "ms_per_step": res["t_ms"] / steps,
-            "paths_kept_last": int(res["stats"][-1][3]), "roofline": res["roof"], "tuning": res["tuning"],
-            "clocks": res["clocks"], "fp64_gpu": {"value": vf, "ms_per_step": ref["t_ms"] / steps,
-                                                  "roofline": ref["roof"]},
-            "speedup_vs_fp64_gpu": v / vf, "rho_max_abs_err_vs_fp64": float(np.abs(res["rho"][:n] - ref["rho"][:n]).max()),
-            "rho_err_steps": n}
+    v = res["ext"] / (res["t_ms"] / 1e3)
+    out = {"workload": name, "M": w.M, "dkmax": w.dkmax, "mask": w.mask_list(), "theta": w.theta, "t0": t0,
+           "steps": steps, "engine": engine, "max_paths": max_paths, "value": v, "unit": "paths/s",
+           "ms_per_step": res["t_ms"] / steps, "paths_kept_last": int(res["stats"][-1][3]), "roofline": res["roof"],
+           "tuning": res["tuning"], "clocks": res["clocks"]}
+    if fp64:
+        ref = run_ours(a, 0, 1, "fp64")
+        n = min(len(res["rho"]), len(ref["rho"]))
+        vf = ref["ext"] / (ref["t_ms"] / 1e3)
+        out.update({"fp64_gpu": {"value": vf, "ms_per_step": ref["t_ms"] / steps, "roofline": ref["roof"]},
+                    "speedup_vs_fp64_gpu": v / vf,
+                    "rho_max_abs_err_vs_fp64": float(np.abs(res["rho"][:n] - ref["rho"][:n]).max()),
+                    "rho_err_steps": n})
+    return out
 
 
 def cpu_baseline(w, steps_total=60, timed_from=None):
@@ -386,6 +414,10 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-sweep measurement")
     ap.add_argument("--no-more-configs", action="store_true",
                     help="skip the three-level chain and full-memory TLS measurements")
+    ap.add_argument("--paper-scale", action="store_true",
+                    help="also the full-memory TLS model at memory 15 and 16 (1.1e9 and 4.3e9 stored paths, c64)")
+    ap.add_argument("--stream-tile", type=int, default=None, help="pin the stream tile (skips the autotuner)")
+    ap.add_argument("--blocks-per-sm", type=int, default=None, help="pin the blocks per SM (skips the autotuner)")
     args = ap.parse_args()
     assert args.warmup >= 3, "at least 3 warm-up steps"
 
@@ -473,7 +505,11 @@ def main():
     line["config"]["tuning"] = res["tuning"]
     if not args.no_more_configs and world == 1:
         line["more_configs"] = [run_more_config("chain3_structured_dk12", 40, 50, 1 << 26),
-                                run_more_config("tls_ohmic_full_dk13", 13, 10, 1 << 27)]
+                                run_more_config("tls_ohmic_full_dk13", 13, 10, 1 << 27),
+                                run_more_config("tls_ohmic_full_dk14", 14, 10, 1 << 28, engine="stream")]
+        if args.paper_scale:
+            line["more_configs"] += [run_more_config("tls_ohmic_full_dk15", 15, 5, 1 << 30, engine="stream", fp64=False),
+                                     run_more_config("tls_ohmic_full_dk16", 16, 5, 1 << 32, engine="stream", fp64=False)]
     if not args.no_batched and world == 1:
         line["batched_sweep"] = run_batched_sweep()
         line["surrogate"] = run_surrogate()

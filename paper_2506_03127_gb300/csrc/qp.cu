@@ -60,6 +60,7 @@ constexpr int kMaxExpandBlocks = 2048;
 constexpr int kPersistThreads = 256;
 constexpr int kMaxInst = 128;                      // instances of one batched context
 constexpr int kStreamMinTile = 256;                 // smallest stream tile (256, 512 or 1024 stored paths)
+constexpr int kRegThreads = 256;                    // threads per block of the regular stream kernel
 constexpr size_t kMaxStreamLut = 32 * 1024;         // history tables staged in shared memory up to this size
 constexpr int kStreamThreads = 256;
 constexpr unsigned kLbAgg = 1u, kLbInc = 2u;        // look-back word states (bits 30-31)
@@ -85,6 +86,7 @@ struct __align__(128) DevState {
     unsigned long long reg_n[2][16];  // stream engine: stored paths per region, by buffer parity
     unsigned int ticket[3];           // stream engine: tile tickets, step t' uses [t' % 3]
     unsigned int pad0;
+    unsigned long long reg_done;      // stream engine: tn + 1 when the regular kernel took step tn, else 0
     unsigned int bar_count;           // grid barrier of the persistent kernel: arrivals
     unsigned int pad1[31];
     unsigned int bar_gen;             // generation (own cache line)
@@ -139,6 +141,13 @@ struct Params {
     unsigned long long prefmask;       // key bits of the prefix positions 0 .. k-1 of P'
     int x_shift;                       // key bit of the one extra position of P' (NX = 4), else -1
     long long region_cap;              // entries per region
+    // regular steps of the stream engine (no filter): while the window fills
+    // every stored path is its own group; with the full mask, once all
+    // full_n = M^(2 dkmax) keys are stored every group is the M*M values of
+    // the oldest point, consecutive in its region.  Either way every child
+    // survives and child c of group g goes to entry g of region c.
+    int reg_fill, reg_merge;
+    unsigned long long full_n;
     unsigned long long *tile_state;    // [max_tiles][M*M] look-back words
     StepRec *stats_ring;               // [rho_hist]
     DevState *st;
@@ -860,6 +869,179 @@ __device__ __forceinline__ unsigned long long lb_word(unsigned epoch, unsigned s
     return ((unsigned long long)epoch << 32) | ((unsigned long long)state << 30) | cnt;
 }
 
+// Regular steps of the stream engine (no filter, see Params): while the
+// window fills every stored path is its own group; with the full mask, once
+// all M^(2 dkmax) keys are stored, every group is the M*M consecutive values
+// of the oldest point.  Every child survives, so child c of group g goes to
+// entry g of output region c: a streaming map, one thread per group (two in
+// flight), no shared-memory tile, no look-back.  The representative does not
+// matter: members differ only in the oldest point, which the history sum
+// does not read and the child key drops.  Launched before the tile kernel on
+// configurations that allow regular steps; it decides on the device, takes
+// the step (reg_done = new t + 1) or leaves it to the tile kernel
+// (reg_done = 0), and publishes the step it takes like the tile kernel.
+template <int M, bool C64>
+__global__ void __launch_bounds__(kRegThreads, 3) k_stream_regular(Params P, int lut_smem) {
+    using X = Expander<M, C64>;
+    using AmpT = typename X::AmpT;
+    constexpr int MM = M * M, NT = kRegThreads, NW = NT / 32;
+    DevState *st = P.st;
+    if (st->err) return;
+    const unsigned long long t = st->t, tn = t + 1;
+    const int in = (int)(t & 1), outp = (int)(tn & 1), cs = (int)(tn % 3);
+    const bool merge = tn >= (unsigned long long)P.dkmax;
+    const long long G = P.region_cap;
+    __shared__ long long s_gb[MM + 1];
+    __shared__ double2 s_w[C64 ? 1 : MM * MM];
+    __shared__ float2 s_wf[MM * MM];
+    __shared__ double2 s_r[NW][MM];
+    __shared__ bool s_last;
+    if (threadIdx.x == 0) {
+        long long acc = 0;
+        const int gsz = merge ? MM : 1;
+        unsigned long long n_in = 0;
+        for (int r = 0; r < MM; ++r) {
+            const long long nr = (long long)__ldcg(&st->reg_n[in][r]);
+            n_in += (unsigned long long)nr;
+            s_gb[r] = acc;
+            acc += nr / gsz;
+        }
+        const bool regular = n_in > 0 && (merge ? (P.reg_merge && n_in == P.full_n) : (P.reg_fill != 0));
+        s_gb[MM] = regular ? acc : -1;
+    }
+    __syncthreads();
+    const long long ngroups = s_gb[MM];
+    if (ngroups < 0) {   // not a regular step: the tile kernel takes it
+        if (blockIdx.x == 0 && threadIdx.x == 0) st->reg_done = 0;
+        return;
+    }
+    const int gs = merge ? MM : 1;
+    const int n_act = (int)min(tn, (unsigned long long)P.dkmax);
+    const int L_child = (int)min(tn + 1, (unsigned long long)P.dkmax);
+    const unsigned long long wmask = (P.b * L_child >= 64) ? ~0ull : ((1ull << (P.b * L_child)) - 1ull);
+    const unsigned long long *keys_in = P.keys[in];
+    const AmpT *amps_in = static_cast<const AmpT *>(P.amps[in]);
+    unsigned long long *keys_out = P.keys[outp];
+    AmpT *amps_out = static_cast<AmpT *>(P.amps[outp]);
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    for (int i = threadIdx.x; i < MM * MM; i += NT) {
+        if constexpr (!C64) s_w[i] = P.wtab[i];
+        s_wf[i] = P.wtabf[i];
+    }
+    Tab tab = tab_global(P, n_act, 0);
+    if (lut_smem && P.ndelta) {
+        const int n = P.nchunks * kLutEntries;
+        if constexpr (C64) {
+            float2 *hi = reinterpret_cast<float2 *>(s_dyn), *lo = hi + n;
+            for (int i = threadIdx.x; i < n; i += NT) {
+                hi[i] = __ldg(tab.hi + i);
+                lo[i] = __ldg(tab.lo + i);
+            }
+            tab.hi = hi;
+            tab.lo = lo;
+        } else {
+            double2 *et = reinterpret_cast<double2 *>(s_dyn);
+            for (int i = threadIdx.x; i < n * P.ndelta; i += NT) et[i] = __ldg(tab.et + i);
+            tab.et = et;
+        }
+    }
+    if (blockIdx.x == 0) {
+        if ((int)threadIdx.x < MM) st->reg_n[outp][threadIdx.x] = (unsigned long long)ngroups;
+        if (threadIdx.x == 0) {
+            st->cnt_out[cs] = (unsigned long long)ngroups * MM;
+            st->cnt_groups[cs] = (unsigned long long)ngroups;
+            st->reg_done = tn + 1;
+        }
+    }
+    __syncthreads();
+    constexpr bool kKahan = C64;
+    typename X::AccT racc[MM], rcmp[MM];
+#pragma unroll
+    for (int k = 0; k < MM; ++k) {
+        racc[k].x = racc[k].y = 0;
+        rcmp[k].x = rcmp[k].y = 0;
+    }
+    // one group: load its members (vector loads: a group of M*M entries
+    // starts on a multiple of M*M of a region whose base is 16-entry
+    // aligned), FP64 sum, children, write, accumulate rho
+    auto group = [&](long long g) {
+        int r = 0;
+        while (r + 1 < MM && g >= s_gb[r + 1]) ++r;
+        const long long j = (g - s_gb[r]) * gs;
+        const unsigned long long rk = __ldcs(keys_in + r * G + j);
+        AmpT v[MM];
+        if (gs == 1) {   // a single member is its own sum, exactly
+            X::children_tab(P, tab, rk, __ldcs(amps_in + r * G + j), s_w, s_wf, v);
+        } else {
+            AmpT a[MM];
+            if constexpr (C64 && MM % 2 == 0) {
+                const float4 *p4 = reinterpret_cast<const float4 *>(amps_in + r * G + j);
+#pragma unroll
+                for (int m = 0; m < MM / 2; ++m) {
+                    const float4 q = __ldcs(p4 + m);
+                    a[2 * m] = make_float2(q.x, q.y);
+                    a[2 * m + 1] = make_float2(q.z, q.w);
+                }
+            } else {
+#pragma unroll
+                for (int m = 0; m < MM; ++m) a[m] = __ldcs(amps_in + r * G + j + m);
+            }
+            double sx = to_d(a[0].x), sy = to_d(a[0].y);   // the group sum in FP64
+#pragma unroll
+            for (int m = 1; m < MM; ++m) {
+                sx += to_d(a[m].x);
+                sy += to_d(a[m].y);
+            }
+            X::children_tab(P, tab, rk, make_double2(sx, sy), s_w, s_wf, v);
+        }
+        const unsigned long long shifted = rk << P.b;
+#pragma unroll
+        for (int c = 0; c < MM; ++c) {
+            const unsigned long long code = (unsigned long long)((c / M) | ((c % M) << P.bs));
+            keys_out[c * G + g] = (shifted | code) & wmask;
+            amps_out[c * G + g] = v[c];
+            if constexpr (kKahan) {
+                X::kahan_add(racc[c], rcmp[c], v[c]);
+            } else {
+                racc[c].x += v[c].x;
+                racc[c].y += v[c].y;
+            }
+        }
+    };
+    const long long stride = (long long)gridDim.x * NT;
+    if (ngroups > G) {   // the outputs would not fit their regions
+        if (threadIdx.x == 0) raise_err(st, kErrPaths);
+    } else {
+        for (long long g = (long long)blockIdx.x * NT + threadIdx.x; g < ngroups; g += stride) group(g);
+    }
+    // block partial of rho(tn) and the children written by this block
+    double2 *mine = rho_part_of(P, tn, MM) + (size_t)blockIdx.x * (MM + 1);
+    float2 lo[MM];
+#pragma unroll
+    for (int k = 0; k < MM; ++k) lo[k] = C64 ? make_float2(-(float)rcmp[k].x, -(float)rcmp[k].y) : make_float2(0.f, 0.f);
+    block_rho_partial<MM, NW, C64>(racc, lo, s_r, mine);
+    if (threadIdx.x == 0) {
+        long long mg = 0;
+        for (long long g0 = (long long)blockIdx.x * NT; g0 < ngroups; g0 += stride) mg += min((long long)NT, ngroups - g0);
+        mine[MM] = make_double2((double)(mg * MM), 0.0);
+    }
+    // last block done: rho(tn) from the partials in block order, publish
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(P.fin_count, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (__ldcg(&st->err)) {   // a failed step is not published
+        if (threadIdx.x == 0) *P.fin_count = 0;
+        return;
+    }
+    phase_finalize(P, tn, 0, rho_part_of(P, tn, MM), gridDim.x, MM);
+    if (threadIdx.x == 0) publish_step(P, st, tn, MM);
+}
+
 // Dynamic shared memory of the stream kernel for a tile of S stored paths
 // (16-byte aligned arrays).  A tile holds at most NG = S + NX - 1 groups: every
 // group has a member in the tile, except sub-groups of the tile's last run
@@ -933,6 +1115,7 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
     static_assert(S % NT == 0 && EPT <= 32, "tile size");
     DevState *st = P.st;
     if (st->err) return;
+    if (st->reg_done == st->t + 1) return;   // the regular kernel just took this step (its new t + 1)
     const unsigned long long t = st->t, tn = t + 1;
     const int in = (int)(t & 1), outp = (int)(tn & 1), cs = (int)(tn % 3);
     const bool merge = tn >= (unsigned long long)P.dkmax;
@@ -1010,7 +1193,6 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
     }
     __syncthreads();
     const long long ntiles = s_tile0[MM];
-
     // rho(t+1) accumulators of this thread: FP64, or on the C64 path FP32
     // with a Kahan compensation term (M = 2; for M >= 3 plain FP32 sums, to
     // stay within the register budget of two blocks per SM), widened to
@@ -1618,7 +1800,8 @@ const char *validate(const qp_config *c) {
     if (!(c->theta >= 0.0) || !std::isfinite(c->theta)) return "theta must be >= 0";
     if (c->max_paths < 1 || c->max_paths > (int64_t(1) << 40)) return "max_paths out of range";
     if (c->max_groups < 0 || c->max_groups > (int64_t(1) << 30)) return "max_groups out of range";
-    if (c->max_groups == 0 && c->max_paths > (int64_t(1) << 30)) return "set max_groups (<= 2^30) for max_paths > 2^30";
+    if (c->engine != QP_ENGINE_STREAM && c->max_groups == 0 && c->max_paths > (int64_t(1) << 30))
+        return "set max_groups (<= 2^30) for max_paths > 2^30 (the merge table; not needed by the stream engine)";
     if (c->rho_history < 0 || c->rho_history > (1 << 24)) return "rho_history out of range";
     if (c->n_inst < 0 || c->n_inst > kMaxInst) return "n_inst out of range (0..128)";
     if (b * c->dkmax + inst_bits(c->n_inst) > 64) return "b*dkmax plus the instance index exceed the 64-bit key";
@@ -1738,6 +1921,9 @@ struct qp_ctx {
     const void *scache_fn = nullptr;   // stream kernel launched last, its dynamic shared memory and
     size_t scache_smem = 0;            // co-resident blocks per SM
     int scache_res = 0;
+    const void *rcache_fn = nullptr;   // the same for the regular stream kernel
+    size_t rcache_smem = 0;
+    int rcache_res = 0;
     bool use_stream = false;           // this propagation runs on the stream engine
     cudaGraphExec_t graph1 = nullptr;  // one-step graph for remainders
     cudaGraphExec_t graph = nullptr;
@@ -1835,13 +2021,42 @@ cudaError_t launch_stream_tile(qp_ctx *c) {
     }
 }
 
-// One step of the stream engine: a single kernel (events 2 -> 3 bracket it;
-// the other intervals of the per-kernel profile are empty).
+// The regular stream kernel (M = 2, no filter): every block resident, at
+// most kMaxExpandBlocks (block partials).
+template <bool C64>
+cudaError_t launch_stream_regular(qp_ctx *c) {
+    const void *fn = (const void *)k_stream_regular<2, C64>;
+    const size_t lutb = stream_lut_bytes(c, C64);
+    if (c->rcache_fn != fn || c->rcache_smem != lutb) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxStreamLut);
+        if (e != cudaSuccess) return e;
+        int nb = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kRegThreads, lutb);
+        if (e != cudaSuccess) return e;
+        if (nb < 1) return cudaErrorInvalidConfiguration;
+        c->rcache_fn = fn;
+        c->rcache_smem = lutb;
+        c->rcache_res = nb;
+    }
+    const int g = std::min(c->nsm * c->rcache_res, kMaxExpandBlocks);
+    k_stream_regular<2, C64><<<g, kRegThreads, lutb, c->stream>>>(c->P, lutb ? 1 : 0);
+    return cudaGetLastError();
+}
+
+// One step of the stream engine: the regular kernel where the configuration
+// allows regular steps (events 0 -> 1), then the tile kernel (events 2 -> 3),
+// which returns at once when the regular kernel took the step.
 template <int M, typename Amp>
 cudaError_t launch_stream_t(qp_ctx *c, cudaEvent_t *ev) {
     constexpr bool C64 = sizeof(Amp) == sizeof(float2);
+    if (ev) cudaEventRecord(ev[0], c->stream);
+    if constexpr (M == 2) {
+        if (c->P.reg_fill) {
+            cudaError_t e = launch_stream_regular<C64>(c);
+            if (e != cudaSuccess) return e;
+        }
+    }
     if (ev) {
-        cudaEventRecord(ev[0], c->stream);
         cudaEventRecord(ev[1], c->stream);
         cudaEventRecord(ev[2], c->stream);
     }
@@ -1983,6 +2198,17 @@ void set_mask_params(qp_ctx *c) {
     P.prefmask = (b * k >= 64) ? ~0ull : ((1ull << (b * k)) - 1ull);
     P.x_shift = nextra == 1 ? b * Pp[k] : -1;
     c->stream_nx = (P.n_inst == 1 && (nextra == 0 || (nextra == 1 && c->cfg.M == 2))) ? (nextra ? 4 : 1) : 0;
+    // regular steps (see Params): no filter; the merge form needs P' = all
+    // positions but the oldest and a complete key set that fits the buffers
+    P.reg_fill = c->cfg.theta == 0.0 ? 1 : 0;
+    P.reg_merge = (c->cfg.theta == 0.0 && c->cfg.dkmax >= 2 && nextra == 0 && k == c->cfg.dkmax - 1) ? 1 : 0;
+    P.full_n = 0;
+    if (2.0 * c->cfg.dkmax * std::log2((double)c->cfg.M) < 62.0) {
+        unsigned long long f = 1;
+        for (int i = 0; i < 2 * c->cfg.dkmax; ++i) f *= (unsigned long long)c->cfg.M;
+        if (f <= (unsigned long long)P.region_cap * (unsigned long long)(c->cfg.M * c->cfg.M)) P.full_n = f;
+    }
+    if (P.full_n == 0) P.reg_merge = 0;
 }
 
 }  // namespace
@@ -2104,7 +2330,7 @@ qp_status qp_create(const qp_config *cfg, void *d_workspace, size_t bytes, void 
     P.inst_shift = P.b * cfg->dkmax;
     P.instmask = P.n_inst > 1 ? (((1ull << inst_bits(P.n_inst)) - 1ull) << P.inst_shift) : 0ull;
     P.lut_stride = L.nlut;
-    P.region_cap = cfg->max_paths / (M * M);
+    P.region_cap = (cfg->max_paths / (M * M)) & ~15ll;   // region bases 16-entry aligned (vector loads)
     P.tile_state = reinterpret_cast<unsigned long long *>(c->ws + L.tile_state);
     P.etab_stride = L.nlut * (size_t)std::max(1, L.nd);
     P.stats_ring = reinterpret_cast<StepRec *>(c->ws + L.stats);
@@ -2265,7 +2491,7 @@ qp_status qp_set_rho0(qp_ctx *c, const double *re, const double *im) {
         return fail(c, QP_ERR_ARG, "the stream engine needs a mask whose P' is a prefix {0..k-1} plus at most one "
                                    "extra position (M = 2) and a single instance");
     c->use_stream = c->cfg.engine == QP_ENGINE_STREAM || (c->cfg.engine == QP_ENGINE_AUTO && c->stream_nx > 0);
-    if (c->use_stream && c->P.region_cap < 1) return fail(c, QP_ERR_CAPACITY, "max_paths < M*M");
+    if (c->use_stream && c->P.region_cap < 1) return fail(c, QP_ERR_CAPACITY, "max_paths < 16 M*M (stream engine)");
     c->P.stream = c->use_stream ? 1 : 0;
     c->graph_dirty = true;
     const size_t n = keys.size();
