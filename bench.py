@@ -38,6 +38,7 @@ WORKLOADS = {
     "spin_boson_ohmic_dk8": W.SPIN_BOSON_OHMIC_DK8,
     "chain3_structured_dk12": W.CHAIN3_STRUCTURED_DK12,
     "tls_ohmic_full_dk14": W.TLS_OHMIC_FULL_DK14,
+    "tls_ohmic_full_dk12": W.tls_ohmic_full(12),
     "tls_ohmic_full_dk13": W.tls_ohmic_full(13),
     "tls_ohmic_full_dk15": W.tls_ohmic_full(15),
     "tls_ohmic_full_dk16": W.tls_ohmic_full(16),

@@ -251,6 +251,7 @@ def qp_test_widen(in_ptr: int, out_ptr: int, n: int, stream: int = 0):
     check(lib.qp_test_widen(in_ptr, out_ptr, n, stream), None)
 
 
+
 def qp_read_stats(ctx, t0: int, count: int):
     arr = (qp_step_stats * count)()
     check(lib.qp_read_stats(ctx, t0, count, arr), ctx)

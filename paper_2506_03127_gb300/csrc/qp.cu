@@ -187,6 +187,9 @@ __device__ __forceinline__ double f2d_exact(float f) {
 __device__ __forceinline__ double to_d(double v) { return v; }
 __device__ __forceinline__ double to_d(float v) { return f2d_exact(v); }
 __device__ __forceinline__ float2 to_f2(float2 v) { return v; }
+// double -> float by the conversion instruction: two per group cost less
+// than the integer rounding that would replace them (measured), unlike the
+// widening above, which runs once per stored path
 __device__ __forceinline__ float2 to_f2(double2 v) { return make_float2((float)v.x, (float)v.y); }
 
 __device__ __forceinline__ unsigned long long table_index(const Params &P, unsigned long long mk) {
@@ -873,8 +876,8 @@ __device__ __forceinline__ unsigned long long lb_word(unsigned epoch, unsigned s
 // window fills every stored path is its own group; with the full mask, once
 // all M^(2 dkmax) keys are stored, every group is the M*M consecutive values
 // of the oldest point.  Every child survives, so child c of group g goes to
-// entry g of output region c: a streaming map, one thread per group (two in
-// flight), no shared-memory tile, no look-back.  The representative does not
+// entry g of output region c: a streaming map, one thread per group, no
+// shared-memory tile, no look-back.  The representative does not
 // matter: members differ only in the oldest point, which the history sum
 // does not read and the child key drops.  Launched before the tile kernel on
 // configurations that allow regular steps; it decides on the device, takes
@@ -961,36 +964,44 @@ __global__ void __launch_bounds__(kRegThreads, 3) k_stream_regular(Params P, int
         racc[k].x = racc[k].y = 0;
         rcmp[k].x = rcmp[k].y = 0;
     }
-    // one group: load its members (vector loads: a group of M*M entries
-    // starts on a multiple of M*M of a region whose base is 16-entry
-    // aligned), FP64 sum, children, write, accumulate rho
-    auto group = [&](long long g) {
+    // a group's members: vector loads (a group of M*M entries starts on a
+    // multiple of M*M of a region whose base is 16-entry aligned)
+    struct Members {
+        unsigned long long rk;
+        AmpT a[MM];
+    };
+    auto load = [&](long long g, Members &mb) {
         int r = 0;
         while (r + 1 < MM && g >= s_gb[r + 1]) ++r;
         const long long j = (g - s_gb[r]) * gs;
-        const unsigned long long rk = __ldcs(keys_in + r * G + j);
+        mb.rk = __ldcs(keys_in + r * G + j);
+        if (gs == 1) {
+            mb.a[0] = __ldcs(amps_in + r * G + j);
+        } else if constexpr (C64 && MM % 2 == 0) {
+            const float4 *p4 = reinterpret_cast<const float4 *>(amps_in + r * G + j);
+#pragma unroll
+            for (int m = 0; m < MM / 2; ++m) {
+                const float4 q = __ldcs(p4 + m);
+                mb.a[2 * m] = make_float2(q.x, q.y);
+                mb.a[2 * m + 1] = make_float2(q.z, q.w);
+            }
+        } else {
+#pragma unroll
+            for (int m = 0; m < MM; ++m) mb.a[m] = __ldcs(amps_in + r * G + j + m);
+        }
+    };
+    // one group: FP64 sum, children, write, accumulate rho
+    auto group = [&](long long g, const Members &mb) {
+        const unsigned long long rk = mb.rk;
         AmpT v[MM];
         if (gs == 1) {   // a single member is its own sum, exactly
-            X::children_tab(P, tab, rk, __ldcs(amps_in + r * G + j), s_w, s_wf, v);
+            X::children_tab(P, tab, rk, mb.a[0], s_w, s_wf, v);
         } else {
-            AmpT a[MM];
-            if constexpr (C64 && MM % 2 == 0) {
-                const float4 *p4 = reinterpret_cast<const float4 *>(amps_in + r * G + j);
-#pragma unroll
-                for (int m = 0; m < MM / 2; ++m) {
-                    const float4 q = __ldcs(p4 + m);
-                    a[2 * m] = make_float2(q.x, q.y);
-                    a[2 * m + 1] = make_float2(q.z, q.w);
-                }
-            } else {
-#pragma unroll
-                for (int m = 0; m < MM; ++m) a[m] = __ldcs(amps_in + r * G + j + m);
-            }
-            double sx = to_d(a[0].x), sy = to_d(a[0].y);   // the group sum in FP64
+            double sx = to_d(mb.a[0].x), sy = to_d(mb.a[0].y);   // the group sum in FP64
 #pragma unroll
             for (int m = 1; m < MM; ++m) {
-                sx += to_d(a[m].x);
-                sy += to_d(a[m].y);
+                sx += to_d(mb.a[m].x);
+                sy += to_d(mb.a[m].y);
             }
             X::children_tab(P, tab, rk, make_double2(sx, sy), s_w, s_wf, v);
         }
@@ -1012,7 +1023,13 @@ __global__ void __launch_bounds__(kRegThreads, 3) k_stream_regular(Params P, int
     if (ngroups > G) {   // the outputs would not fit their regions
         if (threadIdx.x == 0) raise_err(st, kErrPaths);
     } else {
-        for (long long g = (long long)blockIdx.x * NT + threadIdx.x; g < ngroups; g += stride) group(g);
+        // one group per thread at a time: three blocks of eight warps per SM
+        // keep more bytes in flight than two groups per thread at two blocks
+        for (long long g = (long long)blockIdx.x * NT + threadIdx.x; g < ngroups; g += stride) {
+            Members m0;
+            load(g, m0);
+            group(g, m0);
+        }
     }
     // block partial of rho(tn) and the children written by this block
     double2 *mine = rho_part_of(P, tn, MM) + (size_t)blockIdx.x * (MM + 1);
@@ -2920,6 +2937,7 @@ qp_status qp_test_widen(const float *in, double *out, int64_t n, void *stream) {
     k_widen<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(in, out, n);
     return cudaGetLastError() == cudaSuccess ? QP_OK : QP_ERR_CUDA;
 }
+
 
 }  // extern "C"
 

@@ -246,3 +246,4 @@ def test_device_widening_is_exact_for_every_float_class():
     nan = np.isnan(ref)
     assert np.array_equal(np.isnan(got), nan)
     assert np.array_equal(got[~nan].view(np.uint64), ref[~nan].view(np.uint64))
+
