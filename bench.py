@@ -111,6 +111,28 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def ncu_traffic(workload, regular, n_in):
+    """DRAM bytes per step of the stream kernels from one ncu capture
+    (profiles/traffic.txt), or None when none matches the current kernel
+    source.  The regular kernel's capture is scaled by stored paths."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "paper_2506_03127_gb300", "csrc", "qp.cu"), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()[:16]
+        with open(os.path.join(ROOT, "profiles", "traffic.txt")) as f:
+            rows = [ln.split() for ln in f if ln.strip() and not ln.startswith("#")]
+    except OSError:
+        return None
+    for w, k, src, b, n in rows:
+        if src != sha:
+            continue
+        if regular and k == "stream_regular" and workload.startswith("tls_ohmic_full") and int(n) > 0:
+            return float(b) / int(n) * n_in
+        if not regular and k == "stream_tile" and w == workload:
+            return float(b)
+    return None
+
+
 def algorithmic_bytes(stats_rows, M, amp_bytes, merge, engine="hash"):
     """Per-kernel algorithmic DRAM bytes for a list of steps:
     stored path = 8 B key + amp_bytes; merge-table slot 32 B + 8 B key.  The
@@ -221,8 +243,12 @@ def run_ours(args, rank, world, precision):
         dom = int(np.argmax(kern_ms))
         kname = names[dom]
         achieved = abytes[dom] / (kern_ms[dom] / 1e3) / 1e9 if kern_ms[dom] > 0 else 0.0
+    traffic = None
+    if engine == "stream" and precision == "c64":
+        tr = ncu_traffic(args.workload, regular_cfg, float(np.mean([r[3] for r in pprev])))
+        traffic = None if tr is None else round(tr)
     roof = {"bound": "hbm", "kernel": kname, "engine": engine, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": None, "peak_source": peak_src,
+            "frac": round(achieved / peak, 4), "traffic": traffic, "peak_source": peak_src,
             "kernel_share": {n: round(float(m / kern_ms.sum()), 4) for n, m in zip(names, kern_ms) if n != "-"},
             "kernel_avg_us": {n: round(float(m / nprof * 1e3), 2) for n, m in zip(names, kern_ms) if n != "-"}}
 
