@@ -668,30 +668,25 @@ __device__ __forceinline__ void phase_finalize(const Params &P, unsigned long lo
     const int MM1 = MM + 1;
     const size_t pstride = (size_t)P.n_inst * MM1;
     const double2 *src = part + (size_t)inst * MM1;
-    // T threads per element k sum a fixed stride of the partials with four
-    // independent accumulators so that the loads overlap
+    // T threads per element k sum a fixed stride of the partials; each
+    // round issues all of a thread's (up to 8) loads before adding, so that
+    // up to 8T partials per element cost one trip to L2
     const int T = min((int)blockDim.x, 256) / MM1;
     const int k = (int)threadIdx.x / T, sidx = (int)threadIdx.x % T;
-    double2 a0 = make_double2(0.0, 0.0), a1 = a0, a2 = a0, a3 = a0;
+    double2 a = make_double2(0.0, 0.0);
     if (k < MM1 && threadIdx.x < 256) {
-        int b = sidx;
-        for (; b + 3 * T < nblk; b += 4 * T) {
-            const double2 v0 = __ldcg(src + (size_t)b * pstride + k);
-            const double2 v1 = __ldcg(src + (size_t)(b + T) * pstride + k);
-            const double2 v2 = __ldcg(src + (size_t)(b + 2 * T) * pstride + k);
-            const double2 v3 = __ldcg(src + (size_t)(b + 3 * T) * pstride + k);
-            a0.x += v0.x; a0.y += v0.y;
-            a1.x += v1.x; a1.y += v1.y;
-            a2.x += v2.x; a2.y += v2.y;
-            a3.x += v3.x; a3.y += v3.y;
-        }
-        for (; b < nblk; b += T) {
-            const double2 v = __ldcg(src + (size_t)b * pstride + k);
-            a0.x += v.x; a0.y += v.y;
+        for (int b0 = sidx; b0 < nblk; b0 += 8 * T) {
+            double2 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int b = b0 + u * T;
+                v[u] = b < nblk ? __ldcg(src + (size_t)b * pstride + k) : make_double2(0.0, 0.0);
+            }
+            a.x += ((v[0].x + v[1].x) + (v[2].x + v[3].x)) + ((v[4].x + v[5].x) + (v[6].x + v[7].x));
+            a.y += ((v[0].y + v[1].y) + (v[2].y + v[3].y)) + ((v[4].y + v[5].y) + (v[6].y + v[7].y));
         }
     }
-    if (threadIdx.x < 256)
-        s_p[threadIdx.x] = make_double2((a0.x + a1.x) + (a2.x + a3.x), (a0.y + a1.y) + (a2.y + a3.y));
+    if (threadIdx.x < 256) s_p[threadIdx.x] = a;
     __syncthreads();
     // the T partials of element k: pairwise tree in shared memory
     for (int w = 1; w < T; w <<= 1) {
@@ -722,15 +717,24 @@ __device__ __forceinline__ void write_step_totals(const Params &P, unsigned long
     P.stats_ring[tn % (unsigned long long)P.rho_hist] = r;
 }
 
+struct StepCounts {
+    unsigned long long groups, n_out;
+};
+// The step's counters (read through L2: other blocks of the same kernel
+// wrote them); the last block reads them while it sums the partials.
+__device__ __forceinline__ StepCounts step_counts(const Params &P, DevState *st, unsigned long long tn) {
+    const bool merge = tn >= (unsigned long long)P.dkmax;
+    StepCounts c;
+    c.groups = merge ? __ldcg(&st->cnt_groups[tn % 3]) : __ldcg(&st->n_cur);
+    c.n_out = __ldcg(&st->cnt_out[tn % 3]);
+    return c;
+}
 // Publishes step tn (one thread, after every block of the step is done):
 // totals, the new count and time, and zeroed counters of the next step.
-// Counters are read through L2: other blocks of the same kernel may have
-// written them.
-__device__ __forceinline__ void publish_step(const Params &P, DevState *st, unsigned long long tn, int MM) {
+__device__ __forceinline__ void publish_step(const Params &P, DevState *st, unsigned long long tn, int MM,
+                                             StepCounts c) {
     *P.fin_count = 0;
-    const bool merge = tn >= (unsigned long long)P.dkmax;
-    const unsigned long long groups = merge ? __ldcg(&st->cnt_groups[tn % 3]) : __ldcg(&st->n_cur);
-    const unsigned long long n_out = __ldcg(&st->cnt_out[tn % 3]);
+    const unsigned long long groups = c.groups, n_out = c.n_out;
     write_step_totals(P, tn, groups, n_out, MM);
     st->n_cur = n_out;
     st->t = tn;
@@ -768,7 +772,7 @@ __global__ void __launch_bounds__(256) k_finalize(Params P, int MM, int nblk) {
     }
     __syncthreads();
     if (!s_last || threadIdx.x != 0) return;
-    publish_step(P, st, tn, MM);
+    publish_step(P, st, tn, MM, step_counts(P, st, tn));
 }
 
 // Grid-wide barrier of the persistent kernel (all blocks are co-resident: the
@@ -1055,8 +1059,10 @@ __global__ void __launch_bounds__(kRegThreads, 3) k_stream_regular(Params P, int
         if (threadIdx.x == 0) *P.fin_count = 0;
         return;
     }
+    StepCounts cts{};
+    if (threadIdx.x == 0) cts = step_counts(P, st, tn);   // in flight with the partial loads
     phase_finalize(P, tn, 0, rho_part_of(P, tn, MM), gridDim.x, MM);
-    if (threadIdx.x == 0) publish_step(P, st, tn, MM);
+    if (threadIdx.x == 0) publish_step(P, st, tn, MM, cts);
 }
 
 // Dynamic shared memory of the stream kernel for a tile of S stored paths
@@ -1166,6 +1172,7 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
     __shared__ AmpT s_ra_amp[32];
     __shared__ unsigned s_ra_n;   // prefetched paths past the tile end
     __shared__ unsigned s_ticket, s_nseg, s_ng, s_hw[NW];
+    __shared__ int s_St;   // tile size of this step
     __shared__ double2 s_r[NW][MM];
     __shared__ bool s_last;
     __shared__ int s_any;   // the block processed a tile
@@ -1196,11 +1203,24 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
     }
     if (threadIdx.x == 0) {
         s_any = 0;
+        for (int r = 0; r < MM; ++r) s_nr[r] = (long long)__ldcg(&st->reg_n[in][r]);
+        // tile size of this step: the smallest multiple of NT (up to S) whose
+        // tiles do not outnumber the blocks, so that a small step runs in one
+        // wave of short tiles (a large one uses S)
+        int St = S;
+        for (int cand = NT; cand < S; cand += NT) {
+            long long tiles = 0;
+            for (int r = 0; r < MM; ++r) tiles += (s_nr[r] + cand - 1) / cand;
+            if (tiles <= (long long)gridDim.x) {
+                St = cand;
+                break;
+            }
+        }
+        s_St = St;
         long long acc = 0;
         for (int r = 0; r < MM; ++r) {
-            s_nr[r] = (long long)__ldcg(&st->reg_n[in][r]);
             s_tile0[r] = acc;
-            acc += (s_nr[r] + S - 1) / S;
+            acc += (s_nr[r] + St - 1) / St;
         }
         s_tile0[MM] = acc;
         if (acc == 0 && blockIdx.x == 0) {   // empty input: the output is empty
@@ -1210,6 +1230,7 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
     }
     __syncthreads();
     const long long ntiles = s_tile0[MM];
+    const int St = s_St, ept = St / NT;   // entries per thread this step (<= EPT)
     // rho(t+1) accumulators of this thread: FP64, or on the C64 path FP32
     // with a Kahan compensation term (M = 2; for M >= 3 plain FP32 sums, to
     // stay within the register budget of two blocks per SM), widened to
@@ -1243,9 +1264,9 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
         if (threadIdx.x == 0) s_any = 1;
         int r = 0;
         while (r + 1 < MM && ticket >= s_tile0[r + 1]) ++r;
-        const long long e0 = (ticket - s_tile0[r]) * S;
+        const long long e0 = (ticket - s_tile0[r]) * St;
         const long long nr = s_nr[r];
-        const int cnt = (int)min((long long)S, nr - e0);
+        const int cnt = (int)min((long long)St, nr - e0);
         const unsigned long long *kin = keys_in + r * G;
         const AmpT *ain = amps_in + r * G;
         // load the tile; warp 0 prefetches the 32 paths past its end (the
@@ -1256,10 +1277,10 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
             s_amp[i] = __ldcg(ain + e0 + i);
         }
         if (warp == 0) {
-            const bool ok = cnt == S && e0 + S + lane < nr;
+            const bool ok = cnt == St && e0 + St + lane < nr;
             if (ok) {
-                s_ra_key[lane] = __ldcg(kin + e0 + S + lane);
-                s_ra_amp[lane] = __ldcg(ain + e0 + S + lane);
+                s_ra_key[lane] = __ldcg(kin + e0 + St + lane);
+                s_ra_amp[lane] = __ldcg(ain + e0 + St + lane);
             }
             const unsigned okm = __ballot_sync(0xffffffffu, ok);
             if (lane == 0) s_ra_n = __popc(okm);   // a prefix of the 32 lanes
@@ -1273,12 +1294,12 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
         if constexpr (NX > 1)
             for (int i = threadIdx.x; i < S; i += NT) s_xm[i] = 0u;
         __syncthreads();
-        // run heads (EPT consecutive entries per thread), block scan of their count
+        // run heads (ept consecutive entries per thread), block scan of their count
         unsigned hmask = 0;
 #pragma unroll
         for (int u = 0; u < EPT; ++u) {
-            const int i = threadIdx.x * EPT + u;
-            if (i < cnt) {
+            const int i = threadIdx.x * ept + u;
+            if (u < ept && i < cnt) {
                 if (i == 0 && e0 == 0) hmask |= 1u << u;
                 else if ((s_key[i] & pref) != ((i > 0 ? s_key[i - 1] : s_kprev) & pref)) hmask |= 1u << u;
             }
@@ -1308,7 +1329,7 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
             int pos = segbase + 1;
 #pragma unroll
             for (int u = 0; u < EPT; ++u)
-                if (hmask & (1u << u)) s_seg[pos++] = threadIdx.x * EPT + u;
+                if (hmask & (1u << u)) s_seg[pos++] = threadIdx.x * ept + u;
         }
         __syncthreads();
         // extent of the tile's last run past the tile end (warp 0): members
@@ -1320,12 +1341,12 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
             int sg = segbase;
 #pragma unroll
             for (int u = 0; u < EPT; ++u) {
-                const int i = threadIdx.x * EPT + u;
+                const int i = threadIdx.x * ept + u;
                 if (hmask & (1u << u)) ++sg;
-                if (i < cnt && sg >= 0) atomicOr(&s_xm[sg], 1u << xval(s_key[i]));
+                if (u < ept && i < cnt && sg >= 0) atomicOr(&s_xm[sg], 1u << xval(s_key[i]));
             }
         }
-        if (warp == 0 && nseg > 0 && cnt == S) {
+        if (warp == 0 && nseg > 0 && cnt == St) {
             unsigned long long key = s_ra_key[lane];
             bool inrun = lane < s_ra_n && (key & pref) == plast;
             for (int round = 0;; ++round) {
@@ -1402,9 +1423,9 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
             WT wmx = 0;
 #pragma unroll
             for (int u = 0; u < EPT; ++u) {
-                const int i = threadIdx.x * EPT + u;
+                const int i = threadIdx.x * ept + u;
                 if (hmask & (1u << u)) ++sg;
-                if (i < cnt && sg >= 0) {
+                if (u < ept && i < cnt && sg >= 0) {
                     const AmpT a = s_amp[i];
                     const int sl = slot_of(sg, s_key[i]);
                     const WT wb = weight_bits(a);
@@ -1459,9 +1480,9 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
             unsigned long long kmin = kEmpty;
 #pragma unroll
             for (int u = 0; u < EPT; ++u) {
-                const int i = threadIdx.x * EPT + u;
+                const int i = threadIdx.x * ept + u;
                 if (hmask & (1u << u)) ++sg;
-                if (i < cnt && sg >= 0) {
+                if (u < ept && i < cnt && sg >= 0) {
                     const unsigned long long key = s_key[i];
                     const int sl = slot_of(sg, key);
                     if (sl != cur) {
@@ -1680,8 +1701,10 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
         if (threadIdx.x == 0) *P.fin_count = 0;
         return;
     }
+    StepCounts cts{};
+    if (threadIdx.x == 0) cts = step_counts(P, st, tn);   // in flight with the partial loads
     phase_finalize(P, tn, 0, rho_part_of(P, tn, MM), gridDim.x, MM);
-    if (threadIdx.x == 0) publish_step(P, st, tn, MM);
+    if (threadIdx.x == 0) publish_step(P, st, tn, MM, cts);
 }
 
 // The kernels' FP32 -> FP64 widening over an array (test hook).
