@@ -356,7 +356,11 @@ qp_status qp_surrogate_windows(const double *d_rho, int n_inst, int L, const flo
  * same 8 reals as above; steps < t_from must be filled): for t = t_from ..
  * t_to-1, rho(t) = rho(t-1) + net(window) / out_scale with the increment
  * made traceless, projected onto Hermitian matrices.  d_xbuf [n x d_in],
- * d_ybuf [n x 8] device scratch.                                          */
+ * d_ybuf [n x 8] device scratch.  The steps run as CUDA graphs of up to 32
+ * steps captured on the model's stream at the first call with these
+ * arguments and replayed (the step index lives on the device); on the
+ * legacy default stream they are launched one by one.  Synchronous: the
+ * rollout is complete when the call returns.                              */
 qp_status qp_surrogate_rollout(qp_mlp *m, float *d_hist, int n, int T, int L, const float *d_par, int n_par,
                                int t_from, int t_to, float out_scale, float *d_xbuf, float *d_ybuf);
 

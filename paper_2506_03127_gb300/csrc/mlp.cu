@@ -270,8 +270,12 @@ __global__ void k_windows(const double2 *rho, int n_inst, int L, const float *pa
     }
 }
 
-// Rollout input: features of step t from the history hist [n][T][8] (FP32).
-__global__ void k_rollout_input(const float *hist, int n, int T, int L, const float *par, int n_par, int t, float *x) {
+// Rollout input: features of step t (= *tstep) from the history hist
+// [n][T][8] (FP32).  The step index lives on the device so that a captured
+// graph of steps can be replayed.
+__global__ void k_rollout_input(const float *hist, int n, int T, int L, const float *par, int n_par,
+                                const int *tstep, float *x) {
+    const int t = *tstep;
     const int d_in = 8 * L + n_par;
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n * d_in; idx += gridDim.x * blockDim.x) {
         const int i = idx / d_in, f = idx % d_in;
@@ -283,8 +287,20 @@ __global__ void k_rollout_input(const float *hist, int n, int T, int L, const fl
 // trace changes only through the filter, negligibly over a rollout), then
 // projected onto Hermitian matrices (rho_10 = conj rho_01 from their mean,
 // real diagonal).
-__global__ void k_rollout_update(float *hist, int n, int T, int t, const float *y, float out_scale) {
+// The last block to finish advances the step index (every block has read
+// it by then).
+__global__ void k_rollout_update(float *hist, int n, int T, int *tstep, unsigned *done, const float *y,
+                                 float out_scale) {
+    const int t = *tstep;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ bool s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+        *done = 0;
+        *tstep = t + 1;
+    }
     if (i >= n) return;
     const float *prev = hist + ((size_t)i * T + (t - 1)) * 8;
     float d[8];
@@ -325,6 +341,14 @@ struct qp_mlp {
     __nv_bfloat16 *xb, *xT, *h1b, *h1T, *h2b, *h2T, *dyb, *dyT, *dh2b, *dh2T, *dh1b, *dh1T;
     float *h1, *h2, *y;
     double *loss;
+    int *tstep;                   // rollout step index and block counter (device)
+    unsigned *tdone;
+    // rollout graph: steps captured once, replayed (key: arguments it bakes in)
+    cudaGraphExec_t roll_exec = nullptr, roll_exec_rem = nullptr;
+    int roll_steps = 0, roll_rem = 0;
+    const void *roll_key[4] = {nullptr, nullptr, nullptr, nullptr};
+    int roll_dims[6] = {0, 0, 0, 0, 0, 0};
+    float roll_scale = 0.f;
     long long step = 0;
     int last_batch = -1;          // batch of the last backward pass (transposed pads)
     std::string err;
@@ -370,6 +394,7 @@ size_t mlp_layout(qp_mlp *m, int d_in, int width, int d_out, int max_batch, char
     char *dh1b = take((size_t)max_batch * Kw * 2), *dh1T = take((size_t)Kw * Bp * 2);
     char *h1 = take((size_t)max_batch * width * 4), *h2 = take((size_t)max_batch * width * 4);
     char *y = take((size_t)max_batch * d_out * 4), *loss = take(8);
+    char *tstep = take(16);
     if (m && base) {
         m->par = (float *)par;
         m->grad = (float *)grad;
@@ -398,6 +423,8 @@ size_t mlp_layout(qp_mlp *m, int d_in, int width, int d_out, int max_batch, char
         m->dh2T = (__nv_bfloat16 *)dh2T;
         m->dh1b = (__nv_bfloat16 *)dh1b;
         m->dh1T = (__nv_bfloat16 *)dh1T;
+        m->tstep = (int *)tstep;
+        m->tdone = (unsigned *)(tstep + 8);
         m->h1 = (float *)h1;
         m->h2 = (float *)h2;
         m->y = (float *)y;
@@ -566,7 +593,12 @@ qp_status qp_mlp_create(int d_in, int width, int d_out, int max_batch, void *d_w
     return QP_OK;
 }
 
-void qp_mlp_destroy(qp_mlp *m) { delete m; }
+void qp_mlp_destroy(qp_mlp *m) {
+    if (!m) return;
+    if (m->roll_exec) cudaGraphExecDestroy(m->roll_exec);
+    if (m->roll_exec_rem) cudaGraphExecDestroy(m->roll_exec_rem);
+    delete m;
+}
 
 qp_status qp_mlp_num_params(const qp_mlp *m, int64_t *n) {
     if (!m || !n) return QP_ERR_ARG;
@@ -658,11 +690,63 @@ qp_status qp_surrogate_rollout(qp_mlp *m, float *d_hist, int n, int T, int L, co
     if (!m || !d_hist || !d_par || !d_xbuf || !d_ybuf || n < 1 || n > m->max_batch || L < 1 || t_from < L ||
         t_to > T || t_to < t_from || 8 * L + n_par != m->d_in || m->d_out != 8 || !(out_scale > 0.f))
         return QP_ERR_ARG;
-    for (int t = t_from; t < t_to; ++t) {
-        k_rollout_input<<<64, 256, 0, m->stream>>>(d_hist, n, T, L, d_par, n_par, t, d_xbuf);
-        if (forward(m, d_xbuf, n) != cudaSuccess) return mfail(m, QP_ERR_CUDA, "forward");
-        k_rollout_update<<<(n + 127) / 128, 128, 0, m->stream>>>(d_hist, n, T, t, m->y, out_scale);
+    (void)d_ybuf;
+    const int nsteps = t_to - t_from;
+    if (nsteps == 0) return QP_OK;
+    // one rollout step: features, the network, the update (which advances
+    // the device step index)
+    auto one_step = [&]() -> cudaError_t {
+        k_rollout_input<<<64, 256, 0, m->stream>>>(d_hist, n, T, L, d_par, n_par, m->tstep, d_xbuf);
+        cudaError_t e = forward(m, d_xbuf, n);
+        if (e != cudaSuccess) return e;
+        k_rollout_update<<<(n + 127) / 128, 128, 0, m->stream>>>(d_hist, n, T, m->tstep, m->tdone, m->y, out_scale);
+        return cudaGetLastError();
+    };
+    auto capture = [&](int steps, cudaGraphExec_t *exec) -> cudaError_t {
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return e;
+        for (int k = 0; k < steps && e == cudaSuccess; ++k) e = one_step();
+        cudaError_t e2 = cudaStreamEndCapture(m->stream, &g);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(exec, g, 0);
+        if (g) cudaGraphDestroy(g);
+        return e;
+    };
+    // steps are replayed in graphs of up to 32 (the arguments each graph
+    // bakes in form its key; a different call captures again)
+    const int G = std::min(32, nsteps), rem = nsteps % G;
+    const void *key[4] = {d_hist, d_par, d_xbuf, m->ws};
+    const int dims[6] = {n, T, L, n_par, G, rem};
+    bool same = m->roll_exec && m->roll_scale == out_scale && m->roll_steps == G && m->roll_rem == rem;
+    for (int i = 0; i < 4 && same; ++i) same = m->roll_key[i] == key[i];
+    for (int i = 0; i < 6 && same; ++i) same = m->roll_dims[i] == dims[i];
+    if (cudaMemsetAsync(m->tdone, 0, 4, m->stream) != cudaSuccess ||
+        cudaMemcpyAsync(m->tstep, &t_from, 4, cudaMemcpyHostToDevice, m->stream) != cudaSuccess)
+        return mfail(m, QP_ERR_CUDA, "rollout set-up");
+    if (m->stream == nullptr) {   // the legacy default stream cannot be captured: launch step by step
+        for (int k = 0; k < nsteps; ++k)
+            if (one_step() != cudaSuccess) return mfail(m, QP_ERR_CUDA, "rollout");
+        if (cudaStreamSynchronize(m->stream) != cudaSuccess) return mfail(m, QP_ERR_CUDA, "rollout");
+        return QP_OK;
     }
+    if (!same) {
+        if (m->roll_exec) cudaGraphExecDestroy(m->roll_exec);
+        if (m->roll_exec_rem) cudaGraphExecDestroy(m->roll_exec_rem);
+        m->roll_exec = m->roll_exec_rem = nullptr;
+        if (capture(G, &m->roll_exec) != cudaSuccess || (rem && capture(rem, &m->roll_exec_rem) != cudaSuccess))
+            return mfail(m, QP_ERR_CUDA, "rollout graph capture");
+        m->roll_steps = G;
+        m->roll_rem = rem;
+        m->roll_scale = out_scale;
+        for (int i = 0; i < 4; ++i) m->roll_key[i] = key[i];
+        for (int i = 0; i < 6; ++i) m->roll_dims[i] = dims[i];
+    }
+    for (int k = 0; k < nsteps / G; ++k)
+        if (cudaGraphLaunch(m->roll_exec, m->stream) != cudaSuccess) return mfail(m, QP_ERR_CUDA, "rollout graph");
+    if (rem && cudaGraphLaunch(m->roll_exec_rem, m->stream) != cudaSuccess) return mfail(m, QP_ERR_CUDA, "rollout graph");
+    // the host value t_from is read by the copy before the call returns
+    if (cudaStreamSynchronize(m->stream) != cudaSuccess) return mfail(m, QP_ERR_CUDA, "rollout");
     return cudaGetLastError() == cudaSuccess ? QP_OK : mfail(m, QP_ERR_CUDA, "rollout");
 }
 
