@@ -61,6 +61,7 @@ constexpr int kPersistThreads = 256;
 constexpr int kMaxInst = 128;                      // instances of one batched context
 constexpr int kStreamMinTile = 256;                 // smallest stream tile (256, 512 or 1024 stored paths)
 constexpr int kRegThreads = 256;                    // threads per block of the regular stream kernel
+constexpr int kStreamWarps = 8;                     // warps per block of both stream kernels (256 threads)
 constexpr size_t kMaxStreamLut = 32 * 1024;         // history tables staged in shared memory up to this size
 constexpr int kStreamThreads = 256;
 constexpr unsigned kLbAgg = 1u, kLbInc = 2u;        // look-back word states (bits 30-31)
@@ -87,6 +88,9 @@ struct __align__(128) DevState {
     unsigned int ticket[3];           // stream engine: tile tickets, step t' uses [t' % 3]
     unsigned int pad0;
     unsigned long long reg_done;      // stream engine: tn + 1 when the regular kernel took step tn, else 0
+    unsigned long long rho_pending;   // stream engine: step whose block partials of rho are not summed yet (0: none)
+    unsigned int rho_nblk;            // ... and the blocks that wrote them
+    unsigned int pad3;
     unsigned int bar_count;           // grid barrier of the persistent kernel: arrivals
     unsigned int pad1[31];
     unsigned int bar_gen;             // generation (own cache line)
@@ -128,6 +132,8 @@ struct Params {
     double tie_rel;                    // relative window of equal weights (R4)
     double2 *rho_ring;                 // [rho_hist][n_inst][M*M]
     double2 *rho_part;                 // [2 (step parity)][kMaxExpandBlocks][n_inst][M*M + 1] per-block partials
+    float4 *spart;                     // stream engine: [2][kMaxExpandBlocks][M*M] per-block partials (FP32 pairs)
+    long long *scount;                 // stream engine: [2][kMaxExpandBlocks] children written per block
                                        // of rho(t) per instance; element M*M holds the survivor count
     long long *inst_kept;              // [rho_hist][n_inst] stored paths per instance after each step
     unsigned int *fin_count;           // blocks of k_finalize that are done (last one updates the state)
@@ -747,6 +753,145 @@ __device__ __forceinline__ double2 *rho_part_of(const Params &P, unsigned long l
     return P.rho_part + (size_t)(tn & 1) * kMaxExpandBlocks * P.n_inst * (MM + 1);
 }
 
+// Stream engine: each block stores its partial of rho per end point, C64 as
+// an FP32 sum and the rounding error of every addition (warp shuffles, then
+// the warps folded by one thread per end point, all with error-free TwoSum
+// additions, so no FP64 in the kernel's tail), FP64 as a double pair in the
+// same 16 bytes.  s_rt: [NW][M*M] scratch; dst = [M*M] of this block.  All
+// threads of the block call it.
+template <int MM, int NW, bool C64>
+__device__ __forceinline__ void block_rho_pair(const typename std::conditional<C64, float2, double2>::type *hi,
+                                               const float2 *lo, float4 (*s_rt)[MM], float4 *dst) {
+    const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < MM; ++k) {
+        if constexpr (C64) {
+            float sx = hi[k].x, ex = lo[k].x, sy = hi[k].y, ey = lo[k].y;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float bx = __shfl_down_sync(0xffffffffu, sx, o), fx = __shfl_down_sync(0xffffffffu, ex, o);
+                const float by = __shfl_down_sync(0xffffffffu, sy, o), fy = __shfl_down_sync(0xffffffffu, ey, o);
+                const float tx = sx + bx, vx = tx - sx;
+                ex += fx + ((sx - (tx - vx)) + (bx - vx));
+                sx = tx;
+                const float ty = sy + by, vy = ty - sy;
+                ey += fy + ((sy - (ty - vy)) + (by - vy));
+                sy = ty;
+            }
+            if (lane == 0) s_rt[warp][k] = make_float4(sx, ex, sy, ey);
+        } else {
+            double x = hi[k].x, y = hi[k].y;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                x += __shfl_down_sync(0xffffffffu, x, o);
+                y += __shfl_down_sync(0xffffffffu, y, o);
+            }
+            if (lane == 0) reinterpret_cast<double2 *>(&s_rt[warp][0])[k] = make_double2(x, y);
+        }
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < MM) {
+        const int k = threadIdx.x;
+        if constexpr (C64) {
+            float4 a = s_rt[0][k];
+            for (int w = 1; w < NW; ++w) {
+                const float4 b = s_rt[w][k];
+                const float tx = a.x + b.x, vx = tx - a.x;
+                a.y += b.y + ((a.x - (tx - vx)) + (b.x - vx));
+                a.x = tx;
+                const float ty = a.z + b.z, vy = ty - a.z;
+                a.w += b.w + ((a.z - (ty - vy)) + (b.z - vy));
+                a.z = ty;
+            }
+            dst[k] = a;
+        } else {
+            double2 a = reinterpret_cast<const double2 *>(&s_rt[0][0])[k];
+            for (int w = 1; w < NW; ++w) {
+                const double2 b = reinterpret_cast<const double2 *>(&s_rt[w][0])[k];
+                a.x += b.x;
+                a.y += b.y;
+            }
+            reinterpret_cast<double2 *>(dst)[k] = a;
+        }
+    }
+}
+
+__device__ __forceinline__ float4 *spart_of(const Params &P, unsigned long long tn, int MM) {
+    return P.spart + (size_t)(tn & 1) * kMaxExpandBlocks * MM;
+}
+__device__ __forceinline__ long long *scount_of(const Params &P, unsigned long long tn) {
+    return P.scount + (size_t)(tn & 1) * kMaxExpandBlocks;
+}
+
+// rho(tn) of the stream engine from the per-block partials of nblk blocks,
+// summed in FP64 in a fixed order (T threads per component, a pairwise tree
+// over them), and the survivor count.  Block-uniform, 256 threads.
+template <bool C64>
+__device__ __forceinline__ void phase_finalize_stream(const Params &P, unsigned long long tn, int nblk, int MM) {
+    __shared__ double s_p[256];
+    __shared__ long long s_c[256];
+    const float4 *src = spart_of(P, tn, MM);
+    const long long *cnt = scount_of(P, tn);
+    const int ncomp = 2 * MM, n = nblk;   // components (re, im per end point), block partials
+    const int T = 256 / ncomp;
+    const int comp = (int)threadIdx.x / T, sidx = (int)threadIdx.x % T;
+    double a = 0.0;
+    if (comp < ncomp) {
+        const int k = comp >> 1, im = comp & 1;
+        for (int w0 = sidx; w0 < n; w0 += 8 * T) {
+            double v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int w = w0 + u * T;
+                v[u] = 0.0;
+                if (w < n) {
+                    const float4 q = __ldcg(src + (size_t)w * MM + k);
+                    if constexpr (C64) v[u] = im ? f2d_exact(q.z) + f2d_exact(q.w) : f2d_exact(q.x) + f2d_exact(q.y);
+                    else {
+                        const double2 d = *reinterpret_cast<const double2 *>(&q);
+                        v[u] = im ? d.y : d.x;
+                    }
+                }
+            }
+            a += ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
+        }
+    }
+    long long c = 0;
+    for (int b = threadIdx.x; b < nblk; b += 256) c += __ldcg(cnt + b);
+    s_p[threadIdx.x] = a;
+    s_c[threadIdx.x] = c;
+    __syncthreads();
+    for (int w = 1; w < 256; w <<= 1) {   // two pairwise trees: T values per component, 256 counts
+        if (comp < ncomp && sidx % (2 * w) == 0 && sidx + w < T) s_p[threadIdx.x] += s_p[threadIdx.x + w];
+        if ((threadIdx.x % (2 * w)) == 0 && threadIdx.x + w < 256) s_c[threadIdx.x] += s_c[threadIdx.x + w];
+        __syncthreads();
+    }
+    const size_t slot = (size_t)(tn % (unsigned long long)P.rho_hist);
+    if ((int)threadIdx.x < MM)
+        P.rho_ring[slot * MM + threadIdx.x] = make_double2(s_p[2 * threadIdx.x * T], s_p[(2 * threadIdx.x + 1) * T]);
+    if (threadIdx.x == 0) P.inst_kept[slot] = s_c[0];
+    __syncthreads();
+}
+
+// The stream kernels' last block publishes a step's counters and leaves the
+// sum of the blocks' partials of rho to block 0 of the next step (or to
+// k_rho_finalize before a read): rho(t) of a step is complete when the next
+// step starts or the host reads it.  Partials alternate by step parity, so
+// the next step's own partials never overwrite them.  Block-uniform.
+template <bool C64>
+__device__ __forceinline__ void finish_pending_rho(const Params &P, DevState *st, int MM) {
+    const unsigned long long pt = st->rho_pending;
+    if (pt == 0) return;
+    phase_finalize_stream<C64>(P, pt, (int)st->rho_nblk, MM);
+    if (threadIdx.x == 0) st->rho_pending = 0;
+}
+
+template <bool C64>
+__global__ void k_rho_finalize(Params P, int MM) {
+    if (P.st->err) return;
+    finish_pending_rho<C64>(P, P.st, MM);
+}
+
 template <int M, bool C64, bool BATCH>
 __global__ void __launch_bounds__(kExpandThreads) k_expand(Params P) {
     DevState *st = P.st;
@@ -891,7 +1036,8 @@ template <int M, bool C64>
 __global__ void __launch_bounds__(kRegThreads, 3) k_stream_regular(Params P, int lut_smem) {
     using X = Expander<M, C64>;
     using AmpT = typename X::AmpT;
-    constexpr int MM = M * M, NT = kRegThreads, NW = NT / 32;
+    constexpr int MM = M * M, NT = kRegThreads;
+    static_assert(NT / 32 == kStreamWarps, "warp partials");
     DevState *st = P.st;
     if (st->err) return;
     const unsigned long long t = st->t, tn = t + 1;
@@ -901,7 +1047,7 @@ __global__ void __launch_bounds__(kRegThreads, 3) k_stream_regular(Params P, int
     __shared__ long long s_gb[MM + 1];
     __shared__ double2 s_w[C64 ? 1 : MM * MM];
     __shared__ float2 s_wf[MM * MM];
-    __shared__ double2 s_r[NW][MM];
+    __shared__ float4 s_rt[kRegThreads / 32][MM];
     __shared__ bool s_last;
     if (threadIdx.x == 0) {
         long long acc = 0;
@@ -922,6 +1068,7 @@ __global__ void __launch_bounds__(kRegThreads, 3) k_stream_regular(Params P, int
         if (blockIdx.x == 0 && threadIdx.x == 0) st->reg_done = 0;
         return;
     }
+    if (blockIdx.x == 0) finish_pending_rho<C64>(P, st, MM);   // rho of the previous step
     const int gs = merge ? MM : 1;
     const int n_act = (int)min(tn, (unsigned long long)P.dkmax);
     const int L_child = (int)min(tn + 1, (unsigned long long)P.dkmax);
@@ -1035,34 +1182,36 @@ __global__ void __launch_bounds__(kRegThreads, 3) k_stream_regular(Params P, int
             group(g, m0);
         }
     }
-    // block partial of rho(tn) and the children written by this block
-    double2 *mine = rho_part_of(P, tn, MM) + (size_t)blockIdx.x * (MM + 1);
-    float2 lo[MM];
-#pragma unroll
-    for (int k = 0; k < MM; ++k) lo[k] = C64 ? make_float2(-(float)rcmp[k].x, -(float)rcmp[k].y) : make_float2(0.f, 0.f);
-    block_rho_partial<MM, NW, C64>(racc, lo, s_r, mine);
-    if (threadIdx.x == 0) {
-        long long mg = 0;
-        for (long long g0 = (long long)blockIdx.x * NT; g0 < ngroups; g0 += stride) mg += min((long long)NT, ngroups - g0);
-        mine[MM] = make_double2((double)(mg * MM), 0.0);
-    }
-    // last block done: rho(tn) from the partials in block order, publish
+    // arrive first: the last block to arrive publishes the step, for which
+    // it needs the step's counters only; every block then writes its partial
+    // of rho, which the next step's block 0 (or a read-time finalisation)
+    // sums once this kernel has ended
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
         s_last = atomicAdd(P.fin_count, 1u) == gridDim.x - 1;
+        if (s_last) {
+            __threadfence();
+            if (__ldcg(&st->err)) {   // a failed step is not published
+                *P.fin_count = 0;
+            } else {
+                st->rho_nblk = gridDim.x;
+                st->rho_pending = tn;
+                publish_step(P, st, tn, MM, step_counts(P, st, tn));
+            }
+        }
     }
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    if (__ldcg(&st->err)) {   // a failed step is not published
-        if (threadIdx.x == 0) *P.fin_count = 0;
-        return;
+    // block partials of rho(tn) and the children written by this block
+    float4 *mine = spart_of(P, tn, MM) + (size_t)blockIdx.x * MM;
+    float2 lo[MM];
+#pragma unroll
+    for (int k = 0; k < MM; ++k) lo[k] = C64 ? make_float2(-(float)rcmp[k].x, -(float)rcmp[k].y) : make_float2(0.f, 0.f);
+    block_rho_pair<MM, kRegThreads / 32, C64>(racc, lo, s_rt, mine);
+    if (threadIdx.x == 0) {
+        long long mg = 0;
+        for (long long g0 = (long long)blockIdx.x * NT; g0 < ngroups; g0 += stride) mg += min((long long)NT, ngroups - g0);
+        scount_of(P, tn)[blockIdx.x] = mg * MM;
     }
-    StepCounts cts{};
-    if (threadIdx.x == 0) cts = step_counts(P, st, tn);   // in flight with the partial loads
-    phase_finalize(P, tn, 0, rho_part_of(P, tn, MM), gridDim.x, MM);
-    if (threadIdx.x == 0) publish_step(P, st, tn, MM, cts);
 }
 
 // Dynamic shared memory of the stream kernel for a tile of S stored paths
@@ -1136,9 +1285,11 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
     constexpr int NT = kStreamThreads, NW = NT / 32, EPT = S / NT;
     constexpr int NG = Lay::NG;
     static_assert(S % NT == 0 && EPT <= 32, "tile size");
+    static_assert(NW == kStreamWarps, "warp partials");
     DevState *st = P.st;
     if (st->err) return;
     if (st->reg_done == st->t + 1) return;   // the regular kernel just took this step (its new t + 1)
+    if (blockIdx.x == 0) finish_pending_rho<C64>(P, st, M * M);   // rho of the previous step
     const unsigned long long t = st->t, tn = t + 1;
     const int in = (int)(t & 1), outp = (int)(tn & 1), cs = (int)(tn % 3);
     const bool merge = tn >= (unsigned long long)P.dkmax;
@@ -1173,7 +1324,7 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
     __shared__ unsigned s_ra_n;   // prefetched paths past the tile end
     __shared__ unsigned s_ticket, s_nseg, s_ng, s_hw[NW];
     __shared__ int s_St;   // tile size of this step
-    __shared__ double2 s_r[NW][MM];
+    __shared__ float4 s_rt[NW][MM];
     __shared__ bool s_last;
     __shared__ int s_any;   // the block processed a tile
     const double tie_d = 1.0 - P.tie_rel;   // R4 window, once per thread
@@ -1669,10 +1820,29 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
         }
         __syncthreads();
     }
-    // this block's partial sums of rho(t+1) (and survivor count); a block
-    // that processed no tile has zeros (block_kept is block-uniform: thread
-    // 0 holds it, the loop ended with a barrier)
-    double2 *mine = rho_part_of(P, tn, MM) + (size_t)blockIdx.x * (MM + 1);
+    // arrive first: the last block to arrive publishes the step, for which
+    // it needs the step's counters only; every block then writes its partial
+    // of rho, which the next step's block 0 (or a read-time finalisation)
+    // sums once this kernel has ended
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(P.fin_count, 1u) == gridDim.x - 1;
+        if (s_last) {
+            __threadfence();
+            if (__ldcg(&st->err)) {   // a failed step is not published
+                *P.fin_count = 0;
+            } else {
+                st->rho_nblk = gridDim.x;
+                st->rho_pending = tn;
+                publish_step(P, st, tn, MM, step_counts(P, st, tn));
+            }
+        }
+    }
+    // this block's partials of rho(t+1) and survivor count; a block that
+    // processed no tile writes zeros without reducing (s_any: thread 0 holds
+    // block_kept; the barrier below orders it)
+    float4 *mine = spart_of(P, tn, MM) + (size_t)blockIdx.x * MM;
     if (threadIdx.x == 0) s_any = block_kept > 0 || s_any;
     __syncthreads();
     if (s_any) {
@@ -1682,29 +1852,11 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
             if constexpr (kKahan) lo[k] = make_float2(-rcmp[k].x, -rcmp[k].y);
             else lo[k] = make_float2(0.f, 0.f);
         }
-        block_rho_partial<MM, NW, C64>(racc, lo, s_r, mine);
-    } else if (threadIdx.x < MM) {
-        mine[threadIdx.x] = make_double2(0.0, 0.0);
+        block_rho_pair<MM, NW, C64>(racc, lo, s_rt, mine);
+    } else if ((int)threadIdx.x < MM) {
+        mine[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    if (threadIdx.x == 0) mine[MM] = make_double2((double)block_kept, 0.0);
-    // last block done: rho(t+1) from the partials in block order, then the
-    // step is published (no separate finalisation kernel)
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        s_last = atomicAdd(P.fin_count, 1u) == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    if (__ldcg(&st->err)) {   // a failed step is not published
-        if (threadIdx.x == 0) *P.fin_count = 0;
-        return;
-    }
-    StepCounts cts{};
-    if (threadIdx.x == 0) cts = step_counts(P, st, tn);   // in flight with the partial loads
-    phase_finalize(P, tn, 0, rho_part_of(P, tn, MM), gridDim.x, MM);
-    if (threadIdx.x == 0) publish_step(P, st, tn, MM, cts);
+    if (threadIdx.x == 0) scount_of(P, tn)[blockIdx.x] = (long long)block_kept;
 }
 
 // The kernels' FP32 -> FP64 widening over an array (test hook).
@@ -1806,7 +1958,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
     size_t keys[2], amps[2], slots, repk, slot_of, groups, lut, lutf, lutlo, etab, wtab, wtabf, uprop, eta, q, deltas,
-        rho, rho_part, stats, inst_kept, fin_count, tile_state, state, total;
+        rho, rho_part, spart, scount, stats, inst_kept, fin_count, tile_state, state, total;
     long long entries, max_tiles;
     size_t nlut;           // history-table entries of one instance
     int nd;                // distinct nonzero coupling differences
@@ -1927,6 +2079,8 @@ Layout make_layout(const qp_config *c) {
     L.q = take(c->M * sizeof(double));
     L.rho = take((size_t)R * NI * MM * sizeof(double2));
     L.rho_part = take((size_t)2 * kMaxExpandBlocks * NI * (MM + 1) * sizeof(double2));   // by step parity
+    L.spart = take((size_t)2 * kMaxExpandBlocks * MM * sizeof(float4));
+    L.scount = take((size_t)2 * kMaxExpandBlocks * sizeof(long long));
     L.stats = take((size_t)R * sizeof(StepRec));
     L.inst_kept = take((size_t)R * NI * sizeof(long long));
     L.fin_count = take(sizeof(unsigned int));
@@ -2364,6 +2518,8 @@ qp_status qp_create(const qp_config *cfg, void *d_workspace, size_t bytes, void 
     P.tie_rel = cfg->precision == QP_C64 ? kTieRelC64 : kTieRelFP64;
     P.rho_ring = reinterpret_cast<double2 *>(c->ws + L.rho);
     P.rho_part = reinterpret_cast<double2 *>(c->ws + L.rho_part);
+    P.spart = reinterpret_cast<float4 *>(c->ws + L.spart);
+    P.scount = reinterpret_cast<long long *>(c->ws + L.scount);
     P.inst_kept = reinterpret_cast<long long *>(c->ws + L.inst_kept);
     P.fin_count = reinterpret_cast<unsigned int *>(c->ws + L.fin_count);
     P.n_inst = std::max(1, cfg->n_inst);
@@ -2664,6 +2820,11 @@ qp_status qp_read_rho(qp_ctx *c, int64_t t0, int count, double *re, double *im) 
     if (!c) return QP_ERR_ARG;
     if (!re || !im || count < 0) return fail(c, QP_ERR_ARG, "bad output");
     if (!c->have_state) return fail(c, QP_ERR_STATE, "no state");
+    if (c->use_stream) {   // the last step's rho may still be in block partials
+        if (c->cfg.precision == QP_C64) k_rho_finalize<true><<<1, 256, 0, c->stream>>>(c->P, c->cfg.M * c->cfg.M);
+        else k_rho_finalize<false><<<1, 256, 0, c->stream>>>(c->P, c->cfg.M * c->cfg.M);
+        QP_CUDA(c, cudaGetLastError());
+    }
     DevState s;
     qp_status r = read_state(c, &s);
     if (r != QP_OK) return r;
@@ -2688,6 +2849,11 @@ qp_status qp_read_instance_counts(qp_ctx *c, int64_t t, int64_t *kept) {
     if (!c) return QP_ERR_ARG;
     if (!kept) return fail(c, QP_ERR_ARG, "bad output");
     if (!c->have_state) return fail(c, QP_ERR_STATE, "no state");
+    if (c->use_stream) {   // the last step's counts may still be in block partials
+        if (c->cfg.precision == QP_C64) k_rho_finalize<true><<<1, 256, 0, c->stream>>>(c->P, c->cfg.M * c->cfg.M);
+        else k_rho_finalize<false><<<1, 256, 0, c->stream>>>(c->P, c->cfg.M * c->cfg.M);
+        QP_CUDA(c, cudaGetLastError());
+    }
     DevState s;
     qp_status r = read_state(c, &s);
     if (r != QP_OK) return r;
