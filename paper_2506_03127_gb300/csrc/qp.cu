@@ -154,7 +154,8 @@ struct Params {
     // survives and child c of group g goes to entry g of region c.
     int reg_fill, reg_merge;
     unsigned long long full_n;
-    unsigned long long *tile_state;    // [max_tiles][M*M] look-back words
+    unsigned long long *tile_state;    // [M*M][max_tiles] look-back words (a bucket's tiles contiguous)
+    long long max_tiles;
     StepRec *stats_ring;               // [rho_hist]
     DevState *st;
 };
@@ -1721,31 +1722,59 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
 #pragma unroll
         for (int c = 0; c < MM; ++c) tb[c] += s_wsum[warp][c];
         // decoupled look-back, one warp per bucket (buckets c, c + NW, ...):
-        // publish the tile's aggregate, then read 32 predecessors at a time
-        // (relaxed GPU-scope loads, bounded waits) and add aggregates back to
-        // the nearest inclusive prefix
+        // publish the tile's aggregate, then read a window of 32 * LBK
+        // predecessors: position p = j * 32 + lane is tile pred - p, so each
+        // load instruction reads 32 consecutive words of the bucket (relaxed
+        // GPU-scope loads).  With u the nearest unpublished and i the nearest
+        // inclusive position: i < u ends the look-back (sum up to i);
+        // otherwise the published aggregates before u are added and the
+        // window moves to u, waiting (bounded) only for that tile.  A wide
+        // window matters when all tiles run at once: inclusive prefixes then
+        // spread one window per round.
+        constexpr int LBK = 4;
+        constexpr int WIN = 32 * LBK;
         for (int c = warp; c < MM; c += NW) {
-            unsigned long long *my = P.tile_state + (size_t)ticket * MM + c;
+            unsigned long long *bucket = P.tile_state + (size_t)c * P.max_tiles;
             const unsigned long long tot = s_tot[c];
-            if (lane == 0) atomicExch(my, lb_word(epoch, ticket == 0 ? kLbInc : kLbAgg, tot));
+            if (lane == 0) atomicExch(bucket + ticket, lb_word(epoch, ticket == 0 ? kLbInc : kLbAgg, tot));
             unsigned long long excl = 0;
             long long pred = ticket - 1;
             const long long t0 = clock64();
             bool timeout = false, abort = false;   // abort: another block raised an error
             while (pred >= 0) {
-                const long long idx = pred - (long long)lane;
-                unsigned state = 0;
-                unsigned long long val = 0;
-                for (;;) {   // every lane of the window must see its predecessor's word
+                unsigned wv[LBK];   // (state << 30) | count of this step; 0: not yet published
+#pragma unroll
+                for (int j = 0; j < LBK; ++j) {
+                    const long long idx = pred - (long long)j * 32 - lane;
                     if (idx < 0) {
-                        state = kLbInc;   // before the first tile: an inclusive prefix of 0
-                        val = 0;
+                        wv[j] = kLbInc << 30;   // before the first tile: an inclusive prefix of 0
                     } else {
-                        const unsigned long long w = ld_relaxed_gpu(P.tile_state + (size_t)idx * MM + c);
-                        state = (unsigned)(w >> 32) == epoch ? ((unsigned)(w >> 30) & 3u) : 0u;
-                        val = w & ((1ull << 30) - 1ull);
+                        const unsigned long long w = ld_relaxed_gpu(bucket + idx);
+                        wv[j] = (unsigned)(w >> 32) == epoch ? (unsigned)w : 0u;
                     }
-                    if (__all_sync(0xffffffffu, state != 0)) break;
+                }
+                int u = WIN, i = WIN;   // nearest unpublished / inclusive position
+#pragma unroll
+                for (int j = LBK - 1; j >= 0; --j) {
+                    const unsigned um = __ballot_sync(0xffffffffu, wv[j] == 0u);
+                    const unsigned im = __ballot_sync(0xffffffffu, (wv[j] >> 30) == kLbInc);
+                    if (um) u = j * 32 + __ffs(um) - 1;
+                    if (im) i = j * 32 + __ffs(im) - 1;
+                }
+                const bool done = i < u;
+                const int lim = done ? i + 1 : u;   // positions summed this round
+                if (lim > 0) {
+                    unsigned long long part = 0;
+#pragma unroll
+                    for (int j = 0; j < LBK; ++j)
+                        if (j * 32 + (int)lane < lim) part += wv[j] & ((1u << 30) - 1u);
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+                    excl += __shfl_sync(0xffffffffu, part, 0);
+                }
+                if (done) break;
+                pred -= lim;
+                if (lim < WIN) {   // waiting on tile pred: bounded
                     if (*(volatile unsigned *)&st->err) {
                         abort = true;
                         break;
@@ -1756,19 +1785,10 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
                     }
                     __nanosleep(32);
                 }
-                if (timeout || abort) break;
-                const unsigned incm = __ballot_sync(0xffffffffu, state == kLbInc);
-                const int lim = incm ? __ffs(incm) - 1 : 31;   // nearest inclusive predecessor
-                unsigned long long v = (int)lane <= lim ? val : 0ull;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-                excl += __shfl_sync(0xffffffffu, v, 0);
-                if (incm) break;
-                pred -= 32;
             }
             if (timeout && lane == 0) atomicOr(&st->err, kErrTimeout);
             if (lane == 0) {
-                if (ticket > 0) atomicExch(my, lb_word(epoch, kLbInc, excl + tot));
+                if (ticket > 0) atomicExch(bucket + ticket, lb_word(epoch, kLbInc, excl + tot));
                 s_base[c] = excl;
                 if (ticket == ntiles - 1) st->reg_n[outp][c] = excl + tot;   // the last tile knows the region sizes
             }
@@ -2528,6 +2548,7 @@ qp_status qp_create(const qp_config *cfg, void *d_workspace, size_t bytes, void 
     P.lut_stride = L.nlut;
     P.region_cap = (cfg->max_paths / (M * M)) & ~15ll;   // region bases 16-entry aligned (vector loads)
     P.tile_state = reinterpret_cast<unsigned long long *>(c->ws + L.tile_state);
+    P.max_tiles = L.max_tiles;
     P.etab_stride = L.nlut * (size_t)std::max(1, L.nd);
     P.stats_ring = reinterpret_cast<StepRec *>(c->ws + L.stats);
     P.st = reinterpret_cast<DevState *>(c->ws + L.state);
