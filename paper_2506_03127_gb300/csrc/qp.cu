@@ -72,7 +72,7 @@ constexpr double kTieRelC64 = 1e-5;    // same, at complex64 resolution
 
 struct __align__(32) Slot {
     unsigned long long mk;     // masked key, kEmpty when free
-    unsigned long long wmax;   // bit pattern of max |amp|^2 (FP64)
+    unsigned long long wmax;   // bit pattern of max |amp|^2 (FP64; FP32 on the C64 path)
     double sre, sim;           // FP64 group sum
 };
 
@@ -162,15 +162,6 @@ struct Params {
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 
-// Path data and merge-table fields are written by other blocks of the same
-// persistent kernel, so they are read through L2 (ld.global.cg), never L1.
-// Global memory only (never a shared-memory pointer).
-__device__ __forceinline__ double2 load_amp(const double2 *p, unsigned long long i) { return __ldcg(p + i); }
-__device__ __forceinline__ double2 load_amp(const float2 *p, unsigned long long i) {
-    const float2 v = __ldcg(p + i);
-    return make_double2(v.x, v.y);
-}
-
 // float -> double by IEEE-754 fields, exactly, with integer operations only
 // (keeps the widening of FP32 values off the FP64 pipe): the sign is kept;
 // a normal number keeps its 23 fraction bits (shifted up by 29) and its
@@ -191,6 +182,16 @@ __device__ __forceinline__ double f2d_exact(float f) {
     }
     return __longlong_as_double((long long)bits);
 }
+
+// Path data and merge-table fields are written by other blocks of the same
+// persistent kernel, so they are read through L2 (ld.global.cg), never L1.
+// Global memory only (never a shared-memory pointer).
+__device__ __forceinline__ double2 load_amp(const double2 *p, unsigned long long i) { return __ldcg(p + i); }
+__device__ __forceinline__ double2 load_amp(const float2 *p, unsigned long long i) {
+    const float2 v = __ldcg(p + i);
+    return make_double2(f2d_exact(v.x), f2d_exact(v.y));
+}
+
 __device__ __forceinline__ double to_d(double v) { return v; }
 __device__ __forceinline__ double to_d(float v) { return f2d_exact(v); }
 __device__ __forceinline__ float2 to_f2(float2 v) { return v; }
@@ -291,8 +292,16 @@ __device__ __forceinline__ void phase_insert(const Params &P, unsigned long long
             if (found) {
                 atomicAdd(&P.slots[h].sre, a.x);
                 atomicAdd(&P.slots[h].sim, a.y);
-                const double w2 = a.x * a.x + a.y * a.y;
-                atomicMax(&P.slots[h].wmax, (unsigned long long)__double_as_longlong(w2));
+                // weight |a|^2 as ordered bits: FP32 on the C64 path (as in
+                // the stream engine), FP64 otherwise
+                unsigned long long wb;
+                if constexpr (sizeof(Amp) == sizeof(float2)) {
+                    const float ax = (float)a.x, ay = (float)a.y;   // exact: a holds FP32 values
+                    wb = __float_as_uint(ax * ax + ay * ay);
+                } else {
+                    wb = (unsigned long long)__double_as_longlong(a.x * a.x + a.y * a.y);
+                }
+                atomicMax(&P.slots[h].wmax, wb);
                 P.slot_of[i] = (unsigned int)h;
             } else {
                 P.slot_of[i] = kNoSlot;
@@ -318,10 +327,19 @@ __device__ __forceinline__ void phase_tiebreak(const Params &P, unsigned long lo
     for (unsigned long long i = blockIdx.x * (unsigned long long)NT + threadIdx.x; i < n; i += stride) {
         const unsigned int h = __ldcg(P.slot_of + i);
         if (h == kNoSlot) continue;
-        const double2 a = load_amp(amps, i);
-        const double w2 = a.x * a.x + a.y * a.y;
-        const double wm = __longlong_as_double((long long)__ldcg(&P.slots[h].wmax));
-        if (w2 >= (1.0 - P.tie_rel) * wm) atomicMin(&P.repk[h], __ldcg(keys + i));
+        bool tie;
+        if constexpr (sizeof(Amp) == sizeof(float2)) {
+            const float2 a = __ldcg(amps + i);
+            const float w2 = a.x * a.x + a.y * a.y;
+            const float wm = __uint_as_float((unsigned)__ldcg(&P.slots[h].wmax));
+            tie = w2 >= (float)(1.0 - P.tie_rel) * wm;
+        } else {
+            const double2 a = load_amp(amps, i);
+            const double w2 = a.x * a.x + a.y * a.y;
+            const double wm = __longlong_as_double((long long)__ldcg(&P.slots[h].wmax));
+            tie = w2 >= (1.0 - P.tie_rel) * wm;
+        }
+        if (tie) atomicMin(&P.repk[h], __ldcg(keys + i));
     }
 }
 

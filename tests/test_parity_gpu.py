@@ -162,6 +162,29 @@ def test_stream_engine_rerun_and_launch_shapes_agree(precision):
     p.close()
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("c64", 1e-6)])
+def test_stream_rho_read_every_step_equals_history_read_at_the_end(precision, tol):
+    """A stream-engine step publishes its counters; its rho is summed from the
+    blocks' partials when the next step starts or when it is read.  Reading
+    rho after every step and reading the whole history once at the end give
+    the same values (up to the order of FP64 atomic group sums)."""
+    w = W.SPIN_BOSON_STRUCTURED_DK16
+    p1 = Propagator.from_workload(w, precision=precision, engine="stream", max_paths=1 << 21)
+    per_step = []
+    for t in range(1, 41):
+        p1.step(1)
+        per_step.append(p1.rho(t, 1)[0])
+    p1.close()
+    p2 = Propagator.from_workload(w, precision=precision, engine="stream", max_paths=1 << 21)
+    p2.step(40)
+    at_end = p2.rho(1, 40)
+    p2.close()
+    assert np.abs(np.array(per_step) - at_end).max() <= tol
+    if precision == "fp64":
+        t, n, rho_o = load_golden("spin_boson_structured_dk16_rho40.txt")
+        assert np.abs(at_end - rho_o[1:]).max() <= RHO_TOL
+
+
 def test_spin_boson_structured_dk16_full_length_properties():
     """All 2000 steps at full size: properties that hold at any size.  The
     trace is conserved by merging and propagation, so it changes only through
