@@ -379,6 +379,23 @@ def run_surrogate(T_train=100, T_long=1000, L=32, epochs=2000):
             "fallback_instances": int(fb.sum())}
 
 
+def aggregate_over_ranks(t_ms, units):
+    """Whole-job figures of independent replicas (one per rank, no data
+    exchange): the slowest rank's timed-region time (max over ranks) and the
+    units all ranks processed (sum).  Uses the default process group: NCCL
+    with CUDA tensors on GPUs, gloo with CPU tensors otherwise."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(t_ms), float(units)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(t_ms)], dtype=torch.float64, device=dev)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(u[0])
+
+
 def run_more_config(name, t0, steps, max_paths, warmup=3, engine="auto", fp64=True):
     """Another workload of the benchmark set, same measurement as the
     headline (c64, autotuned, L2 flushed between timed steps) with, if fp64,
@@ -502,14 +519,7 @@ def main():
     # path runs the same trajectory for the comparison at a stated rho error
     res = run_ours(args, rank, world, args.precision)
     ref = run_ours(args, rank, world, "fp64") if args.precision != "fp64" else res
-    t_ms, ext = res["t_ms"], res["ext"]
-    if world > 1:
-        import torch
-        tt = torch.tensor([t_ms, ext], dtype=torch.float64, device="cuda")
-        mx = tt.clone()
-        torch.distributed.all_reduce(mx[:1], op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(tt[1:], op=torch.distributed.ReduceOp.SUM)
-        t_ms, ext = float(mx[0]), float(tt[1])
+    t_ms, ext = aggregate_over_ranks(res["t_ms"], res["ext"])
     if rank != 0:
         return
     value = ext / (t_ms / 1e3)
