@@ -221,8 +221,11 @@ qp_status qp_export_paths(qp_ctx *ctx, uint64_t *keys, double *amps, int64_t cap
 
 /* Run nsteps propagation steps like qp_step, but launch the kernels one by
  * one with CUDA events between them, and add each kernel's elapsed time in
- * milliseconds to kernel_ms[k] (synchronises).  Kernel order: k = 0 merge
- * insert, 1 merge tie-break, 2 extension/filter/rho, 3 step finalisation.
+ * milliseconds to kernel_ms[k] (synchronises).  Kernel order, merge-table
+ * engine: k = 0 merge insert, 1 merge tie-break, 2 extension/filter/rho,
+ * 3 step finalisation; stream engine: k = 0 regular map (no time where it is
+ * not launched), 2 tile kernel.  Each step starts with a 50 us delay kernel,
+ * so that the intervals hold device time, not host enqueue time.
  * nk = length of kernel_ms (at most 4 entries are written).               */
 qp_status qp_profile_steps(qp_ctx *ctx, int nsteps, double *kernel_ms, int nk);
 

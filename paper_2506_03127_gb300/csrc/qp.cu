@@ -200,6 +200,22 @@ __device__ __forceinline__ float2 to_f2(float2 v) { return v; }
 // widening above, which runs once per stored path
 __device__ __forceinline__ float2 to_f2(double2 v) { return make_float2((float)v.x, (float)v.y); }
 
+// atomicAdd with acquire-release semantics at GPU scope (returns the old value).
+__device__ __forceinline__ unsigned atom_add_acq_rel_gpu(unsigned *p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+// Asynchronous 16-byte global -> shared copy (both addresses 16-byte
+// aligned); cp_async_wait_all waits for this thread's copies.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+
 __device__ __forceinline__ unsigned long long table_index(const Params &P, unsigned long long mk) {
     if (P.dense) {
         unsigned long long idx = 0;
@@ -1207,10 +1223,10 @@ __global__ void __launch_bounds__(kRegThreads, 3) k_stream_regular(Params P, int
     // sums once this kernel has ended
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
-        s_last = atomicAdd(P.fin_count, 1u) == gridDim.x - 1;
+        // one acquire-release add: releases this block's writes (ordered
+        // before it by the barrier), and the last block acquires the others'
+        s_last = atom_add_acq_rel_gpu(P.fin_count, 1u) == gridDim.x - 1;
         if (s_last) {
-            __threadfence();
             if (__ldcg(&st->err)) {   // a failed step is not published
                 *P.fin_count = 0;
             } else {
@@ -1233,17 +1249,54 @@ __global__ void __launch_bounds__(kRegThreads, 3) k_stream_regular(Params P, int
     }
 }
 
+// Runs of at most this many stored paths are summed by one thread (stream
+// engine); longer ones, which occur only while the window fills, by shared
+// FP64 atomics.
+constexpr int kOwnRun = 32;
+// A group sum formed in FP32 by its run's thread is stored as the float2 in
+// the low 8 bytes of its double2 slot and this signalling-NaN pattern in the
+// high 8 (arithmetic never yields a signalling NaN, so an FP64 atomic sum
+// cannot carry it).
+constexpr unsigned long long kOwnMark = 0x7FF00000514D0001ull;
+
+// s + e += b with the rounding error of the addition carried into e
+// (TwoSum, Knuth; six FP32 additions, exact for any FP32 operands).
+__device__ __forceinline__ void two_sum_acc(float &s, float &e, float b) {
+    const float t = s + b, v = t - s;
+    e += (s - (t - v)) + (b - v);
+    s = t;
+}
+
+__device__ __forceinline__ void store_own_sum(double2 *slot, float2 S) {
+    reinterpret_cast<float2 *>(slot)[0] = S;
+    reinterpret_cast<unsigned long long *>(slot)[1] = kOwnMark;
+}
+
+// The C64 group sum of a slot: the FP32 sum of its run's thread, else the
+// FP64 atomic sum rounded once.
+__device__ __forceinline__ float2 group_sum_f2(double2 d) {
+    if ((unsigned long long)__double_as_longlong(d.y) == kOwnMark) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(d.x);
+        return make_float2(__uint_as_float((unsigned)b), __uint_as_float((unsigned)(b >> 32)));
+    }
+    return to_f2(d);
+}
+
 // Dynamic shared memory of the stream kernel for a tile of S stored paths
 // (16-byte aligned arrays).  A tile holds at most NG = S + NX - 1 groups: every
 // group has a member in the tile, except sub-groups of the tile's last run
 // whose members all lie past the tile end (at most NX - 1 of them).
-//   gS    [NG] FP64 group sums          grep [NG] representative keys
+//   gS    [NG] group sums (16 B each)   grep [NG] representative keys
 //   wm    [NG] maximum weight (bits)    key/amp [S] the tile's stored paths
 //   stage [NSTG][M*M] children amplitudes of the first NSTG groups (S/2
 //         for M = 2, S/3 otherwise) between the two passes (tiles usually
 //         hold fewer groups; later ones are recomputed in pass B)
 //   seg   [S+1] run heads               xm/sb [S]/[S+1] sub-group bits and
 //   keep  [NG] survivor bits                 slot bases per run (NX > 1)
+//   slot  [NG] run << 4 | x of each sub-group slot (NX > 1)
+//   xmask [S][NX] members of each sub-group by offset in its run (offsets
+//         below 32; NX > 1), in the staging buffer, which is free until pass A
+// key/amp hold S + 32 entries: the 32 paths past the tile end follow the tile.
 // followed at run time by the history tables when they are staged.
 template <int M, bool C64, int NX, int S>
 struct StreamLayout {
@@ -1258,13 +1311,14 @@ struct StreamLayout {
     static constexpr size_t grep = gS + a16((size_t)NG * sizeof(double2));
     static constexpr size_t wm = grep + a16((size_t)NG * 8);
     static constexpr size_t key = wm + a16((size_t)NG * sizeof(WT));
-    static constexpr size_t amp = key + a16((size_t)S * 8);
-    static constexpr size_t stg = amp + a16((size_t)S * sizeof(AmpT));
+    static constexpr size_t amp = key + a16((size_t)(S + 32) * 8);
+    static constexpr size_t stg = amp + a16((size_t)(S + 32) * sizeof(AmpT));
     static constexpr size_t seg = stg + (stage ? a16((size_t)NSTG * MM * sizeof(AmpT)) : 0);
     static constexpr size_t xm = seg + a16((size_t)(S + 1) * 4);
     static constexpr size_t sb = xm + (NX > 1 ? a16((size_t)S * 4) : 0);
     static constexpr size_t keep = sb + (NX > 1 ? a16((size_t)(S + 1) * 4) : 0);
-    static constexpr size_t lut = keep + a16((size_t)NG * 2);
+    static constexpr size_t slot = keep + a16((size_t)NG * 2);
+    static constexpr size_t lut = slot + (NX > 1 ? a16((size_t)NG * 4) : 0);
     static constexpr size_t bytes = lut;   // + staged history tables (run time)
 };
 
@@ -1282,8 +1336,8 @@ __device__ __forceinline__ unsigned long long ld_relaxed_gpu(const unsigned long
 // (positions 0 .. k-1 of P'); at most one extra position of P' splits a run
 // into NX sub-groups.  Per tile (dynamic tickets): load (and prefetch the 32
 // paths past the tile end), find run heads; for NX > 1 give each sub-group
-// present a compact slot; sum each group in FP64 and elect its
-// representative (runs start in the tile and may extend past it); compute
+// present a compact slot; sum each group and elect its representative, one
+// thread per run (runs start in the tile and may extend past it); compute
 // the children of every group once, keep them in shared memory, count the
 // survivors per new point and accumulate rho(t+1); get the tile's output
 // offsets per region by a decoupled look-back (one warp, a window of
@@ -1304,6 +1358,7 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
     constexpr int NT = kStreamThreads, NW = NT / 32, EPT = S / NT;
     constexpr int NG = Lay::NG;
     static_assert(S % NT == 0 && EPT <= 32, "tile size");
+    static_assert(NX <= 16, "slot map: 4 bits of x");
     static_assert(NW == kStreamWarps, "warp partials");
     DevState *st = P.st;
     if (st->err) return;
@@ -1334,13 +1389,17 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
     unsigned *s_xm = reinterpret_cast<unsigned *>(s_dyn + Lay::xm);
     int *s_sb = reinterpret_cast<int *>(s_dyn + Lay::sb);
     unsigned short *s_keep = reinterpret_cast<unsigned short *>(s_dyn + Lay::keep);
+    int *s_slot = reinterpret_cast<int *>(s_dyn + Lay::slot);
+    unsigned *s_xmask = reinterpret_cast<unsigned *>(s_dyn + Lay::stg);
+    static_assert(NX == 1 || (Lay::stage && (size_t)Lay::NSTG * MM * sizeof(AmpT) >= (size_t)S * NX * 4),
+                  "sub-group member masks live in the staging buffer");
     __shared__ double2 s_w[C64 ? 1 : MM * MM];   // FP64 weights (FP64 path only)
     __shared__ float2 s_wf[MM * MM];
     __shared__ long long s_nr[MM], s_tile0[MM + 1];
     __shared__ unsigned s_wsum[NW][MM];
-    __shared__ unsigned long long s_base[MM], s_tot[MM], s_kprev, s_ra_key[32];
-    __shared__ AmpT s_ra_amp[32];
+    __shared__ unsigned long long s_base[MM], s_tot[MM], s_kprev;
     __shared__ unsigned s_ra_n;   // prefetched paths past the tile end
+    __shared__ long long s_ahead;   // tile-relative end of the tile's last run
     __shared__ unsigned s_ticket, s_nseg, s_ng, s_hw[NW];
     __shared__ int s_St;   // tile size of this step
     __shared__ float4 s_rt[NW][MM];
@@ -1355,19 +1414,22 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
         s_wf[i] = P.wtabf[i];
     }
     Tab tab = tab_global(P, n_act, 0);
+    // (asynchronous copies, waited for before the first pass A: the tables
+    // arrive while the first tile loads; rows are whole multiples of
+    // kLutEntries entries, so every copy is 16-byte aligned)
     if (lut_smem && P.ndelta) {
         const int n = P.nchunks * kLutEntries;
         if constexpr (C64) {
             float2 *hi = reinterpret_cast<float2 *>(s_dyn + Lay::lut), *lo = hi + n;
-            for (int i = threadIdx.x; i < n; i += NT) {
-                hi[i] = __ldg(tab.hi + i);
-                lo[i] = __ldg(tab.lo + i);
+            for (int i = threadIdx.x; i < n / 2; i += NT) {
+                cp_async16(hi + 2 * i, tab.hi + 2 * i);
+                cp_async16(lo + 2 * i, tab.lo + 2 * i);
             }
             tab.hi = hi;
             tab.lo = lo;
         } else {
             double2 *et = reinterpret_cast<double2 *>(s_dyn + Lay::lut);
-            for (int i = threadIdx.x; i < n * P.ndelta; i += NT) et[i] = __ldg(tab.et + i);
+            for (int i = threadIdx.x; i < n * P.ndelta; i += NT) cp_async16(et + i, tab.et + i);
             tab.et = et;
         }
     }
@@ -1377,20 +1439,24 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
         // tile size of this step: the smallest multiple of NT (up to S) whose
         // tiles do not outnumber the blocks, so that a small step runs in one
         // wave of short tiles (a large one uses S)
+        // (ceil(n / (k NT)) = ceil(ceil(n / NT) / k): 32-bit divisions by k)
+        unsigned q[MM];
+        for (int r = 0; r < MM; ++r) q[r] = (unsigned)((s_nr[r] + NT - 1) / NT);
         int St = S;
-        for (int cand = NT; cand < S; cand += NT) {
+        for (unsigned k = 1; k < (unsigned)EPT; ++k) {
             long long tiles = 0;
-            for (int r = 0; r < MM; ++r) tiles += (s_nr[r] + cand - 1) / cand;
+            for (int r = 0; r < MM; ++r) tiles += (q[r] + k - 1) / k;
             if (tiles <= (long long)gridDim.x) {
-                St = cand;
+                St = (int)k * NT;
                 break;
             }
         }
         s_St = St;
+        const unsigned kst = (unsigned)(St / NT);
         long long acc = 0;
         for (int r = 0; r < MM; ++r) {
             s_tile0[r] = acc;
-            acc += (s_nr[r] + St - 1) / St;
+            acc += (q[r] + kst - 1) / kst;
         }
         s_tile0[MM] = acc;
         if (acc == 0 && blockIdx.x == 0) {   // empty input: the output is empty
@@ -1449,8 +1515,8 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
         if (warp == 0) {
             const bool ok = cnt == St && e0 + St + lane < nr;
             if (ok) {
-                s_ra_key[lane] = __ldcg(kin + e0 + St + lane);
-                s_ra_amp[lane] = __ldcg(ain + e0 + St + lane);
+                s_key[St + lane] = __ldcg(kin + e0 + St + lane);
+                s_amp[St + lane] = __ldcg(ain + e0 + St + lane);
             }
             const unsigned okm = __ballot_sync(0xffffffffu, ok);
             if (lane == 0) s_ra_n = __popc(okm);   // a prefix of the 32 lanes
@@ -1461,8 +1527,10 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
             s_grep[i] = kEmpty;
             s_wm[i] = 0;
         }
-        if constexpr (NX > 1)
+        if constexpr (NX > 1) {
             for (int i = threadIdx.x; i < S; i += NT) s_xm[i] = 0u;
+            for (int i = threadIdx.x; i < St * NX / 4; i += NT) reinterpret_cast<uint4 *>(s_xmask)[i] = make_uint4(0u, 0u, 0u, 0u);
+        }
         __syncthreads();
         // run heads (ept consecutive entries per thread), block scan of their count
         unsigned hmask = 0;
@@ -1508,16 +1576,23 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
         const unsigned long long plast = nseg ? (s_key[s_seg[nseg - 1]] & pref) : 0ull;
         long long ahead = cnt;   // tile-relative end of the last run
         if constexpr (NX > 1) {
-            int sg = segbase;
+            int sg = segbase, rs = segbase >= 0 ? s_seg[segbase] : 0;   // run and its start
 #pragma unroll
             for (int u = 0; u < EPT; ++u) {
                 const int i = threadIdx.x * ept + u;
-                if (hmask & (1u << u)) ++sg;
-                if (u < ept && i < cnt && sg >= 0) atomicOr(&s_xm[sg], 1u << xval(s_key[i]));
+                if (hmask & (1u << u)) {
+                    ++sg;
+                    rs = i;
+                }
+                if (u < ept && i < cnt && sg >= 0) {
+                    const unsigned x = xval(s_key[i]);
+                    if (i - rs < 32) atomicOr(&s_xmask[sg * NX + x], 1u << (i - rs));
+                    else atomicOr(&s_xm[sg], 1u << x);
+                }
             }
         }
         if (warp == 0 && nseg > 0 && cnt == St) {
-            unsigned long long key = s_ra_key[lane];
+            unsigned long long key = s_key[cnt + lane];
             bool inrun = lane < s_ra_n && (key & pref) == plast;
             for (int round = 0;; ++round) {
                 if (round > 0) {
@@ -1530,24 +1605,39 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
                 }
                 const unsigned inm = __ballot_sync(0xffffffffu, inrun);
                 const int nin = inm == 0xffffffffu ? 32 : __ffs(~inm) - 1;   // leading members of the run
-                if constexpr (NX > 1)
-                    if ((int)lane < nin) atomicOr(&s_xm[nseg - 1], 1u << xval(key));
+                if constexpr (NX > 1) {
+                    if ((int)lane < nin) {
+                        const long long off = ahead + lane - s_seg[nseg - 1];
+                        if (off < 32) atomicOr(&s_xmask[(nseg - 1) * NX + xval(key)], 1u << off);
+                        else atomicOr(&s_xm[nseg - 1], 1u << xval(key));
+                    }
+                }
                 ahead += nin;
                 if (nin < 32) break;
             }
         }
+        if (threadIdx.x == 0) s_ahead = ahead;
         __syncthreads();
+        ahead = s_ahead;
         // compact slots: sub-groups of run sg are slots sb[sg] + rank of x
         int ngroups = nseg;
         if constexpr (NX > 1) {
-            // EPT runs per thread: thread-local sum, warp scan, across warps
-            unsigned loc[EPT];
+            // rpt consecutive runs per thread: thread-local sum, warp scan,
+            // across warps.  A run's sub-groups: its members at offsets
+            // below 32 (masks) and beyond (xm bits); the union goes back to xm.
+            const int rpt = (nseg + NT - 1) / NT;
+            unsigned xmv[EPT];
             unsigned lsum = 0;
 #pragma unroll
             for (int u = 0; u < EPT; ++u) {
-                const int g = threadIdx.x * EPT + u;
-                loc[u] = g < nseg ? (unsigned)__popc(s_xm[g]) : 0u;
-                lsum += loc[u];
+                const int g = threadIdx.x * rpt + u;
+                xmv[u] = 0u;
+                if (u < rpt && g < nseg) {
+                    xmv[u] = s_xm[g];
+#pragma unroll
+                    for (int x = 0; x < NX; ++x) xmv[u] |= (s_xmask[g * NX + x] != 0u ? 1u : 0u) << x;
+                }
+                lsum += (unsigned)__popc(xmv[u]);
             }
             unsigned inc = lsum;
 #pragma unroll
@@ -1570,9 +1660,12 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
             unsigned pos = s_wsum[warp][0] + inc - lsum;
 #pragma unroll
             for (int u = 0; u < EPT; ++u) {
-                const int g = threadIdx.x * EPT + u;
-                if (g < nseg) s_sb[g] = (int)pos;
-                pos += loc[u];
+                const int g = threadIdx.x * rpt + u;
+                if (u < rpt && g < nseg) {
+                    s_sb[g] = (int)pos;
+                    s_xm[g] = xmv[u];
+                }
+                for (unsigned m = xmv[u]; m; m &= m - 1u) s_slot[pos++] = (g << 4) | (__ffs(m) - 1);
             }
             ngroups = (int)s_ng;
             __syncthreads();
@@ -1585,105 +1678,181 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
                 return sg;
             }
         };
-        // pass 1: group sums (FP64) and maximum weights; consecutive entries
-        // of a thread in the same slot are combined before the atomics
-        {
-            int sg = segbase, cur = -1;
-            double ax = 0.0, ay = 0.0;
-            WT wmx = 0;
-#pragma unroll
-            for (int u = 0; u < EPT; ++u) {
-                const int i = threadIdx.x * ept + u;
-                if (hmask & (1u << u)) ++sg;
-                if (u < ept && i < cnt && sg >= 0) {
-                    const AmpT a = s_amp[i];
-                    const int sl = slot_of(sg, s_key[i]);
+        // groups of runs of at most kOwnRun members (all runs once the window
+        // is full) have one owner thread each, which visits the group's
+        // members (the whole run, or for NX > 1 the sub-group's mask) twice
+        // in order: walk 1 adds them (C64: FP32 with the rounding error of
+        // every addition kept, TwoSum, rounded once; FP64: FP64) and takes
+        // their maximum weight, walk 2 elects the representative.  No atomics
+        // and no stores in the loops; the result does not depend on the
+        // tiling.  FP64 sub-groups (NX > 1) stay with the shared atomics
+        // below, one entry per thread, which keeps the FP64 pipe (1/64 of the
+        // FP32 rate) to one addition per member.
+        constexpr bool kOwners = NX == 1 || C64;
+        bool any_long = !kOwners && nseg > 0;
+        cp_async_wait_all();   // staged history tables (first tile), published by the barrier below
+        if constexpr (kOwners) {
+            const int nown = NX > 1 ? ngroups : nseg;
+            for (int sl = threadIdx.x; sl < nown; sl += NT) {
+                int g = sl;
+                unsigned x = 0;
+                if constexpr (NX > 1) {
+                    const int gx = s_slot[sl];
+                    g = gx >> 4;
+                    x = (unsigned)gx & 15u;
+                }
+                const int b0 = s_seg[g];
+                const long long b1 = g + 1 < nseg ? (long long)s_seg[g + 1] : ahead;
+                if (b1 - b0 > kOwnRun) {
+                    any_long = true;
+                    continue;
+                }
+                const int n = (int)b1 - b0;   // members past the tile end are in the prefetch
+                typename X::AccT sh, se;
+                sh.x = sh.y = 0;
+                se.x = se.y = 0;
+                WT wmx = 0;
+                auto add = [&](const AmpT &a) {
+                    if constexpr (C64) {
+                        two_sum_acc(sh.x, se.x, a.x);
+                        two_sum_acc(sh.y, se.y, a.y);
+                    } else {
+                        sh.x += a.x;
+                        sh.y += a.y;
+                    }
                     const WT wb = weight_bits(a);
-                    if (sl != cur) {
-                        if (cur >= 0) {
-                            atomicAdd(&s_gS[cur].x, ax);
-                            atomicAdd(&s_gS[cur].y, ay);
-                            atomicMax(&s_wm[cur], wmx);
-                        }
-                        cur = sl;   // the slot's local sum starts at its first member
-                        ax = to_d(a.x);
-                        ay = to_d(a.y);
-                        wmx = wb;
-                    } else {
-                        ax += to_d(a.x);
-                        ay += to_d(a.y);
-                        wmx = wb > wmx ? wb : wmx;
-                    }
+                    wmx = wb > wmx ? wb : wmx;
+                };
+                unsigned mm;   // the group's members by offset in the run
+                if constexpr (NX > 1) {
+                    mm = s_xmask[g * NX + x];
+#pragma unroll 4
+                    for (unsigned m = mm; m; m &= m - 1u) add(s_amp[b0 + __ffs(m) - 1]);
+                } else {
+                    mm = n == 32 ? 0xffffffffu : (1u << n) - 1u;
+#pragma unroll 4
+                    for (int j = 0; j < n; ++j) add(s_amp[b0 + j]);
                 }
-            }
-            if (cur >= 0) {
-                atomicAdd(&s_gS[cur].x, ax);
-                atomicAdd(&s_gS[cur].y, ay);
-                atomicMax(&s_wm[cur], wmx);
-            }
-        }
-        if (warp == 0 && ahead > cnt) {   // members of the last run past the tile end
-            for (long long base = cnt; base < ahead; base += 32) {
-                const long long i = base + lane;
-                if (i < ahead) {
-                    unsigned long long key;
-                    AmpT a;
-                    if (base == cnt) {
-                        key = s_ra_key[lane];
-                        a = s_ra_amp[lane];
-                    } else {
-                        key = __ldcg(kin + e0 + i);
-                        a = __ldcg(ain + e0 + i);
-                    }
-                    const int sl = slot_of(nseg - 1, key);
-                    atomicAdd(&s_gS[sl].x, to_d(a.x));
-                    atomicAdd(&s_gS[sl].y, to_d(a.y));
-                    atomicMax(&s_wm[sl], weight_bits(a));
-                }
-            }
-        }
-        __syncthreads();
-        // pass 2: paths within the tie window of their group's maximum compete
-        // for the representative (smallest key)
-        {
-            int sg = segbase, cur = -1;
-            unsigned long long kmin = kEmpty;
-#pragma unroll
-            for (int u = 0; u < EPT; ++u) {
-                const int i = threadIdx.x * ept + u;
-                if (hmask & (1u << u)) ++sg;
-                if (u < ept && i < cnt && sg >= 0) {
+                unsigned long long kmin = kEmpty;
+                for (unsigned m = mm; m; m &= m - 1u) {
+                    const int i = b0 + __ffs(m) - 1;
                     const unsigned long long key = s_key[i];
-                    const int sl = slot_of(sg, key);
-                    if (sl != cur) {
-                        if (cur >= 0 && kmin != kEmpty) atomicMin(&s_grep[cur], kmin);
-                        cur = sl;
-                        kmin = kEmpty;
-                    }
-                    if (within_tie(weight_bits(s_amp[i]), s_wm[sl]) && key < kmin) kmin = key;
+                    if (within_tie(weight_bits(s_amp[i]), wmx) && key < kmin) kmin = key;
                 }
-            }
-            if (cur >= 0 && kmin != kEmpty) atomicMin(&s_grep[cur], kmin);
-        }
-        if (warp == 0 && ahead > cnt) {
-            for (long long base = cnt; base < ahead; base += 32) {
-                const long long i = base + lane;
-                if (i < ahead) {
-                    unsigned long long key;
-                    AmpT a;
-                    if (base == cnt) {
-                        key = s_ra_key[lane];
-                        a = s_ra_amp[lane];
-                    } else {
-                        key = __ldcg(kin + e0 + i);
-                        a = __ldcg(ain + e0 + i);
-                    }
-                    const int sl = slot_of(nseg - 1, key);
-                    if (within_tie(weight_bits(a), s_wm[sl])) atomicMin(&s_grep[sl], key);
-                }
+                if constexpr (C64) store_own_sum(s_gS + sl, make_float2(sh.x + se.x, sh.y + se.y));
+                else s_gS[sl] = make_double2(sh.x, sh.y);
+                s_grep[sl] = kmin;
             }
         }
-        __syncthreads();
+        // longer runs (only while the window fills): every member adds to its
+        // group in FP64 with shared atomics (consecutive members of a thread
+        // in the same slot combined first), then, after a barrier, the members
+        // within the tie window compete for the representative
+        if (__syncthreads_or(any_long)) {
+            auto run_long = [&](int g) -> bool {
+                if constexpr (!kOwners) return true;
+                const long long b1 = g + 1 < nseg ? (long long)s_seg[g + 1] : ahead;
+                return b1 - s_seg[g] > kOwnRun;
+            };
+            const bool last_long = nseg > 0 && run_long(nseg - 1);
+            {
+                int sg = segbase, cur = -1;
+                bool lng = sg >= 0 && run_long(sg);
+                double ax = 0.0, ay = 0.0;
+                WT wmx = 0;
+#pragma unroll
+                for (int u = 0; u < EPT; ++u) {
+                    const int i = threadIdx.x * ept + u;
+                    if (hmask & (1u << u)) lng = run_long(++sg);
+                    if (u < ept && i < cnt && lng) {
+                        const AmpT a = s_amp[i];
+                        const int sl = slot_of(sg, s_key[i]);
+                        const WT wb = weight_bits(a);
+                        if (sl != cur) {
+                            if (cur >= 0) {
+                                atomicAdd(&s_gS[cur].x, ax);
+                                atomicAdd(&s_gS[cur].y, ay);
+                                atomicMax(&s_wm[cur], wmx);
+                            }
+                            cur = sl;   // the slot's local sum starts at its first member
+                            ax = to_d(a.x);
+                            ay = to_d(a.y);
+                            wmx = wb;
+                        } else {
+                            ax += to_d(a.x);
+                            ay += to_d(a.y);
+                            wmx = wb > wmx ? wb : wmx;
+                        }
+                    }
+                }
+                if (cur >= 0) {
+                    atomicAdd(&s_gS[cur].x, ax);
+                    atomicAdd(&s_gS[cur].y, ay);
+                    atomicMax(&s_wm[cur], wmx);
+                }
+            }
+            if (warp == 0 && last_long && ahead > cnt) {   // members of the last run past the tile end
+                for (long long base = cnt; base < ahead; base += 32) {
+                    const long long i = base + lane;
+                    if (i < ahead) {
+                        unsigned long long key;
+                        AmpT a;
+                        if (base == cnt) {
+                            key = s_key[cnt + lane];
+                            a = s_amp[cnt + lane];
+                        } else {
+                            key = __ldcg(kin + e0 + i);
+                            a = __ldcg(ain + e0 + i);
+                        }
+                        const int sl = slot_of(nseg - 1, key);
+                        atomicAdd(&s_gS[sl].x, to_d(a.x));
+                        atomicAdd(&s_gS[sl].y, to_d(a.y));
+                        atomicMax(&s_wm[sl], weight_bits(a));
+                    }
+                }
+            }
+            __syncthreads();
+            {
+                int sg = segbase, cur = -1;
+                bool lng = sg >= 0 && run_long(sg);
+                unsigned long long kmin = kEmpty;
+#pragma unroll
+                for (int u = 0; u < EPT; ++u) {
+                    const int i = threadIdx.x * ept + u;
+                    if (hmask & (1u << u)) lng = run_long(++sg);
+                    if (u < ept && i < cnt && lng) {
+                        const unsigned long long key = s_key[i];
+                        const int sl = slot_of(sg, key);
+                        if (sl != cur) {
+                            if (cur >= 0 && kmin != kEmpty) atomicMin(&s_grep[cur], kmin);
+                            cur = sl;
+                            kmin = kEmpty;
+                        }
+                        if (within_tie(weight_bits(s_amp[i]), s_wm[sl]) && key < kmin) kmin = key;
+                    }
+                }
+                if (cur >= 0 && kmin != kEmpty) atomicMin(&s_grep[cur], kmin);
+            }
+            if (warp == 0 && last_long && ahead > cnt) {
+                for (long long base = cnt; base < ahead; base += 32) {
+                    const long long i = base + lane;
+                    if (i < ahead) {
+                        unsigned long long key;
+                        AmpT a;
+                        if (base == cnt) {
+                            key = s_key[cnt + lane];
+                            a = s_amp[cnt + lane];
+                        } else {
+                            key = __ldcg(kin + e0 + i);
+                            a = __ldcg(ain + e0 + i);
+                        }
+                        const int sl = slot_of(nseg - 1, key);
+                        if (within_tie(weight_bits(a), s_wm[sl])) atomicMin(&s_grep[sl], key);
+                    }
+                }
+            }
+            __syncthreads();
+        }
         // pass A: children of a contiguous range of groups per thread, once;
         // survivors counted per new point, amplitudes kept in shared memory
         // for pass B (the first NSTG groups)
@@ -1698,7 +1867,7 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
             AmpT v[MM];
             if (rk != kEmpty) {
                 if constexpr (C64) {
-                    const float2 Sf = to_f2(s_gS[g]);
+                    const float2 Sf = group_sum_f2(s_gS[g]);
                     reinterpret_cast<float2 *>(s_gS)[2 * g] = Sf;   // for pass B, if not staged
                     keep = X::children_tab(P, tab, rk, Sf, s_w, s_wf, v);
                 } else {
@@ -1858,16 +2027,17 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
         }
         __syncthreads();
     }
+    cp_async_wait_all();   // a block without a tile: its table copies
     // arrive first: the last block to arrive publishes the step, for which
     // it needs the step's counters only; every block then writes its partial
     // of rho, which the next step's block 0 (or a read-time finalisation)
     // sums once this kernel has ended
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
-        s_last = atomicAdd(P.fin_count, 1u) == gridDim.x - 1;
+        // one acquire-release add: releases this block's writes (ordered
+        // before it by the barrier), and the last block acquires the others'
+        s_last = atom_add_acq_rel_gpu(P.fin_count, 1u) == gridDim.x - 1;
         if (s_last) {
-            __threadfence();
             if (__ldcg(&st->err)) {   // a failed step is not published
                 *P.fin_count = 0;
             } else {
@@ -2970,6 +3140,20 @@ qp_status qp_export_paths(qp_ctx *c, uint64_t *keys, double *amps, int64_t cap, 
     return QP_OK;
 }
 
+// Holds the stream for about ns nanoseconds (one thread; at most 2^20
+// sleeps of 64 ns), so that the host has enqueued a profiled step's events
+// and kernels before the GPU reaches them and event intervals hold device
+// time only.
+__global__ void k_delay(unsigned long long ns) {
+    unsigned long long t0, t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    for (int i = 0; i < (1 << 20); ++i) {
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (t - t0 >= ns) break;
+        __nanosleep(64);
+    }
+}
+
 qp_status qp_profile_steps(qp_ctx *c, int nsteps, double *kernel_ms, int nk) {
     if (!c) return QP_ERR_ARG;
     if (nsteps < 0 || !kernel_ms || nk < 0) return fail(c, QP_ERR_ARG, "bad arguments");
@@ -2979,6 +3163,7 @@ qp_status qp_profile_steps(qp_ctx *c, int nsteps, double *kernel_ms, int nk) {
     for (int k = 0; k <= kStepKernels; ++k) QP_CUDA(c, cudaEventCreate(&ev[k]));
     qp_status st = QP_OK;
     for (int s = 0; s < nsteps && st == QP_OK; ++s) {
+        k_delay<<<1, 1, 0, c->stream>>>(50000ull);
         cudaError_t e = launch_step(c, ev);
         if (e == cudaSuccess) e = cudaEventSynchronize(ev[kStepKernels]);
         if (e != cudaSuccess) {
@@ -2986,6 +3171,9 @@ qp_status qp_profile_steps(qp_ctx *c, int nsteps, double *kernel_ms, int nk) {
             break;
         }
         for (int k = 0; k < kStepKernels && k < nk; ++k) {
+            // stream engine: intervals without a kernel (1, 3, and 0 where
+            // no regular map is launched) hold only event overhead
+            if (c->use_stream && (k == 1 || k == 3 || (k == 0 && !(c->cfg.M == 2 && c->P.reg_fill)))) continue;
             float ms = 0.f;
             cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
             kernel_ms[k] += ms;
