@@ -470,7 +470,7 @@ def main():
     w = WORKLOADS[args.workload]
     cfg = {"workload": w.name, "M": w.M, "dkmax": w.dkmax, "mask": w.mask_list(), "theta": w.theta,
            "dt": w.dt, "t0": args.t0, "precision": args.precision, "engine": f"{args.engine} (used: in roofline)",
-           "amplitudes": "complex64, FP32 influence exponent (Kahan), FP64 eta/merge sums/rho"
+           "amplitudes": "complex64, FP32 influence exponent (Kahan), FP32 error-free (TwoSum) group sums, FP64 eta/rho"
            if args.precision == "c64" else "complex128, FP64 throughout",
            "l2": "flushed between timed steps (512 MB write)", "parallelism": f"replicas{args.gpus}"}
 
