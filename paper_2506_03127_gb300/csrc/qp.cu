@@ -200,6 +200,14 @@ __device__ __forceinline__ float2 to_f2(float2 v) { return v; }
 // widening above, which runs once per stored path
 __device__ __forceinline__ float2 to_f2(double2 v) { return make_float2((float)v.x, (float)v.y); }
 
+// s + e += b with the rounding error of the addition carried into e
+// (TwoSum, Knuth; six FP32 additions, exact for any FP32 operands).
+__device__ __forceinline__ void two_sum_acc(float &s, float &e, float b) {
+    const float t = s + b, v = t - s;
+    e += (s - (t - v)) + (b - v);
+    s = t;
+}
+
 // atomicAdd with acquire-release semantics at GPU scope (returns the old value).
 __device__ __forceinline__ unsigned atom_add_acq_rel_gpu(unsigned *p, unsigned v) {
     unsigned old;
@@ -859,52 +867,66 @@ __device__ __forceinline__ long long *scount_of(const Params &P, unsigned long l
 }
 
 // rho(tn) of the stream engine from the per-block partials of nblk blocks,
-// summed in FP64 in a fixed order (T threads per component, a pairwise tree
-// over them), and the survivor count.  Block-uniform, 256 threads.
+// summed in a fixed order, and the survivor count.  Block-uniform (a
+// multiple of 32 threads, at most 1024).
 template <bool C64>
 __device__ __forceinline__ void phase_finalize_stream(const Params &P, unsigned long long tn, int nblk, int MM) {
-    __shared__ double s_p[256];
-    __shared__ long long s_c[256];
+    // one warp per component (re, im of each end point): lane l adds the
+    // partials of blocks l, l + 32, ... in order, then a shuffle tree.  C64
+    // partials are FP32 pairs: lanes add them with TwoSum and the warp merges
+    // the pairs error-free, so FP64 is used once per component; FP64 pairs
+    // are added in FP64.  Counts: per-thread sums, then a shuffle tree and the
+    // warps in order.
+    __shared__ double s_p[64];
+    __shared__ long long s_c[32];
     const float4 *src = spart_of(P, tn, MM);
     const long long *cnt = scount_of(P, tn);
-    const int ncomp = 2 * MM, n = nblk;   // components (re, im per end point), block partials
-    const int T = 256 / ncomp;
-    const int comp = (int)threadIdx.x / T, sidx = (int)threadIdx.x % T;
-    double a = 0.0;
-    if (comp < ncomp) {
+    const unsigned lane = lane_id(), warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int comp = (int)warp; comp < 2 * MM; comp += (int)nw) {
         const int k = comp >> 1, im = comp & 1;
-        for (int w0 = sidx; w0 < n; w0 += 8 * T) {
-            double v[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int w = w0 + u * T;
-                v[u] = 0.0;
-                if (w < n) {
-                    const float4 q = __ldcg(src + (size_t)w * MM + k);
-                    if constexpr (C64) v[u] = im ? f2d_exact(q.z) + f2d_exact(q.w) : f2d_exact(q.x) + f2d_exact(q.y);
-                    else {
-                        const double2 d = *reinterpret_cast<const double2 *>(&q);
-                        v[u] = im ? d.y : d.x;
-                    }
-                }
+        if constexpr (C64) {
+            float sh = 0.f, se = 0.f;
+#pragma unroll 4
+            for (int w = (int)lane; w < nblk; w += 32) {
+                const float4 q = __ldcg(src + (size_t)w * MM + k);
+                two_sum_acc(sh, se, im ? q.z : q.x);
+                se += im ? q.w : q.y;
             }
-            a += ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float b = __shfl_down_sync(0xffffffffu, sh, o), f = __shfl_down_sync(0xffffffffu, se, o);
+                const float t = sh + b, v = t - sh;
+                se += f + ((sh - (t - v)) + (b - v));
+                sh = t;
+            }
+            if (lane == 0) s_p[comp] = f2d_exact(sh) + f2d_exact(se);
+        } else {
+            double a = 0.0;
+#pragma unroll 4
+            for (int w = (int)lane; w < nblk; w += 32) {
+                const float4 q = __ldcg(src + (size_t)w * MM + k);
+                const double2 d = *reinterpret_cast<const double2 *>(&q);
+                a += im ? d.y : d.x;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+            if (lane == 0) s_p[comp] = a;
         }
     }
     long long c = 0;
-    for (int b = threadIdx.x; b < nblk; b += 256) c += __ldcg(cnt + b);
-    s_p[threadIdx.x] = a;
-    s_c[threadIdx.x] = c;
+    for (int b = (int)threadIdx.x; b < nblk; b += (int)blockDim.x) c += __ldcg(cnt + b);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+    if (lane == 0) s_c[warp] = c;
     __syncthreads();
-    for (int w = 1; w < 256; w <<= 1) {   // two pairwise trees: T values per component, 256 counts
-        if (comp < ncomp && sidx % (2 * w) == 0 && sidx + w < T) s_p[threadIdx.x] += s_p[threadIdx.x + w];
-        if ((threadIdx.x % (2 * w)) == 0 && threadIdx.x + w < 256) s_c[threadIdx.x] += s_c[threadIdx.x + w];
-        __syncthreads();
-    }
     const size_t slot = (size_t)(tn % (unsigned long long)P.rho_hist);
     if ((int)threadIdx.x < MM)
-        P.rho_ring[slot * MM + threadIdx.x] = make_double2(s_p[2 * threadIdx.x * T], s_p[(2 * threadIdx.x + 1) * T]);
-    if (threadIdx.x == 0) P.inst_kept[slot] = s_c[0];
+        P.rho_ring[slot * MM + threadIdx.x] = make_double2(s_p[2 * threadIdx.x], s_p[2 * threadIdx.x + 1]);
+    if (threadIdx.x == 0) {
+        long long tot = 0;
+        for (unsigned w = 0; w < nw; ++w) tot += s_c[w];
+        P.inst_kept[slot] = tot;
+    }
     __syncthreads();
 }
 
@@ -1259,14 +1281,6 @@ constexpr int kOwnRun = 32;
 // cannot carry it).
 constexpr unsigned long long kOwnMark = 0x7FF00000514D0001ull;
 
-// s + e += b with the rounding error of the addition carried into e
-// (TwoSum, Knuth; six FP32 additions, exact for any FP32 operands).
-__device__ __forceinline__ void two_sum_acc(float &s, float &e, float b) {
-    const float t = s + b, v = t - s;
-    e += (s - (t - v)) + (b - v);
-    s = t;
-}
-
 __device__ __forceinline__ void store_own_sum(double2 *slot, float2 S) {
     reinterpret_cast<float2 *>(slot)[0] = S;
     reinterpret_cast<unsigned long long *>(slot)[1] = kOwnMark;
@@ -1366,6 +1380,11 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
     if (blockIdx.x == 0) finish_pending_rho<C64>(P, st, M * M);   // rho of the previous step
     const unsigned long long t = st->t, tn = t + 1;
     const int in = (int)(t & 1), outp = (int)(tn & 1), cs = (int)(tn % 3);
+    // the block's first ticket is taken now (block 0: after the sum above,
+    // so that no tile waits for it): its round trip overlaps the set-up
+    // below; tickets beyond the last tile end the loop as before
+    unsigned first_ticket = ~0u;
+    if (threadIdx.x == 0) first_ticket = atomicAdd(&st->ticket[cs], 1u);
     const bool merge = tn >= (unsigned long long)P.dkmax;
     const unsigned long long pref = merge ? P.prefmask : ~0ull;   // filling: every path is its own group
     const int n_act = (int)min(tn, (unsigned long long)P.dkmax);
@@ -1400,7 +1419,7 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
     __shared__ unsigned long long s_base[MM], s_tot[MM], s_kprev;
     __shared__ unsigned s_ra_n;   // prefetched paths past the tile end
     __shared__ long long s_ahead;   // tile-relative end of the tile's last run
-    __shared__ unsigned s_ticket, s_nseg, s_ng, s_hw[NW];
+    __shared__ unsigned s_ticket, s_first, s_nseg, s_ng, s_hw[NW];
     __shared__ int s_St;   // tile size of this step
     __shared__ float4 s_rt[NW][MM];
     __shared__ bool s_last;
@@ -1459,6 +1478,7 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
             acc += (q[r] + kst - 1) / kst;
         }
         s_tile0[MM] = acc;
+        s_first = first_ticket;
         if (acc == 0 && blockIdx.x == 0) {   // empty input: the output is empty
             for (int r = 0; r < MM; ++r) st->reg_n[outp][r] = 0;
             st->cnt_out[cs] = 0;
@@ -1493,7 +1513,10 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
     };
 
     for (;;) {
-        if (threadIdx.x == 0) s_ticket = atomicAdd(&st->ticket[cs], 1u);
+        if (threadIdx.x == 0) {
+            s_ticket = s_first != ~0u ? s_first : atomicAdd(&st->ticket[cs], 1u);
+            s_first = ~0u;
+        }
         __syncthreads();
         const long long ticket = s_ticket;
         if (ticket >= ntiles) break;
@@ -2331,6 +2354,8 @@ struct qp_ctx {
     cudaGraphExec_t graph = nullptr;
     bool graph_dirty = true;
     bool use_graph = true;
+    void *hpin = nullptr;              // pinned host staging for rho reads (state + rows)
+    size_t hpin_bytes = 0;
     std::string err;
 };
 
@@ -2768,6 +2793,7 @@ void qp_destroy(qp_ctx *ctx) {
     if (!ctx) return;
     if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
     if (ctx->graph1) cudaGraphExecDestroy(ctx->graph1);
+    if (ctx->hpin) cudaFreeHost(ctx->hpin);
     delete ctx;
 }
 
@@ -2992,9 +3018,7 @@ qp_status qp_step(qp_ctx *c, int nsteps) {
     return QP_OK;
 }
 
-static qp_status read_state(qp_ctx *c, DevState *s) {
-    QP_CUDA(c, cudaMemcpyAsync(s, c->P.st, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream));
-    QP_CUDA(c, cudaStreamSynchronize(c->stream));
+static qp_status check_state(qp_ctx *c, const DevState *s) {
     if (s->err) {
         c->failed = true;
         std::string what;
@@ -3007,6 +3031,12 @@ static qp_status read_state(qp_ctx *c, DevState *s) {
         return fail(c, QP_ERR_CAPACITY, "capacity exceeded at step " + std::to_string(s->t + 1) + ":" + what);
     }
     return QP_OK;
+}
+
+static qp_status read_state(qp_ctx *c, DevState *s) {
+    QP_CUDA(c, cudaMemcpyAsync(s, c->P.st, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream));
+    QP_CUDA(c, cudaStreamSynchronize(c->stream));
+    return check_state(c, s);
 }
 
 qp_status qp_sync(qp_ctx *c) {
@@ -3034,22 +3064,39 @@ qp_status qp_read_rho(qp_ctx *c, int64_t t0, int count, double *re, double *im) 
         else k_rho_finalize<false><<<1, 256, 0, c->stream>>>(c->P, c->cfg.M * c->cfg.M);
         QP_CUDA(c, cudaGetLastError());
     }
-    DevState s;
-    qp_status r = read_state(c, &s);
-    if (r != QP_OK) return r;
-    const int64_t R = c->cfg.rho_history, tc = (int64_t)s.t;
-    if (t0 < 0 || t0 + count - 1 > tc || t0 <= tc - R) return fail(c, QP_ERR_ARG, "step outside the kept rho history");
+    // one round trip: the state and the rows of steps t0 .. t0 + count - 1
+    // (ring slots t mod R, at most two contiguous pieces, always inside the
+    // ring) are copied to pinned memory together; the range and the error
+    // flags are then checked on the copied state
+    const int64_t R = c->cfg.rho_history;
+    if (t0 < 0 || count > R) return fail(c, QP_ERR_ARG, "step outside the kept rho history");
     const size_t per = (size_t)c->P.n_inst * c->cfg.M * c->cfg.M;
-    std::vector<double2> buf(per);
-    for (int k = 0; k < count; ++k) {
-        const int64_t t = t0 + k;
-        QP_CUDA(c, cudaMemcpyAsync(buf.data(), c->P.rho_ring + (size_t)(t % R) * per, per * sizeof(double2),
+    const size_t soff = (sizeof(DevState) + 15) & ~(size_t)15;
+    const size_t need = soff + (size_t)count * per * sizeof(double2);
+    if (need > c->hpin_bytes) {
+        if (c->hpin) cudaFreeHost(c->hpin);
+        c->hpin = nullptr;
+        c->hpin_bytes = 0;
+        QP_CUDA(c, cudaMallocHost(&c->hpin, need));
+        c->hpin_bytes = need;
+    }
+    DevState *hs = static_cast<DevState *>(c->hpin);
+    double2 *rows = reinterpret_cast<double2 *>(static_cast<char *>(c->hpin) + soff);
+    QP_CUDA(c, cudaMemcpyAsync(hs, c->P.st, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream));
+    for (int64_t done = 0; done < count;) {
+        const int64_t slot = (t0 + done) % R, n = std::min<int64_t>(count - done, R - slot);
+        QP_CUDA(c, cudaMemcpyAsync(rows + (size_t)done * per, c->P.rho_ring + (size_t)slot * per, (size_t)n * per * sizeof(double2),
                                    cudaMemcpyDeviceToHost, c->stream));
-        QP_CUDA(c, cudaStreamSynchronize(c->stream));
-        for (size_t i = 0; i < per; ++i) {
-            re[(size_t)k * per + i] = buf[i].x;
-            im[(size_t)k * per + i] = buf[i].y;
-        }
+        done += n;
+    }
+    QP_CUDA(c, cudaStreamSynchronize(c->stream));
+    qp_status r = check_state(c, hs);
+    if (r != QP_OK) return r;
+    const int64_t tc = (int64_t)hs->t;
+    if (t0 + count - 1 > tc || t0 <= tc - R) return fail(c, QP_ERR_ARG, "step outside the kept rho history");
+    for (size_t i = 0; i < (size_t)count * per; ++i) {
+        re[i] = rows[i].x;
+        im[i] = rows[i].y;
     }
     return QP_OK;
 }
