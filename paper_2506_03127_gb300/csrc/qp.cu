@@ -1380,11 +1380,6 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
     if (blockIdx.x == 0) finish_pending_rho<C64>(P, st, M * M);   // rho of the previous step
     const unsigned long long t = st->t, tn = t + 1;
     const int in = (int)(t & 1), outp = (int)(tn & 1), cs = (int)(tn % 3);
-    // the block's first ticket is taken now (block 0: after the sum above,
-    // so that no tile waits for it): its round trip overlaps the set-up
-    // below; tickets beyond the last tile end the loop as before
-    unsigned first_ticket = ~0u;
-    if (threadIdx.x == 0) first_ticket = atomicAdd(&st->ticket[cs], 1u);
     const bool merge = tn >= (unsigned long long)P.dkmax;
     const unsigned long long pref = merge ? P.prefmask : ~0ull;   // filling: every path is its own group
     const int n_act = (int)min(tn, (unsigned long long)P.dkmax);
@@ -1419,7 +1414,7 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
     __shared__ unsigned long long s_base[MM], s_tot[MM], s_kprev;
     __shared__ unsigned s_ra_n;   // prefetched paths past the tile end
     __shared__ long long s_ahead;   // tile-relative end of the tile's last run
-    __shared__ unsigned s_ticket, s_first, s_nseg, s_ng, s_hw[NW];
+    __shared__ unsigned s_ticket, s_nseg, s_ng, s_hw[NW];
     __shared__ int s_St;   // tile size of this step
     __shared__ float4 s_rt[NW][MM];
     __shared__ bool s_last;
@@ -1478,7 +1473,6 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
             acc += (q[r] + kst - 1) / kst;
         }
         s_tile0[MM] = acc;
-        s_first = first_ticket;
         if (acc == 0 && blockIdx.x == 0) {   // empty input: the output is empty
             for (int r = 0; r < MM; ++r) st->reg_n[outp][r] = 0;
             st->cnt_out[cs] = 0;
@@ -1513,10 +1507,7 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
     };
 
     for (;;) {
-        if (threadIdx.x == 0) {
-            s_ticket = s_first != ~0u ? s_first : atomicAdd(&st->ticket[cs], 1u);
-            s_first = ~0u;
-        }
+        if (threadIdx.x == 0) s_ticket = atomicAdd(&st->ticket[cs], 1u);
         __syncthreads();
         const long long ticket = s_ticket;
         if (ticket >= ntiles) break;
