@@ -206,6 +206,17 @@ qp_status qp_current(qp_ctx *ctx, int64_t *t, int64_t *n_paths);
  * [count][n_inst][M*M] (n_inst = 1 for a single problem).                  */
 qp_status qp_read_rho(qp_ctx *ctx, int64_t t0, int count, double *rho_re, double *rho_im);
 
+/* The same rows without waiting: enqueues on the context's stream the sum of
+ * the last step's block partials (stream engine) and the copy of rho(t) for
+ * t = t0 .. t0+count-1 into dst, interleaved (re, im) FP64,
+ * [count][n_inst][M*M] (the layout of a complex128 array).  dst is host
+ * memory owned by the caller; page-locked memory (cudaMallocHost, a pinned
+ * tensor) makes the copy asynchronous, other memory makes it synchronous.
+ * The values are in place once qp_sync (or any synchronising call) returns;
+ * device errors are reported there.  The range is checked against the steps
+ * enqueued since qp_set_rho0 (QP_ERR_ARG outside the last rho_history).    */
+qp_status qp_read_rho_async(qp_ctx *ctx, int64_t t0, int count, double *dst);
+
 /* Stored paths of each instance after step t: kept[n_inst] (synchronises). */
 qp_status qp_read_instance_counts(qp_ctx *ctx, int64_t t, int64_t *kept);
 

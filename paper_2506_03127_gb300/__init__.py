@@ -85,6 +85,18 @@ class Propagator:
         """rho(t0..t0+count-1): (count, M, M), or (count, n_inst, M, M) for a batch."""
         return _abi().qp_read_rho(self.ctx, t0, count, self.M, self.n_inst)
 
+    def rho_async(self, t0, out, count=1):
+        """Enqueue the copy of rho(t0 .. t0+count-1) into out, a contiguous
+        page-locked complex128 tensor of at least count * n_inst * M * M
+        elements (torch.empty(..., dtype=torch.complex128, pin_memory=True));
+        the values are in place after sync()."""
+        import torch
+
+        need = count * self.n_inst * self.M * self.M
+        if out.dtype != torch.complex128 or not out.is_contiguous() or out.numel() < need or out.device.type != "cpu":
+            raise ValueError("out: a contiguous host complex128 tensor of at least %d elements" % need)
+        _abi().qp_read_rho_async(self.ctx, t0, count, out.data_ptr())
+
     def set_eta_instance(self, inst, eta):
         _abi().qp_set_eta_instance(self.ctx, inst, eta)
 

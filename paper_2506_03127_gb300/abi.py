@@ -77,6 +77,7 @@ def _load():
         "qp_sync": (ctypes.c_int, [ctypes.c_void_p]),
         "qp_current": (ctypes.c_int, [ctypes.c_void_p, _i64p, _i64p]),
         "qp_read_rho": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, _dp, _dp]),
+        "qp_read_rho_async": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p]),
         "qp_read_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
                                          ctypes.POINTER(qp_step_stats)]),
         "qp_export_paths": (ctypes.c_int, [ctypes.c_void_p, _u64p, _dp, ctypes.c_int64, _i64p]),
@@ -211,6 +212,12 @@ def qp_read_rho(ctx, t0: int, count: int, M: int, n_inst: int = 1) -> np.ndarray
     check(lib.qp_read_rho(ctx, t0, count, _ptr(re), _ptr(im)), ctx)
     r = (re + 1j * im)
     return r.reshape(count, M, M) if n_inst == 1 else r.reshape(count, n_inst, M, M)
+
+
+def qp_read_rho_async(ctx, t0: int, count: int, dst_addr: int):
+    """Enqueue the copy of rho(t0 .. t0+count-1) to host memory at dst_addr
+    (complex128 [count][n_inst][M*M]); in place after qp_sync."""
+    check(lib.qp_read_rho_async(ctx, t0, count, ctypes.c_void_p(dst_addr)), ctx)
 
 
 def qp_set_eta_instance(ctx, inst: int, eta):

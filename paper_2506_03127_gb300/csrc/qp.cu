@@ -2345,6 +2345,7 @@ struct qp_ctx {
     cudaGraphExec_t graph = nullptr;
     bool graph_dirty = true;
     bool use_graph = true;
+    int64_t host_t = 0;                // steps enqueued since qp_set_rho0 (set from the device at every state read)
     void *hpin = nullptr;              // pinned host staging for rho reads (state + rows)
     size_t hpin_bytes = 0;
     std::string err;
@@ -2953,6 +2954,7 @@ qp_status qp_set_rho0(qp_ctx *c, const double *re, const double *im) {
     QP_CUDA(c, cudaStreamSynchronize(c->stream));
     c->have_state = true;
     c->failed = false;
+    c->host_t = 0;
     c->err.clear();
     return QP_OK;
 }
@@ -2981,6 +2983,7 @@ qp_status qp_step(qp_ctx *c, int nsteps) {
     if (!c->have_state) return fail(c, QP_ERR_STATE, "qp_set_rho0 must come before qp_step");
     if (c->failed) return fail(c, QP_ERR_STATE, "context holds a device error; call qp_set_rho0");
     if (nsteps == 0) return QP_OK;
+    c->host_t += nsteps;
     if (c->use_persistent && !c->use_stream) {
         const cudaError_t e = launch_persistent(c, nsteps);
         if (e != cudaSuccess) return fail(c, QP_ERR_CUDA, std::string("persistent launch: ") + cudaGetErrorString(e));
@@ -3027,6 +3030,7 @@ static qp_status check_state(qp_ctx *c, const DevState *s) {
 static qp_status read_state(qp_ctx *c, DevState *s) {
     QP_CUDA(c, cudaMemcpyAsync(s, c->P.st, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream));
     QP_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->host_t = (int64_t)s->t;
     return check_state(c, s);
 }
 
@@ -3081,6 +3085,7 @@ qp_status qp_read_rho(qp_ctx *c, int64_t t0, int count, double *re, double *im) 
         done += n;
     }
     QP_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->host_t = (int64_t)hs->t;
     qp_status r = check_state(c, hs);
     if (r != QP_OK) return r;
     const int64_t tc = (int64_t)hs->t;
@@ -3088,6 +3093,30 @@ qp_status qp_read_rho(qp_ctx *c, int64_t t0, int count, double *re, double *im) 
     for (size_t i = 0; i < (size_t)count * per; ++i) {
         re[i] = rows[i].x;
         im[i] = rows[i].y;
+    }
+    return QP_OK;
+}
+
+qp_status qp_read_rho_async(qp_ctx *c, int64_t t0, int count, double *dst) {
+    if (!c) return QP_ERR_ARG;
+    if (!dst || count < 0) return fail(c, QP_ERR_ARG, "bad output");
+    if (!c->have_state) return fail(c, QP_ERR_STATE, "no state");
+    if (c->failed) return fail(c, QP_ERR_STATE, "context holds a device error; call qp_set_rho0");
+    const int64_t R = c->cfg.rho_history, tc = c->host_t;
+    if (t0 < 0 || count > R || t0 + count - 1 > tc || t0 <= tc - R)
+        return fail(c, QP_ERR_ARG, "step outside the kept rho history");
+    if (c->use_stream) {   // the last step's rho may still be in block partials
+        if (c->cfg.precision == QP_C64) k_rho_finalize<true><<<1, 256, 0, c->stream>>>(c->P, c->cfg.M * c->cfg.M);
+        else k_rho_finalize<false><<<1, 256, 0, c->stream>>>(c->P, c->cfg.M * c->cfg.M);
+        QP_CUDA(c, cudaGetLastError());
+    }
+    const size_t per = (size_t)c->P.n_inst * c->cfg.M * c->cfg.M;
+    double2 *out = reinterpret_cast<double2 *>(dst);
+    for (int64_t done = 0; done < count;) {   // ring slots t mod R: at most two pieces
+        const int64_t slot = (t0 + done) % R, n = std::min<int64_t>(count - done, R - slot);
+        QP_CUDA(c, cudaMemcpyAsync(out + (size_t)done * per, c->P.rho_ring + (size_t)slot * per, (size_t)n * per * sizeof(double2),
+                                   cudaMemcpyDeviceToHost, c->stream));
+        done += n;
     }
     return QP_OK;
 }
@@ -3203,6 +3232,7 @@ qp_status qp_profile_steps(qp_ctx *c, int nsteps, double *kernel_ms, int nk) {
     for (int s = 0; s < nsteps && st == QP_OK; ++s) {
         k_delay<<<1, 1, 0, c->stream>>>(50000ull);
         cudaError_t e = launch_step(c, ev);
+        ++c->host_t;
         if (e == cudaSuccess) e = cudaEventSynchronize(ev[kStepKernels]);
         if (e != cudaSuccess) {
             st = fail(c, QP_ERR_CUDA, std::string("profile: ") + cudaGetErrorString(e));

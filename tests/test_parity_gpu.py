@@ -185,6 +185,29 @@ def test_stream_rho_read_every_step_equals_history_read_at_the_end(precision, to
         assert np.abs(at_end - rho_o[1:]).max() <= RHO_TOL
 
 
+@pytest.mark.parametrize("engine,precision", [("stream", "c64"), ("stream", "fp64"), ("hash", "fp64")])
+def test_async_rho_reads_equal_the_history(engine, precision):
+    """qp_read_rho_async after every step (stream-ordered copies to pinned
+    host memory, one synchronisation at the end) gives the rows a synchronous
+    read of the history gives; a step not yet taken, or one older than the
+    history ring, is rejected without a copy."""
+    w = W.SPIN_BOSON_STRUCTURED_DK16
+    p = Propagator.from_workload(w, precision=precision, engine=engine, max_paths=1 << 21, rho_history=64)
+    buf = torch.empty((100, 2, 2), dtype=torch.complex128, pin_memory=True)
+    for t in range(1, 101):
+        p.step(1)
+        p.rho_async(t, buf[t - 1])
+    p.sync()
+    assert np.array_equal(buf.numpy()[40:], p.rho(41, 60))
+    if precision == "fp64":
+        t, n, rho_o = load_golden("spin_boson_structured_dk16_rho40.txt")
+        assert np.abs(buf.numpy()[:40] - rho_o[1:]).max() <= RHO_TOL
+    for bad in (101, 36):   # not taken yet / no longer in the ring of 64
+        with pytest.raises(abi.QPError):
+            p.rho_async(bad, buf[0])
+    p.close()
+
+
 def test_spin_boson_structured_dk16_full_length_properties():
     """All 2000 steps at full size: properties that hold at any size.  The
     trace is conserved by merging and propagation, so it changes only through
