@@ -1198,18 +1198,28 @@ __global__ void __launch_bounds__(kRegThreads, 3) k_stream_regular(Params P, int
             for (int m = 0; m < MM; ++m) mb.a[m] = __ldcs(amps_in + r * G + j + m);
         }
     };
-    // one group: FP64 sum, children, write, accumulate rho
+    // one group: sum (C64: FP32 with every rounding error kept, TwoSum, in
+    // member order and rounded once, as the tile kernel's owner threads do;
+    // FP64: FP64), children, write, accumulate rho
     auto group = [&](long long g, const Members &mb) {
         const unsigned long long rk = mb.rk;
         AmpT v[MM];
         if (gs == 1) {   // a single member is its own sum, exactly
             X::children_tab(P, tab, rk, mb.a[0], s_w, s_wf, v);
-        } else {
-            double sx = to_d(mb.a[0].x), sy = to_d(mb.a[0].y);   // the group sum in FP64
+        } else if constexpr (C64) {
+            float sx = mb.a[0].x, sy = mb.a[0].y, ex = 0.f, ey = 0.f;
 #pragma unroll
             for (int m = 1; m < MM; ++m) {
-                sx += to_d(mb.a[m].x);
-                sy += to_d(mb.a[m].y);
+                two_sum_acc(sx, ex, mb.a[m].x);
+                two_sum_acc(sy, ey, mb.a[m].y);
+            }
+            X::children_tab(P, tab, rk, make_float2(sx + ex, sy + ey), s_w, s_wf, v);
+        } else {
+            double sx = mb.a[0].x, sy = mb.a[0].y;
+#pragma unroll
+            for (int m = 1; m < MM; ++m) {
+                sx += mb.a[m].x;
+                sy += mb.a[m].y;
             }
             X::children_tab(P, tab, rk, make_double2(sx, sy), s_w, s_wf, v);
         }
