@@ -142,7 +142,8 @@ def test_stream_engine_rerun_and_launch_shapes_agree(precision):
     """Look-back words carry the step number, which restarts with every
     qp_set_rho0: a second propagation on the same context, and the same
     propagation with every tile size and grid, give the same survivor counts
-    and rho (group sums are FP64 atomics, so rho only up to rounding)."""
+    and rho (up to rounding: the groups of runs longer than 32 paths, while the
+    window fills, are summed with FP64 atomics in no fixed order)."""
     w = W.SPIN_BOSON_STRUCTURED_DK16
     p = Propagator.from_workload(w, precision=precision, engine="stream", max_paths=1 << 21)
     runs = []
@@ -167,7 +168,7 @@ def test_stream_rho_read_every_step_equals_history_read_at_the_end(precision, to
     """A stream-engine step publishes its counters; its rho is summed from the
     blocks' partials when the next step starts or when it is read.  Reading
     rho after every step and reading the whole history once at the end give
-    the same values (up to the order of FP64 atomic group sums)."""
+    the same values (up to the order of the FP64 atomic sums of long runs)."""
     w = W.SPIN_BOSON_STRUCTURED_DK16
     p1 = Propagator.from_workload(w, precision=precision, engine="stream", max_paths=1 << 21)
     per_step = []
