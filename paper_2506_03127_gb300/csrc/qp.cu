@@ -1515,6 +1515,23 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
     auto xval = [&](unsigned long long key) -> unsigned {
         return NX > 1 ? (unsigned)((key >> P.x_shift) & (NX - 1)) : 0u;
     };
+    // first wave: block b prefetches tile b's stored paths into L2 (one
+    // address inside the tile per 128-byte line of keys and amplitudes), so
+    // that whichever block takes tile b finds it there
+    if ((long long)blockIdx.x < ntiles) {
+        const long long tk = blockIdx.x;
+        int rr = 0;
+        while (rr + 1 < MM && tk >= s_tile0[rr + 1]) ++rr;
+        const long long b0 = (tk - s_tile0[rr]) * St;
+        const long long n = min((long long)St, s_nr[rr] - b0);
+        const char *kp = reinterpret_cast<const char *>(keys_in + rr * G + b0);
+        const char *ap = reinterpret_cast<const char *>(amps_in + rr * G + b0);
+        const int kl = (int)((n * 8 + 127) / 128), al = (int)((n * (long long)sizeof(AmpT) + 127) / 128);
+        for (int l = threadIdx.x; l < kl + al; l += NT) {
+            const char *a = l < kl ? kp + (size_t)l * 128 : ap + (size_t)(l - kl) * 128;
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+        }
+    }
 
     for (;;) {
         if (threadIdx.x == 0) s_ticket = atomicAdd(&st->ticket[cs], 1u);
