@@ -210,8 +210,10 @@ qp_status qp_read_rho(qp_ctx *ctx, int64_t t0, int count, double *rho_re, double
  * the last step's block partials (stream engine) and the copy of rho(t) for
  * t = t0 .. t0+count-1 into dst, interleaved (re, im) FP64,
  * [count][n_inst][M*M] (the layout of a complex128 array).  dst is host
- * memory owned by the caller; page-locked memory (cudaMallocHost, a pinned
- * tensor) makes the copy asynchronous, other memory makes it synchronous.
+ * memory owned by the caller, at least count*n_inst*M*M*16 bytes.
+ * Page-locked memory that the device can address (cudaMallocHost, a pinned
+ * tensor) is written by the finalising kernel itself; other memory receives
+ * a cudaMemcpyAsync (synchronous for pageable memory).
  * The values are in place once qp_sync (or any synchronising call) returns;
  * device errors are reported there.  The range is checked against the steps
  * enqueued since qp_set_rho0 (QP_ERR_ARG outside the last rho_history).    */

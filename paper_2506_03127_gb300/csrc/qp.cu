@@ -949,6 +949,19 @@ __global__ void k_rho_finalize(Params P, int MM) {
     finish_pending_rho<C64>(P, P.st, MM);
 }
 
+// The same (finalize: stream engine), then rho(t0 ...) for nelem = count *
+// n_inst * M*M entries written to dst, host memory the device can address
+// (page-locked): no separate copy.  One block.
+template <bool C64>
+__global__ void k_rho_read_to(Params P, int MM, int finalize, double2 *dst, long long t0, long long nelem) {
+    if (finalize && !P.st->err) finish_pending_rho<C64>(P, P.st, MM);
+    const long long per = (long long)P.n_inst * MM;
+    for (long long i = threadIdx.x; i < nelem; i += blockDim.x) {
+        const long long t = t0 + i / per;
+        dst[i] = P.rho_ring[(size_t)(t % P.rho_hist) * per + i % per];
+    }
+}
+
 template <int M, bool C64, bool BATCH>
 __global__ void __launch_bounds__(kExpandThreads) k_expand(Params P) {
     DevState *st = P.st;
@@ -3132,12 +3145,24 @@ qp_status qp_read_rho_async(qp_ctx *c, int64_t t0, int count, double *dst) {
     const int64_t R = c->cfg.rho_history, tc = c->host_t;
     if (t0 < 0 || count > R || t0 + count - 1 > tc || t0 <= tc - R)
         return fail(c, QP_ERR_ARG, "step outside the kept rho history");
+    const size_t per = (size_t)c->P.n_inst * c->cfg.M * c->cfg.M;
+    // page-locked dst the device can address: one kernel finalises and writes
+    // the rows there (no copy); other memory: finalise, then cudaMemcpyAsync
+    cudaPointerAttributes attr{};
+    if (cudaPointerGetAttributes(&attr, dst) == cudaSuccess && attr.type == cudaMemoryTypeHost && attr.devicePointer) {
+        double2 *ddst = static_cast<double2 *>(attr.devicePointer);
+        const int MM = c->cfg.M * c->cfg.M, fin = c->use_stream ? 1 : 0;
+        if (c->cfg.precision == QP_C64) k_rho_read_to<true><<<1, 256, 0, c->stream>>>(c->P, MM, fin, ddst, t0, (long long)count * per);
+        else k_rho_read_to<false><<<1, 256, 0, c->stream>>>(c->P, MM, fin, ddst, t0, (long long)count * per);
+        QP_CUDA(c, cudaGetLastError());
+        return QP_OK;
+    }
+    cudaGetLastError();   // a pointer the runtime does not know is not an error here
     if (c->use_stream) {   // the last step's rho may still be in block partials
         if (c->cfg.precision == QP_C64) k_rho_finalize<true><<<1, 256, 0, c->stream>>>(c->P, c->cfg.M * c->cfg.M);
         else k_rho_finalize<false><<<1, 256, 0, c->stream>>>(c->P, c->cfg.M * c->cfg.M);
         QP_CUDA(c, cudaGetLastError());
     }
-    const size_t per = (size_t)c->P.n_inst * c->cfg.M * c->cfg.M;
     double2 *out = reinterpret_cast<double2 *>(dst);
     for (int64_t done = 0; done < count;) {   // ring slots t mod R: at most two pieces
         const int64_t slot = (t0 + done) % R, n = std::min<int64_t>(count - done, R - slot);
