@@ -211,6 +211,35 @@ def test_async_rho_reads_equal_the_history(engine, precision, pinned):
     p.close()
 
 
+def test_c64_group_sums_agree_with_fp64_sums_rounded():
+    """Reading of the complex64 group sum: the stream engine forms it as an
+    error-free FP32 pair rounded once, the merge-table engine adds the members
+    in FP64 and rounds.  Both expand with the same arithmetic, so the stored
+    sets agree bit for bit before the first merge; after the first merging
+    step the survivors are the same and the amplitudes agree bit for bit
+    except where an exact sum lies next to an FP32 rounding midpoint (then
+    within a few units in the last place)."""
+    w = W.SPIN_BOSON_STRUCTURED_DK16
+    for steps in (w.dkmax - 1, w.dkmax):
+        got = []
+        for engine in ("stream", "hash"):
+            p = Propagator.from_workload(w, precision="c64", engine=engine, max_paths=1 << 21)
+            p.step(steps)
+            p.sync()
+            k, a = p.export_paths()
+            p.close()
+            o = np.argsort(k)
+            got.append((k[o], a[o]))
+        (ks, a_s), (kh, a_h) = got
+        np.testing.assert_array_equal(ks, kh)
+        if steps < w.dkmax:
+            assert np.array_equal(a_s, a_h)
+        else:
+            diff = a_s != a_h
+            assert diff.mean() <= 1e-3, diff.mean()
+            assert np.all(np.abs(a_s - a_h)[diff] <= 2.0 ** -21 * np.abs(a_h)[diff])
+
+
 def test_spin_boson_structured_dk16_full_length_properties():
     """All 2000 steps at full size: properties that hold at any size.  The
     trace is conserved by merging and propagation, so it changes only through
