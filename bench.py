@@ -508,7 +508,9 @@ def main():
         line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "paths/s", "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic", "config": dict(cfg, t0=t_start, precision="fp64", engine="oracle"),
+                "data": "synthetic", "config": dict(cfg, t0=t_start, precision="fp64", engine="oracle",
+                                                     amplitudes="complex128, FP64 throughout (the CPU oracle)",
+                                                     l2="not applicable (host cores)"),
                 "cpu_baseline": {"value": v, "unit": "paths/s", "cores": 1, "kind": "oracle",
                                  "sample": f"{args.steps} oracle steps after t={t_start + args.warmup}"},
                 "e2e": {"value": v, "unit": "paths/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
