@@ -286,7 +286,7 @@ __global__ void k_rollout_input(const float *hist, int n, int T, int L, const fl
 // rho(t) = rho(t-1) + y / out_scale with the increment made traceless (the
 // trace changes only through the filter, negligibly over a rollout), then
 // projected onto Hermitian matrices (rho_10 = conj rho_01 from their mean,
-// real diagonal).
+// real diagonal) and onto positive semidefinite ones of the same trace.
 // The last block to finish advances the step index (every block has read
 // it by then).
 __global__ void k_rollout_update(float *hist, int n, int T, int *tstep, unsigned *done, const float *y,
@@ -317,6 +317,20 @@ __global__ void k_rollout_update(float *hist, int n, int T, int *tstep, unsigned
     r[5] = -im;
     r[1] = 0.f;
     r[7] = 0.f;
+    // positive semidefinite: with c = tr/2, z = (rho_00 - rho_11)/2, b =
+    // rho_01 the eigenvalues are c +- sqrt(z^2 + |b|^2); a radius above c is
+    // scaled back to c (the nearest such state of the same trace)
+    const float c = 0.5f * (r[0] + r[6]), z = 0.5f * (r[0] - r[6]);
+    const float rad = sqrtf(z * z + r[2] * r[2] + r[3] * r[3]);
+    if (c > 0.f && rad > c) {
+        const float f = c / rad;
+        r[0] = c + f * z;
+        r[6] = c - f * z;
+        r[2] *= f;
+        r[3] *= f;
+        r[4] = r[2];
+        r[5] = -r[3];
+    }
     float *out = hist + ((size_t)i * T + t) * 8;
     for (int k = 0; k < 8; ++k) out[k] = r[k];
 }

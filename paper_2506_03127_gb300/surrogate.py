@@ -9,7 +9,7 @@ its judge at checkpoints and its fallback.
 Features of one prediction: the last L values of rho(t) (8 reals each: Re,
 Im of rho_00, rho_01, rho_10, rho_11) and the instance's bath parameters
 (w0, 10 lambda); output: (rho(t) - rho(t-1)) * out_scale, added to rho(t-1)
-and projected onto Hermitian matrices.
+and projected onto Hermitian, positive semidefinite matrices of the same trace.
 """
 from __future__ import annotations
 
