@@ -372,8 +372,9 @@ qp_status qp_surrogate_windows(const double *d_rho, int n_inst, int L, const flo
  * same 8 reals as above; steps < t_from must be filled): for t = t_from ..
  * t_to-1, rho(t) = rho(t-1) + net(window) / out_scale with the increment
  * made traceless, projected onto Hermitian matrices and then onto positive
- * semidefinite ones of the same trace (a density matrix).  d_xbuf [n x d_in],
- * d_ybuf [n x 8] device scratch.  The steps run as CUDA graphs of up to 32
+ * semidefinite ones of the same trace (a density matrix).  d_xbuf [n x d_in]
+ * and d_ybuf [n x 8] (device floats) are kept in the signature; the rollout
+ * packs its input in the model's workspace and does not write them.  The steps run as CUDA graphs of up to 32
  * steps captured on the model's stream at the first call with these
  * arguments and replayed (the step index lives on the device); on the
  * legacy default stream they are launched one by one.  Synchronous: the

@@ -271,15 +271,19 @@ __global__ void k_windows(const double2 *rho, int n_inst, int L, const float *pa
 }
 
 // Rollout input: features of step t (= *tstep) from the history hist
-// [n][T][8] (FP32).  The step index lives on the device so that a captured
-// graph of steps can be replayed.
-__global__ void k_rollout_input(const float *hist, int n, int T, int L, const float *par, int n_par,
-                                const int *tstep, float *x) {
+// [n][T][8] (FP32): the last L values of rho and the bath parameters.  The
+// step index lives on the device so that a captured graph of steps can be
+// replayed.  They are rounded to BF16 straight into row i of the first
+// layer's input (ld = ldx; pads stay zero): the rollout needs no FP32 copy
+// and no transposed one (that is for the weight gradients of training).
+__global__ void k_rollout_pack(const float *hist, int n, int T, int L, const float *par, int n_par,
+                               const int *tstep, __nv_bfloat16 *xb, int ldx) {
     const int t = *tstep;
     const int d_in = 8 * L + n_par;
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n * d_in; idx += gridDim.x * blockDim.x) {
         const int i = idx / d_in, f = idx % d_in;
-        x[idx] = f < 8 * L ? hist[((size_t)i * T + (t - L + f / 8)) * 8 + (f % 8)] : par[(size_t)i * n_par + f - 8 * L];
+        const float v = f < 8 * L ? hist[((size_t)i * T + (t - L + f / 8)) * 8 + (f % 8)] : par[(size_t)i * n_par + f - 8 * L];
+        xb[(size_t)i * ldx + f] = __float2bfloat16_rn(v);
     }
 }
 
@@ -486,8 +490,8 @@ cudaError_t gemm(qp_mlp *m, const __nv_bfloat16 *A, int lda, const __nv_bfloat16
     return cudaGetLastError();
 }
 
-cudaError_t forward(qp_mlp *m, const float *d_x, int batch) {
-    k_pack_input<<<256, 256, 0, m->stream>>>(d_x, batch, m->d_in, m->xb, m->K1, m->xT, m->Bp);
+// The three layers on the packed input m->xb.
+cudaError_t forward_layers(qp_mlp *m, int batch) {
     EpiArgs e1{};
     e1.bias = m->b[0];
     e1.out_f32 = m->h1;
@@ -510,6 +514,11 @@ cudaError_t forward(qp_mlp *m, const float *d_x, int batch) {
     e3.out_f32 = m->y;
     e3.ldo = m->d_out;
     return gemm<EPI_LINEAR>(m, m->h2b, m->Kw, m->WbT[2], m->Kw, batch, m->d_out, m->Kw, e3);
+}
+
+cudaError_t forward(qp_mlp *m, const float *d_x, int batch) {
+    k_pack_input<<<256, 256, 0, m->stream>>>(d_x, batch, m->d_in, m->xb, m->K1, m->xT, m->Bp);
+    return forward_layers(m, batch);
 }
 
 // The weight-gradient GEMMs contract over the batch padded to 32: the
@@ -707,11 +716,11 @@ qp_status qp_surrogate_rollout(qp_mlp *m, float *d_hist, int n, int T, int L, co
     (void)d_ybuf;
     const int nsteps = t_to - t_from;
     if (nsteps == 0) return QP_OK;
-    // one rollout step: features, the network, the update (which advances
-    // the device step index)
+    // one rollout step: features packed for the first layer, the network,
+    // the update (which advances the device step index)
     auto one_step = [&]() -> cudaError_t {
-        k_rollout_input<<<64, 256, 0, m->stream>>>(d_hist, n, T, L, d_par, n_par, m->tstep, d_xbuf);
-        cudaError_t e = forward(m, d_xbuf, n);
+        k_rollout_pack<<<64, 256, 0, m->stream>>>(d_hist, n, T, L, d_par, n_par, m->tstep, m->xb, m->K1);
+        cudaError_t e = forward_layers(m, n);
         if (e != cudaSuccess) return e;
         k_rollout_update<<<(n + 127) / 128, 128, 0, m->stream>>>(d_hist, n, T, m->tstep, m->tdone, m->y, out_scale);
         return cudaGetLastError();
