@@ -134,9 +134,10 @@ def ncu_traffic(workload, regular, n_in):
 
 
 def algorithmic_bytes(stats_rows, M, amp_bytes, merge, engine="hash"):
-    """Per-kernel algorithmic DRAM bytes for a list of steps:
-    stored path = 8 B key + amp_bytes; merge-table slot 32 B + 8 B key.  The
-    stream engine reads the stored set once and writes the survivors."""
+    """Per-kernel algorithmic DRAM bytes for a list of steps: stored path =
+    8 B key + amp_bytes; merge-table slot 32 B + 8 B key.  The stream engine
+    reads the stored set once and writes the survivors (N_in E + N_out E);
+    the merge-table kernels read the stored set and the slots they touch."""
     E = 8 + amp_bytes
     ins = tie = exp = 0
     for (t, groups, extended, kept), n_in in stats_rows:

@@ -19,7 +19,7 @@ Definitions followed (paper sections and equations):
     filter threshold are dropped, and rho(t) is the sum of the surviving
     children by end point.
 
-Readings where the paper is silent (each listed in the design doc):
+Readings where the paper is silent:
   R1 box convention: point k >= 1 carries the box ((k-1) dt, k dt]; point 0
      (the initial state) carries none, so it enters S but not the influence
      functional.  The newest point's influence is applied when it is created.
