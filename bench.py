@@ -111,14 +111,42 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def code_hash(path):
+    """sha256 prefix (16 hex digits) of a C++/CUDA source's code: comments
+    removed (string and character literals kept whole) and white space
+    collapsed, so that DRAM counters, which depend on the code only, stay
+    tied to it across edits of its comments."""
+    import hashlib
+    with open(path, encoding="utf-8") as f:
+        src = f.read()
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        else:
+            out.append(c)
+            i += 1
+    return hashlib.sha256(" ".join("".join(out).split()).encode()).hexdigest()[:16]
+
+
 def ncu_traffic(workload, regular, n_in):
     """DRAM bytes per step of the stream kernels from one ncu capture
     (profiles/traffic.txt), or None when none matches the current kernel
-    source.  The regular kernel's capture is scaled by stored paths."""
-    import hashlib
+    code.  The regular kernel's capture is scaled by stored paths."""
     try:
-        with open(os.path.join(ROOT, "paper_2506_03127_gb300", "csrc", "qp.cu"), "rb") as f:
-            sha = hashlib.sha256(f.read()).hexdigest()[:16]
+        sha = code_hash(os.path.join(ROOT, "paper_2506_03127_gb300", "csrc", "qp.cu"))
         with open(os.path.join(ROOT, "profiles", "traffic.txt")) as f:
             rows = [ln.split() for ln in f if ln.strip() and not ln.startswith("#")]
     except OSError:

@@ -1294,9 +1294,9 @@ __global__ void __launch_bounds__(kRegThreads, 3) k_stream_regular(Params P, int
     }
 }
 
-// Runs of at most this many stored paths are summed by one thread (stream
-// engine); longer ones, which occur only while the window fills, by shared
-// FP64 atomics.
+// The groups of runs of at most this many stored paths are summed by one
+// owner thread each (stream engine); longer runs, which occur only while the
+// window fills, by shared FP64 atomics.
 constexpr int kOwnRun = 32;
 // A group sum formed in FP32 by its run's thread is stored as the float2 in
 // the low 8 bytes of its double2 slot and this signalling-NaN pattern in the
@@ -1374,7 +1374,8 @@ __device__ __forceinline__ unsigned long long ld_relaxed_gpu(const unsigned long
 // into NX sub-groups.  Per tile (dynamic tickets): load (and prefetch the 32
 // paths past the tile end), find run heads; for NX > 1 give each sub-group
 // present a compact slot; sum each group and elect its representative, one
-// thread per run (runs start in the tile and may extend past it); compute
+// owner thread per group (runs start in the tile and may extend past it;
+// runs longer than 32 paths use shared FP64 atomics); compute
 // the children of every group once, keep them in shared memory, count the
 // survivors per new point and accumulate rho(t+1); get the tile's output
 // offsets per region by a decoupled look-back (one warp, a window of

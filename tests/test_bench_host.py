@@ -1,7 +1,6 @@
 """Host logic of the bench's roofline figures (no GPU): the algorithmic bytes
 per kernel and the DRAM traffic taken from committed ncu captures, which
 apply only to the kernel source they were measured on."""
-import hashlib
 import os
 import sys
 
@@ -34,15 +33,28 @@ def _fake_tree(tmp_path, src, rows):
     (tmp_path / "profiles").mkdir()
     (tmp_path / "paper_2506_03127_gb300" / "csrc" / "qp.cu").write_bytes(src)
     (tmp_path / "profiles" / "traffic.txt").write_text("# header\n" + "\n".join(rows) + "\n")
-    return hashlib.sha256(src).hexdigest()[:16]
 
 
-def test_ncu_traffic_applies_only_to_the_captured_source(tmp_path, monkeypatch):
-    src = b"// kernel source\n"
-    sha = hashlib.sha256(src).hexdigest()[:16]
-    _fake_tree(tmp_path, src, [f"spin_boson_structured_dk16 stream_tile {sha} 2340608 0",
-                               f"tls_ohmic_full_dk12 stream_regular {sha} 400 16",
-                               "chain3_structured_dk12 stream_tile 0123456789abcdef 777 0"])
+def test_code_hash_ignores_comments_and_layout_but_not_code(tmp_path):
+    def h(text):
+        f = tmp_path / "k.cu"
+        f.write_text(text)
+        return bench.code_hash(str(f))
+    base = h('int f(int x) {\n    return x + 1;   // one more\n}\nconst char *s = "a // b";\n')
+    assert h('// a new comment\nint f(int x) { /* same */ return x + 1; }\nconst char *s = "a // b";\n') == base
+    assert h('int f(int x) {\n    return x + 2;\n}\nconst char *s = "a // b";\n') != base
+    assert h('int f(int x) {\n    return x + 1;\n}\nconst char *s = "a // c";\n') != base   # inside a string: code
+    assert h("char c = '\"'; int g;  // it's\n") == h("char c = '\"';\nint g;\n")
+
+
+def test_ncu_traffic_applies_only_to_the_captured_code(tmp_path, monkeypatch):
+    src = b"__global__ void k() {}   // kernel source\n"
+    _fake_tree(tmp_path, src, [])
+    sha = bench.code_hash(str(tmp_path / "paper_2506_03127_gb300" / "csrc" / "qp.cu"))
+    _rows = [f"spin_boson_structured_dk16 stream_tile {sha} 2340608 0",
+             f"tls_ohmic_full_dk12 stream_regular {sha} 400 16",
+             "chain3_structured_dk12 stream_tile 0123456789abcdef 777 0"]
+    (tmp_path / "profiles" / "traffic.txt").write_text("# header\n" + "\n".join(_rows) + "\n")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench.ncu_traffic("spin_boson_structured_dk16", False, 150000) == 2340608
     # the regular kernel's capture is scaled by stored paths (25 B per path here)
@@ -50,6 +62,8 @@ def test_ncu_traffic_applies_only_to_the_captured_source(tmp_path, monkeypatch):
     # a row taken on another source does not apply; nor does a missing workload
     assert bench.ncu_traffic("chain3_structured_dk12", False, 1) is None
     assert bench.ncu_traffic("spin_boson_ohmic_dk8", False, 1) is None
-    # the source changes: every row goes stale
+    # a comment changes: the rows still apply; the code changes: they go stale
     (tmp_path / "paper_2506_03127_gb300" / "csrc" / "qp.cu").write_bytes(src + b"// edited\n")
+    assert bench.ncu_traffic("spin_boson_structured_dk16", False, 150000) == 2340608
+    (tmp_path / "paper_2506_03127_gb300" / "csrc" / "qp.cu").write_bytes(src + b"int edited;\n")
     assert bench.ncu_traffic("spin_boson_structured_dk16", False, 150000) is None
