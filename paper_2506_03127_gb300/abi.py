@@ -110,6 +110,10 @@ def _load():
                                                 ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                                 ctypes.c_int, ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p]),
         "qp_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+        "qp_step_noalloc": (ctypes.c_int, [ctypes.POINTER(qp_config), _dp, _dp, ctypes.c_int, _ip, ctypes.c_int,
+                                           ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, _i64p, _dp, _dp,
+                                           ctypes.c_void_p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -289,11 +293,6 @@ def qp_step_noalloc(cfg, eta, mask, t, d_keys_in, d_amps_in, n_in, d_keys_out, d
     """One step without allocation or context (see include/qp.h).  Device
     buffers are passed as integer addresses; returns (n_out, rho(t+1))."""
     f = lib.qp_step_noalloc
-    if f.argtypes is None:
-        f.restype = ctypes.c_int
-        f.argtypes = [ctypes.POINTER(qp_config), _dp, _dp, ctypes.c_int, _ip, ctypes.c_int, ctypes.c_int64,
-                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
-                      ctypes.c_int64, _i64p, _dp, _dp, ctypes.c_void_p]
     M = cfg.M
     eta = np.asarray(eta, dtype=np.complex128)
     er, ei = _arr(eta.real), _arr(eta.imag)

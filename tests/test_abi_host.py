@@ -34,6 +34,29 @@ def test_every_declared_symbol_is_exported():
     assert not missing, missing
 
 
+def declared_prototypes():
+    """{name: number of parameters} of every function include/qp.h declares."""
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    out = {}
+    for m in re.finditer(r"\b(qp_[a-z0-9_]+)\s*\(([^;{}]*?)\)\s*;", src, flags=re.S):
+        params = m.group(2).strip()
+        out[m.group(1)] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_matches_every_declared_prototype():
+    """The ctypes binding gives every entry point of the C ABI as many
+    argument types as its prototype has parameters."""
+    protos = declared_prototypes()
+    assert set(protos) == set(declared_functions())
+    wrong = {}
+    for name, n in protos.items():
+        f = getattr(abi.lib, name)
+        if f.argtypes is None or len(f.argtypes) != n:
+            wrong[name] = (n, None if f.argtypes is None else len(f.argtypes))
+    assert not wrong, wrong
+
+
 def test_version_and_status_strings():
     assert abi.lib.qp_version() >= 100
     assert abi.lib.qp_status_string(abi.QP_ERR_CAPACITY).decode() == "capacity exceeded"
