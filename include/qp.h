@@ -201,9 +201,12 @@ qp_status qp_sync(qp_ctx *ctx);
 /* Current time step and number of stored paths (synchronises).              */
 qp_status qp_current(qp_ctx *ctx, int64_t *t, int64_t *n_paths);
 
-/* rho(t) for count consecutive steps t0 .. t0+count-1 (synchronises).  Each
- * step must be among the last rho_history steps.  re/im:
- * [count][n_inst][M*M] (n_inst = 1 for a single problem).                  */
+/* rho(t) for count consecutive steps t0 .. t0+count-1 (synchronises): the
+ * reduced density matrix of Eq. quapi_red_rho, the surviving children of
+ * each step summed by end point (Sec. 3.2).  Each step must be among the
+ * last rho_history steps (QP_ERR_ARG otherwise).  re/im:
+ * [count][n_inst][M*M] (n_inst = 1 for a single problem), caller-owned.
+ * The device state and the rows are copied in one round trip.              */
 qp_status qp_read_rho(qp_ctx *ctx, int64_t t0, int count, double *rho_re, double *rho_im);
 
 /* The same rows without waiting: enqueues on the context's stream the sum of
