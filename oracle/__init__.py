@@ -19,9 +19,10 @@ Contents
              with the influence functional truncated at the memory length.
 
 Parity status: every function is pinned by tests/test_oracle_pins.py against
-closed forms or brute force, except the masked pre-merge together with a
-nonzero bath, for which the paper prints no values ("parity unpinned" for
-that combination; it is pinned only by invariants: exactness at zero
-coupling, trace conservation without a filter, reduction to the unmasked
-result for the full mask).
+closed forms or brute force; the filter (its rule |amp| >= theta and its
+place before rho) by the filtered Markov map at memory length 1 and a
+hand-made set.  The masked pre-merge together with a nonzero bath has no
+value the paper prints ("parity unpinned" for that combination; it is
+pinned only by invariants: exactness at zero coupling, trace conservation
+without a filter, reduction to the unmasked result for the full mask).
 """

@@ -3,8 +3,9 @@
 Every check here compares the oracle with something other than itself:
 closed forms of Q(t), closed forms of U, brute-force enumeration of the path
 sum, Rabi oscillation at zero coupling, exact pure dephasing at zero
-tunnelling, the Markov map at memory length 1, and invariants (trace,
-Hermiticity).  The mutation tests at the end plant typical mistakes in a
+tunnelling, the Markov map at memory length 1 (with and without the filter,
+whose rule and order the filtered map pins), a hand-made filter case, and
+invariants (trace, Hermiticity).  The mutation tests at the end plant typical mistakes in a
 copy of the oracle and check that at least one pin catches each.
 """
 import math
@@ -217,6 +218,97 @@ def test_filter_removes_paths_and_trace_loss_grows():
     assert losses[0] < 1e-13 and losses[-1] > losses[0]
 
 
+# ---------------------------------------------------------------- filter
+
+def _tls_propagator(delta, dt):
+    """Closed form of exp(-i (delta/2) sigma_x dt)."""
+    c, s = math.cos(delta * dt / 2), math.sin(delta * dt / 2)
+    return np.array([[c, -1j * s], [-1j * s, c]])
+
+
+def filtered_markov(U, q, e0, theta, rho0, steps):
+    """Memory length 1 with the filter, written out term by term.
+
+    A stored path then holds its newest point only, so the pre-merge groups
+    the stored set by newest point and each group sum is an element of
+    rho(t-1).  Child (a, b) of group (a', b') is the single term
+        T = U[a, a'] rho(t-1)[a', b'] conj(U[b, b']) exp(-(q_a-q_b)(e0 q_a - e0* q_b)),
+    and the filter acts on every such term separately: a term of modulus
+    below theta is dropped before it enters rho(t), and is not carried to
+    the next step (Sec. 2.1 filtering; Sec. 3.2: propagation, then
+    filtering, then the density matrix).  Returns rho(0..steps) and the
+    number of dropped terms and of kept terms with |T| >= theta > |T|^2."""
+    M = len(q)
+    out = [np.array(rho0, dtype=complex)]
+    dropped = straddle = 0
+    for _ in range(steps):
+        cur, nxt = out[-1], np.zeros((M, M), dtype=complex)
+        for a in range(M):
+            for b in range(M):
+                f = np.exp(-(q[a] - q[b]) * (e0 * q[a] - np.conj(e0) * q[b]))
+                for ap in range(M):
+                    for bp in range(M):
+                        if cur[ap, bp] == 0:
+                            continue          # no stored path ends there
+                        term = U[a, ap] * cur[ap, bp] * np.conj(U[b, bp]) * f
+                        if abs(term) >= theta:
+                            nxt[a, b] += term
+                            straddle += abs(term) ** 2 < theta
+                        else:
+                            dropped += 1
+        out.append(nxt)
+    return np.array(out), dropped, straddle
+
+
+FILTER_PIN = dict(delta=1.0, dt=0.9, q=(1.0, -1.0), e0=0.04 + 0.03j, theta=0.06, steps=8,
+                  rho0=((0.7, 0.2 - 0.3j), (0.2 + 0.3j, 0.3)))
+
+
+def _filter_pin_error(mod):
+    c = FILTER_PIN
+    U = _tls_propagator(c["delta"], c["dt"])
+    hs = np.array([[0, c["delta"] / 2], [c["delta"] / 2, 0]], dtype=complex)
+    rho0 = np.array(c["rho0"], dtype=complex)
+    want, _, _ = filtered_markov(U, np.array(c["q"]), c["e0"], c["theta"], rho0, c["steps"])
+    r = mod.propagate(2, c["q"], hs, c["dt"], np.array([c["e0"]]), 1, None, c["theta"], rho0, c["steps"])
+    return np.abs(r.rho - want).max()
+
+
+def test_filtered_markov_map_at_memory_one():
+    """The filter pinned by the term-wise Markov map (the case exercises
+    dropped terms and kept terms whose squared modulus is below theta)."""
+    c = FILTER_PIN
+    U = _tls_propagator(c["delta"], c["dt"])
+    _, dropped, straddle = filtered_markov(U, np.array(c["q"]), c["e0"], c["theta"],
+                                           np.array(c["rho0"], dtype=complex), c["steps"])
+    assert dropped >= 5 and straddle >= 5
+    assert _filter_pin_error(iquapi) <= 1e-14
+
+
+@pytest.mark.parametrize("theta,amps,kept", [
+    # |amp| >= theta > |amp|^2 is kept; |amp| < theta is dropped
+    (0.1, (0.2, 0.05j, -0.05j, 0.8), (0, 3)),
+    # |amp| < theta <= |amp|^2 (theta > 1) is dropped
+    (2.0, (1.5, 0.5j, -0.5j, 2.5), (3,)),
+])
+def test_filter_rule_on_a_hand_made_set(theta, amps, kept):
+    """H_S = 0 and eta = 0 make every child a copy of its parent (the other
+    children are exactly zero): the surviving children and rho(t) follow
+    from the rule |amp| >= theta, applied before rho is summed."""
+    sp = np.array([[0], [0], [1], [1]])
+    sm = np.array([[0], [1], [0], [1]])
+    paths = iquapi.Paths(sp, sm, np.array(amps, dtype=complex))
+    U = iquapi.short_time_propagator(np.zeros((2, 2)), 0.1)
+    out, rho, st = iquapi.step(paths, 1, U, np.array([1.0, -1.0]), np.zeros(1), 1, [0], theta, 2)
+    want_keys = sorted(int(sp[i, 0]) | int(sm[i, 0]) << 1 for i in kept)
+    assert sorted(int(k) for k in iquapi.packed_keys(out.sp, out.sm, 2)) == want_keys
+    want_rho = np.zeros((2, 2), dtype=complex)
+    for i in kept:
+        want_rho[sp[i, 0], sm[i, 0]] = amps[i]
+    np.testing.assert_array_equal(rho, want_rho)
+    assert st.kept == len(kept)
+
+
 def test_mask_validation():
     with pytest.raises(ValueError):
         iquapi.check_mask((0, 2), 6)
@@ -263,6 +355,8 @@ MUTATIONS = {
     "history misses the last lag": ("for d in range(1, n_act):", "for d in range(1, n_act - 1):"),
     "sum keeps one member per group": ("np.add.at(S, inv, paths.amp)", "S[inv] = paths.amp"),
     "new point enters the history sum": ("for d in range(1, n_act):", "for d in range(0, n_act):"),
+    "theta not squared in the filter": ("keep = w2 >= th2", "keep = w2 >= theta"),
+    "rho summed before the filter": ("rho[a, b] = child[keep].sum()", "rho[a, b] = child.sum()"),
 }
 
 
@@ -293,6 +387,15 @@ def _pins_pass(mod):
         r = mod.propagate(2, q, hs, 0.2, eta, 8, (0, 1, 2, 5), 0.0, rho0, 16)
         if np.abs(np.trace(r.rho, axis1=1, axis2=2) - 1).max() > 1e-13:
             return False
+        if _filter_pin_error(mod) > 1e-14:
+            return False
+        for theta, amps, kept in [(0.1, (0.2, 0.05j, -0.05j, 0.8), (0, 3)), (2.0, (1.5, 0.5j, -0.5j, 2.5), (3,))]:
+            paths = mod.Paths(np.array([[0], [0], [1], [1]]), np.array([[0], [1], [0], [1]]),
+                              np.array(amps, dtype=complex))
+            _, rho, _ = mod.step(paths, 1, np.eye(2, dtype=complex), np.array([1.0, -1.0]), np.zeros(1), 1, [0],
+                                 theta, 2)
+            if not np.array_equal(np.diag(rho), [amps[0] if 0 in kept else 0, amps[3] if 3 in kept else 0]):
+                return False
         return True
     except Exception:
         return False
