@@ -61,7 +61,12 @@ typedef enum {
 
 enum { QP_FP64 = 0,       /* complex128 amplitudes, FP64 everywhere */
        QP_C64 = 1 };      /* complex64 amplitudes, FP32 influence exponent
-                             with compensated sums; FP64 eta, merge sums, rho */
+                             with compensated (Kahan) sums; FP64 eta and rho.
+                             Group sums of the pre-merge: FP64 in the merge
+                             table; in the stream engine the FP32 members are
+                             added in FP32 with every rounding error kept in
+                             a second word (TwoSum) and the pair is rounded
+                             once to FP32, the precision of the children   */
 
 enum { QP_ENGINE_AUTO = 0,    /* library picks: the stream engine where the
                                  mask allows it (single problems), else the
@@ -268,6 +273,16 @@ qp_status qp_autotune(qp_ctx *ctx, int trial_steps, int use_cache, qp_tuning *be
  * is not applied and the next synchronising call returns QP_ERR_TIMEOUT.
  * qp_set_rho0 restores a usable context.                                    */
 qp_status qp_test_stall_barrier(qp_ctx *ctx);
+
+/* Test hook for the bounded wait of the stream engine's look-back (the wait
+ * of a tile for the survivor counts of the tiles before it, Sec. 3.1 order
+ * of the stored set): the first tile of the next stream-engine step publishes
+ * no count, so the step's other tiles wait for it until their bounded wait
+ * gives up (about two seconds).  Tiles whose wait gave up write nothing, the
+ * step is not applied and the next synchronising call returns
+ * QP_ERR_TIMEOUT; qp_set_rho0 restores a usable context.  QP_ERR_STATE when
+ * the running propagation is not on the stream engine.                    */
+qp_status qp_test_stall_lookback(qp_ctx *ctx);
 
 /* Test hook: out[i] = in[i] widened from FP32 to FP64 exactly as the step
  * kernels widen FP32 amplitudes and partial sums before FP64 arithmetic

@@ -88,6 +88,7 @@ def _load():
         "qp_set_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
         "qp_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, _dp]),
         "qp_test_stall_barrier": (ctypes.c_int, [ctypes.c_void_p]),
+        "qp_test_stall_lookback": (ctypes.c_int, [ctypes.c_void_p]),
         "qp_test_widen": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
         "qp_mlp_workspace_size": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                  ctypes.POINTER(ctypes.c_size_t)]),
@@ -255,6 +256,10 @@ def qp_autotune(ctx, trial_steps: int = 8, use_cache: bool = True):
 
 def qp_test_stall_barrier(ctx):
     check(lib.qp_test_stall_barrier(ctx), ctx)
+
+
+def qp_test_stall_lookback(ctx):
+    check(lib.qp_test_stall_lookback(ctx), ctx)
 
 
 def qp_test_widen(in_ptr: int, out_ptr: int, n: int, stream: int = 0):

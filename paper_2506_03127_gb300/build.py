@@ -2,7 +2,7 @@
 
     python -m paper_2506_03127_gb300.build
 
-Both translation units are compiled in parallel, then linked into
+The three translation units (qp.cu, mlp.cu, host_numerics.cpp) are compiled in parallel, then linked into
 paper_2506_03127_gb300/libqp.so.  A rebuild happens only when a source is
 newer than the library (or force=True).
 """

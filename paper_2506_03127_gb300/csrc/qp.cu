@@ -29,7 +29,11 @@
 //
 // Precision (template parameter Amp): double2 amplitudes (QP_FP64) or
 // float2 amplitudes (QP_C64) with the influence exponent accumulated in FP32
-// with compensated (Kahan) sums; group sums, eta and rho stay FP64.
+// with compensated (Kahan) sums.  On the C64 path eta and rho stay FP64; the
+// group sums are FP64 atomic sums in the merge table (k_insert), while the
+// stream kernels add a group's FP32 members in FP32 with the rounding error
+// of every addition kept in a second word (TwoSum) and round the pair once
+// to FP32, the precision the children are formed in.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -68,7 +72,7 @@ constexpr unsigned kLbAgg = 1u, kLbInc = 2u;        // look-back word states (bi
 constexpr long long kBarrierCycles = 4000000000ll;  // ~2 s at 2 GHz: a grid barrier gives up after this
 constexpr int kMaxDelta = 12;
 constexpr double kTieRelFP64 = 1e-12;  // weights equal to this relative width are ties (R4)
-constexpr double kTieRelC64 = 1e-5;    // same, at complex64 resolution
+constexpr double kTieRelC64 = 1e-6;    // same, at complex64 resolution (about 17 units in the last place of |amp|^2)
 
 struct __align__(32) Slot {
     unsigned long long mk;     // masked key, kEmpty when free
@@ -82,7 +86,7 @@ struct __align__(128) DevState {
     unsigned long long cnt_groups[3]; // step t' uses [t' % 3]: merge groups claimed
     unsigned long long cnt_out[3];    // step t' uses [t' % 3]: survivors appended
     unsigned int err;                 // error bits, sticky until qp_set_rho0
-    unsigned int pad;
+    unsigned int stall_tile;          // test hook: tile ticket + 1 whose look-back words are withheld (0: none)
     unsigned long long err_t;         // step at which the error was raised
     unsigned long long reg_n[2][16];  // stream engine: stored paths per region, by buffer parity
     unsigned int ticket[3];           // stream engine: tile tickets, step t' uses [t' % 3]
@@ -123,7 +127,7 @@ struct Params {
     const float2 *lutf;                // same, FP32 hi part
     const float2 *lutf_lo;             // FP32 residual (hi + lo = FP64 value)
     const double2 *wtab;               // [M*M child][M*M parent newest] propagator x new-point influence
-    const float2 *wtabf;               // same, FP32
+    const float4 *wtabf;               // same, FP32 pairs: (hi.x, hi.y, lo.x, lo.y), hi + lo = the FP64 value
     const double2 *etab;               // [dkmax][ndelta][nchunks][256] exp(-delta_d T) tables (FP64 path)
     int ndelta;                        // distinct nonzero q_a - q_b
     float deltaf[12];                  // their values (FP32 path)
@@ -455,14 +459,14 @@ struct Expander {
     // FP32 (float2)
     template <typename SumT>
     static __device__ __forceinline__ unsigned children(const Params &P, int n_act, int inst, unsigned long long rep,
-                                                        SumT S, const double2 *w, const float2 *wf, AmpT *v) {
+                                                        SumT S, const double2 *w, const float4 *wf, AmpT *v) {
         return children_tab(P, tab_global(P, n_act, inst), rep, S, w, wf, v);
     }
 
     // the same with the history tables given (tb: global or shared memory)
     template <typename SumT>
     static __device__ __forceinline__ unsigned children_tab(const Params &P, const Tab &tb, unsigned long long rep,
-                                                            SumT S, const double2 *w, const float2 *wf, AmpT *v) {
+                                                            SumT S, const double2 *w, const float4 *wf, AmpT *v) {
         const unsigned c0 = (unsigned)(rep & ((1u << P.b) - 1u));
         const int pidx = (int)(c0 & ((1u << P.bs) - 1u)) * M + (int)(c0 >> P.bs);
         unsigned keep = 0;
@@ -497,7 +501,13 @@ struct Expander {
             const float2 Sf = to_f2(S);
 #pragma unroll
             for (int k = 0; k < MM; ++k) {
-                float2 a = cmulf(Sf, wf[k * MM + pidx]);
+                // S (W_hi + W_lo): the table's FP32 rounding error is carried
+                // (it would otherwise enter every step with the same sign and
+                // add up over the trajectory); products of the small lo part
+                // first, then fused into the hi products
+                const float4 wv = wf[k * MM + pidx];
+                const float lr = Sf.x * wv.z - Sf.y * wv.w, li = Sf.x * wv.w + Sf.y * wv.z;
+                float2 a = make_float2(fmaf(Sf.x, wv.x, fmaf(-Sf.y, wv.y, lr)), fmaf(Sf.x, wv.y, fmaf(Sf.y, wv.x, li)));
                 const int d = P.dsel[k];
                 if (d >= 0) a = cmulf(a, pick(Ed, d));
                 v[k] = a;
@@ -600,7 +610,7 @@ __device__ __forceinline__ void phase_expand(const Params &P, unsigned long long
     AmpT *amps_out = static_cast<AmpT *>(P.amps[tn & 1]);
 
     __shared__ double2 s_w[MM * MM];
-    __shared__ float2 s_wf[MM * MM];
+    __shared__ float4 s_wf[MM * MM];
     __shared__ double2 s_r[NW][MM];
     extern __shared__ double2 s_acc[];   // BATCH: [n_inst][MM + 1]
     if constexpr (BATCH) {
@@ -1116,7 +1126,7 @@ __global__ void __launch_bounds__(kRegThreads, 3) k_stream_regular(Params P, int
     const long long G = P.region_cap;
     __shared__ long long s_gb[MM + 1];
     __shared__ double2 s_w[C64 ? 1 : MM * MM];
-    __shared__ float2 s_wf[MM * MM];
+    __shared__ float4 s_wf[MM * MM];
     __shared__ float4 s_rt[kRegThreads / 32][MM];
     __shared__ bool s_last;
     if (threadIdx.x == 0) {
@@ -1432,7 +1442,7 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
     static_assert(NX == 1 || (Lay::stage && (size_t)Lay::NSTG * MM * sizeof(AmpT) >= (size_t)S * NX * 4),
                   "sub-group member masks live in the staging buffer");
     __shared__ double2 s_w[C64 ? 1 : MM * MM];   // FP64 weights (FP64 path only)
-    __shared__ float2 s_wf[MM * MM];
+    __shared__ float4 s_wf[MM * MM];
     __shared__ long long s_nr[MM], s_tile0[MM + 1];
     __shared__ unsigned s_wsum[NW][MM];
     __shared__ unsigned long long s_base[MM], s_tot[MM], s_kprev;
@@ -1443,7 +1453,9 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
     __shared__ float4 s_rt[NW][MM];
     __shared__ bool s_last;
     __shared__ int s_any;   // the block processed a tile
+    __shared__ int s_lbfail;   // the tile's look-back gave up (timeout, or another block's error)
     const double tie_d = 1.0 - P.tie_rel;   // R4 window, once per thread
+    const unsigned stall = st->stall_tile;   // test hook (0 in normal operation)
     const float tie_f = (float)tie_d;
 
     // weights and the history tables of this window length
@@ -1975,10 +1987,13 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
         // spread one window per round.
         constexpr int LBK = 4;
         constexpr int WIN = 32 * LBK;
+        const bool withhold = stall != 0u && (long long)stall == ticket + 1;   // test hook: publish nothing
+        if (threadIdx.x == 0) s_lbfail = 0;
+        __syncthreads();
         for (int c = warp; c < MM; c += NW) {
             unsigned long long *bucket = P.tile_state + (size_t)c * P.max_tiles;
             const unsigned long long tot = s_tot[c];
-            if (lane == 0) atomicExch(bucket + ticket, lb_word(epoch, ticket == 0 ? kLbInc : kLbAgg, tot));
+            if (lane == 0 && !withhold) atomicExch(bucket + ticket, lb_word(epoch, ticket == 0 ? kLbInc : kLbAgg, tot));
             unsigned long long excl = 0;
             long long pred = ticket - 1;
             const long long t0 = clock64();
@@ -2030,13 +2045,18 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
             }
             if (timeout && lane == 0) atomicOr(&st->err, kErrTimeout);
             if (lane == 0) {
-                if (ticket > 0) atomicExch(bucket + ticket, lb_word(epoch, kLbInc, excl + tot));
-                s_base[c] = excl;
-                if (ticket == ntiles - 1) st->reg_n[outp][c] = excl + tot;   // the last tile knows the region sizes
+                if (timeout || abort) {
+                    s_lbfail = 1;   // offsets unknown: this tile writes nothing (the step fails)
+                } else {
+                    if (ticket > 0 && !withhold) atomicExch(bucket + ticket, lb_word(epoch, kLbInc, excl + tot));
+                    s_base[c] = excl;
+                    if (ticket == ntiles - 1) st->reg_n[outp][c] = excl + tot;   // the last tile knows the region sizes
+                }
             }
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
+        const bool lbfail = s_lbfail != 0;
+        if (threadIdx.x == 0 && !lbfail) {
             for (int c = 0; c < MM; ++c) block_kept += s_tot[c];
             if (ngroups) atomicAdd(&st->cnt_groups[cs], (unsigned long long)ngroups);
             if (ticket == ntiles - 1) {
@@ -2046,7 +2066,7 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
             }
         }
         // pass B: write the survivors to their regions
-        for (int g = g0; g < g1; ++g) {
+        for (int g = g0; g < (lbfail ? g0 : g1); ++g) {
             const unsigned keep = s_keep[g];
             if (!keep) continue;
             const unsigned long long rk = s_grep[g];
@@ -2174,7 +2194,7 @@ __global__ void k_build_lut(double2 *lut, float2 *lutf, float2 *lutlo, const dou
 }
 
 // W[(a,b)][(a',b')] = U[a,a'] conj(U[b,b']) exp(-(q_a - q_b)(eta_0 q_a - conj(eta_0) q_b))
-__global__ void k_build_w(double2 *w, float2 *wf, const double2 *U, const double2 *eta, const double *q, int M) {
+__global__ void k_build_w(double2 *w, float4 *wf, const double2 *U, const double2 *eta, const double *q, int M) {
     const int MM = M * M;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < MM * MM; i += gridDim.x * blockDim.x) {
         const int child = i / MM, par = i % MM;
@@ -2191,8 +2211,10 @@ __global__ void k_build_w(double2 *w, float2 *wf, const double2 *U, const double
         double s, c;
         sincos(zi, &s, &c);
         const double m = exp(zr);
-        w[i] = cmul(prop, make_double2(m * c, m * s));
-        wf[i] = make_float2((float)w[i].x, (float)w[i].y);
+        const double2 wv = cmul(prop, make_double2(m * c, m * s));
+        w[i] = wv;
+        const float hx = (float)wv.x, hy = (float)wv.y;
+        wf[i] = make_float4(hx, hy, (float)(wv.x - (double)hx), (float)(wv.y - (double)hy));
     }
 }
 
@@ -2335,7 +2357,7 @@ Layout make_layout(const qp_config *c) {
     L.nd = nd;
     L.etab = take(NI * nlut * std::max(1, nd) * sizeof(double2));
     L.wtab = take((size_t)NI * MM * MM * sizeof(double2));
-    L.wtabf = take((size_t)NI * MM * MM * sizeof(float2));
+    L.wtabf = take((size_t)NI * MM * MM * sizeof(float4));
     L.deltas = take(kMaxDelta * sizeof(double));
     L.uprop = take(MM * sizeof(double2));
     L.eta = take((size_t)NI * c->dkmax * sizeof(double2));
@@ -2769,7 +2791,7 @@ qp_status qp_create(const qp_config *cfg, void *d_workspace, size_t bytes, void 
     P.lutf = reinterpret_cast<const float2 *>(c->ws + L.lutf);
     P.lutf_lo = reinterpret_cast<const float2 *>(c->ws + L.lutlo);
     P.wtab = reinterpret_cast<const double2 *>(c->ws + L.wtab);
-    P.wtabf = reinterpret_cast<const float2 *>(c->ws + L.wtabf);
+    P.wtabf = reinterpret_cast<const float4 *>(c->ws + L.wtabf);
     P.etab = reinterpret_cast<const double2 *>(c->ws + L.etab);
     {
         std::vector<double> dv;
@@ -2860,7 +2882,7 @@ static qp_status set_eta_one(qp_ctx *c, int inst, const double *re, const double
         QP_CUDA(c, cudaGetLastError());
     }
     k_build_w<<<1, 256, 0, c->stream>>>(reinterpret_cast<double2 *>(c->ws + c->L.wtab) + (size_t)inst * MM * MM,
-                                        reinterpret_cast<float2 *>(c->ws + c->L.wtabf) + (size_t)inst * MM * MM,
+                                        reinterpret_cast<float4 *>(c->ws + c->L.wtabf) + (size_t)inst * MM * MM,
                                         reinterpret_cast<const double2 *>(c->ws + c->L.uprop), ed, qd, M);
     QP_CUDA(c, cudaGetLastError());
     if (P.nchunks > 0 && P.ndelta > 0) {
@@ -3465,6 +3487,18 @@ qp_status qp_test_stall_barrier(qp_ctx *c) {
     return QP_OK;
 }
 
+qp_status qp_test_stall_lookback(qp_ctx *c) {
+    if (!c) return QP_ERR_ARG;
+    if (!c->have_state) return fail(c, QP_ERR_STATE, "no state");
+    if (!c->use_stream) return fail(c, QP_ERR_STATE, "the propagation does not run on the stream engine");
+    // the first tile of the next step publishes no look-back word: the
+    // step's other tiles wait for it until their bounded wait gives up
+    const unsigned int first = 1u;
+    QP_CUDA(c, cudaMemcpyAsync(&c->P.st->stall_tile, &first, sizeof(first), cudaMemcpyHostToDevice, c->stream));
+    QP_CUDA(c, cudaStreamSynchronize(c->stream));
+    return QP_OK;
+}
+
 const char *qp_last_error(const qp_ctx *c) { return c ? c->err.c_str() : "null context"; }
 
 qp_status qp_test_widen(const float *in, double *out, int64_t n, void *stream) {
@@ -3708,13 +3742,16 @@ extern "C" qp_status qp_step_noalloc(const qp_config *cfg, const double *eta_re,
     float2 *lutlo = reinterpret_cast<float2 *>(take(nlut * sizeof(float2)));
     double2 *etab = reinterpret_cast<double2 *>(take(nlut * kMaxDelta * sizeof(double2)));
     double2 *wtab = reinterpret_cast<double2 *>(take(256 * sizeof(double2)));
-    float2 *wtabf = reinterpret_cast<float2 *>(take(256 * sizeof(float2)));
+    float4 *wtabf = reinterpret_cast<float4 *>(take(256 * sizeof(float4)));
     double2 *Ud = reinterpret_cast<double2 *>(take(16 * sizeof(double2)));
     double2 *etad = reinterpret_cast<double2 *>(take(kNaMaxDk * sizeof(double2)));
     double *qd = reinterpret_cast<double *>(take(4 * sizeof(double)));
     double *deltad = reinterpret_cast<double *>(take(kMaxDelta * sizeof(double)));
     P.rho_ring = reinterpret_cast<double2 *>(take(2 * 16 * sizeof(double2)));
-    P.rho_part = reinterpret_cast<double2 *>(take((size_t)2 * kMaxExpandBlocks * 16 * sizeof(double2)));
+    // per-block partials of rho by step parity: M*M values and the survivor
+    // count per block (the stride rho_part_of and phase_finalize use), for
+    // the largest M
+    P.rho_part = reinterpret_cast<double2 *>(take((size_t)2 * kMaxExpandBlocks * (16 + 1) * sizeof(double2)));
     P.stats_ring = reinterpret_cast<StepRec *>(take(2 * sizeof(StepRec)));
     P.inst_kept = reinterpret_cast<long long *>(take(2 * sizeof(long long)));
     P.fin_count = reinterpret_cast<unsigned int *>(take(sizeof(unsigned int)));

@@ -4,7 +4,7 @@ Calls only oracle/ (and the input module workloads.py).  Each file holds one
 line per time step t: t, the number of stored paths after the step, then
 Re and Im of rho(t) row-major.  Regenerate with
 
-    python tests/golden/make_golden.py
+    python tests/golden/make_golden.py [file ...]
 """
 import os
 import sys
@@ -42,6 +42,22 @@ def load(fname):
     return t, n, rho.reshape(-1, M, M)
 
 
+# (workload, steps, file): the trajectories the GPU tests compare with.  The
+# three-level chain with memory 12 stops at t = 10 (1.6e7 stored paths; the
+# window fills at t = 12 with about 1e8, beyond what the oracle finishes in
+# seconds); its memory-7 variant covers that model's merging steps.
+GOLDEN = [
+    (W.SPIN_BOSON_OHMIC_DK8, W.SPIN_BOSON_OHMIC_DK8.steps, "spin_boson_ohmic_dk8_rho.txt"),
+    (W.SPIN_BOSON_STRUCTURED_DK16, 40, "spin_boson_structured_dk16_rho40.txt"),
+    (W.SPIN_BOSON_STRUCTURED_DK16, 200, "spin_boson_structured_dk16_rho200.txt"),
+    (W.CHAIN3_STRUCTURED_DK7, W.CHAIN3_STRUCTURED_DK7.steps, "chain3_structured_dk7_rho60.txt"),
+    (W.CHAIN3_STRUCTURED_DK12, 10, "chain3_structured_dk12_rho10.txt"),
+    (W.tls_ohmic_full(8), W.tls_ohmic_full(8).steps, "tls_ohmic_full_dk8_rho117.txt"),
+    (W.tls_ohmic_full(10), 30, "tls_ohmic_full_dk10_rho30.txt"),
+]
+
 if __name__ == "__main__":
-    write(W.SPIN_BOSON_OHMIC_DK8, W.SPIN_BOSON_OHMIC_DK8.steps, "spin_boson_ohmic_dk8_rho.txt")
-    write(W.SPIN_BOSON_STRUCTURED_DK16, 40, "spin_boson_structured_dk16_rho40.txt")
+    only = set(sys.argv[1:])
+    for w, steps, fname in GOLDEN:
+        if not only or fname in only:
+            write(w, steps, fname)

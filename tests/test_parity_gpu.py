@@ -325,3 +325,35 @@ def test_device_widening_is_exact_for_every_float_class():
     assert np.array_equal(np.isnan(got), nan)
     assert np.array_equal(got[~nan].view(np.uint64), ref[~nan].view(np.uint64))
 
+
+
+def test_stream_lookback_wait_is_bounded():
+    """A tile that never publishes its survivor counts: the step's other
+    tiles give up waiting after their bound and write nothing, the step is
+    not applied, the context reports QP_ERR_TIMEOUT, refuses to step
+    (QP_ERR_STATE) and propagates correctly again after qp_set_rho0."""
+    case = W.random_case(43, 2, 8)
+    mask, theta = None, 1e-7            # about 26 000 stored paths from t = 10
+    p = Propagator(2, 8, case["dt"], case["q"], case["hs"], theta, engine="stream", max_paths=1 << 18)
+    p.set_eta(case["eta"])
+    p.set_mask(mask)
+    p.set_rho0(case["rho0"])
+    p.set_tuning(stream_tile=256, expand_blocks_per_sm=1)
+    p.step(10)
+    p.sync()
+    t_before, n_before = p.current()
+    assert n_before > 8 * 256          # several tiles in the next step
+    abi.qp_test_stall_lookback(p.ctx)
+    p.step(2)
+    with pytest.raises(abi.QPError) as e:
+        p.sync()
+    assert e.value.status == abi.QP_ERR_TIMEOUT
+    with pytest.raises(abi.QPError) as e2:
+        p.step(1)
+    assert e2.value.status == abi.QP_ERR_STATE
+    p.set_rho0(case["rho0"])
+    p.step(12)
+    p.sync()
+    o = iquapi.propagate(2, case["q"], case["hs"], case["dt"], case["eta"], 8, mask, theta, case["rho0"], 12)
+    assert np.abs(p.rho(0, 13) - o.rho).max() <= RHO_TOL
+    p.close()

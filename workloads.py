@@ -97,6 +97,11 @@ CHAIN3_STRUCTURED_DK12 = Workload(
     dt=0.1, dkmax=12, mask=(0, 1, 2, 3, 4, 5, 6, 7, 8), theta=1e-10,
     rho0=((1.0, 0.0, 0.0), (0.0, 0.0, 0.0), (0.0, 0.0, 0.0)), steps=300)
 
+# The same chain with memory 7 and mask {0..5}: about 2.5e5 stored paths, a
+# case whose merging steps the oracle runs in seconds.
+CHAIN3_STRUCTURED_DK7 = replace(CHAIN3_STRUCTURED_DK12, name="chain3_structured_dk7", dkmax=7,
+                                mask=(0, 1, 2, 3, 4, 5), steps=60)
+
 # The paper's distributed-memory scaling model (Sec. 4.2): TLS with
 # H_S = (Delta/2) sigma_x, ohmic J = (gamma/pi) w exp(-w/wc), gamma = 1/16,
 # wc = 10, kT = 0.2, dt = 0.3, t_max = 35, full QUAPI (no mask, no filter),
