@@ -13,7 +13,8 @@ stream, outside the timed events).  Metric: extended paths per second =
 sum over timed steps of (groups * M^2) / sum of the steps' CUDA-event times.
 
 --impl reference times the FP64 CPU oracle (the deliberately plain
-reference) on the same workload and metric on the host cores.
+reference) on the same workload, steps and metric on all host cores
+(independent replicas in spawned processes).
 Multi-GPU (torchrun): independent replicas of the workload, one per rank.
 """
 from __future__ import annotations
@@ -281,9 +282,13 @@ def run_ours(args, rank, world, precision):
             "kernel_share": {n: round(float(m / kern_ms.sum()), 4) for n, m in zip(names, kern_ms) if n != "-"},
             "kernel_avg_us": {n: round(float(m / nprof * 1e3), 2) for n, m in zip(names, kern_ms) if n != "-"}}
 
-    # end to end through the public API from host inputs: set eta/mask/rho0
-    # from host arrays, then per step qp_step + a copy of rho(t) to pinned
-    # host memory (qp_read_rho_async, stream-ordered; one qp_sync at the end)
+    # end to end through the public API, from host inputs.  (a) The whole
+    # trajectory: eta, mask and rho(0) set from host arrays, then per step
+    # qp_step and qp_read_rho_async of rho(t) into pinned host memory
+    # (stream-ordered; one qp_sync at the end).  (b) The same steps as the
+    # timed region: set-up and the first steps untimed, then the timed steps
+    # each with qp_step and the read of rho(t); the stored set, the step's
+    # input, stays on the device, so the per-step host->device bytes are 0.
     e2e_steps = args.t0 + args.warmup + args.steps
     from paper_2506_03127_gb300 import eta_from_bath
     eta_h = eta_from_bath(w.bath, w.dt, w.dkmax)
@@ -299,19 +304,37 @@ def run_ours(args, rank, world, precision):
     p.sync()
     e1 = time.perf_counter()
     e_stats = p.stats(1, e2e_steps)
-    e2e_ext = float(sum(r[2] for r in e_stats))
-    h2d = (eta_h.size * 16 + len(w.mask_list()) * 4 + w.M * w.M * 16) / e2e_steps
+    e2e_traj = float(sum(r[2] for r in e_stats)) / (e1 - e0)
+    setup_h2d = eta_h.size * 16 + len(w.mask_list()) * 4 + w.M * w.M * 16
     d2h = w.M * w.M * 16
     # the rows read during the run are the propagation's rho history (the
     # last 4000 steps, which the history ring still holds)
     n_chk = min(e2e_steps, 4000)
     e2e_hist = p.rho(e2e_steps - n_chk + 1, n_chk)
     assert np.array_equal(rho_pinned.numpy()[e2e_steps - n_chk:], e2e_hist), "asynchronous rho reads differ from the history"
+    # (b): the timed steps start where the device-timed ones started
+    t_start = t_first - 1
+    p.set_eta(eta_h)
+    p.set_mask(w.mask)
+    p.set_rho0(w.rho0_array())
+    p.step(t_start)
+    p.sync()
+    rows = torch.empty((args.steps, w.M, w.M), dtype=torch.complex128, pin_memory=True)
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    for k in range(args.steps):
+        p.step(1)
+        p.rho_async(t_start + k + 1, rows[k])
+    p.sync()
+    e1 = time.perf_counter()
+    e2e_same = float(sum(r[2] for r in p.stats(t_start + 1, args.steps))) / (e1 - e0)
+    assert np.array_equal(rows.numpy(), p.rho(t_start + 1, args.steps)), "asynchronous rho reads differ from the history"
     p.close()
 
-    res = dict(ext=extended, t_ms=t_ms, wall=wall1 - wall0, e2e=e2e_ext / (e1 - e0), roof=roof, tuning=tuning.as_dict(),
-               clocks=clocks.summary(), h2d=h2d, d2h=d2h, step_ms=step_ms, stats=stats,
-               kernels_per_step=(2 if regular_cfg else 1) if engine == "stream" else 4, rho=rho_hist)
+    res = dict(ext=extended, t_ms=t_ms, wall=wall1 - wall0, e2e=e2e_same, e2e_traj=e2e_traj, roof=roof,
+               tuning=tuning.as_dict(), clocks=clocks.summary(), setup_h2d=setup_h2d, d2h=d2h, step_ms=step_ms,
+               stats=stats, kernels_per_step=(2 if regular_cfg else 1) if engine == "stream" else 4, rho=rho_hist,
+               t_first=t_first)
     return res
 
 
@@ -433,51 +456,113 @@ def aggregate_over_ranks(t_ms, units):
     return float(t[0]), float(u[0])
 
 
-def run_more_config(name, t0, steps, max_paths, warmup=3, engine="auto", fp64=True):
-    """Another workload of the benchmark set, same measurement as the
-    headline (c64, autotuned, L2 flushed between timed steps) with, if fp64,
-    the plain FP64 GPU path on the same trajectory for the speed and rho
-    comparison."""
+GOLDEN = {   # oracle trajectories (tests/golden/, written by make_golden.py from oracle/ only)
+    "spin_boson_structured_dk16": "spin_boson_structured_dk16_rho200.txt",
+    "spin_boson_ohmic_dk8": "spin_boson_ohmic_dk8_rho.txt",
+    "chain3_structured_dk12": "chain3_structured_dk12_rho10.txt",
+    # the first 10 steps do not depend on the memory length (window filling)
+    "tls_ohmic_full_dk13": "tls_ohmic_full_dk14_rho10.txt",
+    "tls_ohmic_full_dk14": "tls_ohmic_full_dk14_rho10.txt",
+}
+
+
+def oracle_error(name, rho_hist):
+    """max_t max_ab |rho(t) - rho_oracle(t)| over the steps t = 1 .. n the
+    stored oracle trajectory covers (rho_hist[k] = rho(k + 1)); (err, n)."""
+    fname = GOLDEN.get(name)
+    if fname is None:
+        return None, 0
+    rows = np.loadtxt(os.path.join(ROOT, "tests", "golden", fname), comments="#")
+    v = rows[:, 2:]
+    rho_o = (v[:, 0::2] + 1j * v[:, 1::2]).reshape(len(rows), rho_hist.shape[-1], rho_hist.shape[-1])
+    n = min(len(rows) - 1, len(rho_hist))
+    return float(np.abs(rho_hist[:n] - rho_o[1:n + 1]).max()), n
+
+
+def run_config(name, t0, steps, max_paths, warmup=3, engine="auto", precisions=("c64", "fp64")):
+    """Another workload of the benchmark set, measured like the headline
+    (autotuned, L2 flushed between timed steps) in each precision on the
+    same trajectory; the first precision is the configuration's own, the
+    others are compared with it (speed, rho)."""
     a = argparse.Namespace(workload=name, t0=t0, steps=steps, warmup=warmup, max_paths=max_paths, engine=engine,
                            stream_tile=None, blocks_per_sm=None)
     w = WORKLOADS[name]
-    res = run_ours(a, 0, 1, "c64")
-    v = res["ext"] / (res["t_ms"] / 1e3)
+    runs = {pr: run_ours(a, 0, 1, pr) for pr in precisions}
     out = {"workload": name, "M": w.M, "dkmax": w.dkmax, "mask": w.mask_list(), "theta": w.theta, "t0": t0,
-           "steps": steps, "engine": engine, "max_paths": max_paths, "value": v, "unit": "paths/s",
-           "ms_per_step": res["t_ms"] / steps, "paths_kept_last": int(res["stats"][-1][3]), "roofline": res["roof"],
-           "tuning": res["tuning"], "clocks": res["clocks"]}
-    if fp64:
-        ref = run_ours(a, 0, 1, "fp64")
-        n = min(len(res["rho"]), len(ref["rho"]))
-        vf = ref["ext"] / (ref["t_ms"] / 1e3)
-        out.update({"fp64_gpu": {"value": vf, "ms_per_step": ref["t_ms"] / steps, "roofline": ref["roof"]},
-                    "speedup_vs_fp64_gpu": v / vf,
-                    "rho_max_abs_err_vs_fp64": float(np.abs(res["rho"][:n] - ref["rho"][:n]).max()),
-                    "rho_err_steps": n})
+           "steps": steps, "engine": engine, "max_paths": max_paths}
+    for pr, r in runs.items():
+        e_or, n_or = oracle_error(name, r["rho"])
+        out[pr] = {"value": r["ext"] / (r["t_ms"] / 1e3), "unit": "paths/s", "ms_per_step": r["t_ms"] / steps,
+                   "paths_kept_last": int(r["stats"][-1][3]), "roofline": r["roof"], "tuning": r["tuning"],
+                   "clocks": r["clocks"], "e2e": r["e2e"], "rho_max_abs_err_vs_oracle": e_or, "oracle_steps": n_or}
+    if "fp64" in runs and "c64" in runs:
+        n = min(len(runs["c64"]["rho"]), len(runs["fp64"]["rho"]))
+        out["c64"]["rho_max_abs_err_vs_fp64"] = float(np.abs(runs["c64"]["rho"][:n] - runs["fp64"]["rho"][:n]).max())
+        out["c64"]["rho_err_steps"] = n
+        out["c64"]["speedup_vs_fp64_gpu"] = out["c64"]["value"] / out["fp64"]["value"]
+    out["precision"] = precisions[0]
     return out
 
 
-def cpu_baseline(w, steps_total=60, timed_from=None):
-    """Oracle (FP64 CPU, as it stands) on a bounded sample of the workload:
-    propagate from t = 0 and time the steps after the window is full."""
+def compact(cfg):
+    """One configuration in a few numbers (the end of the bench line)."""
+    pr = cfg["precision"]
+    r = cfg[pr]
+    g = lambda x: None if x is None else float(f"{x:.3g}")   # noqa: E731
+    d = {"prec": pr, "paths_s": g(r["value"]), "ms_step": g(r["ms_per_step"]), "frac": r["roofline"]["frac"],
+         "err_oracle": g(r["rho_max_abs_err_vs_oracle"]), "oracle_t": r["oracle_steps"]}
+    other = "fp64" if pr == "c64" else "c64"
+    if other in cfg:
+        o = cfg[other]
+        d[other] = {"paths_s": g(o["value"]), "ms_step": g(o["ms_per_step"]), "frac": o["roofline"]["frac"],
+                    "err_oracle": g(o["rho_max_abs_err_vs_oracle"])}
+        d["err_c64_vs_fp64"] = g(cfg["c64"].get("rho_max_abs_err_vs_fp64"))
+    return d
+
+
+def _oracle_sample(job):
+    """One replica of the oracle on a bounded sample of a workload: the steps
+    1 .. t_end, with t_from .. t_end timed.  Returns (extended paths, seconds
+    of the timed steps).  Runs in a spawned process."""
+    name, t_from, t_end = job
+    sys.path.insert(0, ROOT)
+    import workloads as W_  # noqa: F401
     from oracle import bath, iquapi
+    w = WORKLOADS[name]
     eta = bath.eta_coefficients(w.bath, w.dt, w.dkmax)
     P = iquapi.check_mask(w.mask_list(), w.dkmax)
     Pp = iquapi.premerge_positions(P, w.dkmax)
     U = iquapi.short_time_propagator(w.hs_array(), w.dt)
     q = np.asarray(w.q)
     paths = iquapi.initial_paths(w.rho0_array())
-    timed_from = w.dkmax + 1 if timed_from is None else timed_from
     ext, sec = 0, 0.0
-    for t in range(1, steps_total + 1):
-        t0 = time.perf_counter()
+    for t in range(1, t_end + 1):
+        a = time.perf_counter()
         paths, rho, st = iquapi.step(paths, t, U, q, eta, w.dkmax, Pp, w.theta, w.M)
-        dt = time.perf_counter() - t0
-        if t >= timed_from:
+        b = time.perf_counter()
+        if t >= t_from:
             ext += st.extended
-            sec += dt
-    return ext / sec, f"oracle steps 1..{steps_total} of {w.name}, timed steps {timed_from}..{steps_total}"
+            sec += b - a
+    return ext, sec
+
+
+def oracle_on_host_cores(name, t_from, t_end, procs=None):
+    """The oracle as it stands (one thread per process) on every host core:
+    independent replicas of the same bounded sample, started together in
+    spawned processes; the value is the sum of the replicas' rates.  Also
+    one replica alone first (single-core figure).  Returns a dict."""
+    import multiprocessing as mp
+    procs = procs or os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(procs) as pool:
+        e1, s1 = pool.apply(_oracle_sample, ((name, t_from, t_end),))
+        res = pool.map(_oracle_sample, [(name, t_from, t_end)] * procs)
+    ext = sum(r[0] for r in res)
+    return {"value": float(sum(e / s for e, s in res)), "unit": "paths/s", "cores": procs, "kind": "oracle",
+            "single_core": float(e1 / s1), "seconds_per_replica": float(max(s for _, s in res)),
+            "extended_total": int(ext),
+            "sample": f"{procs} replicas (one per host core) of oracle steps 1..{t_end} of {name}, "
+                      f"steps {t_from}..{t_end} timed; value = sum of the replicas' rates"}
 
 
 def main():
@@ -514,34 +599,20 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        # each benchmark step = one oracle propagation step of the workload
-        from oracle import bath, iquapi
-        eta = bath.eta_coefficients(w.bath, w.dt, w.dkmax)
-        P = iquapi.check_mask(w.mask_list(), w.dkmax)
-        Pp = iquapi.premerge_positions(P, w.dkmax)
-        U = iquapi.short_time_propagator(w.hs_array(), w.dt)
-        paths = iquapi.initial_paths(w.rho0_array())
-        t = 0
-        t_start = w.dkmax + 1
-        while t < t_start + args.warmup:
-            t += 1
-            paths, _, _ = iquapi.step(paths, t, U, np.asarray(w.q), eta, w.dkmax, Pp, w.theta, w.M)
-        ext, sec = 0, 0.0
-        for _ in range(args.steps):
-            t += 1
-            a = time.perf_counter()
-            paths, _, st = iquapi.step(paths, t, U, np.asarray(w.q), eta, w.dkmax, Pp, w.theta, w.M)
-            sec += time.perf_counter() - a
-            ext += st.extended
-        v = ext / sec
+        # the oracle as it stands, on every host core (independent replicas,
+        # spawned processes), over the same steps the GPU arm times
+        t_from = args.t0 + args.warmup + 1
+        t_end = t_from + args.steps - 1
+        cb = oracle_on_host_cores(args.workload, t_from, t_end)
+        v = cb["value"]
         line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "paths/s", "n_gpus": args.gpus,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * cb["seconds_per_replica"] / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic", "config": dict(cfg, t0=t_start, precision="fp64", engine="oracle",
+                "data": "synthetic", "config": dict(cfg, precision="fp64", engine="oracle",
                                                      amplitudes="complex128, FP64 throughout (the CPU oracle)",
-                                                     l2="not applicable (host cores)"),
-                "cpu_baseline": {"value": v, "unit": "paths/s", "cores": 1, "kind": "oracle",
-                                 "sample": f"{args.steps} oracle steps after t={t_start + args.warmup}"},
+                                                     l2="not applicable (host cores)",
+                                                     parallelism=f"{cb['cores']} host processes (replicas)"),
+                "cpu_baseline": cb,
                 "e2e": {"value": v, "unit": "paths/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
         return
@@ -565,34 +636,56 @@ def main():
     n = min(len(res["rho"]), len(ref["rho"]))
     rho_err = float(np.abs(res["rho"][:n] - ref["rho"][:n]).max())
     fp64_value = ref["ext"] / (ref["t_ms"] / 1e3)
-    line = {"metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "c64" if args.precision == "c64" else "f64", "data": "synthetic",
-            "config": cfg, "clocks": res["clocks"], "roofline": res["roof"],
-            "e2e": {"value": res["e2e"], "unit": "paths/s", "h2d_bytes_per_step": round(res["h2d"], 2),
-                    "d2h_bytes_per_step": res["d2h"]},
-            "gpu_launches": args.steps * res["kernels_per_step"],
-            "s_per_step": t_ms / args.steps / 1e3,
-            "paths_per_step": {"extended_mean": ext / args.steps / max(1, world),
-                               "kept_last": int(res["stats"][-1][3])},
-            "vs_fp64_gpu": {"fp64_value": fp64_value, "fp64_ms_per_step": ref["t_ms"] / args.steps,
-                            "speedup": value / fp64_value, "rho_max_abs_err": rho_err,
-                            "rho_err_steps": n, "fp64_roofline": ref["roof"], "fp64_e2e": ref["e2e"]}}
-    line["config"]["tuning"] = res["tuning"]
+    err_or, n_or = oracle_error(args.workload, res["rho"])
+    err_or64, _ = oracle_error(args.workload, ref["rho"])
+    head = {"workload": args.workload, "precision": args.precision,
+            args.precision: {"value": value, "ms_per_step": t_ms / args.steps, "roofline": res["roof"],
+                             "rho_max_abs_err_vs_oracle": err_or, "oracle_steps": n_or}}
+    if args.precision != "fp64":
+        head["fp64"] = {"value": fp64_value, "ms_per_step": ref["t_ms"] / args.steps, "roofline": ref["roof"],
+                        "rho_max_abs_err_vs_oracle": err_or64, "oracle_steps": n_or}
+        head["c64"]["rho_max_abs_err_vs_fp64"] = rho_err
+    line = {}
+    # detail blocks first: the end of the line carries the figures the
+    # metric is defined by (each configuration in a few numbers, the
+    # comparison with the plain FP64 path, the oracle on the host cores)
+    configs = []
     if not args.no_more_configs and world == 1:
-        line["more_configs"] = [run_more_config("chain3_structured_dk12", 40, 50, 1 << 26),
-                                run_more_config("tls_ohmic_full_dk13", 13, 10, 1 << 27),
-                                run_more_config("tls_ohmic_full_dk14", 14, 10, 1 << 28, engine="stream")]
+        configs = [run_config("spin_boson_ohmic_dk8", 8, min(args.steps, 80), 1 << 20, precisions=("fp64", "c64")),
+                   run_config("chain3_structured_dk12", 40, 50, 1 << 26),
+                   run_config("tls_ohmic_full_dk13", 13, 10, 1 << 27),
+                   run_config("tls_ohmic_full_dk14", 14, 10, 1 << 28, engine="stream")]
         if args.paper_scale:
-            line["more_configs"] += [run_more_config("tls_ohmic_full_dk15", 15, 5, 1 << 30, engine="stream", fp64=False),
-                                     run_more_config("tls_ohmic_full_dk16", 16, 5, 1 << 32, engine="stream", fp64=False)]
+            configs += [run_config("tls_ohmic_full_dk15", 15, 5, 1 << 30, engine="stream", precisions=("c64",)),
+                        run_config("tls_ohmic_full_dk16", 16, 5, 1 << 32, engine="stream", precisions=("c64",))]
+        line["more_configs"] = configs
     if not args.no_batched and world == 1:
         line["batched_sweep"] = run_batched_sweep()
         line["surrogate"] = run_surrogate()
+    line.update({"metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": args.gpus, "steps": args.steps,
+                 "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+                 "scaling": "weak", "vs_baseline": None, "dtype": "c64" if args.precision == "c64" else "f64",
+                 "data": "synthetic", "config": cfg, "clocks": res["clocks"], "roofline": res["roof"],
+                 "e2e": {"value": res["e2e"], "unit": "paths/s", "h2d_bytes_per_step": 0,
+                         "d2h_bytes_per_step": res["d2h"],
+                         "how": "the timed steps again through the public API, rho(t) to pinned host memory every "
+                                "step; the stored set (the step's input) stays on the device",
+                         "trajectory_value": res["e2e_traj"], "setup_h2d_bytes": res["setup_h2d"]},
+                 "gpu_launches": args.steps * res["kernels_per_step"],
+                 "s_per_step": t_ms / args.steps / 1e3,
+                 "paths_per_step": {"extended_mean": ext / args.steps / max(1, world),
+                                    "kept_last": int(res["stats"][-1][3])}})
+    line["config"]["tuning"] = res["tuning"]
+    g = lambda x: None if x is None else float(f"{x:.3g}")   # noqa: E731
+    line["summary"] = {args.workload: compact(head)}
+    line["summary"].update({c["workload"]: compact(c) for c in configs})
+    line["vs_fp64_gpu"] = {"fp64_value": g(fp64_value), "fp64_ms_per_step": g(ref["t_ms"] / args.steps),
+                           "speedup": g(value / fp64_value), "rho_max_abs_err_vs_fp64": g(rho_err),
+                           "rho_err_steps": n, "rho_max_abs_err_vs_oracle": g(err_or),
+                           "fp64_rho_max_abs_err_vs_oracle": g(err_or64), "oracle_steps": n_or}
     if not args.no_cpu_baseline and world == 1:
-        v, sample = cpu_baseline(W.SPIN_BOSON_STRUCTURED_DK16 if args.workload == "spin_boson_structured_dk16"
-                                 else WORKLOADS[args.workload])
-        line["cpu_baseline"] = {"value": v, "unit": "paths/s", "cores": 1, "kind": "oracle", "sample": sample}
+        name = args.workload
+        line["cpu_baseline"] = oracle_on_host_cores(name, WORKLOADS[name].dkmax + 1, WORKLOADS[name].dkmax + 40)
     print(json.dumps(line))
 
 

@@ -54,6 +54,10 @@ GOLDEN = [
     (W.CHAIN3_STRUCTURED_DK12, 10, "chain3_structured_dk12_rho10.txt"),
     (W.tls_ohmic_full(8), W.tls_ohmic_full(8).steps, "tls_ohmic_full_dk8_rho117.txt"),
     (W.tls_ohmic_full(10), 30, "tls_ohmic_full_dk10_rho30.txt"),
+    # the first 10 steps of the memory-14 model (4^11 stored paths at t = 10);
+    # while the window fills (t < memory) the trajectory does not depend on
+    # the memory length, so these are also the first 10 steps at memory 13
+    (W.tls_ohmic_full(14), 10, "tls_ohmic_full_dk14_rho10.txt"),
 ]
 
 if __name__ == "__main__":
