@@ -131,6 +131,9 @@ struct Params {
     const double2 *etab;               // [dkmax][ndelta][nchunks][256] exp(-delta_d T) tables (FP64 path)
     int ndelta;                        // distinct nonzero q_a - q_b
     float deltaf[12];                  // their values (FP32 path)
+    int qeq;                           // 1: q equally spaced, q_a = q_0 + a s (s != 0)
+    int d_pos, d_neg;                  // ... indices of +s and -s among the differences
+    float qstepf;                      // ... s (FP32 path)
     signed char dsel[16];              // child k -> delta index, -1 when q_a == q_b
     float theta2f;
     double tie_rel;                    // relative window of equal weights (R4)
@@ -470,8 +473,16 @@ struct Expander {
         const unsigned c0 = (unsigned)(rep & ((1u << P.b) - 1u));
         const int pidx = (int)(c0 & ((1u << P.bs) - 1u)) * M + (int)(c0 >> P.bs);
         unsigned keep = 0;
+        // Equally spaced coupling eigenvalues (q_a = q_0 + a s, P.qeq): the
+        // difference of child (a, b) is (a - b) s, so its factor
+        // exp(-(q_a - q_b) H) is E^(a-b) with E = exp(-s H) (or (1/E)^(b-a)):
+        // one exponential and one sine/cosine per group, then products; which
+        // power a child takes is fixed at compile time.  Otherwise one
+        // factor per distinct difference, selected per child.
+        const bool eq = P.qeq != 0;
         if constexpr (C64) {
             float2 Ed[ND];
+            float2 Ep[M], En[M];   // Ep[n] = E^n, En[n] = E^-n (n >= 1)
             if (P.ndelta) {
                 float sx = 0.f, sy = 0.f, cx = 0.f, cy = 0.f, lx = 0.f, ly = 0.f;
                 for (int j = 0; j < P.nchunks; ++j) {
@@ -488,14 +499,28 @@ struct Expander {
                     ly += lo.y;
                 }
                 const float hx = sx + (lx - cx), hy = sy + (ly - cy);
-#pragma unroll
-                for (int d = 0; d < ND; ++d) {
-                    if (d >= P.ndelta) break;
-                    const float zr = -P.deltaf[d] * hx, zi = -P.deltaf[d] * hy;
+                if (eq) {
+                    const float zr = -P.qstepf * hx, zi = -P.qstepf * hy;
                     float sn, cs;
                     sincosf(zi, &sn, &cs);
-                    const float m = expf(zr);
-                    Ed[d] = make_float2(m * cs, m * sn);
+                    const float mp = expf(zr), mn = expf(-zr);
+                    Ep[1] = make_float2(mp * cs, mp * sn);
+                    En[1] = make_float2(mn * cs, -mn * sn);
+#pragma unroll
+                    for (int n = 2; n < M; ++n) {
+                        Ep[n] = cmulf(Ep[n - 1], Ep[1]);
+                        En[n] = cmulf(En[n - 1], En[1]);
+                    }
+                } else {
+#pragma unroll
+                    for (int d = 0; d < ND; ++d) {
+                        if (d >= P.ndelta) break;
+                        const float zr = -P.deltaf[d] * hx, zi = -P.deltaf[d] * hy;
+                        float sn, cs;
+                        sincosf(zi, &sn, &cs);
+                        const float m = expf(zr);
+                        Ed[d] = make_float2(m * cs, m * sn);
+                    }
                 }
             }
             const float2 Sf = to_f2(S);
@@ -508,26 +533,59 @@ struct Expander {
                 const float4 wv = wf[k * MM + pidx];
                 const float lr = Sf.x * wv.z - Sf.y * wv.w, li = Sf.x * wv.w + Sf.y * wv.z;
                 float2 a = make_float2(fmaf(Sf.x, wv.x, fmaf(-Sf.y, wv.y, lr)), fmaf(Sf.x, wv.y, fmaf(Sf.y, wv.x, li)));
-                const int d = P.dsel[k];
-                if (d >= 0) a = cmulf(a, pick(Ed, d));
+                if (P.ndelta) {
+                    if (eq) {
+                        const int n = k / M - k % M;   // a - b
+                        if (n > 0) a = cmulf(a, Ep[n]);
+                        else if (n < 0) a = cmulf(a, En[-n]);
+                    } else {
+                        const int d = P.dsel[k];
+                        if (d >= 0) a = cmulf(a, pick(Ed, d));
+                    }
+                }
                 v[k] = a;
                 if (a.x * a.x + a.y * a.y >= P.theta2f) keep |= 1u << k;
             }
         } else {
             double2 Ed[ND];
+            double2 Ep[M], En[M];
             const int dstride = P.nchunks * kLutEntries;
+            if (eq && P.ndelta) {
+                double2 ep = make_double2(1.0, 0.0), en = make_double2(1.0, 0.0);
+                for (int j = 0; j < P.nchunks; ++j) {
+                    const int idx = j * kLutEntries + (int)key_byte(rep, j);
+                    ep = cmul(ep, tb.et[P.d_pos * dstride + idx]);
+                    en = cmul(en, tb.et[P.d_neg * dstride + idx]);
+                }
+                Ep[1] = ep;
+                En[1] = en;
 #pragma unroll
-            for (int d = 0; d < ND; ++d) {
-                if (d >= P.ndelta) break;
-                double2 e = make_double2(1.0, 0.0);
-                for (int j = 0; j < P.nchunks; ++j) e = cmul(e, tb.et[d * dstride + j * kLutEntries + (int)key_byte(rep, j)]);
-                Ed[d] = e;
+                for (int n = 2; n < M; ++n) {
+                    Ep[n] = cmul(Ep[n - 1], ep);
+                    En[n] = cmul(En[n - 1], en);
+                }
+            } else {
+#pragma unroll
+                for (int d = 0; d < ND; ++d) {
+                    if (d >= P.ndelta) break;
+                    double2 e = make_double2(1.0, 0.0);
+                    for (int j = 0; j < P.nchunks; ++j) e = cmul(e, tb.et[d * dstride + j * kLutEntries + (int)key_byte(rep, j)]);
+                    Ed[d] = e;
+                }
             }
 #pragma unroll
             for (int k = 0; k < MM; ++k) {
                 double2 a = cmul(S, w[k * MM + pidx]);
-                const int d = P.dsel[k];
-                if (d >= 0) a = cmul(a, pick(Ed, d));
+                if (P.ndelta) {
+                    if (eq) {
+                        const int n = k / M - k % M;
+                        if (n > 0) a = cmul(a, Ep[n]);
+                        else if (n < 0) a = cmul(a, En[-n]);
+                    } else {
+                        const int d = P.dsel[k];
+                        if (d >= 0) a = cmul(a, pick(Ed, d));
+                    }
+                }
                 v[k] = a;
                 if (a.x * a.x + a.y * a.y >= P.theta2) keep |= 1u << k;
             }
@@ -2315,6 +2373,29 @@ int distinct_deltas(int M, const double *q, std::vector<double> *vals, signed ch
     return (int)v.size();
 }
 
+// Equally spaced coupling eigenvalues q_a = q_0 + a s (s != 0, exact in
+// FP64): the children's influence factors are powers of exp(-s H).  Sets
+// P.qeq and the indices of +s and -s among the distinct differences.
+void set_equispaced(Params &P, int M, const double *q, const double *deltas, int nd) {
+    P.qeq = 0;
+    P.d_pos = P.d_neg = 0;
+    P.qstepf = 0.f;
+    const double s = q[1] - q[0];
+    if (s == 0.0) return;
+    for (int a = 0; a < M; ++a)
+        if (q[a] - q[0] != (double)a * s) return;
+    int ip = -1, in = -1;
+    for (int k = 0; k < nd; ++k) {
+        if (deltas[k] == s) ip = k;
+        if (deltas[k] == -s) in = k;
+    }
+    if (ip < 0 || in < 0) return;
+    P.qeq = 1;
+    P.d_pos = ip;
+    P.d_neg = in;
+    P.qstepf = (float)s;
+}
+
 Layout make_layout(const qp_config *c) {
     Layout L{};
     const long long mp = c->max_paths;
@@ -2798,6 +2879,7 @@ qp_status qp_create(const qp_config *cfg, void *d_workspace, size_t bytes, void 
         signed char dsel[16];
         for (int k = 0; k < 16; ++k) dsel[k] = -1;
         P.ndelta = distinct_deltas(M, cfg->q, &dv, dsel);
+        set_equispaced(P, M, cfg->q, dv.data(), P.ndelta);
         for (int k = 0; k < 16; ++k) P.dsel[k] = dsel[k];
         for (int k = 0; k < kMaxDelta; ++k) P.deltaf[k] = k < P.ndelta ? (float)dv[k] : 0.f;
         c->deltas = dv;
@@ -3724,6 +3806,7 @@ extern "C" qp_status qp_step_noalloc(const qp_config *cfg, const double *eta_re,
             }
         su.ndelta = nd;
         P.ndelta = nd;
+        set_equispaced(P, M, cfg->q, su.deltas, nd);
         for (int k = 0; k < 16; ++k) P.dsel[k] = dsel[k];
         for (int k = 0; k < kMaxDelta; ++k) P.deltaf[k] = k < nd ? (float)su.deltas[k] : 0.f;
     }

