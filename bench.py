@@ -401,7 +401,7 @@ def run_surrogate(T_train=100, T_long=1000, L=32, epochs=2000):
     them against the plain path at checkpoints; times of both."""
     import torch
     from paper_2506_03127_gb300 import batch_from_workloads
-    from paper_2506_03127_gb300.surrogate import Surrogate, bath_features, judge
+    from paper_2506_03127_gb300.surrogate import Surrogate, bath_features, judge, truncated_memory_baselines
 
     ws = W.resonance_sweep(64)
     p = batch_from_workloads(ws, precision="c64", max_paths=1 << 23)
@@ -426,6 +426,20 @@ def run_surrogate(T_train=100, T_long=1000, L=32, epochs=2000):
     rs = s.rollout(rp[:L].transpose(1, 0, 2, 3), par[48:], T_long)
     t_sur = time.perf_counter() - t0
     errs, raw, fb = judge(rs, rp, (200, 400, 600, 800, 999))
+    # the path update's own cheaper settings on the same instances: shorter
+    # memory (1 = the Markov map) at the same filter, against the full path
+    base = truncated_memory_baselines(ws[48:], T_long, rp, (200, 400, 600, 800, 999))
+    err_s = max(raw.values())
+    us_s = 1e6 * t_sur / (T_long - L)
+    faster = [dk for dk, b in base.items() if b["us_per_step"] <= us_s]
+    as_accurate = [dk for dk, b in base.items() if b["err_max"] <= err_s]
+    outcome = (f"surrogate {us_s:.1f} us/step at max error {err_s:.3f}; "
+               + (f"memory <= {max(faster)} is as fast but its error is >= "
+                  f"{min(base[d]['err_max'] for d in faster):.3f}; " if faster else "no shorter memory is as fast; ")
+               + (f"memory {min(as_accurate)} is as accurate at {base[min(as_accurate)]['us_per_step']:.1f} us/step"
+                  if as_accurate else f"no memory up to {max(base)} is as accurate "
+                                      f"(best {min(b['err_max'] for b in base.values()):.3f}); the full memory 8 "
+                                      f"takes {1e6 * t_plain / (T_long - 1):.1f} us/step"))
     return {"network": "MLP %d-256-256-8, tanh, BF16 weights/activations, FP32 accumulation" % (8 * L + 2),
             "train": {"instances": 48, "steps": T_train, "windows": 48 * (T_train + 1 - L), "epochs": epochs,
                       "seconds": round(t_fit, 3), "loss_first": hist[0][1], "loss_last": hist[-1][1]},
@@ -436,7 +450,10 @@ def run_surrogate(T_train=100, T_long=1000, L=32, epochs=2000):
             "speedup_note": "fallback instances are charged the plain path's time",
             "rho_max_abs_err_at_checkpoints": {str(k): round(v, 5) for k, v in errs.items()},
             "rho_max_abs_err_raw_surrogate": {str(k): round(v, 5) for k, v in raw.items()},
-            "fallback_instances": int(fb.sum())}
+            "fallback_instances": int(fb.sum()),
+            "plain_shorter_memory": {str(dk): {"us_per_step": round(b["us_per_step"], 1), "err_max": round(b["err_max"], 4)}
+                                     for dk, b in base.items()},
+            "matched_comparison": outcome}
 
 
 def aggregate_over_ranks(t_ms, units):

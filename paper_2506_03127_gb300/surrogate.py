@@ -157,3 +157,36 @@ def judge(rho_sur, rho_plain, checkpoints, trace_tol=0.05, eig_tol=0.02):
         d = np.abs(rho_sur[:, c] - rho_plain[c]).reshape(n, -1).max(axis=1)
         combined[int(c)] = float(np.where(fallback, 0.0, d).max())
     return combined, raw, fallback
+
+
+def truncated_memory_baselines(ws, T, rho_ref, checkpoints, dks=(1, 2, 3, 4, 5, 6, 7), precision="c64",
+                               max_paths=1 << 22):
+    """The cheaper settings of the path update itself, for the comparison
+    the surrogate has to win: the same instances propagated with a shorter
+    memory (Delta k_max = dk; dk = 1 is the Markov map), each batched and
+    timed over the T - 1 steps (CUDA-synchronised wall time), with the
+    largest |rho - rho_ref| over instances and entries at each checkpoint.
+    rho_ref [T][n][2][2] from the full-memory path.  Returns {dk: dict}."""
+    import time
+    from dataclasses import replace
+
+    import torch
+
+    from . import batch_from_workloads
+    out = {}
+    for dk in dks:
+        wsx = [replace(w, dkmax=dk, mask=None) for w in ws]
+        q = batch_from_workloads(wsx, precision=precision, max_paths=max_paths)
+        q.step(3)      # graphs captured before timing
+        q.sync()
+        q.set_rho0(wsx[0].rho0_array())
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        q.step(T - 1)
+        q.sync()
+        dt = time.perf_counter() - t0
+        r = q.rho(0, T)
+        q.close()
+        errs = {int(c): float(np.abs(r[c] - rho_ref[c]).max()) for c in checkpoints}
+        out[dk] = {"seconds": dt, "us_per_step": 1e6 * dt / (T - 1), "err_max": max(errs.values()), "errors": errs}
+    return out

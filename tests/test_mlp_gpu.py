@@ -38,21 +38,46 @@ def test_forward_matches_oracle(d_in, w, d_out, B):
     net.close()
 
 
+def _grad_magnitudes(p, x, t, d_in, w, d_out):
+    """Per parameter, the sum of the magnitudes of the terms the oracle adds
+    for its gradient, (|A|^T |B|)_ij over the same BF16-rounded operands
+    (for a bias: the sum of |dh| over the batch)."""
+    W1, b1, W2, b2, W3, b3 = O.unpack(p, d_in, w, d_out)
+    r = O.bf16_round
+    y, (h1, h2) = O.forward(p, x, d_in, w, d_out, bf16=True)
+    B = x.shape[0]
+    dy = 2.0 * (y - t) / (B * d_out)
+    dh2 = (r(dy) @ r(W3).T) * (1.0 - h2 * h2)
+    dh1 = (r(dh2) @ r(W2).T) * (1.0 - h1 * h1)
+    a = np.abs
+    return O.pack([a(r(x)).T @ a(r(dh1)), a(dh1).sum(axis=0), a(r(h1)).T @ a(r(dh2)), a(dh2).sum(axis=0),
+                   a(r(h2)).T @ a(r(dy)), a(dy).sum(axis=0)])
+
+
 @pytest.mark.parametrize("d_in,w,d_out,B", [(258, 256, 8, 77), (7, 5, 3, 13), (64, 96, 8, 200)])
 def test_gradients_match_oracle(d_in, w, d_out, B):
+    """Element by element: both sides multiply the same BF16 operands; the
+    kernels accumulate in FP32, and a back-propagated operand (dy, dh2, dh1)
+    that the kernels form in FP32 may round to the neighbouring BF16 value,
+    one unit (2^-8 relative) from the oracle's.  Every gradient element is
+    therefore within 2^-8 of the sum of its terms' magnitudes (all terms
+    flipped, the worst case) plus FP32 accumulation; a wrong row or column
+    would miss by the size of the terms."""
     net, p, x, t, xd, td = _setup(d_in, w, d_out, B, 2)
     loss, g = net.gradients(xd, td)
     lo, go = O.loss_and_grads(p, x, t, d_in, w, d_out, bf16=True)
     assert abs(loss - lo) <= 1e-3 * lo
     g = g.astype(np.float64)
-    # per parameter block: W1 b1 W2 b2 W3 b3; BF16 rounding of the back-
-    # propagated terms bounds the agreement at ~2^-8 relative
-    sizes = [d_in * w, w, w * w, w, w * d_out, d_out]
-    o = 0
-    for n in sizes:
-        a, b = g[o:o + n], go[o:o + n]
-        assert np.linalg.norm(a - b) <= 1.5e-2 * np.linalg.norm(b) + 1e-9, (n, np.linalg.norm(a - b) / np.linalg.norm(b))
-        o += n
+    mag = _grad_magnitudes(p, x, t, d_in, w, d_out)
+    bound = (2.0 ** -8 + B * 2.0 ** -23) * mag + 1e-12
+    worst = np.max(np.abs(g - go) / bound)
+    assert worst <= 1.0, worst
+    # most elements agree to the accumulation alone (flips are rare): within
+    # twice the batch times 2^-23 of their terms' magnitude (the tensor
+    # cores' FP32 accumulation is not rounded to nearest at every addition)
+    close = np.abs(g - go) <= B * 2.0 ** -22 * mag + 1e-12
+    print(f"gradients: worst {worst:.3f} of the bound; {close.mean():.4f} within the accumulation alone")
+    assert close.mean() >= 0.9
     net.close()
 
 

@@ -8,7 +8,10 @@ t = 1000 and judges the surrogate at the checkpoints 200, 400, ..., 1000.
 The test asserts the surrogate is faster than the plain path over the same
 steps, stays within the stated error, and keeps rho a density matrix
 (Hermitian and positive semidefinite by projection), so that no instance
-falls back to the plain path.
+falls back to the plain path.  Against the path update's own cheaper
+settings (memory 1, the Markov map, to 7): every setting about as fast as
+the surrogate is at least twice less accurate, and every setting as
+accurate is at least twice slower.
 """
 import time
 
@@ -26,7 +29,7 @@ if not torch.cuda.is_available():  # pragma: no cover - CPU container
 from paper_2506_03127_gb300 import batch_from_workloads, build  # noqa: E402
 
 build.build()
-from paper_2506_03127_gb300.surrogate import Surrogate, bath_features, judge  # noqa: E402
+from paper_2506_03127_gb300.surrogate import Surrogate, bath_features, judge, truncated_memory_baselines  # noqa: E402
 
 T_TRAIN, T_LONG, L = 100, 1000, 32
 CHECKPOINTS = (200, 400, 600, 800, 999)
@@ -62,3 +65,16 @@ def test_surrogate_gain_and_error_at_checkpoints():
     np.testing.assert_allclose(rs, np.conj(np.swapaxes(rs, 2, 3)), atol=1e-7)   # Hermitian by projection
     ev = np.linalg.eigvalsh(rs[:, L:])
     assert ev.min() >= -1e-6, ev.min()   # positive semidefinite by projection
+    # against the path update's own cheaper settings (shorter memory, the
+    # Markov map at memory 1): the surrogate must be more accurate than each
+    # setting that is not slower than it, and faster than each setting that
+    # is as accurate as it
+    base = truncated_memory_baselines(ws[48:], T_LONG, rp, CHECKPOINTS)
+    err_s = max(raw.values())
+    for dk, b in base.items():
+        print(f"memory {dk}: {b['us_per_step']:.1f} us/step, error {b['err_max']:.4f}; "
+              f"surrogate {1e6 * t_sur / (T_LONG - L):.1f} us/step, error {err_s:.4f}")
+        if b["seconds"] <= 2 * t_sur:
+            assert err_s < b["err_max"] / 2, (dk, err_s, b)
+        if b["err_max"] <= err_s:
+            assert t_sur < b["seconds"] / 2, (dk, t_sur, b)
