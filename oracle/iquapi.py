@@ -34,6 +34,11 @@ Readings where the paper is silent:
      concurrent insert leaves the choice among equal weights open).
   R5 filter: a child is kept when |amp|^2 >= theta^2, applied before rho.
 
+The original post-merging order (Sec. 2.1, Scheme macgic; step_post) is the
+comparison the paper makes: every stored path is extended with its own
+history and the children are merged on the mask P itself after the step;
+the peak intermediate set is M^2 times the merged one.
+
 Packed key used for the tie-break order and for exporting paths: with
 bs = max(1, ceil(log2 M)) bits per state and b = 2 bs bits per point, window
 position p (0 = newest) occupies bits [b p, b p + b): s+ in the low bs bits,
@@ -188,9 +193,65 @@ def step(paths: Paths, t: int, U, q, eta, dkmax: int, Pp, theta: float, M: int):
     return out, rho, st
 
 
+def merge_on(paths: Paths, positions, M: int):
+    """Merge the paths identical on the given window positions: one entry per
+    group, the member of largest |amp| (reading R4) with the summed
+    amplitude.  Returns (merged Paths, near-tie count)."""
+    rsp, rsm, S, near_tie = premerge(paths, positions, M)
+    return Paths(sp=rsp, sm=rsm, amp=S), near_tie
+
+
+def step_post(paths: Paths, t: int, U, q, eta, dkmax: int, P, theta: float, M: int):
+    """One step t-1 -> t of the original post-merging order (Sec. 2.1, Scheme
+    macgic): every stored path is extended by the M^2 new points with its
+    own history (routine propagation()), children below the filter are
+    dropped, rho(t) sums the survivors by end point, and the unmerged set
+    Omega(t, unmerged) is then merged on the mask P itself (sorting() and
+    merging()) once its window is full (t >= dkmax - 1; reading R3: no
+    merging while the window fills).  Returns (merged paths, rho(t),
+    stats): groups = paths extended, kept = children surviving the filter
+    (the unmerged intermediate set), merged = stored paths after merging."""
+    n_act = min(t, dkmax)
+    # the own history of every stored path: lags d = 1 .. n_act-1
+    H = np.zeros(paths.amp.size, dtype=np.complex128)
+    for d in range(1, n_act):
+        H += eta[d] * q[paths.sp[:, d - 1]] - np.conj(eta[d]) * q[paths.sm[:, d - 1]]
+    L_child = min(t + 1, dkmax)
+    rho = np.zeros((M, M), dtype=np.complex128)
+    new_sp, new_sm, new_amp = [], [], []
+    near_theta = 0
+    th2 = theta * theta
+    for a in range(M):
+        for b in range(M):
+            prop = U[a, paths.sp[:, 0]] * np.conj(U[b, paths.sm[:, 0]])
+            phase = -(q[a] - q[b]) * (H + eta[0] * q[a] - np.conj(eta[0]) * q[b])
+            child = paths.amp * prop * np.exp(phase)
+            w2 = child.real ** 2 + child.imag ** 2
+            keep = w2 >= th2
+            if th2 > 0:
+                near_theta += int(np.count_nonzero(np.abs(w2 - th2) <= 2e-12 * th2))
+            rho[a, b] = child[keep].sum()
+            k = int(np.count_nonzero(keep))
+            new_sp.append(np.hstack([np.full((k, 1), a, dtype=np.int64), paths.sp[keep, :L_child - 1]]))
+            new_sm.append(np.hstack([np.full((k, 1), b, dtype=np.int64), paths.sm[keep, :L_child - 1]]))
+            new_amp.append(child[keep])
+    unmerged = Paths(sp=np.vstack(new_sp), sm=np.vstack(new_sm), amp=np.concatenate(new_amp))
+    near_tie = 0
+    if L_child == dkmax and unmerged.amp.size:
+        out, near_tie = merge_on(unmerged, sorted(P), M)
+    else:
+        out = unmerged
+    st = StepStats(t=t, groups=paths.amp.size, extended=paths.amp.size * M * M, kept=unmerged.amp.size,
+                   near_tie=near_tie, near_theta=near_theta)
+    st.merged = out.amp.size
+    return out, rho, st
+
+
 def propagate(M: int, q, hs, dt: float, eta, dkmax: int, mask, theta: float,
-              rho0, steps: int, keep_stats: bool = True) -> Result:
-    """Run `steps` propagation steps from rho0; rho[t] for t = 0 .. steps."""
+              rho0, steps: int, keep_stats: bool = True, scheme: str = "pre") -> Result:
+    """Run `steps` propagation steps from rho0; rho[t] for t = 0 .. steps.
+    scheme "pre": the pre-merging order of Sec. 3.1 (step); "post": the
+    original post-merging order of Sec. 2.1 (step_post)."""
     q = np.asarray(q, dtype=np.float64)
     eta = np.asarray(eta, dtype=np.complex128)
     if eta.size < dkmax:
@@ -202,8 +263,13 @@ def propagate(M: int, q, hs, dt: float, eta, dkmax: int, mask, theta: float,
     paths = initial_paths(rho0)
     rhos = [rho0.copy()]
     stats = []
+    if scheme not in ("pre", "post"):
+        raise ValueError("scheme must be 'pre' or 'post'")
     for t in range(1, steps + 1):
-        paths, rho, st = step(paths, t, U, q, eta, dkmax, Pp, theta, M)
+        if scheme == "pre":
+            paths, rho, st = step(paths, t, U, q, eta, dkmax, Pp, theta, M)
+        else:
+            paths, rho, st = step_post(paths, t, U, q, eta, dkmax, P, theta, M)
         rhos.append(rho)
         if keep_stats:
             stats.append(st)

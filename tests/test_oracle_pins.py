@@ -342,6 +342,55 @@ def test_representative_is_largest_weight_then_smallest_key():
     assert int(iquapi.packed_keys(rsp, rsm, M)[0]) == want
 
 
+# ---------------------------------------------------------------- post-merging order
+
+@pytest.mark.parametrize("M,dkmax,N,seed", [(2, 1, 5, 1), (2, 2, 5, 2), (2, 3, 6, 3), (2, 4, 5, 4),
+                                            (3, 1, 3, 6), (3, 2, 4, 7), (3, 3, 4, 8)])
+def test_post_merging_equals_brute_force_without_mask(M, dkmax, N, seed):
+    """Without a mask the post-merge joins only children identical on the
+    whole window, i.e. of parents that differ in the departing point alone,
+    whose histories (lags < dkmax) are equal: the exact path sum."""
+    c = W.random_case(seed, M, dkmax)
+    rb = brute.rho_by_enumeration(M, c["q"], c["hs"], c["dt"], c["eta"], dkmax, c["rho0"], N)
+    r = iquapi.propagate(M, c["q"], c["hs"], c["dt"], c["eta"], dkmax, None, 0.0, c["rho0"], N, scheme="post")
+    np.testing.assert_allclose(r.rho[N], rb, rtol=0, atol=2e-14)
+    # the merged set holds at most one path per distinct window
+    assert all(st.merged <= (M * M) ** min(st.t + 1, dkmax) for st in r.stats)
+
+
+@pytest.mark.parametrize("mask,dkmax", [((0, 1, 2, 4), 6), ((0, 1), 5), ((0, 1, 2, 3, 4, 5, 7), 9)])
+def test_post_merging_rabi_at_zero_coupling(mask, dkmax):
+    delta, dt, steps = 1.0, 0.25, 24
+    hs = np.array([[0, delta / 2], [delta / 2, 0]], dtype=complex)
+    r = iquapi.propagate(2, [1.0, -1.0], hs, dt, np.zeros(dkmax), dkmax, mask, 0.0,
+                         np.array([[1, 0], [0, 0]], dtype=complex), steps, scheme="post")
+    t = dt * np.arange(steps + 1)
+    np.testing.assert_allclose((r.rho[:, 0, 0] - r.rho[:, 1, 1]).real, np.cos(delta * t), atol=1e-13)
+    np.testing.assert_allclose(r.rho[:, 0, 1], 0.5j * np.sin(delta * t), atol=1e-13)
+
+
+@pytest.mark.parametrize("M,mask", [(2, (0, 1, 2, 5)), (3, (0, 1, 3))])
+def test_post_merging_conserves_trace_and_bounds_the_merged_set(M, mask):
+    q, hs, eta, rho0 = _structured_case(M, 8 if M == 2 else 5)
+    dk = 8 if M == 2 else 5
+    r = iquapi.propagate(M, q, hs, 0.2, eta, dk, mask, 0.0, rho0, 16, scheme="post")
+    tr = np.trace(r.rho, axis1=1, axis2=2)
+    np.testing.assert_allclose(tr, np.ones_like(tr), atol=1e-13)
+    full = [st for st in r.stats if st.t + 1 >= dk]
+    assert full and all(st.merged <= (M * M) ** len(mask) for st in full)
+
+
+def test_post_merging_filtered_markov_map():
+    c = FILTER_PIN
+    U = _tls_propagator(c["delta"], c["dt"])
+    hs = np.array([[0, c["delta"] / 2], [c["delta"] / 2, 0]], dtype=complex)
+    rho0 = np.array(c["rho0"], dtype=complex)
+    want, _, _ = filtered_markov(U, np.array(c["q"]), c["e0"], c["theta"], rho0, c["steps"])
+    r = iquapi.propagate(2, c["q"], hs, c["dt"], np.array([c["e0"]]), 1, None, c["theta"], rho0, c["steps"],
+                         scheme="post")
+    assert np.abs(r.rho - want).max() <= 1e-14
+
+
 # ---------------------------------------------------------------- planted mistakes
 
 MUTATIONS = {
@@ -409,3 +458,48 @@ def test_planted_mistake_is_caught(name):
 
 def test_unmutated_oracle_passes_mutation_harness():
     assert _pins_pass(iquapi)
+
+
+POST_MUTATIONS = {
+    "post: own history index off by one": ("q[paths.sp[:, d - 1]] - np.conj(eta[d]) * q[paths.sm[:, d - 1]]",
+                                           "q[paths.sp[:, d]] - np.conj(eta[d]) * q[paths.sm[:, d]]"),
+    "post: merged on one position too few": ("out, near_tie = merge_on(unmerged, sorted(P), M)",
+                                             "out, near_tie = merge_on(unmerged, sorted(P)[:-1], M)"),
+    "post: never merged": ("if L_child == dkmax and unmerged.amp.size:", "if False:"),
+    "post: backward branch not conjugated": ("prop = U[a, paths.sp[:, 0]] * np.conj(U[b, paths.sm[:, 0]])",
+                                             "prop = U[a, paths.sp[:, 0]] * U[b, paths.sm[:, 0]]"),
+    "post: rho summed before the filter": ("            rho[a, b] = child[keep].sum()\n            k = int(np.count_nonzero(keep))\n            new_sp.append(np.hstack([np.full",
+                                           "            rho[a, b] = child.sum()\n            k = int(np.count_nonzero(keep))\n            new_sp.append(np.hstack([np.full"),
+}
+
+
+def _post_pins_pass(mod):
+    try:
+        for (M, dkmax, N, seed) in [(2, 3, 6, 3), (3, 2, 4, 7)]:
+            c = W.random_case(seed, M, dkmax)
+            rb = brute.rho_by_enumeration(M, c["q"], c["hs"], c["dt"], c["eta"], dkmax, c["rho0"], N)
+            r = mod.propagate(M, c["q"], c["hs"], c["dt"], c["eta"], dkmax, None, 0.0, c["rho0"], N, scheme="post")
+            if np.abs(r.rho[N] - rb).max() > 2e-14:
+                return False
+            if any(st.merged > (M * M) ** min(st.t + 1, dkmax) for st in r.stats):
+                return False
+        c = FILTER_PIN
+        hs = np.array([[0, c["delta"] / 2], [c["delta"] / 2, 0]], dtype=complex)
+        rho0 = np.array(c["rho0"], dtype=complex)
+        want, _, _ = filtered_markov(_tls_propagator(c["delta"], c["dt"]), np.array(c["q"]), c["e0"], c["theta"],
+                                     rho0, c["steps"])
+        r = mod.propagate(2, c["q"], hs, c["dt"], np.array([c["e0"]]), 1, None, c["theta"], rho0, c["steps"],
+                          scheme="post")
+        return np.abs(r.rho - want).max() <= 1e-14
+    except Exception:
+        return False
+
+
+@pytest.mark.parametrize("name", sorted(POST_MUTATIONS))
+def test_planted_post_merging_mistake_is_caught(name):
+    old, new = POST_MUTATIONS[name]
+    assert not _post_pins_pass(_mutant(old, new)), f"pins missed: {name}"
+
+
+def test_unmutated_oracle_passes_post_merging_harness():
+    assert _post_pins_pass(iquapi)
