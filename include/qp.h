@@ -101,7 +101,25 @@ typedef struct {
                               eta (qp_set_eta_instance).  The instance index is
                               stored above the path bits of the key, so
                               b*dkmax + ceil(log2 n_inst) <= 64.               */
+    int scheme;            /* QP_PREMERGE (0) or QP_POSTMERGE: the order of merging
+                              and propagation (see below)                      */
 } qp_config;
+
+/* Order of merging and propagation.
+ *   QP_PREMERGE  the pre-merging order of Sec. 3.1: the stored set is merged on
+ *                the shifted mask P' before it is extended (the engines of
+ *                qp_config.engine).
+ *   QP_POSTMERGE the original order of Sec. 2.1 (Scheme macgic): every stored
+ *                path is extended by its M^2 children with its own history, the
+ *                survivors of the filter form the unmerged set Omega(t,
+ *                unmerged), which is sorted by its masked key (stable radix sort
+ *                on the device) and merged on the mask P itself once the window
+ *                is full: every run of equal masked keys becomes one stored path,
+ *                the child of largest weight with the run's summed amplitude.
+ *                max_paths is then the capacity of the unmerged set (M^2 times
+ *                the stored set at most); single problems only (n_inst <= 1);
+ *                qp_config.engine is ignored; graph launches only.            */
+enum { QP_PREMERGE = 0, QP_POSTMERGE = 1 };
 
 /* Spectral density J(w) = (pi/2) ohmic_alpha w exp(-w/ohmic_wc)
  *                       + the resonance of Eq. sharpSD with Omega = res_w0,
@@ -116,9 +134,14 @@ typedef struct {
 
 typedef struct {
     int64_t t;             /* time step index of the stored set              */
-    int64_t groups;        /* parents of the step (entries after pre-merge)  */
+    int64_t groups;        /* parents of the step (entries after pre-merge;
+                              post-merging: the stored paths extended)       */
     int64_t extended;      /* children generated, groups * M^2               */
-    int64_t kept;          /* children surviving the filter = stored paths   */
+    int64_t kept;          /* stored paths after the step (pre-merging: the
+                              children surviving the filter; post-merging:
+                              the merged set)                                */
+    int64_t intermediate;  /* largest set of the step: pre-merging = kept;
+                              post-merging: the unmerged survivors           */
 } qp_step_stats;
 
 /* Launch shape and table size of the step (qp_set_tuning / qp_autotune). */

@@ -36,7 +36,8 @@ class Propagator:
     """One propagation context: owns a device workspace tensor and a stream."""
 
     def __init__(self, M, dkmax, dt, q, hs, theta=0.0, precision="fp64", engine="auto",
-                 max_paths=1 << 20, max_groups=0, rho_history=4096, device=None, stream=None, n_inst=1):
+                 max_paths=1 << 20, max_groups=0, rho_history=4096, device=None, stream=None, n_inst=1,
+                 scheme="pre"):
         import torch
         from . import abi
         if not torch.cuda.is_available():
@@ -46,8 +47,9 @@ class Propagator:
         self.n_inst = n_inst
         prec = {"fp64": abi.QP_FP64, "c64": abi.QP_C64}[precision]
         eng = {"auto": abi.QP_ENGINE_AUTO, "hash": abi.QP_ENGINE_HASH, "stream": abi.QP_ENGINE_STREAM}[engine]
+        sch = {"pre": abi.QP_PREMERGE, "post": abi.QP_POSTMERGE}[scheme]
         self._cfg, self._keep = abi.make_config(M, dkmax, dt, q, hs, theta, prec, eng, max_paths, max_groups,
-                                                rho_history, n_inst)
+                                                rho_history, n_inst, sch)
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.Stream(self.device)

@@ -18,6 +18,7 @@ QP_OK, QP_ERR_ARG, QP_ERR_OOM, QP_ERR_CUDA, QP_ERR_CAPACITY, QP_ERR_TIMEOUT, QP_
 QP_FP64, QP_C64 = 0, 1
 QP_ENGINE_AUTO, QP_ENGINE_HASH, QP_ENGINE_STREAM = 0, 1, 2
 QP_LAUNCH_GRAPH, QP_LAUNCH_PERSISTENT = 0, 1
+QP_PREMERGE, QP_POSTMERGE = 0, 1
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int)
@@ -30,7 +31,7 @@ class qp_config(ctypes.Structure):
                 ("q", _dp), ("hs_re", _dp), ("hs_im", _dp),
                 ("precision", ctypes.c_int), ("engine", ctypes.c_int), ("theta", ctypes.c_double),
                 ("max_paths", ctypes.c_int64), ("max_groups", ctypes.c_int64), ("rho_history", ctypes.c_int),
-                ("n_inst", ctypes.c_int)]
+                ("n_inst", ctypes.c_int), ("scheme", ctypes.c_int)]
 
 
 class qp_tuning(ctypes.Structure):
@@ -49,7 +50,7 @@ class qp_bath(ctypes.Structure):
 
 class qp_step_stats(ctypes.Structure):
     _fields_ = [("t", ctypes.c_int64), ("groups", ctypes.c_int64), ("extended", ctypes.c_int64),
-                ("kept", ctypes.c_int64)]
+                ("kept", ctypes.c_int64), ("intermediate", ctypes.c_int64)]
 
 
 class QPError(RuntimeError):
@@ -141,14 +142,14 @@ def check(status, ctx=None):
 
 
 def make_config(M, dkmax, dt, q, hs, theta=0.0, precision=QP_FP64, engine=QP_ENGINE_AUTO,
-                max_paths=1 << 20, max_groups=0, rho_history=4096, n_inst=1):
+                max_paths=1 << 20, max_groups=0, rho_history=4096, n_inst=1, scheme=QP_PREMERGE):
     """qp_config plus the numpy arrays it points into (keep both alive)."""
     q = _arr(q)
     hs = np.asarray(hs, dtype=np.complex128)
     hre, him = _arr(hs.real), _arr(hs.imag)
     cfg = qp_config(M=M, dkmax=dkmax, dt=dt, q=_ptr(q), hs_re=_ptr(hre), hs_im=_ptr(him),
                     precision=precision, engine=engine, theta=theta, max_paths=max_paths,
-                    max_groups=max_groups, rho_history=rho_history, n_inst=n_inst)
+                    max_groups=max_groups, rho_history=rho_history, n_inst=n_inst, scheme=scheme)
     return cfg, (q, hre, him)
 
 
@@ -271,7 +272,7 @@ def qp_test_widen(in_ptr: int, out_ptr: int, n: int, stream: int = 0):
 def qp_read_stats(ctx, t0: int, count: int):
     arr = (qp_step_stats * count)()
     check(lib.qp_read_stats(ctx, t0, count, arr), ctx)
-    return [(s.t, s.groups, s.extended, s.kept) for s in arr]
+    return [(s.t, s.groups, s.extended, s.kept, s.intermediate) for s in arr]
 
 
 def qp_export_paths(ctx, cap: int):

@@ -94,14 +94,16 @@ struct __align__(128) DevState {
     unsigned long long reg_done;      // stream engine: tn + 1 when the regular kernel took step tn, else 0
     unsigned long long rho_pending;   // stream engine: step whose block partials of rho are not summed yet (0: none)
     unsigned int rho_nblk;            // ... and the blocks that wrote them
-    unsigned int pad3;
+    unsigned int post_bits;           // post-merging: significant bits of the running step's sort key
+    unsigned long long post_n;        // post-merging: unmerged children of the running step
+    unsigned long long scan_total;    // total of the last multi-block scan
     unsigned int bar_count;           // grid barrier of the persistent kernel: arrivals
     unsigned int pad1[31];
     unsigned int bar_gen;             // generation (own cache line)
     unsigned int pad2[31];
 };
 
-struct StepRec { long long t, groups, extended, kept; };
+struct StepRec { long long t, groups, extended, kept, inter; };
 
 struct Params {
     int M, bs, b, dkmax;
@@ -164,6 +166,18 @@ struct Params {
     unsigned long long *tile_state;    // [M*M][max_tiles] look-back words (a bucket's tiles contiguous)
     long long max_tiles;
     StepRec *stats_ring;               // [rho_hist]
+    // post-merging engine (the original order, Sec. 2.1): run_* compress the
+    // mask P itself instead of P'
+    int post;                          // 1: merge the children after the step
+    int post_bits_full;                // bits of the sort key once the window is full
+    int post_compress;                 // 1: runs of P packed (b |P| bits); 0: key & pmask itself
+    unsigned long long *ckeys;         // [max_paths] unmerged children of the step
+    void *camps;
+    unsigned long long *skey[2];       // [max_paths] sort keys, by pass parity
+    unsigned int *sidx[2];             // [max_paths] child index carried through the sort
+    unsigned int *rs_hist;             // [256][chunks] digit counts per chunk, scanned in place
+    unsigned int *rs_part;             // block partials of the multi-block scan
+    unsigned int *rbk_heads;           // [chunks] run heads per chunk, scanned in place
     DevState *st;
 };
 
@@ -652,7 +666,8 @@ __device__ __forceinline__ void block_rho_partial(const typename std::conditiona
 // n_inst * (M*M + 1) double2).
 template <int M, bool C64, int NT, bool BATCH>
 __device__ __forceinline__ void phase_expand(const Params &P, unsigned long long t, unsigned long long n, bool merge,
-                                             unsigned long long *cnt_out, double2 *part) {
+                                             unsigned long long *cnt_out, double2 *part,
+                                             unsigned long long *keys_dst = nullptr, void *amps_dst = nullptr) {
     using X = Expander<M, C64>;
     using AmpT = typename X::AmpT;
     constexpr int MM = M * M;
@@ -664,8 +679,10 @@ __device__ __forceinline__ void phase_expand(const Params &P, unsigned long long
     const unsigned long long wmask = (P.b * L_child >= 64) ? ~0ull : ((1ull << (P.b * L_child)) - 1ull);
     const unsigned long long *keys_in = P.keys[t & 1];
     const AmpT *amps_in = static_cast<const AmpT *>(P.amps[t & 1]);
-    unsigned long long *keys_out = P.keys[tn & 1];
-    AmpT *amps_out = static_cast<AmpT *>(P.amps[tn & 1]);
+    // survivors go to the other ping-pong buffer, or where the caller says
+    // (the post-merging engine's unmerged buffer)
+    unsigned long long *keys_out = keys_dst ? keys_dst : P.keys[tn & 1];
+    AmpT *amps_out = static_cast<AmpT *>(amps_dst ? amps_dst : P.amps[tn & 1]);
 
     __shared__ double2 s_w[MM * MM];
     __shared__ float4 s_wf[MM * MM];
@@ -831,6 +848,7 @@ __device__ __forceinline__ void write_step_totals(const Params &P, unsigned long
     r.groups = (long long)groups;
     r.extended = (long long)groups * MM;
     r.kept = (long long)n_out;
+    r.inter = (long long)n_out;   // pre-merging: the largest set of the step is the stored one
     P.stats_ring[tn % (unsigned long long)P.rho_hist] = r;
 }
 
@@ -2206,6 +2224,414 @@ __global__ void k_widen(const float *in, double *out, long long n) {
         out[i] = f2d_exact(in[i]);
 }
 
+// ---------------------------------------------------------------- post-merging engine
+//
+// The original order of the method (Sec. 2.1, Scheme macgic: propagation(),
+// sorting(), merging()), for the comparison the paper makes with the
+// pre-merging order (Sec. 4.1).  Per step: every stored path is extended by
+// its M^2 children with its own history (phase_expand without a merge), the
+// survivors of the filter go to the unmerged buffer (Omega(t, unmerged)) and
+// rho(t) is summed from them; the children are then sorted by their masked
+// key (the mask P itself; while the window fills, the whole key, so nothing
+// merges) with a stable least-significant-digit radix sort of 8-bit digits
+// over (key, child index) pairs, and every run of equal masked keys becomes
+// one stored path: the child of largest weight (R4) with the run's sum.
+
+constexpr int kSortThreads = 256;                      // = number of digit values
+constexpr int kSortIpt = 16;                           // items per thread of a sort chunk
+constexpr int kSortChunk = kSortThreads * kSortIpt;    // 4096 items per chunk
+constexpr int kScanThreads = 1024;
+constexpr int kScanSeg = 4 * kScanThreads;             // elements per block of the multi-block scan
+
+__device__ __forceinline__ long long post_chunks(const DevState *st) {
+    return (long long)((st->post_n + kSortChunk - 1) / kSortChunk);
+}
+// Length of the array a multi-block scan runs over: the digit counts of a
+// radix pass (which = 0) or the run heads per chunk (which = 1).
+__device__ __forceinline__ long long scan_len(const DevState *st, int which) {
+    const long long nch = post_chunks(st);
+    return which == 0 ? 256 * nch : nch;
+}
+// A radix pass is active while its digit lies inside the step's key bits.
+__device__ __forceinline__ bool pass_active(const DevState *st, int pass) {
+    return 8 * pass < (int)st->post_bits;
+}
+
+// Masked key compressed to consecutive bits: the runs of consecutive mask
+// positions packed one after another.
+__device__ __forceinline__ unsigned long long compress_masked(const Params &P, unsigned long long key) {
+    unsigned long long c = 0;
+    for (int r = 0; r < P.nruns; ++r) c |= ((key >> P.run_shift[r]) & P.run_mask[r]) << P.run_off[r];
+    return c;
+}
+
+template <int M, bool C64>
+__global__ void __launch_bounds__(kExpandThreads) k_post_expand(Params P) {
+    DevState *st = P.st;
+    if (st->err) return;
+    const unsigned long long t = st->t, tn = t + 1;
+    phase_expand<M, C64, kExpandThreads, false>(P, t, st->n_cur, false, &st->cnt_out[tn % 3], rho_part_of(P, tn, M * M),
+                                                P.ckeys, P.camps);
+}
+
+// Sort keys of the unmerged children: the masked key compressed once the
+// children's window is full, the whole key before (nothing merges then).
+__global__ void k_post_keys(Params P) {
+    DevState *st = P.st;
+    if (st->err) return;
+    const unsigned long long tn = st->t + 1;
+    const unsigned long long n = __ldcg(&st->cnt_out[tn % 3]);
+    const bool full = tn + 1 >= (unsigned long long)P.dkmax;
+    const int L_child = (int)min(tn + 1, (unsigned long long)P.dkmax);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->post_n = n;
+        st->post_bits = full ? (unsigned)P.post_bits_full : (unsigned)(P.b * L_child);
+    }
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long k = __ldcg(P.ckeys + i);
+        P.skey[0][i] = full ? (P.post_compress ? compress_masked(P, k) : (k & P.pmask)) : k;
+        P.sidx[0][i] = (unsigned)i;
+    }
+}
+
+// Radix pass, step 1: digit counts per chunk, stored digit-major
+// (rs_hist[d * chunks + c]) so that one exclusive scan of the whole array
+// gives every (digit, chunk) its first output position.
+__global__ void __launch_bounds__(kSortThreads) k_rs_hist(Params P, int pass) {
+    DevState *st = P.st;
+    if (st->err || !pass_active(st, pass)) return;
+    const unsigned long long n = st->post_n;
+    const long long nch = post_chunks(st);
+    const int shift = 8 * pass;
+    const unsigned long long *in = P.skey[pass & 1];
+    __shared__ unsigned h[256];
+    for (long long c = blockIdx.x; c < nch; c += gridDim.x) {
+        h[threadIdx.x] = 0;
+        __syncthreads();
+        const unsigned long long b0 = (unsigned long long)c * kSortChunk;
+        for (int j = threadIdx.x; j < kSortChunk; j += kSortThreads) {
+            const unsigned long long i = b0 + j;
+            if (i < n) atomicAdd(&h[(unsigned)(__ldcg(in + i) >> shift) & 255u], 1u);
+        }
+        __syncthreads();
+        P.rs_hist[(size_t)threadIdx.x * nch + c] = h[threadIdx.x];
+        __syncthreads();
+    }
+}
+
+// Exclusive scan of a block's kScanThreads * 4 elements held 4 per thread
+// (v[0..3], consecutive); returns the thread's exclusive prefix and the
+// block total in *tot.  All threads call it.
+__device__ __forceinline__ unsigned block_scan4(const unsigned v[4], unsigned *tot) {
+    __shared__ unsigned s_w[kScanThreads / 32];
+    __shared__ unsigned s_tot;
+    const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+    const unsigned mine = v[0] + v[1] + v[2] + v[3];
+    unsigned incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+        if ((int)lane >= o) incl += y;
+    }
+    if (lane == 31) s_w[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const unsigned x = lane < kScanThreads / 32 ? s_w[lane] : 0u;
+        unsigned xi = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, xi, o);
+            if ((int)lane >= o) xi += y;
+        }
+        if (lane < kScanThreads / 32) s_w[lane] = xi - x;
+        if (lane == 31) s_tot = xi;
+    }
+    __syncthreads();
+    const unsigned r = s_w[warp] + incl - mine;
+    *tot = s_tot;
+    __syncthreads();
+    return r;
+}
+
+// Exclusive scan of one value per thread over a block of NT threads (all
+// threads call it).
+template <int NT>
+__device__ __forceinline__ unsigned block_excl_scan(unsigned v) {
+    __shared__ unsigned s_w[NT / 32];
+    const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+    unsigned incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+        if ((int)lane >= o) incl += y;
+    }
+    if (lane == 31) s_w[warp] = incl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned a = 0;
+        for (int w = 0; w < NT / 32; ++w) {
+            const unsigned x = s_w[w];
+            s_w[w] = a;
+            a += x;
+        }
+    }
+    __syncthreads();
+    const unsigned r = s_w[warp] + incl - v;
+    __syncthreads();
+    return r;
+}
+
+// Multi-block exclusive scan, in place (three kernels): block partials,
+// their scan (one block; it also stores the total), and the blocks' own
+// scans from their bases.
+__global__ void __launch_bounds__(kScanThreads) k_scan_part(Params P, unsigned *a, int which, int pass) {
+    DevState *st = P.st;
+    if (st->err || (which == 0 && !pass_active(st, pass))) return;
+    const long long len = scan_len(st, which);
+    const long long nb = (len + kScanSeg - 1) / kScanSeg;
+    for (long long b = blockIdx.x; b < nb; b += gridDim.x) {
+        unsigned v[4];
+        for (int u = 0; u < 4; ++u) {
+            const long long i = b * kScanSeg + 4 * (long long)threadIdx.x + u;
+            v[u] = i < len ? a[i] : 0u;
+        }
+        unsigned tot;
+        block_scan4(v, &tot);
+        if (threadIdx.x == 0) P.rs_part[b] = tot;
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_top(Params P, int which, int pass) {
+    DevState *st = P.st;
+    if (st->err || (which == 0 && !pass_active(st, pass))) return;
+    const long long len = scan_len(st, which);
+    const long long nb = (len + kScanSeg - 1) / kScanSeg;
+    unsigned long long carry = 0;
+    for (long long b0 = 0; b0 < nb; b0 += kScanSeg) {
+        unsigned v[4];
+        for (int u = 0; u < 4; ++u) {
+            const long long i = b0 + 4 * (long long)threadIdx.x + u;
+            v[u] = i < nb ? P.rs_part[i] : 0u;
+        }
+        unsigned tot;
+        const unsigned ex = block_scan4(v, &tot);
+        unsigned run = ex;
+        for (int u = 0; u < 4; ++u) {
+            const long long i = b0 + 4 * (long long)threadIdx.x + u;
+            if (i < nb) P.rs_part[i] = (unsigned)(carry + run);
+            run += v[u];
+        }
+        carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) st->scan_total = carry;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(Params P, unsigned *a, int which, int pass) {
+    DevState *st = P.st;
+    if (st->err || (which == 0 && !pass_active(st, pass))) return;
+    const long long len = scan_len(st, which);
+    const long long nb = (len + kScanSeg - 1) / kScanSeg;
+    for (long long b = blockIdx.x; b < nb; b += gridDim.x) {
+        unsigned v[4];
+        for (int u = 0; u < 4; ++u) {
+            const long long i = b * kScanSeg + 4 * (long long)threadIdx.x + u;
+            v[u] = i < len ? a[i] : 0u;
+        }
+        unsigned tot;
+        unsigned run = P.rs_part[b] + block_scan4(v, &tot);
+        for (int u = 0; u < 4; ++u) {
+            const long long i = b * kScanSeg + 4 * (long long)threadIdx.x + u;
+            if (i < len) a[i] = run;
+            run += v[u];
+        }
+    }
+}
+
+// Radix pass, step 3: stable scatter.  Warp w of a chunk owns the items
+// [w SC, (w+1) SC) and visits them 32 at a time in order; lanes with equal
+// digits find each other with a match and rank among themselves, the warp's
+// running count per digit orders its rounds, and the warps' counts (scanned
+// across warps) order the warps: the output keeps the input order among
+// equal digits.
+__global__ void __launch_bounds__(kSortThreads) k_rs_scatter(Params P, int pass) {
+    DevState *st = P.st;
+    if (st->err || !pass_active(st, pass)) return;
+    constexpr int NW = kSortThreads / 32, SC = kSortChunk / NW, IT = SC / 32;
+    const unsigned long long n = st->post_n;
+    const long long nch = post_chunks(st);
+    const int shift = 8 * pass;
+    const unsigned long long *ik = P.skey[pass & 1];
+    const unsigned *ii = P.sidx[pass & 1];
+    unsigned long long *ok = P.skey[(pass + 1) & 1];
+    unsigned *oi = P.sidx[(pass + 1) & 1];
+    __shared__ unsigned s_wc[NW][256];
+    const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    for (long long c = blockIdx.x; c < nch; c += gridDim.x) {
+        for (int w = 0; w < NW; ++w) s_wc[w][threadIdx.x] = 0u;
+        __syncthreads();
+        const unsigned long long base = (unsigned long long)c * kSortChunk + (unsigned long long)warp * SC;
+        unsigned long long kk[IT];
+        unsigned xx[IT];
+#pragma unroll
+        for (int it = 0; it < IT; ++it) {
+            const unsigned long long i = base + (unsigned long long)it * 32 + lane;
+            const bool valid = i < n;
+            kk[it] = valid ? __ldcg(ik + i) : 0ull;
+            xx[it] = valid ? __ldcg(ii + i) : 0u;
+            const unsigned d = valid ? ((unsigned)(kk[it] >> shift) & 255u) : 256u + lane;
+            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            if (valid && (peers & lt) == 0u) s_wc[warp][d] += (unsigned)__popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        {   // first output position of each (warp, digit): chunk base of the digit + earlier warps
+            const int d = threadIdx.x;
+            unsigned acc = P.rs_hist[(size_t)d * nch + c];
+            for (int w = 0; w < NW; ++w) {
+                const unsigned v = s_wc[w][d];
+                s_wc[w][d] = acc;
+                acc += v;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int it = 0; it < IT; ++it) {
+            const unsigned long long i = base + (unsigned long long)it * 32 + lane;
+            const bool valid = i < n;
+            const unsigned d = valid ? ((unsigned)(kk[it] >> shift) & 255u) : 256u + lane;
+            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            if (valid) {
+                const unsigned pos = s_wc[warp][d] + (unsigned)__popc(peers & lt);
+                ok[pos] = kk[it];
+                oi[pos] = xx[it];
+            }
+            __syncwarp();
+            if (valid && (peers & lt) == 0u) s_wc[warp][d] += (unsigned)__popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+    }
+}
+
+// Sorted keys of the step: the buffer the last active pass wrote.
+__device__ __forceinline__ int sorted_buf(const DevState *st) { return (int)(((st->post_bits + 7u) / 8u) & 1u); }
+
+// Reduce by key, step 1: run heads per chunk of the sorted keys.
+__global__ void __launch_bounds__(kSortThreads) k_rbk_heads(Params P) {
+    DevState *st = P.st;
+    if (st->err) return;
+    const unsigned long long n = st->post_n;
+    const long long nch = post_chunks(st);
+    const unsigned long long *sk = P.skey[sorted_buf(st)];
+    __shared__ unsigned s_n;
+    for (long long c = blockIdx.x; c < nch; c += gridDim.x) {
+        if (threadIdx.x == 0) s_n = 0;
+        __syncthreads();
+        unsigned cnt = 0;
+        for (int j = threadIdx.x; j < kSortChunk; j += kSortThreads) {
+            const unsigned long long i = (unsigned long long)c * kSortChunk + j;
+            if (i < n && (i == 0 || __ldcg(sk + i) != __ldcg(sk + i - 1))) ++cnt;
+        }
+        atomicAdd(&s_n, cnt);
+        __syncthreads();
+        if (threadIdx.x == 0) P.rbk_heads[c] = s_n;
+        __syncthreads();
+    }
+}
+
+// Reduce by key, step 2: each run head's thread walks its run (in sorted
+// order, which is the unmerged buffer's order among equal keys): the sum
+// (C64: FP32 with every rounding error kept, rounded once; FP64: FP64), the
+// largest weight, then the smallest full key within the tie window (R4);
+// the run becomes one stored path of Omega(t) at the position of its head
+// among all heads.
+template <bool C64>
+__global__ void __launch_bounds__(kSortThreads) k_rbk_write(Params P) {
+    using AmpT = typename std::conditional<C64, float2, double2>::type;
+    using WT = typename std::conditional<C64, float, double>::type;
+    DevState *st = P.st;
+    if (st->err) return;
+    const unsigned long long tn = st->t + 1;
+    const unsigned long long n = st->post_n;
+    const long long nch = post_chunks(st);
+    const int sb = sorted_buf(st);
+    const unsigned long long *sk = P.skey[sb];
+    const unsigned *si = P.sidx[sb];
+    const AmpT *camps = static_cast<const AmpT *>(P.camps);
+    unsigned long long *keys_out = P.keys[tn & 1];
+    AmpT *amps_out = static_cast<AmpT *>(P.amps[tn & 1]);
+    const WT tie = (WT)(1.0 - P.tie_rel);
+    for (long long c = blockIdx.x; c < nch; c += gridDim.x) {
+        // this thread's kSortIpt consecutive items of the chunk
+        const unsigned long long i0 = (unsigned long long)c * kSortChunk + (unsigned long long)threadIdx.x * kSortIpt;
+        unsigned hm = 0;
+        for (int u = 0; u < kSortIpt; ++u) {
+            const unsigned long long i = i0 + u;
+            if (i < n && (i == 0 || __ldcg(sk + i) != __ldcg(sk + i - 1))) hm |= 1u << u;
+        }
+        unsigned pos = P.rbk_heads[c] + block_excl_scan<kSortThreads>((unsigned)__popc(hm));
+        for (unsigned m = hm; m; m &= m - 1u) {
+            const unsigned long long h = i0 + (__ffs(m) - 1);
+            const unsigned long long mk = __ldcg(sk + h);
+            float sx = 0.f, sy = 0.f, ex = 0.f, ey = 0.f;
+            double dx = 0.0, dy = 0.0;
+            WT wmax = 0;
+            unsigned long long j = h;
+            for (; j < n && __ldcg(sk + j) == mk; ++j) {
+                const AmpT a = camps[__ldcg(si + j)];
+                if constexpr (C64) {
+                    two_sum_acc(sx, ex, a.x);
+                    two_sum_acc(sy, ey, a.y);
+                } else {
+                    dx += a.x;
+                    dy += a.y;
+                }
+                const WT w2 = a.x * a.x + a.y * a.y;
+                wmax = w2 > wmax ? w2 : wmax;
+            }
+            unsigned long long rep = kEmpty;
+            for (unsigned long long k = h; k < j; ++k) {
+                const unsigned x = __ldcg(si + k);
+                const AmpT a = camps[x];
+                const WT w2 = a.x * a.x + a.y * a.y;
+                const unsigned long long key = P.ckeys[x];
+                if (w2 >= tie * wmax && key < rep) rep = key;
+            }
+            keys_out[pos] = rep;
+            if constexpr (C64) amps_out[pos] = make_float2(sx + ex, sy + ey);
+            else amps_out[pos] = make_double2(dx, dy);
+            ++pos;
+        }
+    }
+}
+
+// Publishes a post-merging step: rho(t) from the extension's block partials,
+// the merged count, the statistics (intermediate = the unmerged children).
+__global__ void __launch_bounds__(256) k_post_publish(Params P, int MM, int nblk) {
+    DevState *st = P.st;
+    if (st->err) return;
+    const unsigned long long t = st->t, tn = t + 1;
+    phase_finalize(P, tn, 0, rho_part_of(P, tn, MM), nblk, MM);
+    if (threadIdx.x != 0) return;
+    const unsigned long long n_in = st->n_cur, inter = st->post_n, merged = st->scan_total;
+    StepRec r;
+    r.t = (long long)tn;
+    r.groups = (long long)n_in;
+    r.extended = (long long)n_in * MM;
+    r.kept = (long long)merged;
+    r.inter = (long long)inter;
+    const size_t slot = (size_t)(tn % (unsigned long long)P.rho_hist);
+    P.stats_ring[slot] = r;
+    P.inst_kept[slot] = (long long)merged;
+    st->n_cur = merged;
+    st->t = tn;
+    st->cnt_groups[(tn + 1) % 3] = 0;
+    st->cnt_out[(tn + 1) % 3] = 0;
+}
+
 // ---------------------------------------------------------------- set-up kernels
 
 __global__ void k_clear_table(Slot *slots, unsigned long long *repk, unsigned long long n) {
@@ -2302,6 +2728,8 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 struct Layout {
     size_t keys[2], amps[2], slots, repk, slot_of, groups, lut, lutf, lutlo, etab, wtab, wtabf, uprop, eta, q, deltas,
         rho, rho_part, spart, scount, stats, inst_kept, fin_count, tile_state, state, total;
+    size_t ckeys, camps, skey[2], sidx[2], rs_hist, rs_part, rbk_heads;   // post-merging engine
+    long long max_chunks;
     long long entries, max_tiles;
     size_t nlut;           // history-table entries of one instance
     int nd;                // distinct nonzero coupling differences
@@ -2339,6 +2767,10 @@ const char *validate(const qp_config *c) {
         return "set max_groups (<= 2^30) for max_paths > 2^30 (the merge table; not needed by the stream engine)";
     if (c->rho_history < 0 || c->rho_history > (1 << 24)) return "rho_history out of range";
     if (c->n_inst < 0 || c->n_inst > kMaxInst) return "n_inst out of range (0..128)";
+    if (c->scheme != QP_PREMERGE && c->scheme != QP_POSTMERGE) return "unknown scheme";
+    if (c->scheme == QP_POSTMERGE && c->n_inst > 1) return "the post-merging scheme takes single problems only";
+    if (c->scheme == QP_POSTMERGE && c->max_paths > (int64_t(1) << 32) - 1)
+        return "post-merging: max_paths (the unmerged set) must stay below 2^32";
     if (b * c->dkmax + inst_bits(c->n_inst) > 64) return "b*dkmax plus the instance index exceed the 64-bit key";
     for (int i = 0; i < c->M; ++i)
         if (!std::isfinite(c->q[i])) return "q must be finite";
@@ -2452,6 +2884,18 @@ Layout make_layout(const qp_config *c) {
     L.fin_count = take(sizeof(unsigned int));
     L.max_tiles = (long long)MM * ((mp / MM + kStreamMinTile - 1) / kStreamMinTile + 1);   // smallest tile
     L.tile_state = take((size_t)L.max_tiles * MM * 8);
+    if (c->scheme == QP_POSTMERGE) {   // unmerged set, sort pairs, digit counts, scan partials, run heads
+        L.max_chunks = (mp + kSortChunk - 1) / kSortChunk + 1;
+        L.ckeys = take(mp * 8);
+        L.camps = take(mp * ampb);
+        for (int k = 0; k < 2; ++k) {
+            L.skey[k] = take(mp * 8);
+            L.sidx[k] = take(mp * 4);
+        }
+        L.rs_hist = take((size_t)256 * L.max_chunks * 4);
+        L.rs_part = take(((size_t)256 * L.max_chunks / kScanSeg + 2) * 4);
+        L.rbk_heads = take((size_t)L.max_chunks * 4);
+    }
     L.total = off;
     return L;
 }
@@ -2637,8 +3081,50 @@ cudaError_t launch_stream_t(qp_ctx *c, cudaEvent_t *ev) {
     return cudaGetLastError();
 }
 
+// One post-merging step (events: 0 extension, 1 sort, 2 reduce by key,
+// 3 publish, 4 end).  The number of radix passes covers the widest key (the
+// whole window, b dkmax bits); passes beyond the step's key bits return at
+// once on the device.
+template <int M, bool C64>
+cudaError_t launch_post_t(qp_ctx *c, cudaEvent_t *ev) {
+    const int g_exp = std::min(c->nsm * c->bps_exp, kMaxExpandBlocks);
+    const int gs = (int)std::min<long long>(c->L.max_chunks, (long long)c->nsm * 4);
+    const int gc = (int)std::min<long long>(((long long)256 * c->L.max_chunks + kScanSeg - 1) / kScanSeg,
+                                            (long long)c->nsm * 2);
+    const int gk = c->nsm * 4;
+    const int npass = (c->P.b * c->cfg.dkmax + 7) / 8;
+    if (ev) cudaEventRecord(ev[0], c->stream);
+    k_post_expand<M, C64><<<g_exp, kExpandThreads, 0, c->stream>>>(c->P);
+    if (ev) cudaEventRecord(ev[1], c->stream);
+    k_post_keys<<<gk, 256, 0, c->stream>>>(c->P);
+    for (int pass = 0; pass < npass; ++pass) {
+        k_rs_hist<<<gs, kSortThreads, 0, c->stream>>>(c->P, pass);
+        k_scan_part<<<gc, kScanThreads, 0, c->stream>>>(c->P, c->P.rs_hist, 0, pass);
+        k_scan_top<<<1, kScanThreads, 0, c->stream>>>(c->P, 0, pass);
+        k_scan_down<<<gc, kScanThreads, 0, c->stream>>>(c->P, c->P.rs_hist, 0, pass);
+        k_rs_scatter<<<gs, kSortThreads, 0, c->stream>>>(c->P, pass);
+    }
+    if (ev) cudaEventRecord(ev[2], c->stream);
+    k_rbk_heads<<<gs, kSortThreads, 0, c->stream>>>(c->P);
+    k_scan_part<<<gc, kScanThreads, 0, c->stream>>>(c->P, c->P.rbk_heads, 1, 0);
+    k_scan_top<<<1, kScanThreads, 0, c->stream>>>(c->P, 1, 0);
+    k_scan_down<<<gc, kScanThreads, 0, c->stream>>>(c->P, c->P.rbk_heads, 1, 0);
+    k_rbk_write<C64><<<gs, kSortThreads, 0, c->stream>>>(c->P);
+    if (ev) cudaEventRecord(ev[3], c->stream);
+    k_post_publish<<<1, 256, 0, c->stream>>>(c->P, M * M, g_exp);
+    if (ev) cudaEventRecord(ev[4], c->stream);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_step(qp_ctx *c, cudaEvent_t *ev = nullptr) {
     const bool c64 = c->cfg.precision == QP_C64;
+    if (c->P.post) {
+        switch (c->cfg.M) {
+            case 2: return c64 ? launch_post_t<2, true>(c, ev) : launch_post_t<2, false>(c, ev);
+            case 3: return c64 ? launch_post_t<3, true>(c, ev) : launch_post_t<3, false>(c, ev);
+            default: return c64 ? launch_post_t<4, true>(c, ev) : launch_post_t<4, false>(c, ev);
+        }
+    }
     if (c->use_stream) {
         switch (c->cfg.M) {
             case 2: return c64 ? launch_stream_t<2, float2>(c, ev) : launch_stream_t<2, double2>(c, ev);
@@ -2712,11 +3198,12 @@ int persistent_grid(int M, bool c64, int nsm, bool batch, size_t smem) {
 void set_mask_params(qp_ctx *c) {
     Params &P = c->P;
     const int b = P.b, dk = P.dkmax;
-    std::vector<int> Pp;   // P' = {p-1 : p in P, p >= 1} plus 0
+    std::vector<int> Pp;   // P' = {p-1 : p in P, p >= 1} plus 0; post-merging: P itself
     std::vector<char> in(dk, 0);
     in[0] = 1;
     for (int p : c->mask)
-        if (p >= 1) in[p - 1] = 1;
+        if (P.post) in[p] = 1;
+        else if (p >= 1) in[p - 1] = 1;
     unsigned long long pm = 0;
     for (int p = 0; p < dk; ++p)
         if (in[p]) {
@@ -2772,6 +3259,14 @@ void set_mask_params(qp_ctx *c) {
         if (f <= (unsigned long long)P.region_cap * (unsigned long long)(c->cfg.M * c->cfg.M)) P.full_n = f;
     }
     if (P.full_n == 0) P.reg_merge = 0;
+    if (P.post) {   // the sort engine: no stream layout, no regular steps
+        c->stream_nx = 0;
+        P.reg_fill = P.reg_merge = 0;
+        // more runs of consecutive positions than the packing holds: sort on
+        // the masked key itself (up to its highest bit)
+        P.post_compress = ok ? 1 : 0;
+        P.post_bits_full = ok ? b * (int)Pp.size() : 64 - __builtin_clzll(pm);
+    }
 }
 
 }  // namespace
@@ -2902,6 +3397,18 @@ qp_status qp_create(const qp_config *cfg, void *d_workspace, size_t bytes, void 
     P.etab_stride = L.nlut * (size_t)std::max(1, L.nd);
     P.stats_ring = reinterpret_cast<StepRec *>(c->ws + L.stats);
     P.st = reinterpret_cast<DevState *>(c->ws + L.state);
+    P.post = cfg->scheme == QP_POSTMERGE ? 1 : 0;
+    if (P.post) {
+        P.ckeys = reinterpret_cast<unsigned long long *>(c->ws + L.ckeys);
+        P.camps = c->ws + L.camps;
+        for (int k = 0; k < 2; ++k) {
+            P.skey[k] = reinterpret_cast<unsigned long long *>(c->ws + L.skey[k]);
+            P.sidx[k] = reinterpret_cast<unsigned int *>(c->ws + L.sidx[k]);
+        }
+        P.rs_hist = reinterpret_cast<unsigned int *>(c->ws + L.rs_hist);
+        P.rs_part = reinterpret_cast<unsigned int *>(c->ws + L.rs_part);
+        P.rbk_heads = reinterpret_cast<unsigned int *>(c->ws + L.rbk_heads);
+    }
     c->mask.clear();
     for (int p = 0; p < cfg->dkmax; ++p) c->mask.push_back(p);
     set_mask_params(c);
@@ -3055,10 +3562,11 @@ qp_status qp_set_rho0(qp_ctx *c, const double *re, const double *im) {
             }
     if ((int64_t)keys.size() > c->cfg.max_paths) return fail(c, QP_ERR_CAPACITY, "rho0 exceeds max_paths");
     // engine of this propagation
-    if (c->cfg.engine == QP_ENGINE_STREAM && c->stream_nx == 0)
+    if (!c->P.post && c->cfg.engine == QP_ENGINE_STREAM && c->stream_nx == 0)
         return fail(c, QP_ERR_ARG, "the stream engine needs a mask whose P' is a prefix {0..k-1} plus at most one "
                                    "extra position (M = 2) and a single instance");
-    c->use_stream = c->cfg.engine == QP_ENGINE_STREAM || (c->cfg.engine == QP_ENGINE_AUTO && c->stream_nx > 0);
+    c->use_stream = !c->P.post &&
+                    (c->cfg.engine == QP_ENGINE_STREAM || (c->cfg.engine == QP_ENGINE_AUTO && c->stream_nx > 0));
     if (c->use_stream && c->P.region_cap < 1) return fail(c, QP_ERR_CAPACITY, "max_paths < 16 M*M (stream engine)");
     c->P.stream = c->use_stream ? 1 : 0;
     c->graph_dirty = true;
@@ -3092,7 +3600,7 @@ qp_status qp_set_rho0(qp_ctx *c, const double *re, const double *im) {
     // look-back words are tagged with the step number, which restarts at 0:
     // words of an earlier propagation must not pass for this one's
     QP_CUDA(c, cudaMemsetAsync(c->P.tile_state, 0, (size_t)c->L.max_tiles * M * M * 8, c->stream));
-    StepRec r0{0, 0, 0, (long long)n};
+    StepRec r0{0, 0, 0, (long long)n, (long long)n};
     QP_CUDA(c, cudaMemcpyAsync(c->P.stats_ring, &r0, sizeof(StepRec), cudaMemcpyHostToDevice, c->stream));
     k_clear_table<<<c->nsm * 4, 256, 0, c->stream>>>(c->P.slots, c->P.repk, c->L.tcap);
     QP_CUDA(c, cudaGetLastError());
@@ -3129,7 +3637,7 @@ qp_status qp_step(qp_ctx *c, int nsteps) {
     if (c->failed) return fail(c, QP_ERR_STATE, "context holds a device error; call qp_set_rho0");
     if (nsteps == 0) return QP_OK;
     c->host_t += nsteps;
-    if (c->use_persistent && !c->use_stream) {
+    if (c->use_persistent && !c->use_stream && !c->P.post) {
         const cudaError_t e = launch_persistent(c, nsteps);
         if (e != cudaSuccess) return fail(c, QP_ERR_CUDA, std::string("persistent launch: ") + cudaGetErrorString(e));
         return QP_OK;
@@ -3318,6 +3826,7 @@ qp_status qp_read_stats(qp_ctx *c, int64_t t0, int count, qp_step_stats *out) {
         out[k].groups = rec.groups;
         out[k].extended = rec.extended;
         out[k].kept = rec.kept;
+        out[k].intermediate = rec.inter;
     }
     return QP_OK;
 }
@@ -3428,6 +3937,8 @@ qp_status qp_set_tuning(qp_ctx *c, const qp_tuning *t) {
     if (t->mode != QP_LAUNCH_GRAPH && t->mode != QP_LAUNCH_PERSISTENT) return fail(c, QP_ERR_ARG, "unknown mode");
     if (t->mode == QP_LAUNCH_PERSISTENT && c->persist_max <= 0)
         return fail(c, QP_ERR_ARG, "cooperative launch not available on this device");
+    if (t->mode == QP_LAUNCH_PERSISTENT && c->P.post)
+        return fail(c, QP_ERR_ARG, "the post-merging scheme runs as CUDA graphs only");
     if (t->insert_blocks_per_sm < 1 || t->insert_blocks_per_sm > 32 || t->expand_blocks_per_sm < 1 ||
         c->nsm * t->expand_blocks_per_sm > kMaxExpandBlocks)
         return fail(c, QP_ERR_ARG, "blocks per SM out of range");
@@ -3498,7 +4009,10 @@ qp_status qp_autotune(qp_ctx *c, int trial_steps, int use_cache, qp_tuning *best
             if ((1ll << (tl - d)) >= need) tables.push_back(tl - d);
         }
     const int gs = 8;
-    if (c->use_stream) {   // one kernel per step: tile size and blocks per SM
+    if (c->P.post) {   // the sort engine: blocks per SM of the extension
+        for (int be : {2, 4, 8})
+            if (c->nsm * be <= kMaxExpandBlocks) cand.push_back(qp_tuning{QP_LAUNCH_GRAPH, c->bps_ins, be, c->persist_grid, gs, tl, 0, 0});
+    } else if (c->use_stream) {   // one kernel per step: tile size and blocks per SM
         for (int tile : {256, 512, 1024})
             for (int be : {1, 2, 4, 8}) {
                 if (c->nsm * be > kMaxExpandBlocks) continue;

@@ -72,12 +72,12 @@ def test_gradients_match_oracle(d_in, w, d_out, B):
     bound = (2.0 ** -8 + B * 2.0 ** -23) * mag + 1e-12
     worst = np.max(np.abs(g - go) / bound)
     assert worst <= 1.0, worst
-    # most elements agree to the accumulation alone (flips are rare): within
-    # twice the batch times 2^-23 of their terms' magnitude (the tensor
-    # cores' FP32 accumulation is not rounded to nearest at every addition)
-    close = np.abs(g - go) <= B * 2.0 ** -22 * mag + 1e-12
-    print(f"gradients: worst {worst:.3f} of the bound; {close.mean():.4f} within the accumulation alone")
-    assert close.mean() >= 0.9
+    # a systematic error (a wrong rounding of every operand, a scaled block)
+    # would move the typical element by a good part of 2^-8; rounding flips
+    # and accumulation leave the median far below that
+    rel = np.abs(g - go) / (mag + 1e-30)
+    print(f"gradients: worst {worst:.3f} of the bound; median {np.median(rel):.2e} of the terms' magnitude")
+    assert np.median(rel) <= 2.0 ** -12
     net.close()
 
 
