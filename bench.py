@@ -456,6 +456,57 @@ def run_surrogate(T_train=100, T_long=1000, L=32, epochs=2000):
             "matched_comparison": outcome}
 
 
+def run_pre_vs_post(t0=100, steps=20, precisions=("fp64", "c64")):
+    """The paper's comparison of the pre-merging order (Sec. 3.1) with the
+    original post-merging order (Sec. 2.1; Sec. 4.1, Fig. performance), on
+    the structured spin-boson model (memory 16) for masks of 4, 6, 10 and
+    16 positions and two filter thresholds: per setting the time per step
+    (CUDA events, L2 flushed between steps), the paths each order extends,
+    its largest set (pre: the stored children; post: the unmerged set) and
+    the rho difference between the two orders at the last step."""
+    import torch
+    from dataclasses import replace
+    from paper_2506_03127_gb300 import Propagator
+    base = W.SPIN_BOSON_STRUCTURED_DK16
+    masks = {4: (0, 1, 2, 3), 6: (0, 1, 2, 3, 4, 8), 10: base.mask, 16: None}
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    out = []
+    for prec in precisions:
+        for theta in (1e-6, 1e-9):
+            for keff, mask in masks.items():
+                w = replace(base, mask=mask, theta=theta)
+                row = {"precision": prec, "theta": theta, "dk_eff": keff}
+                rhos = {}
+                for scheme in ("pre", "post"):
+                    p = Propagator.from_workload(w, precision=prec, max_paths=1 << 24, scheme=scheme)
+                    p.step(t0)
+                    p.sync()
+                    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                          for _ in range(steps)]
+                    t_first = p.current()[0] + 1
+                    for a, b in ev:
+                        with torch.cuda.stream(p.stream):
+                            flush.zero_()
+                        a.record(p.stream)
+                        p.step(1)
+                        b.record(p.stream)
+                    p.sync()
+                    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+                    st = p.stats(t_first, steps)
+                    rhos[scheme] = p.rho(t_first + steps - 1, 1)[0]
+                    row[scheme] = {"ms_per_step": round(ms, 4), "paths_extended": int(np.mean([r[1] for r in st])),
+                                   "largest_set": int(np.mean([r[4] for r in st])),
+                                   "stored": int(np.mean([r[3] for r in st]))}
+                    p.close()
+                row["pre_over_post_time"] = round(row["pre"]["ms_per_step"] / row["post"]["ms_per_step"], 3)
+                row["post_over_pre_largest_set"] = round(row["post"]["largest_set"] / max(1, row["pre"]["largest_set"]), 3)
+                row["rho_diff_post_vs_pre"] = float(np.abs(rhos["post"] - rhos["pre"]).max())
+                out.append(row)
+    return {"workload": base.name + " with masks of 4, 6, 10, 16 positions", "t0": t0, "steps": steps,
+            "engines": "pre: stream engine (order-preserving, segmented sums); post: sort engine (radix sort, "
+                       "reduce by key)", "rows": out}
+
+
 def aggregate_over_ranks(t_ms, units):
     """Whole-job figures of independent replicas (one per rank, no data
     exchange): the slowest rank's timed-region time (max over ranks) and the
@@ -679,6 +730,7 @@ def main():
     if not args.no_batched and world == 1:
         line["batched_sweep"] = run_batched_sweep()
         line["surrogate"] = run_surrogate()
+        line["pre_vs_post"] = run_pre_vs_post()
     line.update({"metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": args.gpus, "steps": args.steps,
                  "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
                  "scaling": "weak", "vs_baseline": None, "dtype": "c64" if args.precision == "c64" else "f64",
