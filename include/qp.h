@@ -297,6 +297,32 @@ qp_status qp_autotune(qp_ctx *ctx, int trial_steps, int use_cache, qp_tuning *be
  * qp_set_rho0 restores a usable context.                                    */
 qp_status qp_test_stall_barrier(qp_ctx *ctx);
 
+/* Sharded propagation over several GPUs (the distributed pre-merge of
+ * Sec. 3.2 in a GPU form).  One context per rank holds the stored paths the
+ * rank owns: a path belongs to the owner of its next pre-merge group,
+ *   owner = ((key & B) * 0x9E3779B97F4A7C15 mod 2^64) / 2^32  mod n_ranks,
+ * B = the key bits of the pre-merge positions P' (qp_set_mask), so every
+ * group of the next pre-merge lies on one rank.  A step on n ranks: each
+ * rank runs qp_step(ctx, 1) on its paths (rho(t) of the context is the
+ * rank's part: the sum over ranks is rho(t)), partitions its stored set by
+ * owner (qp_partition_paths), exchanges the parts (an all-to-all, outside
+ * the library) and replaces its set with what it received
+ * (qp_import_paths).  Needs the merge-table engine (QP_ENGINE_HASH), the
+ * pre-merging order and a single problem (QP_ERR_STATE otherwise).
+ *
+ * qp_partition_paths: copies the stored set Omega(t) into d_keys (uint64)
+ * and d_amps (interleaved (re, im) in the context's precision: FP64 or FP32)
+ * grouped by owner, rank 0's paths first; counts[n_ranks] gets the paths per
+ * rank.  Device buffers owned by the caller, cap entries each
+ * (QP_ERR_CAPACITY when the set is larger).  1 <= n_ranks <= 1024.
+ * Synchronises.                                                            */
+qp_status qp_partition_paths(qp_ctx *ctx, int n_ranks, uint64_t *d_keys, void *d_amps, int64_t cap, int64_t *counts);
+
+/* Replaces the stored set of the current time step with n paths from device
+ * arrays (the layout qp_partition_paths writes), copied before the call
+ * returns (synchronises).  n <= max_paths (QP_ERR_CAPACITY).              */
+qp_status qp_import_paths(qp_ctx *ctx, const uint64_t *d_keys, const void *d_amps, int64_t n);
+
 /* Test hook for the bounded wait of the stream engine's look-back (the wait
  * of a tile for the survivor counts of the tiles before it, Sec. 3.1 order
  * of the stored set): the first tile of the next stream-engine step publishes

@@ -90,6 +90,9 @@ def _load():
         "qp_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, _dp]),
         "qp_test_stall_barrier": (ctypes.c_int, [ctypes.c_void_p]),
         "qp_test_stall_lookback": (ctypes.c_int, [ctypes.c_void_p]),
+        "qp_partition_paths": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                              ctypes.c_int64, _i64p]),
+        "qp_import_paths": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
         "qp_test_widen": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
         "qp_mlp_workspace_size": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                  ctypes.POINTER(ctypes.c_size_t)]),
@@ -261,6 +264,18 @@ def qp_test_stall_barrier(ctx):
 
 def qp_test_stall_lookback(ctx):
     check(lib.qp_test_stall_lookback(ctx), ctx)
+
+
+def qp_partition_paths(ctx, n_ranks: int, d_keys: int, d_amps: int, cap: int):
+    """Stored set grouped by owner rank into device buffers; counts per rank."""
+    counts = np.zeros(n_ranks, dtype=np.int64)
+    check(lib.qp_partition_paths(ctx, n_ranks, ctypes.c_void_p(d_keys), ctypes.c_void_p(d_amps), cap,
+                                 _ptr(counts, _i64p)), ctx)
+    return counts
+
+
+def qp_import_paths(ctx, d_keys: int, d_amps: int, n: int):
+    check(lib.qp_import_paths(ctx, ctypes.c_void_p(d_keys), ctypes.c_void_p(d_amps), n), ctx)
 
 
 def qp_test_widen(in_ptr: int, out_ptr: int, n: int, stream: int = 0):

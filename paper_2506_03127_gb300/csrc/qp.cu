@@ -2632,6 +2632,58 @@ __global__ void __launch_bounds__(256) k_post_publish(Params P, int MM, int nblk
     st->cnt_out[(tn + 1) % 3] = 0;
 }
 
+// ---------------------------------------------------------------- ranks
+//
+// Sharded propagation over several GPUs (the distributed pre-merge of Sec.
+// 3.2, in a GPU form: owner routing instead of the sequential broadcast
+// rounds).  Every stored path belongs to the rank that owns its next
+// pre-merge group, so that each rank's groups are complete:
+//   owner = ((key & P'-bits) * 0x9E3779B97F4A7C15 >> 32) mod n_ranks.
+// k_part_count counts the stored paths per owner, k_part_scatter copies
+// them grouped by owner (rank 0's first) into the caller's buffers.
+
+constexpr int kMaxRanks = 1024;
+
+__device__ __forceinline__ unsigned owner_rank(const Params &P, unsigned long long key, unsigned n_ranks) {
+    const unsigned long long h = ((key & P.pmask) * 0x9E3779B97F4A7C15ull) >> 32;
+    return (unsigned)(h % n_ranks);
+}
+
+__global__ void k_part_count(Params P, unsigned n_ranks, unsigned long long *cnt) {
+    __shared__ unsigned s_c[kMaxRanks];
+    const DevState *st = P.st;
+    const unsigned long long n = st->n_cur;
+    const unsigned long long *keys = P.keys[st->t & 1];
+    for (unsigned r = threadIdx.x; r < n_ranks; r += blockDim.x) s_c[r] = 0;
+    __syncthreads();
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x)
+        atomicAdd(&s_c[owner_rank(P, keys[i], n_ranks)], 1u);
+    __syncthreads();
+    for (unsigned r = threadIdx.x; r < n_ranks; r += blockDim.x)
+        if (s_c[r]) atomicAdd(&cnt[r], (unsigned long long)s_c[r]);
+}
+
+template <typename Amp>
+__global__ void k_part_scatter(Params P, unsigned n_ranks, const unsigned long long *base, unsigned long long *cursor,
+                               unsigned long long *keys_out, Amp *amps_out) {
+    const DevState *st = P.st;
+    const unsigned long long n = st->n_cur;
+    const unsigned long long *keys = P.keys[st->t & 1];
+    const Amp *amps = static_cast<const Amp *>(P.amps[st->t & 1]);
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long k = keys[i];
+        const unsigned r = owner_rank(P, k, n_ranks);
+        const unsigned long long o = base[r] + atomicAdd(&cursor[r], 1ull);
+        keys_out[o] = k;
+        amps_out[o] = amps[i];
+    }
+}
+
+// Sets the stored count after an import (one thread).
+__global__ void k_set_count(DevState *st, unsigned long long n) { st->n_cur = n; }
+
 // ---------------------------------------------------------------- set-up kernels
 
 __global__ void k_clear_table(Slot *slots, unsigned long long *repk, unsigned long long n) {
@@ -2729,6 +2781,7 @@ struct Layout {
     size_t keys[2], amps[2], slots, repk, slot_of, groups, lut, lutf, lutlo, etab, wtab, wtabf, uprop, eta, q, deltas,
         rho, rho_part, spart, scount, stats, inst_kept, fin_count, tile_state, state, total;
     size_t ckeys, camps, skey[2], sidx[2], rs_hist, rs_part, rbk_heads;   // post-merging engine
+    size_t ranks;                                                        // per-rank counts, bases, cursors
     long long max_chunks;
     long long entries, max_tiles;
     size_t nlut;           // history-table entries of one instance
@@ -2884,6 +2937,7 @@ Layout make_layout(const qp_config *c) {
     L.fin_count = take(sizeof(unsigned int));
     L.max_tiles = (long long)MM * ((mp / MM + kStreamMinTile - 1) / kStreamMinTile + 1);   // smallest tile
     L.tile_state = take((size_t)L.max_tiles * MM * 8);
+    L.ranks = take((size_t)3 * kMaxRanks * 8);
     if (c->scheme == QP_POSTMERGE) {   // unmerged set, sort pairs, digit counts, scan partials, run heads
         L.max_chunks = (mp + kSortChunk - 1) / kSortChunk + 1;
         L.ckeys = take(mp * 8);
@@ -4091,6 +4145,68 @@ qp_status qp_test_stall_lookback(qp_ctx *c) {
     // step's other tiles wait for it until their bounded wait gives up
     const unsigned int first = 1u;
     QP_CUDA(c, cudaMemcpyAsync(&c->P.st->stall_tile, &first, sizeof(first), cudaMemcpyHostToDevice, c->stream));
+    QP_CUDA(c, cudaStreamSynchronize(c->stream));
+    return QP_OK;
+}
+
+qp_status qp_partition_paths(qp_ctx *c, int n_ranks, uint64_t *d_keys, void *d_amps, int64_t cap, int64_t *counts) {
+    if (!c) return QP_ERR_ARG;
+    if (n_ranks < 1 || n_ranks > kMaxRanks || !counts || cap < 0 || (cap > 0 && (!d_keys || !d_amps)))
+        return fail(c, QP_ERR_ARG, "bad arguments");
+    if (!c->have_state) return fail(c, QP_ERR_STATE, "no state");
+    if (c->use_stream || c->P.post || c->P.n_inst > 1)
+        return fail(c, QP_ERR_STATE, "ranks need the merge-table engine, the pre-merging order and a single problem");
+    DevState s;
+    qp_status r = read_state(c, &s);
+    if (r != QP_OK) return r;
+    if ((int64_t)s.n_cur > cap) return fail(c, QP_ERR_CAPACITY, "partition buffer too small");
+    unsigned long long *cnt = reinterpret_cast<unsigned long long *>(c->ws + c->L.ranks);
+    unsigned long long *base = cnt + kMaxRanks, *cursor = cnt + 2 * kMaxRanks;
+    QP_CUDA(c, cudaMemsetAsync(cnt, 0, (size_t)n_ranks * 8, c->stream));
+    const int g = std::max(1, std::min(c->nsm * 4, (int)((s.n_cur + 255) / 256)));
+    k_part_count<<<g, 256, 0, c->stream>>>(c->P, (unsigned)n_ranks, cnt);
+    QP_CUDA(c, cudaGetLastError());
+    std::vector<unsigned long long> hc(n_ranks), hb(n_ranks);
+    QP_CUDA(c, cudaMemcpyAsync(hc.data(), cnt, (size_t)n_ranks * 8, cudaMemcpyDeviceToHost, c->stream));
+    QP_CUDA(c, cudaStreamSynchronize(c->stream));
+    unsigned long long a = 0;
+    for (int i = 0; i < n_ranks; ++i) {
+        hb[i] = a;
+        a += hc[i];
+        counts[i] = (int64_t)hc[i];
+    }
+    QP_CUDA(c, cudaMemcpyAsync(base, hb.data(), (size_t)n_ranks * 8, cudaMemcpyHostToDevice, c->stream));
+    QP_CUDA(c, cudaMemsetAsync(cursor, 0, (size_t)n_ranks * 8, c->stream));
+    if (c->cfg.precision == QP_C64)
+        k_part_scatter<float2><<<g, 256, 0, c->stream>>>(c->P, (unsigned)n_ranks, base, cursor,
+                                                         reinterpret_cast<unsigned long long *>(d_keys), static_cast<float2 *>(d_amps));
+    else
+        k_part_scatter<double2><<<g, 256, 0, c->stream>>>(c->P, (unsigned)n_ranks, base, cursor,
+                                                          reinterpret_cast<unsigned long long *>(d_keys), static_cast<double2 *>(d_amps));
+    QP_CUDA(c, cudaGetLastError());
+    QP_CUDA(c, cudaStreamSynchronize(c->stream));   // hb must outlive the copy; the caller reads the buffers next
+    return QP_OK;
+}
+
+qp_status qp_import_paths(qp_ctx *c, const uint64_t *d_keys, const void *d_amps, int64_t n) {
+    if (!c) return QP_ERR_ARG;
+    if (n < 0 || (n > 0 && (!d_keys || !d_amps))) return fail(c, QP_ERR_ARG, "bad arguments");
+    if (!c->have_state) return fail(c, QP_ERR_STATE, "no state");
+    if (c->failed) return fail(c, QP_ERR_STATE, "context holds a device error; call qp_set_rho0");
+    if (c->use_stream || c->P.post || c->P.n_inst > 1)
+        return fail(c, QP_ERR_STATE, "ranks need the merge-table engine, the pre-merging order and a single problem");
+    if (n > c->cfg.max_paths) return fail(c, QP_ERR_CAPACITY, "more paths than max_paths");
+    DevState s;
+    qp_status r = read_state(c, &s);
+    if (r != QP_OK) return r;
+    const int buf = (int)(s.t & 1);
+    const size_t ab = c->cfg.precision == QP_C64 ? sizeof(float2) : sizeof(double2);
+    if (n > 0) {
+        QP_CUDA(c, cudaMemcpyAsync(c->P.keys[buf], d_keys, (size_t)n * 8, cudaMemcpyDeviceToDevice, c->stream));
+        QP_CUDA(c, cudaMemcpyAsync(c->P.amps[buf], d_amps, (size_t)n * ab, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    k_set_count<<<1, 1, 0, c->stream>>>(c->P.st, (unsigned long long)n);
+    QP_CUDA(c, cudaGetLastError());
     QP_CUDA(c, cudaStreamSynchronize(c->stream));
     return QP_OK;
 }
