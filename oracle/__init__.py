@@ -16,7 +16,10 @@ Contents
              SysP) and the influence factor (Eq. inf_fun), filtering
              (Sec. 2.1) and the reduced density matrix (Eq. quapi_red_rho).
   brute.py   the full path sum of Eq. quapi_red_rho enumerated path by path
-             with the influence functional truncated at the memory length.
+             with the influence functional truncated at the memory length,
+             for the right-box reading and for the symmetric Trotter
+             splitting (intervals centred on the points, half intervals at
+             both ends).
 
 Parity status: every function is pinned by tests/test_oracle_pins.py against
 closed forms or brute force; the filter (its rule |amp| >= theta and its

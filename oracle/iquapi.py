@@ -118,11 +118,17 @@ class Result:
     stats: List[StepStats] = field(default_factory=list)
 
 
-def initial_paths(rho0: np.ndarray) -> Paths:
+def initial_paths(rho0: np.ndarray, q=None, ep: Optional[EndPoints] = None) -> Paths:
+    """One path per nonzero element of rho(0); with the symmetric splitting
+    each carries point 0's half-interval self factor."""
     a, b = np.nonzero(rho0)
+    amp = rho0[a, b].astype(np.complex128)
+    if ep is not None:
+        q = np.asarray(q, dtype=np.float64)
+        amp = amp * np.exp(-(q[a] - q[b]) * (ep.eta00 * q[a] - np.conj(ep.eta00) * q[b]))
     return Paths(sp=a.reshape(-1, 1).astype(np.int64),
                  sm=b.reshape(-1, 1).astype(np.int64),
-                 amp=rho0[a, b].astype(np.complex128))
+                 amp=amp)
 
 
 def premerge(paths: Paths, Pp, M: int):
@@ -153,8 +159,50 @@ def premerge(paths: Paths, Pp, M: int):
     return paths.sp[rep_of], paths.sm[rep_of], S, near_tie
 
 
-def step(paths: Paths, t: int, U, q, eta, dkmax: int, Pp, theta: float, M: int):
-    """One propagation step t-1 -> t.  Returns (new paths, rho(t), stats)."""
+@dataclass
+class EndPoints:
+    """Coefficients of the symmetric Trotter splitting (Sec. 2, Eq.
+    quapi_red_rho: "applying a symmetric Trotter splitting"; Eq. inf_fun
+    sums from point 0 to point N).  Point k holds the bath over the interval
+    centred on k dt: interior points a full interval, point 0 the half
+    [0, dt/2] and the newest point N the half [N dt - dt/2, N dt].  With
+    Qh[j] = Q(j dt / 2) (Q the double integral of the bath correlation,
+    oracle/bath.py) and the memory cut at lags >= dkmax:
+      eta00 = Q(dt/2)                     self term of a half interval
+      eta0[k]  (k >= 1)                   interior point k with point 0
+      etaE[d]  (d >= 1)                   the newest point with an interior point d back
+      etaE0[N] (N >= 1)                   the newest point N with point 0
+    Interior pairs keep the full-interval coefficients eta_d of the
+    right-box reading (the same double integrals, shifted by dt/2)."""
+    eta00: complex
+    eta0: np.ndarray      # [dkmax], index k; eta0[0] unused
+    etaE: np.ndarray      # [dkmax], index d; etaE[0] unused
+    etaE0: np.ndarray     # [dkmax], index N; etaE0[0] unused
+
+
+def end_points_from_Q(Qh, dkmax: int) -> EndPoints:
+    """The symmetric splitting's end-point coefficients from Qh[j] = Q(j dt/2),
+    j = 0 .. 2 dkmax (and more; Qh[0] = 0)."""
+    Qh = np.asarray(Qh, dtype=np.complex128)
+    eta0 = np.zeros(dkmax, dtype=np.complex128)
+    etaE = np.zeros(dkmax, dtype=np.complex128)
+    etaE0 = np.zeros(dkmax, dtype=np.complex128)
+    for k in range(1, dkmax):
+        eta0[k] = Qh[2 * k + 1] - Qh[2 * k] - Qh[2 * k - 1] + Qh[2 * k - 2]
+        etaE[k] = Qh[2 * k + 1] - Qh[2 * k - 1] - Qh[2 * k] + Qh[2 * k - 2]
+        etaE0[k] = Qh[2 * k] - 2.0 * Qh[2 * k - 1] + Qh[2 * k - 2]
+    return EndPoints(eta00=complex(Qh[1]), eta0=eta0, etaE=etaE, etaE0=etaE0)
+
+
+def step(paths: Paths, t: int, U, q, eta, dkmax: int, Pp, theta: float, M: int, ep: Optional[EndPoints] = None):
+    """One propagation step t-1 -> t.  Returns (new paths, rho(t), stats).
+
+    ep: the symmetric splitting's end points (None: the right-box reading
+    R1).  The stored amplitudes then carry every factor with the newest
+    point treated as interior (as it will be once later points exist) and
+    point 0 with its half interval; rho(t) multiplies each surviving child
+    by the difference between the newest point's end-point and interior
+    factors."""
     if t >= dkmax:                                  # window full: pre-merge on P'
         rsp, rsm, S, near_tie = premerge(paths, Pp, M)
     else:                                           # nothing merges yet (R3)
@@ -166,6 +214,19 @@ def step(paths: Paths, t: int, U, q, eta, dkmax: int, Pp, theta: float, M: int):
     H = np.zeros(G, dtype=np.complex128)
     for d in range(1, n_act):
         H += eta[d] * q[rsp[:, d - 1]] - np.conj(eta[d]) * q[rsm[:, d - 1]]
+    if ep is not None:
+        # symmetric splitting: point 0 (t steps back, position t-1 while the
+        # window holds it) within memory; and the newest point's end-point
+        # correction for rho(t)
+        HE = np.zeros(G, dtype=np.complex128)
+        for d in range(1, n_act):
+            dE = ep.etaE[d] - eta[d]
+            HE += dE * q[rsp[:, d - 1]] - np.conj(dE) * q[rsm[:, d - 1]]
+        if t < dkmax:
+            H += ep.eta0[t] * q[rsp[:, t - 1]] - np.conj(ep.eta0[t]) * q[rsm[:, t - 1]]
+            dE0 = ep.etaE0[t] - ep.eta0[t]
+            HE += dE0 * q[rsp[:, t - 1]] - np.conj(dE0) * q[rsm[:, t - 1]]
+        dS = ep.eta00 - eta[0]           # the newest point's half interval against a full one
     L_child = min(t + 1, dkmax)
     rho = np.zeros((M, M), dtype=np.complex128)
     new_sp, new_sm, new_amp = [], [], []
@@ -180,7 +241,11 @@ def step(paths: Paths, t: int, U, q, eta, dkmax: int, Pp, theta: float, M: int):
             keep = w2 >= th2
             if th2 > 0:
                 near_theta += int(np.count_nonzero(np.abs(w2 - th2) <= 2e-12 * th2))
-            rho[a, b] = child[keep].sum()
+            if ep is None:
+                rho[a, b] = child[keep].sum()
+            else:
+                corr = np.exp(-(q[a] - q[b]) * (HE + dS * q[a] - np.conj(dS) * q[b]))
+                rho[a, b] = (child * corr)[keep].sum()
             k = int(np.count_nonzero(keep))
             col_a = np.full((k, 1), a, dtype=np.int64)
             col_b = np.full((k, 1), b, dtype=np.int64)
@@ -248,10 +313,12 @@ def step_post(paths: Paths, t: int, U, q, eta, dkmax: int, P, theta: float, M: i
 
 
 def propagate(M: int, q, hs, dt: float, eta, dkmax: int, mask, theta: float,
-              rho0, steps: int, keep_stats: bool = True, scheme: str = "pre") -> Result:
+              rho0, steps: int, keep_stats: bool = True, scheme: str = "pre", Qh=None) -> Result:
     """Run `steps` propagation steps from rho0; rho[t] for t = 0 .. steps.
     scheme "pre": the pre-merging order of Sec. 3.1 (step); "post": the
-    original post-merging order of Sec. 2.1 (step_post)."""
+    original post-merging order of Sec. 2.1 (step_post).  Qh (Q at
+    multiples of dt/2): the symmetric splitting's end points (pre-merging
+    order only); None: the right-box reading R1."""
     q = np.asarray(q, dtype=np.float64)
     eta = np.asarray(eta, dtype=np.complex128)
     if eta.size < dkmax:
@@ -260,14 +327,17 @@ def propagate(M: int, q, hs, dt: float, eta, dkmax: int, mask, theta: float,
     P = check_mask(range(dkmax) if mask is None else mask, dkmax)
     Pp = premerge_positions(P, dkmax)
     U = short_time_propagator(hs, dt)
-    paths = initial_paths(rho0)
+    ep = None if Qh is None else end_points_from_Q(Qh, dkmax)
+    if ep is not None and scheme != "pre":
+        raise ValueError("the symmetric splitting is given for the pre-merging order")
+    paths = initial_paths(rho0, q, ep)
     rhos = [rho0.copy()]
     stats = []
     if scheme not in ("pre", "post"):
         raise ValueError("scheme must be 'pre' or 'post'")
     for t in range(1, steps + 1):
         if scheme == "pre":
-            paths, rho, st = step(paths, t, U, q, eta, dkmax, Pp, theta, M)
+            paths, rho, st = step(paths, t, U, q, eta, dkmax, Pp, theta, M, ep)
         else:
             paths, rho, st = step_post(paths, t, U, q, eta, dkmax, P, theta, M)
         rhos.append(rho)

@@ -391,6 +391,61 @@ def test_post_merging_filtered_markov_map():
     assert np.abs(r.rho - want).max() <= 1e-14
 
 
+# ---------------------------------------------------------------- symmetric splitting
+
+def _random_Qh(seed, n):
+    """Any sequence Q(j dt/2) with Q(0) = 0 defines coefficients both sides
+    must agree on (the pins below need no bath)."""
+    rng = np.random.default_rng(seed)
+    j = np.arange(n)
+    return (0.02 * j ** 1.5 * (1 + 0.1 * rng.normal(size=n))
+            + 1j * 0.01 * j ** 2 * (1 + 0.1 * rng.normal(size=n))) * (j > 0)
+
+
+def eta_from_Qh(Qh, dkmax):
+    """Interior coefficients of full intervals from Q at half steps."""
+    eta = np.zeros(dkmax, dtype=complex)
+    eta[0] = Qh[2]
+    for d in range(1, dkmax):
+        eta[d] = Qh[2 * d + 2] - 2 * Qh[2 * d] + Qh[2 * d - 2]
+    return eta
+
+
+@pytest.mark.parametrize("M,dkmax,N,seed", [(2, 1, 4, 1), (2, 2, 5, 2), (2, 3, 5, 3), (2, 6, 5, 4), (2, 4, 6, 9),
+                                            (3, 2, 4, 5), (3, 3, 3, 6)])
+def test_symmetric_splitting_equals_brute_force(M, dkmax, N, seed):
+    """The iterative propagation with the symmetric splitting's end points
+    (point 0's half interval carried by the stored amplitudes, the newest
+    point's half interval applied to rho(t) only) against the path sum
+    over intervals, written independently from Q at the intervals' ends."""
+    c = W.random_case(seed, M, dkmax)
+    Qh = _random_Qh(seed, 2 * max(dkmax, N) + 4)
+    eta = eta_from_Qh(Qh, dkmax)
+    r = iquapi.propagate(M, c["q"], c["hs"], c["dt"], eta, dkmax, None, 0.0, c["rho0"], N, Qh=Qh)
+    for n in range(1, N + 1):
+        rb = brute.rho_by_enumeration_symmetric(M, c["q"], c["hs"], c["dt"], Qh, dkmax, c["rho0"], n)
+        np.testing.assert_allclose(r.rho[n], rb, rtol=0, atol=2e-14)
+
+
+@pytest.mark.parametrize("mask", [None, (0, 1, 3)])
+def test_symmetric_splitting_pure_dephasing_exact(mask):
+    """H_S = 0: the intervals tile [0, t], so within the memory the exact
+    decoherence function exp(-(q_a-q_b)(q_a Q(t) - q_b Q*(t))) holds for the
+    symmetric splitting too (it pins the end-point coefficients)."""
+    alpha, wc, beta, dt, dkmax, steps = 0.1, 5.0, 5.0, 0.25, 7, 6
+    bath = W.Bath(beta=beta, ohmic_alpha=alpha, ohmic_wc=wc)
+    Qh = ohmic_Q_closed(alpha, wc, beta, 0.5 * dt * np.arange(2 * dkmax + 4))
+    eta = eta_from_Qh(Qh, dkmax)
+    for M, q in [(2, np.array([1.0, -1.0])), (3, np.array([-1.0, 0.0, 1.0]))]:
+        rho0 = np.full((M, M), 1.0 / M, dtype=complex)
+        r = iquapi.propagate(M, q, np.zeros((M, M)), dt, eta, dkmax, mask, 0.0, rho0, steps, Qh=Qh)
+        for n in range(1, steps + 1):
+            Q = ohmic_Q_closed(alpha, wc, beta, n * dt)
+            expect = rho0 * np.exp(-(q[:, None] - q[None, :]) * (q[:, None] * Q - q[None, :] * np.conj(Q)))
+            np.testing.assert_allclose(r.rho[n], expect, atol=1e-13)
+    assert bath.beta == beta
+
+
 # ---------------------------------------------------------------- planted mistakes
 
 MUTATIONS = {
@@ -503,3 +558,38 @@ def test_planted_post_merging_mistake_is_caught(name):
 
 def test_unmutated_oracle_passes_post_merging_harness():
     assert _post_pins_pass(iquapi)
+
+
+SYM_MUTATIONS = {
+    "sym: point 0 without its half interval": ("        amp = amp * np.exp(-(q[a] - q[b]) * (ep.eta00 * q[a] - np.conj(ep.eta00) * q[b]))",
+                                               "        amp = amp * 1.0"),
+    "sym: no end-point correction of rho": ("                rho[a, b] = (child * corr)[keep].sum()", "                rho[a, b] = child[keep].sum()"),
+    "sym: point 0 with the interior coefficient": ("            H += ep.eta0[t] * q[rsp[:, t - 1]] - np.conj(ep.eta0[t]) * q[rsm[:, t - 1]]",
+                                                   "            H += eta[t] * q[rsp[:, t - 1]] - np.conj(eta[t]) * q[rsm[:, t - 1]]"),
+    "sym: end point as interior for the history": ("            dE = ep.etaE[d] - eta[d]", "            dE = 0.0 * eta[d]"),
+    "sym: half interval of the newest point ignored": ("        dS = ep.eta00 - eta[0]", "        dS = 0.0 * eta[0]"),
+}
+
+
+def _sym_pins_pass(mod):
+    try:
+        for (M, dkmax, N, seed) in [(2, 3, 5, 3), (3, 2, 4, 5), (2, 6, 4, 4)]:
+            c = W.random_case(seed, M, dkmax)
+            Qh = _random_Qh(seed, 2 * max(dkmax, N) + 4)
+            r = mod.propagate(M, c["q"], c["hs"], c["dt"], eta_from_Qh(Qh, dkmax), dkmax, None, 0.0, c["rho0"], N, Qh=Qh)
+            rb = brute.rho_by_enumeration_symmetric(M, c["q"], c["hs"], c["dt"], Qh, dkmax, c["rho0"], N)
+            if np.abs(r.rho[N] - rb).max() > 2e-14:
+                return False
+        return True
+    except Exception:
+        return False
+
+
+@pytest.mark.parametrize("name", sorted(SYM_MUTATIONS))
+def test_planted_symmetric_splitting_mistake_is_caught(name):
+    old, new = SYM_MUTATIONS[name]
+    assert not _sym_pins_pass(_mutant(old, new)), f"pins missed: {name}"
+
+
+def test_unmutated_oracle_passes_symmetric_harness():
+    assert _sym_pins_pass(iquapi)
