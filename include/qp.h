@@ -202,6 +202,31 @@ qp_status qp_eta_from_bath(const qp_bath *bath, double dt, int n, double *eta_re
  * device tables of the history sum and of propagator x new-point influence. */
 qp_status qp_set_eta(qp_ctx *ctx, const double *eta_re, const double *eta_im, int n);
 
+/* Q(t) = int_0^t dt' int_0^t' dt'' alpha(t'') at t = j h, j = 0 .. n-1 (the
+ * double integral of the bath correlation function of qp_eta_from_bath, whose
+ * second differences are the coefficients of full intervals).  Host FP64
+ * quadrature, no GPU needed; re/im: [n] caller-owned; 1 <= n <= 8192.      */
+qp_status qp_Q_from_bath(const qp_bath *bath, double h, int n, double *re, double *im);
+
+/* The symmetric Trotter splitting of Eq. quapi_red_rho ("applying a
+ * symmetric Trotter splitting"; Eq. inf_fun sums from point 0 to point N)
+ * instead of the right-box reading of qp_eta_from_bath: point k holds the
+ * bath over the interval centred on k dt, point 0 over [0, dt/2] and the
+ * newest point over [t - dt/2, t].  Given Q at multiples of dt/2,
+ * Qh[j] = Q(j dt/2) for j = 0 .. n-1 (n >= 2 dkmax + 1, Qh[0] = 0; e.g. from
+ * qp_Q_from_bath with h = dt/2), the library forms the interior coefficients
+ * (which replace those of qp_set_eta), the coefficients of point 0 and of
+ * the newest point with every other point, and the half-interval self terms
+ * (memory cut at lags >= dkmax).  The stored amplitudes carry point 0's half
+ * interval and treat the newest point as interior (as it will be once later
+ * points exist); rho(t) multiplies every surviving child by the difference
+ * between its newest point's end-point and interior factors.  Merge-table
+ * engine, pre-merging order, single problems (QP_ERR_STATE otherwise: set
+ * engine QP_ENGINE_HASH or QP_ENGINE_AUTO).  Takes effect at the next
+ * qp_set_rho0; qp_set_eta returns to the right-box reading.  Host arrays
+ * copied before the call returns.                                          */
+qp_status qp_set_end_points(qp_ctx *ctx, const double *qh_re, const double *qh_im, int n);
+
 /* eta of one instance of a batched context (after qp_set_eta, which sets
  * every instance).  inst in [0, n_inst).                                    */
 qp_status qp_set_eta_instance(qp_ctx *ctx, int inst, const double *eta_re, const double *eta_im, int n);

@@ -68,6 +68,10 @@ class Propagator:
     def set_eta(self, eta):
         _abi().qp_set_eta(self.ctx, eta)
 
+    def set_end_points(self, Qh):
+        """Symmetric Trotter splitting from Q at multiples of dt/2 (see qp.h)."""
+        _abi().qp_set_end_points(self.ctx, Qh)
+
     def set_mask(self, positions):
         _abi().qp_set_mask(self.ctx, positions)
 

@@ -90,6 +90,8 @@ def _load():
         "qp_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, _dp]),
         "qp_test_stall_barrier": (ctypes.c_int, [ctypes.c_void_p]),
         "qp_test_stall_lookback": (ctypes.c_int, [ctypes.c_void_p]),
+        "qp_Q_from_bath": (ctypes.c_int, [ctypes.POINTER(qp_bath), ctypes.c_double, ctypes.c_int, _dp, _dp]),
+        "qp_set_end_points": (ctypes.c_int, [ctypes.c_void_p, _dp, _dp, ctypes.c_int]),
         "qp_partition_paths": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                               ctypes.c_int64, _i64p]),
         "qp_import_paths": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
@@ -260,6 +262,21 @@ def qp_autotune(ctx, trial_steps: int = 8, use_cache: bool = True):
 
 def qp_test_stall_barrier(ctx):
     check(lib.qp_test_stall_barrier(ctx), ctx)
+
+
+def qp_Q_from_bath(bath, h: float, n: int) -> np.ndarray:
+    """Q(j h), j = 0 .. n-1 (host quadrature in libqp)."""
+    b = qp_bath(beta=bath.beta, ohmic_alpha=bath.ohmic_alpha, ohmic_wc=bath.ohmic_wc, res_w0=bath.res_w0,
+                res_gamma=bath.res_gamma, res_lambda=bath.res_lambda)
+    re, im = np.zeros(n), np.zeros(n)
+    check(lib.qp_Q_from_bath(ctypes.byref(b), h, n, _ptr(re), _ptr(im)))
+    return re + 1j * im
+
+
+def qp_set_end_points(ctx, Qh):
+    Qh = np.asarray(Qh, dtype=np.complex128)
+    re, im = _arr(Qh.real), _arr(Qh.imag)
+    check(lib.qp_set_end_points(ctx, _ptr(re), _ptr(im), Qh.size), ctx)
 
 
 def qp_test_stall_lookback(ctx):

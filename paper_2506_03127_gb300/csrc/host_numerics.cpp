@@ -129,6 +129,33 @@ struct EtaIntegrand {
     }
 };
 
+// Q(t) = (1/pi) int J(w)/w^2 [coth(beta w/2)(1 - cos wt) - i (wt - sin wt)] dw
+// at t = j h, j = 0 .. n-1 (times pi): the double integral of the bath
+// correlation function from 0, whose second differences are the influence
+// coefficients of full intervals.
+struct QIntegrand {
+    const qp_bath *b;
+    double h;
+    int n;
+    void operator()(double w, double *out) const {
+        const double jw = spectral_density(*b, w) / (w * w);
+        const double coth = 1.0 / std::tanh(0.5 * b->beta * w);
+        for (int j = 0; j < n; ++j) {
+            const double x = w * h * j;
+            double xms;
+            if (x < 0.1) {
+                const double x2 = x * x;
+                xms = x * x2 / 6.0 * (1 - x2 / 20.0 * (1 - x2 / 42.0 * (1 - x2 / 72.0 * (1 - x2 / 110.0))));
+            } else {
+                xms = x - std::sin(x);
+            }
+            const double sh = std::sin(0.5 * x);
+            out[2 * j] = jw * coth * 2.0 * sh * sh;
+            out[2 * j + 1] = -jw * xms;
+        }
+    }
+};
+
 struct Quad {
     std::vector<double> x20, w20, x40, w40;
     Quad() {
@@ -137,7 +164,8 @@ struct Quad {
     }
 };
 
-void panel(const EtaIntegrand &f, const Quad &Q, double a, double b, int nout,
+template <typename F>
+void panel(const F &f, const Quad &Q, double a, double b, int nout,
            std::vector<double> &r20, std::vector<double> &r40, std::vector<double> &buf) {
     const double c = 0.5 * (a + b), h = 0.5 * (b - a);
     std::fill(r20.begin(), r20.end(), 0.0);
@@ -154,14 +182,11 @@ void panel(const EtaIntegrand &f, const Quad &Q, double a, double b, int nout,
 
 }  // namespace
 
-int eta_from_bath(const qp_bath &b, double dt, int n, std::vector<cplx> &eta) {
-    if (!(b.beta > 0.0) || !(dt > 0.0) || n < 1) return 1;
-    if (b.ohmic_alpha != 0.0 && !(b.ohmic_wc > 0.0)) return 1;
-    if (b.res_lambda != 0.0 && (!(b.res_w0 > 0.0) || !(b.res_gamma > 0.0) || b.res_gamma >= 2.0 * b.res_w0))
-        return 1;
+// Adaptive Gauss-Legendre (20/40 points) of nout integrands over frequency,
+// split at the bath's scales; panels no wider than hmax.  acc gets the sums.
+template <typename F>
+void integrate_bath(const qp_bath &b, const F &f, int nout, double hmax, std::vector<double> &acc) {
     const Quad Q;
-    EtaIntegrand f{&b, dt, n};
-    const int nout = 2 * n;
     // breakpoints: ohmic scale and the resonance peak; oscillation period of
     // the largest lag bounds the panel width
     std::vector<double> pts{0.0};
@@ -181,8 +206,8 @@ int eta_from_bath(const qp_bath &b, double dt, int n, std::vector<cplx> &eta) {
     std::sort(pts.begin(), pts.end());
     pts.erase(std::remove_if(pts.begin(), pts.end(), [&](double p) { return p < 0.0 || p > wmax; }), pts.end());
     pts.erase(std::unique(pts.begin(), pts.end()), pts.end());
-    const double hmax = std::max(1e-3, 1.0 / (dt * std::max(1, n)));
-    std::vector<double> acc(nout, 0.0), r20(nout), r40(nout), buf(nout);
+    acc.assign(nout, 0.0);
+    std::vector<double> r20(nout), r40(nout), buf(nout);
     struct Seg { double a, b; int depth; };
     std::vector<Seg> stack;
     for (size_t i = 0; i + 1 < pts.size(); ++i) {
@@ -204,8 +229,33 @@ int eta_from_bath(const qp_bath &b, double dt, int n, std::vector<cplx> &eta) {
             }
         }
     }
+}
+
+static bool bath_ok(const qp_bath &b) {
+    if (!(b.beta > 0.0)) return false;
+    if (b.ohmic_alpha != 0.0 && !(b.ohmic_wc > 0.0)) return false;
+    if (b.res_lambda != 0.0 && (!(b.res_w0 > 0.0) || !(b.res_gamma > 0.0) || b.res_gamma >= 2.0 * b.res_w0))
+        return false;
+    return true;
+}
+
+int eta_from_bath(const qp_bath &b, double dt, int n, std::vector<cplx> &eta) {
+    if (!bath_ok(b) || !(dt > 0.0) || n < 1) return 1;
+    EtaIntegrand f{&b, dt, n};
+    std::vector<double> acc;
+    integrate_bath(b, f, 2 * n, std::max(1e-3, 1.0 / (dt * std::max(1, n))), acc);
     eta.assign(n, cplx(0.0, 0.0));
     for (int d = 0; d < n; ++d) eta[d] = cplx(acc[2 * d], acc[2 * d + 1]) / M_PI;
+    return 0;
+}
+
+int Q_from_bath(const qp_bath &b, double h, int n, std::vector<cplx> &Q) {
+    if (!bath_ok(b) || !(h > 0.0) || n < 1) return 1;
+    QIntegrand f{&b, h, n};
+    std::vector<double> acc;
+    integrate_bath(b, f, 2 * n, std::max(1e-3, 1.0 / (h * std::max(1, n))), acc);
+    Q.assign(n, cplx(0.0, 0.0));
+    for (int j = 0; j < n; ++j) Q[j] = cplx(acc[2 * j], acc[2 * j + 1]) / M_PI;
     return 0;
 }
 

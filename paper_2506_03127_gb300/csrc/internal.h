@@ -22,4 +22,7 @@ double spectral_density(const qp_bath &b, double w);
 // eta_0 .. eta_{n-1}, box double integrals of the bath correlation function.
 int eta_from_bath(const qp_bath &b, double dt, int n, std::vector<cplx> &eta);
 
+// Q(j h), j = 0 .. n-1: the double integral of the bath correlation from 0.
+int Q_from_bath(const qp_bath &b, double h, int n, std::vector<cplx> &Q);
+
 }  // namespace qp

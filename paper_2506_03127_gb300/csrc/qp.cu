@@ -133,6 +133,16 @@ struct Params {
     const double2 *etab;               // [dkmax][ndelta][nchunks][256] exp(-delta_d T) tables (FP64 path)
     int ndelta;                        // distinct nonzero q_a - q_b
     float deltaf[12];                  // their values (FP32 path)
+    // symmetric Trotter splitting (merge-table engine, single problems):
+    // history tables with point 0 on its half interval, and for rho(t) the
+    // newest point's end-point correction: tables of the coefficient
+    // differences and the per-child half-interval factor (wEt)
+    int sym;
+    const double2 *lutE;
+    const float2 *lutEf, *lutElo;
+    const double2 *etabE;
+    const double2 *wEt;                // [M*M child][M*M parent], the same for every parent
+    const float4 *wEtf;
     int qeq;                           // 1: q equally spaced, q_a = q_0 + a s (s != 0)
     int d_pos, d_neg;                  // ... indices of +s and -s among the differences
     float qstepf;                      // ... s (FP32 path)
@@ -443,6 +453,16 @@ __device__ __forceinline__ Tab tab_global(const Params &P, int n_act, int inst) 
     return t;
 }
 
+// The end-point correction's tables (symmetric splitting) at a window length.
+__device__ __forceinline__ Tab tab_E(const Params &P, int n_act) {
+    const size_t row = (size_t)(n_act - 1) * P.nchunks * kLutEntries;
+    Tab t;
+    t.hi = P.lutEf + row;
+    t.lo = P.lutElo + row;
+    t.et = P.etabE + (size_t)P.ndelta * row;
+    return t;
+}
+
 template <int M, bool C64>
 struct Expander {
     static constexpr int MM = M * M;
@@ -744,16 +764,35 @@ __device__ __forceinline__ void phase_expand(const Params &P, unsigned long long
                 if (keepbits) atomicAdd(&acc[MM].x, (double)__popc(keepbits));
             } else {
                 keepbits = X::children(P, n_act, 0, rep, S, s_w, s_wf, camp);
+                if (P.sym) {
+                    // symmetric splitting: rho(t) takes every surviving child
+                    // times its newest point's end-point correction (the
+                    // stored child keeps the interior factors)
+                    AmpT cr[MM];
+                    X::children_tab(P, tab_E(P, n_act), rep, make_double2(1.0, 0.0), P.wEt, P.wEtf, cr);
 #pragma unroll
-                for (int k = 0; k < MM; ++k)
-                    if (keepbits & (1u << k)) {
-                        if constexpr (C64) {
-                            X::kahan_add(racc[k], rcmp[k], camp[k]);
-                        } else {
-                            racc[k].x += camp[k].x;
-                            racc[k].y += camp[k].y;
+                    for (int k = 0; k < MM; ++k)
+                        if (keepbits & (1u << k)) {
+                            if constexpr (C64) {
+                                X::kahan_add(racc[k], rcmp[k], cmulf(camp[k], cr[k]));
+                            } else {
+                                const double2 v = cmul(camp[k], cr[k]);
+                                racc[k].x += v.x;
+                                racc[k].y += v.y;
+                            }
                         }
-                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < MM; ++k)
+                        if (keepbits & (1u << k)) {
+                            if constexpr (C64) {
+                                X::kahan_add(racc[k], rcmp[k], camp[k]);
+                            } else {
+                                racc[k].x += camp[k].x;
+                                racc[k].y += camp[k].y;
+                            }
+                        }
+                }
             }
         }
         const unsigned cnt = __popc(keepbits);
@@ -2702,8 +2741,11 @@ __global__ void k_clear_table(Slot *slots, unsigned long long *repk, unsigned lo
 // History tables: for n_act = 1..dkmax, chunk j (one byte of the key), byte
 // value v: sum over the positions p of the byte with p <= n_act - 2 of
 // eta_{p+1} q[s+_p] - conj(eta_{p+1}) q[s-_p] (lag p+1 of the new point).
+// eta0 (symmetric splitting, else NULL): while the window fills (n_act <
+// dkmax) the oldest position n_act - 1 holds point 0, which enters with its
+// own coefficient eta0[n_act] (its half interval) instead of being left out.
 __global__ void k_build_lut(double2 *lut, float2 *lutf, float2 *lutlo, const double2 *eta, const double *q,
-                            int M, int bs, int b, int dkmax, int nchunks) {
+                            int M, int bs, int b, int dkmax, int nchunks, const double2 *eta0) {
     const int total = dkmax * nchunks * kLutEntries;
     const int ppc = 8 / b;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
@@ -2713,11 +2755,12 @@ __global__ void k_build_lut(double2 *lut, float2 *lutf, float2 *lutlo, const dou
         double hx = 0.0, hy = 0.0;
         for (int k = 0; k < ppc; ++k) {
             const int p = j * ppc + k;
-            if (p > n_act - 2) continue;
+            const bool point0 = eta0 != nullptr && n_act < dkmax && p == n_act - 1;
+            if (p > n_act - 2 && !point0) continue;
             const int code = (v >> (b * k)) & ((1 << b) - 1);
             const int sp = code & ((1 << bs) - 1), sm = code >> bs;
             if (sp >= M || sm >= M) continue;   // codes that never occur
-            const double2 e = eta[p + 1];
+            const double2 e = point0 ? eta0[n_act] : eta[p + 1];
             // eta q+ - conj(eta) q-
             hx += e.x * q[sp] - e.x * q[sm];
             hy += e.y * q[sp] + e.y * q[sm];
@@ -2782,6 +2825,7 @@ struct Layout {
         rho, rho_part, spart, scount, stats, inst_kept, fin_count, tile_state, state, total;
     size_t ckeys, camps, skey[2], sidx[2], rs_hist, rs_part, rbk_heads;   // post-merging engine
     size_t ranks;                                                        // per-rank counts, bases, cursors
+    size_t lutE, lutEf, lutElo, etabE, wEt, wEtf, eta0d, dEd, dE0d;       // symmetric splitting
     long long max_chunks;
     long long entries, max_tiles;
     size_t nlut;           // history-table entries of one instance
@@ -2938,6 +2982,17 @@ Layout make_layout(const qp_config *c) {
     L.max_tiles = (long long)MM * ((mp / MM + kStreamMinTile - 1) / kStreamMinTile + 1);   // smallest tile
     L.tile_state = take((size_t)L.max_tiles * MM * 8);
     L.ranks = take((size_t)3 * kMaxRanks * 8);
+    if (NI == 1) {   // symmetric splitting (single problems): correction tables, coefficient arrays
+        L.lutE = take(nlut * sizeof(double2));
+        L.lutEf = take(nlut * sizeof(float2));
+        L.lutElo = take(nlut * sizeof(float2));
+        L.etabE = take(nlut * std::max(1, nd) * sizeof(double2));
+        L.wEt = take((size_t)MM * MM * sizeof(double2));
+        L.wEtf = take((size_t)MM * MM * sizeof(float4));
+        L.eta0d = take((size_t)c->dkmax * sizeof(double2));
+        L.dEd = take((size_t)c->dkmax * sizeof(double2));
+        L.dE0d = take((size_t)c->dkmax * sizeof(double2));
+    }
     if (c->scheme == QP_POSTMERGE) {   // unmerged set, sort pairs, digit counts, scan partials, run heads
         L.max_chunks = (mp + kSortChunk - 1) / kSortChunk + 1;
         L.ckeys = take(mp * 8);
@@ -2983,6 +3038,8 @@ struct qp_ctx {
     size_t rcache_smem = 0;
     int rcache_res = 0;
     bool use_stream = false;           // this propagation runs on the stream engine
+    bool sym = false;                  // symmetric Trotter splitting (qp_set_end_points)
+    qp::cplx eta00;                    // ... point 0's half-interval self coefficient
     cudaGraphExec_t graph1 = nullptr;  // one-step graph for remainders
     cudaGraphExec_t graph = nullptr;
     bool graph_dirty = true;
@@ -3506,7 +3563,7 @@ qp_status qp_eta_from_bath(const qp_bath *bath, double dt, int n, double *eta_re
     return QP_OK;
 }
 
-static qp_status set_eta_one(qp_ctx *c, int inst, const double *re, const double *im) {
+static qp_status set_eta_one(qp_ctx *c, int inst, const double *re, const double *im, const double2 *eta0 = nullptr) {
     const int dk = c->cfg.dkmax, M = c->cfg.M, MM = M * M;
     std::vector<double2> e(dk);
     for (int i = 0; i < dk; ++i) {
@@ -3521,7 +3578,7 @@ static qp_status set_eta_one(qp_ctx *c, int inst, const double *re, const double
     if (P.nchunks > 0) {
         k_build_lut<<<64, 256, 0, c->stream>>>(lut, reinterpret_cast<float2 *>(c->ws + c->L.lutf) + inst * P.lut_stride,
                                                reinterpret_cast<float2 *>(c->ws + c->L.lutlo) + inst * P.lut_stride, ed,
-                                               qd, M, P.bs, P.b, dk, P.nchunks);
+                                               qd, M, P.bs, P.b, dk, P.nchunks, eta0);
         QP_CUDA(c, cudaGetLastError());
     }
     k_build_w<<<1, 256, 0, c->stream>>>(reinterpret_cast<double2 *>(c->ws + c->L.wtab) + (size_t)inst * MM * MM,
@@ -3541,11 +3598,116 @@ static qp_status set_eta_one(qp_ctx *c, int inst, const double *re, const double
 qp_status qp_set_eta(qp_ctx *c, const double *re, const double *im, int n) {
     if (!c) return QP_ERR_ARG;
     if (!re || !im || n < c->cfg.dkmax) return fail(c, QP_ERR_ARG, "need dkmax influence coefficients");
+    c->sym = false;   // back to the right-box reading
+    c->P.sym = 0;
+    c->graph_dirty = true;
     for (int inst = 0; inst < c->P.n_inst; ++inst) {
         const qp_status st = set_eta_one(c, inst, re, im);
         if (st != QP_OK) return st;
     }
     c->have_eta = true;
+    return QP_OK;
+}
+
+qp_status qp_Q_from_bath(const qp_bath *bath, double h, int n, double *re, double *im) {
+    if (!bath || !re || !im || n < 1 || n > 8192) return QP_ERR_ARG;
+    std::vector<qp::cplx> Q;
+    if (qp::Q_from_bath(*bath, h, n, Q)) return QP_ERR_ARG;
+    for (int i = 0; i < n; ++i) {
+        re[i] = Q[i].real();
+        im[i] = Q[i].imag();
+    }
+    return QP_OK;
+}
+
+qp_status qp_set_end_points(qp_ctx *c, const double *qr, const double *qi, int n) {
+    if (!c) return QP_ERR_ARG;
+    const int dk = c->cfg.dkmax, M = c->cfg.M, MM = M * M;
+    if (!qr || !qi || n < 2 * dk + 1) return fail(c, QP_ERR_ARG, "need Q at multiples of dt/2 up to 2 dkmax");
+    if (c->P.n_inst > 1 || c->P.post || c->cfg.engine == QP_ENGINE_STREAM)
+        return fail(c, QP_ERR_STATE, "the symmetric splitting runs on the merge-table engine, pre-merging order, "
+                                     "single problems");
+    std::vector<qp::cplx> Qh(n);
+    for (int j = 0; j < n; ++j) {
+        if (!std::isfinite(qr[j]) || !std::isfinite(qi[j])) return fail(c, QP_ERR_ARG, "Q must be finite");
+        Qh[j] = qp::cplx(qr[j], qi[j]);
+    }
+    // interior (full-interval) coefficients, point 0 with an interior point,
+    // the newest point with an interior point and with point 0 (memory cut at
+    // lags >= dkmax); the corrections are end-point minus interior values
+    std::vector<double> er(dk), ei(dk);
+    std::vector<double2> eta0(dk), dE(dk), dE0(dk);
+    std::vector<qp::cplx> eta(dk);
+    eta[0] = Qh[2];
+    for (int d = 1; d < dk; ++d) eta[d] = Qh[2 * d + 2] - 2.0 * Qh[2 * d] + Qh[2 * d - 2];
+    for (int d = 0; d < dk; ++d) {
+        er[d] = eta[d].real();
+        ei[d] = eta[d].imag();
+    }
+    eta0[0] = dE[0] = dE0[0] = make_double2(0.0, 0.0);
+    for (int k = 1; k < dk; ++k) {
+        const qp::cplx e0 = Qh[2 * k + 1] - Qh[2 * k] - Qh[2 * k - 1] + Qh[2 * k - 2];
+        const qp::cplx eE = Qh[2 * k + 1] - Qh[2 * k - 1] - Qh[2 * k] + Qh[2 * k - 2];
+        const qp::cplx eE0 = Qh[2 * k] - 2.0 * Qh[2 * k - 1] + Qh[2 * k - 2];
+        eta0[k] = make_double2(e0.real(), e0.imag());
+        dE[k] = make_double2((eE - eta[k]).real(), (eE - eta[k]).imag());
+        dE0[k] = make_double2((eE0 - e0).real(), (eE0 - e0).imag());
+    }
+    const qp::cplx dS = Qh[1] - eta[0];   // the newest point's half interval against a full one
+    std::vector<double2> wE((size_t)MM * MM);
+    std::vector<float4> wEf((size_t)MM * MM);
+    for (int k = 0; k < MM; ++k) {
+        const int a = k / M, b = k % M;
+        const double qa = c->q[a], qb = c->q[b];
+        const qp::cplx z = -(qa - qb) * (dS * qa - std::conj(dS) * qb);
+        const qp::cplx f = std::exp(z);
+        for (int par = 0; par < MM; ++par) {
+            wE[(size_t)k * MM + par] = make_double2(f.real(), f.imag());
+            const float hx = (float)f.real(), hy = (float)f.imag();
+            wEf[(size_t)k * MM + par] = make_float4(hx, hy, (float)(f.real() - (double)hx), (float)(f.imag() - (double)hy));
+        }
+    }
+    const Params &P = c->P;
+    double2 *eta0d = reinterpret_cast<double2 *>(c->ws + c->L.eta0d);
+    double2 *dEd = reinterpret_cast<double2 *>(c->ws + c->L.dEd);
+    double2 *dE0d = reinterpret_cast<double2 *>(c->ws + c->L.dE0d);
+    QP_CUDA(c, cudaMemcpyAsync(eta0d, eta0.data(), dk * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
+    QP_CUDA(c, cudaMemcpyAsync(dEd, dE.data(), dk * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
+    QP_CUDA(c, cudaMemcpyAsync(dE0d, dE0.data(), dk * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
+    QP_CUDA(c, cudaMemcpyAsync(c->ws + c->L.wEt, wE.data(), wE.size() * sizeof(double2), cudaMemcpyHostToDevice,
+                               c->stream));
+    QP_CUDA(c, cudaMemcpyAsync(c->ws + c->L.wEtf, wEf.data(), wEf.size() * sizeof(float4), cudaMemcpyHostToDevice,
+                               c->stream));
+    // the propagation's own tables, with point 0 on its half interval
+    qp_status st = set_eta_one(c, 0, er.data(), ei.data(), eta0d);
+    if (st != QP_OK) return st;
+    // the correction's history tables (and their exp(-delta T) products for FP64)
+    const double *qd = reinterpret_cast<const double *>(c->ws + c->L.q);
+    double2 *lutE = reinterpret_cast<double2 *>(c->ws + c->L.lutE);
+    if (P.nchunks > 0) {
+        k_build_lut<<<64, 256, 0, c->stream>>>(lutE, reinterpret_cast<float2 *>(c->ws + c->L.lutEf),
+                                               reinterpret_cast<float2 *>(c->ws + c->L.lutElo), dEd, qd, M, P.bs, P.b,
+                                               dk, P.nchunks, dE0d);
+        QP_CUDA(c, cudaGetLastError());
+        if (P.ndelta > 0) {
+            k_build_etab<<<256, 256, 0, c->stream>>>(reinterpret_cast<double2 *>(c->ws + c->L.etabE), lutE,
+                                                     reinterpret_cast<const double *>(c->ws + c->L.deltas), P.ndelta,
+                                                     dk, P.nchunks);
+            QP_CUDA(c, cudaGetLastError());
+        }
+    }
+    QP_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->P.lutE = lutE;
+    c->P.lutEf = reinterpret_cast<const float2 *>(c->ws + c->L.lutEf);
+    c->P.lutElo = reinterpret_cast<const float2 *>(c->ws + c->L.lutElo);
+    c->P.etabE = reinterpret_cast<const double2 *>(c->ws + c->L.etabE);
+    c->P.wEt = reinterpret_cast<const double2 *>(c->ws + c->L.wEt);
+    c->P.wEtf = reinterpret_cast<const float4 *>(c->ws + c->L.wEtf);
+    c->P.sym = 1;
+    c->sym = true;
+    c->eta00 = Qh[1];
+    c->have_eta = true;
+    c->graph_dirty = true;
     return QP_OK;
 }
 
@@ -3619,13 +3781,22 @@ qp_status qp_set_rho0(qp_ctx *c, const double *re, const double *im) {
     if (!c->P.post && c->cfg.engine == QP_ENGINE_STREAM && c->stream_nx == 0)
         return fail(c, QP_ERR_ARG, "the stream engine needs a mask whose P' is a prefix {0..k-1} plus at most one "
                                    "extra position (M = 2) and a single instance");
-    c->use_stream = !c->P.post &&
+    c->use_stream = !c->P.post && !c->sym &&
                     (c->cfg.engine == QP_ENGINE_STREAM || (c->cfg.engine == QP_ENGINE_AUTO && c->stream_nx > 0));
     if (c->use_stream && c->P.region_cap < 1) return fail(c, QP_ERR_CAPACITY, "max_paths < 16 M*M (stream engine)");
     c->P.stream = c->use_stream ? 1 : 0;
     c->graph_dirty = true;
     const size_t n = keys.size();
     const size_t ab = c->cfg.precision == QP_C64 ? sizeof(float2) : sizeof(double2);
+    if (c->sym) {   // point 0 on its half interval: its self factor in the stored amplitudes
+        for (size_t i = 0; i < n; ++i) {
+            const int a = (int)(keys[i] & ((1u << bs) - 1u)), b = (int)((keys[i] >> bs) & ((1u << bs) - 1u));
+            const double qa = c->q[a], qb = c->q[b];
+            const qp::cplx f = std::exp(-(qa - qb) * (c->eta00 * qa - std::conj(c->eta00) * qb)) *
+                               qp::cplx(amps[i].x, amps[i].y);
+            amps[i] = make_double2(f.real(), f.imag());
+        }
+    }
     std::vector<float2> af(n);
     for (size_t i = 0; i < n; ++i) af[i] = make_float2((float)amps[i].x, (float)amps[i].y);
     const void *asrc = c->cfg.precision == QP_C64 ? (const void *)af.data() : (const void *)amps.data();
@@ -4486,7 +4657,7 @@ extern "C" qp_status qp_step_noalloc(const qp_config *cfg, const double *eta_re,
     k_na_setup<<<1, 32, 0, stream>>>(su, etad, qd, Ud, deltad, st, P.fin_count);
     k_clear_table<<<nsm * 4, 256, 0, stream>>>(P.slots, P.repk, 1ull << kNaTcapLog2);
     if (P.nchunks > 0)
-        k_build_lut<<<64, 256, 0, stream>>>(lut, lutf, lutlo, etad, qd, M, P.bs, P.b, dk, P.nchunks);
+        k_build_lut<<<64, 256, 0, stream>>>(lut, lutf, lutlo, etad, qd, M, P.bs, P.b, dk, P.nchunks, nullptr);
     k_build_w<<<1, 256, 0, stream>>>(wtab, wtabf, Ud, etad, qd, M);
     if (P.nchunks > 0 && P.ndelta > 0) k_build_etab<<<256, 256, 0, stream>>>(etab, lut, deltad, P.ndelta, dk, P.nchunks);
     // the step: the same kernels as qp_step

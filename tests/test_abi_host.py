@@ -118,3 +118,13 @@ def test_eta_from_bath_rejects_bad_bath():
     b = abi.qp_bath(beta=-1.0, ohmic_alpha=0.1, ohmic_wc=5.0)
     re, im = np.zeros(4), np.zeros(4)
     assert abi.lib.qp_eta_from_bath(ctypes.byref(b), 0.1, 4, abi._ptr(re), abi._ptr(im)) == abi.QP_ERR_ARG
+
+
+@pytest.mark.parametrize("w", [W.SPIN_BOSON_OHMIC_DK8, W.SPIN_BOSON_STRUCTURED_DK16], ids=lambda w: w.name)
+def test_library_Q_at_half_steps_matches_oracle(w):
+    """Q(j dt/2), the input of the symmetric splitting, by the library's host
+    quadrature against the oracle's (scipy) quadrature."""
+    n = 2 * w.dkmax + 2
+    ql = abi.qp_Q_from_bath(w.bath, 0.5 * w.dt, n)
+    qo = np.concatenate([[0.0], B.Q_of_t(w.bath, 0.5 * w.dt * np.arange(1, n))])
+    np.testing.assert_allclose(ql, qo, rtol=0, atol=1e-13)
