@@ -88,7 +88,6 @@ struct __align__(128) DevState {
     unsigned int err;                 // error bits, sticky until qp_set_rho0
     unsigned int stall_tile;          // test hook: tile ticket + 1 whose look-back words are withheld (0: none)
     unsigned long long err_t;         // step at which the error was raised
-    unsigned long long reg_n[2][16];  // stream engine: stored paths per region, by buffer parity
     unsigned int ticket[3];           // stream engine: tile tickets, step t' uses [t' % 3]
     unsigned int pad0;
     unsigned long long reg_done;      // stream engine: tn + 1 when the regular kernel took step tn, else 0
@@ -166,6 +165,7 @@ struct Params {
     unsigned long long prefmask;       // key bits of the prefix positions 0 .. k-1 of P'
     int x_shift;                       // key bit of the one extra position of P' (NX = 4), else -1
     long long region_cap;              // entries per region
+    unsigned long long *reg_n;         // [2 (buffer parity)][n_inst][M*M] stored paths per region (stream engine)
     // regular steps of the stream engine (no filter): while the window fills
     // every stored path is its own group; with the full mask, once all
     // full_n = M^(2 dkmax) keys are stored every group is the M*M values of
@@ -1068,10 +1068,26 @@ __device__ __forceinline__ void finish_pending_rho(const Params &P, DevState *st
     if (threadIdx.x == 0) st->rho_pending = 0;
 }
 
+// Batches of the stream engine: rho(t) and the survivor count of the
+// pending step per instance, instance i by block i (then i + gridDim.x, ...),
+// from the blocks' partials ([block][instance][M*M + 1], phase_finalize:
+// summed in block order).  The step kernels leave the mark (each block
+// reads it; the next step's last block replaces it); a one-block read-time
+// call clears it.  Block-uniform.
+__device__ __forceinline__ void finish_pending_rho_batch(const Params &P, DevState *st, int MM, bool clear) {
+    const unsigned long long pt = __ldcg(&st->rho_pending);
+    if (pt == 0) return;
+    const int nblk = (int)__ldcg(&st->rho_nblk);
+    for (int inst = blockIdx.x; inst < P.n_inst; inst += gridDim.x)
+        phase_finalize(P, pt, inst, rho_part_of(P, pt, MM), nblk, MM);
+    if (clear && threadIdx.x == 0) st->rho_pending = 0;
+}
+
 template <bool C64>
 __global__ void k_rho_finalize(Params P, int MM) {
     if (P.st->err) return;
-    finish_pending_rho<C64>(P, P.st, MM);
+    if (P.n_inst > 1) finish_pending_rho_batch(P, P.st, MM, gridDim.x == 1);
+    else finish_pending_rho<C64>(P, P.st, MM);
 }
 
 // The same (finalize: stream engine), then rho(t0 ...) for nelem = count *
@@ -1079,7 +1095,10 @@ __global__ void k_rho_finalize(Params P, int MM) {
 // (page-locked): no separate copy.  One block.
 template <bool C64>
 __global__ void k_rho_read_to(Params P, int MM, int finalize, double2 *dst, long long t0, long long nelem) {
-    if (finalize && !P.st->err) finish_pending_rho<C64>(P, P.st, MM);
+    if (finalize && !P.st->err) {
+        if (P.n_inst > 1) finish_pending_rho_batch(P, P.st, MM, true);
+        else finish_pending_rho<C64>(P, P.st, MM);
+    }
     const long long per = (long long)P.n_inst * MM;
     for (long long i = threadIdx.x; i < nelem; i += blockDim.x) {
         const long long t = t0 + i / per;
@@ -1249,7 +1268,7 @@ __global__ void __launch_bounds__(kRegThreads, 3) k_stream_regular(Params P, int
         const int gsz = merge ? MM : 1;
         unsigned long long n_in = 0;
         for (int r = 0; r < MM; ++r) {
-            const long long nr = (long long)__ldcg(&st->reg_n[in][r]);
+            const long long nr = (long long)__ldcg(&P.reg_n[in * MM + r]);
             n_in += (unsigned long long)nr;
             s_gb[r] = acc;
             acc += nr / gsz;
@@ -1295,7 +1314,7 @@ __global__ void __launch_bounds__(kRegThreads, 3) k_stream_regular(Params P, int
         }
     }
     if (blockIdx.x == 0) {
-        if ((int)threadIdx.x < MM) st->reg_n[outp][threadIdx.x] = (unsigned long long)ngroups;
+        if ((int)threadIdx.x < MM) P.reg_n[outp * MM + threadIdx.x] = (unsigned long long)ngroups;
         if (threadIdx.x == 0) {
             st->cnt_out[cs] = (unsigned long long)ngroups * MM;
             st->cnt_groups[cs] = (unsigned long long)ngroups;
@@ -1484,6 +1503,89 @@ struct StreamLayout {
     static constexpr size_t bytes = lut;   // + staged history tables (run time)
 };
 
+// Batches of the stream engine: the step's tile size (the smallest multiple
+// of NT, up to EPT NT, whose tiles do not outnumber the blocks) into *s_St
+// and the first tile of each of the R regions into s_t0[0 .. R] (exclusive
+// scan of the regions' tile counts, R <= 2048); block 0 also empties the
+// output regions of instances without tiles (otherwise an instance's last
+// tile writes its sizes).  All threads; ends with a barrier.
+template <int NT, int EPT>
+__device__ __forceinline__ void stream_batch_tiles(const unsigned long long *rn_in, unsigned long long *rn_out, int R,
+                                                   int MM, int *s_t0, int *s_St) {
+    constexpr int NW = NT / 32;
+    constexpr int RPT = 2048 / NT;   // regions per thread at most
+    __shared__ unsigned long long s_ks[EPT];
+    __shared__ unsigned s_ws[NW];
+    const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+    const int rpt = (R + NT - 1) / NT;
+    const int r0 = (int)threadIdx.x * rpt;
+    unsigned q[RPT];   // tiles of NT paths per region
+#pragma unroll
+    for (int u = 0; u < RPT; ++u) {
+        const int r = r0 + u;
+        q[u] = (u < rpt && r < R) ? (unsigned)((__ldcg(rn_in + r) + NT - 1) / NT) : 0u;
+    }
+    if ((int)threadIdx.x < EPT) s_ks[threadIdx.x] = 0;
+    __syncthreads();
+#pragma unroll
+    for (int k = 1; k < EPT; ++k) {   // tiles at k NT paths per tile
+        unsigned long long tk = 0;
+#pragma unroll
+        for (int u = 0; u < RPT; ++u) tk += (q[u] + k - 1) / k;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) tk += __shfl_down_sync(0xffffffffu, tk, o);
+        if (lane == 0 && tk) atomicAdd(&s_ks[k], tk);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int St = EPT * NT;
+        for (int k = 1; k < EPT; ++k)
+            if (s_ks[k] <= (unsigned long long)gridDim.x) {
+                St = k * NT;
+                break;
+            }
+        *s_St = St;
+    }
+    __syncthreads();
+    const unsigned kst = (unsigned)(*s_St / NT);
+    unsigned cnt[RPT], lsum = 0;
+#pragma unroll
+    for (int u = 0; u < RPT; ++u) {
+        cnt[u] = (q[u] + kst - 1) / kst;
+        lsum += cnt[u];
+    }
+    unsigned inc = lsum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
+        if ((int)lane >= o) inc += y;
+    }
+    if (lane == 31) s_ws[warp] = inc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned a = 0;
+        for (int w = 0; w < NW; ++w) {
+            const unsigned v = s_ws[w];
+            s_ws[w] = a;
+            a += v;
+        }
+        s_t0[R] = (int)a;
+    }
+    __syncthreads();
+    unsigned pos = s_ws[warp] + inc - lsum;
+#pragma unroll
+    for (int u = 0; u < RPT; ++u)
+        if (u < rpt && r0 + u < R) {
+            s_t0[r0 + u] = (int)pos;
+            pos += cnt[u];
+        }
+    __syncthreads();
+    if (blockIdx.x == 0)
+        for (int i = threadIdx.x; i < R / MM; i += NT)
+            if (s_t0[i * MM] == s_t0[(i + 1) * MM])
+                for (int c = 0; c < MM; ++c) rn_out[i * MM + c] = 0;
+}
+
 // Relaxed GPU-scope load of a word other blocks publish (no L1, no
 // hoisting; independent loads stay in flight together).
 __device__ __forceinline__ unsigned long long ld_relaxed_gpu(const unsigned long long *p) {
@@ -1510,9 +1612,8 @@ __device__ __forceinline__ unsigned long long ld_relaxed_gpu(const unsigned long
 // last block to finish sums the blocks' partials of rho(t+1) and publishes
 // the step.  lut_smem: the history tables of this window length are copied
 // into shared memory once per block.
-template <int M, bool C64, int NX, int S>
-__global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 2 : 1)
-    k_stream_step(Params P, int lut_smem) {
+template <int M, bool C64, int NX, int S, bool BATCH>
+__device__ __forceinline__ void stream_step_body(const Params &P, int lut_smem) {
     using X = Expander<M, C64>;
     using Lay = StreamLayout<M, C64, NX, S>;
     using AmpT = typename X::AmpT;
@@ -1523,11 +1624,15 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
     static_assert(S % NT == 0 && EPT <= 32, "tile size");
     static_assert(NX <= 16, "slot map: 4 bits of x");
     static_assert(NW == kStreamWarps, "warp partials");
+    static_assert(!BATCH || NX == 1, "batches: P' a prefix of the window");
     DevState *st = P.st;
-    if (st->err) return;
-    if (st->reg_done == st->t + 1) return;   // the regular kernel just took this step (its new t + 1)
-    if (blockIdx.x == 0) finish_pending_rho<C64>(P, st, M * M);   // rho of the previous step
-    const unsigned long long t = st->t, tn = t + 1;
+    // (device state read through L2: the persistent batch kernel runs
+    // several steps in one launch)
+    if (__ldcg(&st->err)) return;
+    const unsigned long long t = __ldcg(&st->t), tn = t + 1;
+    if (__ldcg(&st->reg_done) == tn) return;   // the regular kernel just took this step (its new t + 1)
+    if constexpr (BATCH) finish_pending_rho_batch(P, st, M * M, false);   // blocks b < n_inst: instance b
+    else if (blockIdx.x == 0) finish_pending_rho<C64>(P, st, M * M);   // rho of the previous step
     const int in = (int)(t & 1), outp = (int)(tn & 1), cs = (int)(tn % 3);
     const bool merge = tn >= (unsigned long long)P.dkmax;
     const unsigned long long pref = merge ? P.prefmask : ~0ull;   // filling: every path is its own group
@@ -1556,8 +1661,8 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
     unsigned *s_xmask = reinterpret_cast<unsigned *>(s_dyn + Lay::stg);
     static_assert(NX == 1 || (Lay::stage && (size_t)Lay::NSTG * MM * sizeof(AmpT) >= (size_t)S * NX * 4),
                   "sub-group member masks live in the staging buffer");
-    __shared__ double2 s_w[C64 ? 1 : MM * MM];   // FP64 weights (FP64 path only)
-    __shared__ float4 s_wf[MM * MM];
+    __shared__ double2 s_w[C64 || BATCH ? 1 : MM * MM];   // FP64 weights (FP64 path only)
+    __shared__ float4 s_wf[BATCH ? 1 : MM * MM];
     __shared__ long long s_nr[MM], s_tile0[MM + 1];
     __shared__ unsigned s_wsum[NW][MM];
     __shared__ unsigned long long s_base[MM], s_tot[MM], s_kprev;
@@ -1570,19 +1675,27 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
     __shared__ int s_any;   // the block processed a tile
     __shared__ int s_lbfail;   // the tile's look-back gave up (timeout, or another block's error)
     const double tie_d = 1.0 - P.tie_rel;   // R4 window, once per thread
-    const unsigned stall = st->stall_tile;   // test hook (0 in normal operation)
+    const unsigned stall = __ldcg(&st->stall_tile);   // test hook (0 in normal operation)
+    // batches: R = n_inst * M*M regions (instance, newest point); behind the
+    // tile buffers (no staged tables) each instance's block sums of rho and
+    // survivors, [n_inst][M*M + 1], and the first tile of every region
+    const int R = BATCH ? P.n_inst * MM : MM;
+    double2 *s_acc = reinterpret_cast<double2 *>(s_dyn + Lay::lut);
+    int *s_t0 = reinterpret_cast<int *>(s_dyn + Lay::lut + (((size_t)(BATCH ? P.n_inst : 1) * (MM + 1) * 16 + 15) & ~(size_t)15));
     const float tie_f = (float)tie_d;
 
-    // weights and the history tables of this window length
-    for (int i = threadIdx.x; i < MM * MM; i += NT) {
-        if constexpr (!C64) s_w[i] = P.wtab[i];
-        s_wf[i] = P.wtabf[i];
-    }
+    // weights and the history tables of this window length (batches read
+    // their instance's from global memory per tile)
+    if constexpr (!BATCH)
+        for (int i = threadIdx.x; i < MM * MM; i += NT) {
+            if constexpr (!C64) s_w[i] = P.wtab[i];
+            s_wf[i] = P.wtabf[i];
+        }
     Tab tab = tab_global(P, n_act, 0);
     // (asynchronous copies, waited for before the first pass A: the tables
     // arrive while the first tile loads; rows are whole multiples of
     // kLutEntries entries, so every copy is 16-byte aligned)
-    if (lut_smem && P.ndelta) {
+    if (!BATCH && lut_smem && P.ndelta) {
         const int n = P.nchunks * kLutEntries;
         if constexpr (C64) {
             float2 *hi = reinterpret_cast<float2 *>(s_dyn + Lay::lut), *lo = hi + n;
@@ -1598,9 +1711,12 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
             tab.et = et;
         }
     }
-    if (threadIdx.x == 0) {
-        s_any = 0;
-        for (int r = 0; r < MM; ++r) s_nr[r] = (long long)__ldcg(&st->reg_n[in][r]);
+    if (threadIdx.x == 0) s_any = 0;
+    if constexpr (BATCH) {
+        for (int i = threadIdx.x; i < P.n_inst * (MM + 1); i += NT) s_acc[i] = make_double2(0.0, 0.0);
+        stream_batch_tiles<NT, EPT>(P.reg_n + (size_t)in * R, P.reg_n + (size_t)outp * R, R, MM, s_t0, &s_St);
+    } else if (threadIdx.x == 0) {
+        for (int r = 0; r < MM; ++r) s_nr[r] = (long long)__ldcg(&P.reg_n[in * MM + r]);
         // tile size of this step: the smallest multiple of NT (up to S) whose
         // tiles do not outnumber the blocks, so that a small step runs in one
         // wave of short tiles (a large one uses S)
@@ -1625,12 +1741,37 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
         }
         s_tile0[MM] = acc;
         if (acc == 0 && blockIdx.x == 0) {   // empty input: the output is empty
-            for (int r = 0; r < MM; ++r) st->reg_n[outp][r] = 0;
+            for (int r = 0; r < MM; ++r) P.reg_n[outp * MM + r] = 0;
             st->cnt_out[cs] = 0;
         }
     }
     __syncthreads();
-    const long long ntiles = s_tile0[MM];
+    const long long ntiles = BATCH ? (long long)s_t0[R] : s_tile0[MM];
+    // region of a tile (the last region whose first tile is at or before it),
+    // its first tile and its stored paths
+    auto region_of = [&](long long tk) -> int {
+        if constexpr (BATCH) {
+            int lo = 0, hi = R;
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if ((long long)s_t0[mid] <= tk) lo = mid;
+                else hi = mid;
+            }
+            return lo;
+        } else {
+            int rr = 0;
+            while (rr + 1 < MM && tk >= s_tile0[rr + 1]) ++rr;
+            return rr;
+        }
+    };
+    auto tile0_of = [&](int rr) -> long long {
+        if constexpr (BATCH) return (long long)s_t0[rr];
+        else return s_tile0[rr];
+    };
+    auto nr_of = [&](int rr) -> long long {
+        if constexpr (BATCH) return (long long)__ldcg(P.reg_n + (size_t)in * R + rr);
+        else return s_nr[rr];
+    };
     const int St = s_St, ept = St / NT;   // entries per thread this step (<= EPT)
     // rho(t+1) accumulators of this thread: FP64, or on the C64 path FP32
     // with a Kahan compensation term (M = 2; for M >= 3 plain FP32 sums, to
@@ -1661,10 +1802,9 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
     // that whichever block takes tile b finds it there
     if ((long long)blockIdx.x < ntiles) {
         const long long tk = blockIdx.x;
-        int rr = 0;
-        while (rr + 1 < MM && tk >= s_tile0[rr + 1]) ++rr;
-        const long long b0 = (tk - s_tile0[rr]) * St;
-        const long long n = min((long long)St, s_nr[rr] - b0);
+        const int rr = region_of(tk);
+        const long long b0 = (tk - tile0_of(rr)) * St;
+        const long long n = min((long long)St, nr_of(rr) - b0);
         const char *kp = reinterpret_cast<const char *>(keys_in + rr * G + b0);
         const char *ap = reinterpret_cast<const char *>(amps_in + rr * G + b0);
         const int kl = (int)((n * 8 + 127) / 128), al = (int)((n * (long long)sizeof(AmpT) + 127) / 128);
@@ -1680,10 +1820,23 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
         const long long ticket = s_ticket;
         if (ticket >= ntiles) break;
         if (threadIdx.x == 0) s_any = 1;
-        int r = 0;
-        while (r + 1 < MM && ticket >= s_tile0[r + 1]) ++r;
-        const long long e0 = (ticket - s_tile0[r]) * St;
-        const long long nr = s_nr[r];
+        const int r = region_of(ticket);
+        const long long e0 = (ticket - tile0_of(r)) * St;
+        const long long nr = nr_of(r);
+        // the tile's instance (batches): its tables, its first output region
+        // and the tiles of its regions, which bound the look-back
+        const int inst = BATCH ? r / MM : 0, rb = BATCH ? inst * MM : 0;
+        Tab tab_t = tab;
+        const double2 *w_t = s_w;
+        const float4 *wf_t = s_wf;
+        long long lb0 = 0, tlast = ntiles - 1;
+        if constexpr (BATCH) {
+            tab_t = tab_global(P, n_act, inst);
+            w_t = P.wtab + (size_t)inst * MM * MM;
+            wf_t = P.wtabf + (size_t)inst * MM * MM;
+            lb0 = s_t0[rb];
+            tlast = (long long)s_t0[rb + MM] - 1;
+        }
         const int cnt = (int)min((long long)St, nr - e0);
         const unsigned long long *kin = keys_in + r * G;
         const AmpT *ain = amps_in + r * G;
@@ -2051,9 +2204,9 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
                 if constexpr (C64) {
                     const float2 Sf = group_sum_f2(s_gS[g]);
                     reinterpret_cast<float2 *>(s_gS)[2 * g] = Sf;   // for pass B, if not staged
-                    keep = X::children_tab(P, tab, rk, Sf, s_w, s_wf, v);
+                    keep = X::children_tab(P, tab_t, rk, Sf, w_t, wf_t, v);
                 } else {
-                    keep = X::children_tab(P, tab, rk, s_gS[g], s_w, s_wf, v);
+                    keep = X::children_tab(P, tab_t, rk, s_gS[g], w_t, wf_t, v);
                 }
             }
             s_keep[g] = (unsigned short)keep;
@@ -2108,18 +2261,18 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
         for (int c = warp; c < MM; c += NW) {
             unsigned long long *bucket = P.tile_state + (size_t)c * P.max_tiles;
             const unsigned long long tot = s_tot[c];
-            if (lane == 0 && !withhold) atomicExch(bucket + ticket, lb_word(epoch, ticket == 0 ? kLbInc : kLbAgg, tot));
+            if (lane == 0 && !withhold) atomicExch(bucket + ticket, lb_word(epoch, ticket == lb0 ? kLbInc : kLbAgg, tot));
             unsigned long long excl = 0;
             long long pred = ticket - 1;
             const long long t0 = clock64();
             bool timeout = false, abort = false;   // abort: another block raised an error
-            while (pred >= 0) {
+            while (pred >= lb0) {
                 unsigned wv[LBK];   // (state << 30) | count of this step; 0: not yet published
 #pragma unroll
                 for (int j = 0; j < LBK; ++j) {
                     const long long idx = pred - (long long)j * 32 - lane;
-                    if (idx < 0) {
-                        wv[j] = kLbInc << 30;   // before the first tile: an inclusive prefix of 0
+                    if (idx < lb0) {
+                        wv[j] = kLbInc << 30;   // before the instance's first tile: an inclusive prefix of 0
                     } else {
                         const unsigned long long w = ld_relaxed_gpu(bucket + idx);
                         wv[j] = (unsigned)(w >> 32) == epoch ? (unsigned)w : 0u;
@@ -2163,9 +2316,9 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
                 if (timeout || abort) {
                     s_lbfail = 1;   // offsets unknown: this tile writes nothing (the step fails)
                 } else {
-                    if (ticket > 0 && !withhold) atomicExch(bucket + ticket, lb_word(epoch, kLbInc, excl + tot));
+                    if (ticket > lb0 && !withhold) atomicExch(bucket + ticket, lb_word(epoch, kLbInc, excl + tot));
                     s_base[c] = excl;
-                    if (ticket == ntiles - 1) st->reg_n[outp][c] = excl + tot;   // the last tile knows the region sizes
+                    if (ticket == tlast) P.reg_n[(size_t)outp * R + rb + c] = excl + tot;   // the last tile knows the sizes
                 }
             }
         }
@@ -2174,10 +2327,11 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
         if (threadIdx.x == 0 && !lbfail) {
             for (int c = 0; c < MM; ++c) block_kept += s_tot[c];
             if (ngroups) atomicAdd(&st->cnt_groups[cs], (unsigned long long)ngroups);
-            if (ticket == ntiles - 1) {
+            if (ticket == tlast) {
                 unsigned long long sumc = 0;
                 for (int c = 0; c < MM; ++c) sumc += s_base[c] + s_tot[c];
-                st->cnt_out[cs] = sumc;
+                if constexpr (BATCH) atomicAdd(&st->cnt_out[cs], sumc);   // zeroed by the previous step
+                else st->cnt_out[cs] = sumc;
             }
         }
         // pass B: write the survivors to their regions
@@ -2191,9 +2345,9 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
                 for (int c = 0; c < MM; ++c)
                     if (keep & (1u << c)) v[c] = s_stg[g * MM + c];
             } else if constexpr (C64) {
-                X::children_tab(P, tab, rk, reinterpret_cast<const float2 *>(s_gS)[2 * g], s_w, s_wf, v);
+                X::children_tab(P, tab_t, rk, reinterpret_cast<const float2 *>(s_gS)[2 * g], w_t, wf_t, v);
             } else {
-                X::children_tab(P, tab, rk, s_gS[g], s_w, s_wf, v);
+                X::children_tab(P, tab_t, rk, s_gS[g], w_t, wf_t, v);
             }
             const unsigned long long shifted = rk << P.b;
 #pragma unroll
@@ -2205,14 +2359,43 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
                     continue;
                 }
                 const unsigned long long code = (unsigned long long)((c / M) | ((c % M) << P.bs));
-                keys_out[c * G + o] = (shifted | code) & wmask;
-                amps_out[c * G + o] = v[c];
+                keys_out[(rb + c) * G + o] = (shifted | code) & wmask;
+                amps_out[(rb + c) * G + o] = v[c];
                 if constexpr (kKahan) {
                     X::kahan_add(racc[c], rcmp[c], v[c]);
                 } else {
                     racc[c].x += v[c].x;
                     racc[c].y += v[c].y;
                 }
+            }
+        }
+        if constexpr (BATCH) {
+            // the tile's part of its instance's rho(t+1) and survivor count:
+            // FP64 warp sums added to the block's sums (shared FP64 atomics)
+            double2 *acc = s_acc + (size_t)inst * (MM + 1);
+#pragma unroll
+            for (int k = 0; k < MM; ++k) {
+                double x = to_d(racc[k].x), y = to_d(racc[k].y);
+                if constexpr (kKahan) {
+                    x -= to_d(rcmp[k].x);
+                    y -= to_d(rcmp[k].y);
+                    rcmp[k].x = rcmp[k].y = 0;
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    x += __shfl_down_sync(0xffffffffu, x, o);
+                    y += __shfl_down_sync(0xffffffffu, y, o);
+                }
+                if (lane == 0 && (x != 0.0 || y != 0.0)) {
+                    atomicAdd(&acc[k].x, x);
+                    atomicAdd(&acc[k].y, y);
+                }
+                racc[k].x = racc[k].y = 0;
+            }
+            if (threadIdx.x == 0 && !lbfail) {
+                unsigned long long kt = 0;
+                for (int c = 0; c < MM; ++c) kt += s_tot[c];
+                atomicAdd(&acc[MM].x, (double)kt);
             }
         }
         __syncthreads();
@@ -2237,6 +2420,11 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
             }
         }
     }
+    if constexpr (BATCH) {   // this block's sums per instance (complete: the loop ended with a barrier)
+        double2 *part = rho_part_of(P, tn, MM) + (size_t)blockIdx.x * P.n_inst * (MM + 1);
+        for (int i = threadIdx.x; i < P.n_inst * (MM + 1); i += NT) part[i] = s_acc[i];
+        return;
+    }
     // this block's partials of rho(t+1) and survivor count; a block that
     // processed no tile writes zeros without reducing (s_any: thread 0 holds
     // block_kept; the barrier below orders it)
@@ -2255,6 +2443,27 @@ __global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 
         mine[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     if (threadIdx.x == 0) scount_of(P, tn)[blockIdx.x] = (long long)block_kept;
+}
+
+template <int M, bool C64, int NX, int S>
+__global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 2 : 1)
+    k_stream_step(Params P, int lut_smem) {
+    stream_step_body<M, C64, NX, S, false>(P, lut_smem);
+}
+
+// Batched stream engine: nsteps steps of all instances, separated by
+// bounded grid barriers (a cooperative launch when nsteps > 1; one step is
+// an ordinary launch).  The stored set lives in n_inst * M*M regions
+// (instance, newest point); tickets run over the tiles of all regions in
+// order, so an instance's tiles are consecutive and its look-back stops at
+// its first tile.
+template <int M, bool C64, int S>
+__global__ void __launch_bounds__(kStreamThreads, (M == 2 || (M == 3 && C64)) ? 2 : 1)
+    k_stream_batch(Params P, int nsteps) {
+    for (int s = 0; s < nsteps; ++s) {
+        stream_step_body<M, C64, 1, S, true>(P, 0);
+        if (s + 1 < nsteps && grid_barrier(P.st)) break;
+    }
 }
 
 // The kernels' FP32 -> FP64 widening over an array (test hook).
@@ -2822,7 +3031,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
     size_t keys[2], amps[2], slots, repk, slot_of, groups, lut, lutf, lutlo, etab, wtab, wtabf, uprop, eta, q, deltas,
-        rho, rho_part, spart, scount, stats, inst_kept, fin_count, tile_state, state, total;
+        rho, rho_part, spart, scount, stats, inst_kept, fin_count, tile_state, reg_n, state, total;
     size_t ckeys, camps, skey[2], sidx[2], rs_hist, rs_part, rbk_heads;   // post-merging engine
     size_t ranks;                                                        // per-rank counts, bases, cursors
     size_t lutE, lutEf, lutElo, etabE, wEt, wEtf, eta0d, dEd, dE0d;       // symmetric splitting
@@ -2979,8 +3188,12 @@ Layout make_layout(const qp_config *c) {
     L.stats = take((size_t)R * sizeof(StepRec));
     L.inst_kept = take((size_t)R * NI * sizeof(long long));
     L.fin_count = take(sizeof(unsigned int));
-    L.max_tiles = (long long)MM * ((mp / MM + kStreamMinTile - 1) / kStreamMinTile + 1);   // smallest tile
+    // stream regions: one per (instance, newest point); at the smallest tile
+    // every region may end in a partial tile
+    const long long nreg = (long long)NI * MM;
+    L.max_tiles = nreg * ((mp / nreg + kStreamMinTile - 1) / kStreamMinTile + 1);
     L.tile_state = take((size_t)L.max_tiles * MM * 8);
+    L.reg_n = take((size_t)2 * nreg * 8);
     L.ranks = take((size_t)3 * kMaxRanks * 8);
     if (NI == 1) {   // symmetric splitting (single problems): correction tables, coefficient arrays
         L.lutE = take(nlut * sizeof(double2));
@@ -3130,6 +3343,56 @@ cudaError_t launch_stream_kernel(qp_ctx *c, int blocks_per_sm) {
     return cudaGetLastError();
 }
 
+// Batched stream kernel: an ordinary launch of one step (every block
+// resident, at most blocks_per_sm per SM), or (coop) one cooperative launch
+// of nsteps steps over at most persistent_blocks co-resident blocks.
+// Dynamic shared memory: the tile buffers, then the per-instance sums and
+// the regions' first tiles.
+template <int M, bool C64, int S>
+cudaError_t launch_stream_batch_kernel(qp_ctx *c, int nsteps, bool coop) {
+    using Lay = StreamLayout<M, C64, 1, S>;
+    constexpr int MM = M * M;
+    const void *fn = (const void *)k_stream_batch<M, C64, S>;
+    auto extra = [](int ni) { return Lay::a16((size_t)ni * (MM + 1) * 16) + ((size_t)ni * MM + 1) * 4; };
+    const size_t sm = Lay::bytes + extra(c->P.n_inst);
+    if (c->scache_fn != fn || c->scache_smem != sm) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(Lay::bytes + extra(kMaxInst)));
+        if (e != cudaSuccess) return e;
+        int nb = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kStreamThreads, sm);
+        if (e != cudaSuccess) return e;
+        if (nb < 1) return cudaErrorInvalidConfiguration;
+        c->scache_fn = fn;
+        c->scache_smem = sm;
+        c->scache_res = nb;
+    }
+    if (coop) {
+        const int g = std::min(std::min(c->persist_grid, c->nsm * c->scache_res), kMaxExpandBlocks);
+        Params P = c->P;
+        void *args[] = {(void *)&P, (void *)&nsteps};
+        return cudaLaunchCooperativeKernel(fn, dim3(g), dim3(kStreamThreads), args, sm, c->stream);
+    }
+    const int g = std::min(c->nsm * std::min(c->bps_exp, c->scache_res), kMaxExpandBlocks);
+    k_stream_batch<M, C64, S><<<g, kStreamThreads, sm, c->stream>>>(c->P, 1);
+    return cudaGetLastError();
+}
+
+template <int M, bool C64>
+cudaError_t launch_stream_batch_t(qp_ctx *c, int nsteps, bool coop) {
+    return c->stream_tile == 1024 ? launch_stream_batch_kernel<M, C64, 1024>(c, nsteps, coop)
+                                  : launch_stream_batch_kernel<M, C64, 512>(c, nsteps, coop);
+}
+
+cudaError_t launch_stream_batch(qp_ctx *c, int nsteps, bool coop) {
+    const bool c64 = c->cfg.precision == QP_C64;
+    switch (c->cfg.M) {
+        case 2: return c64 ? launch_stream_batch_t<2, true>(c, nsteps, coop) : launch_stream_batch_t<2, false>(c, nsteps, coop);
+        case 3: return c64 ? launch_stream_batch_t<3, true>(c, nsteps, coop) : launch_stream_batch_t<3, false>(c, nsteps, coop);
+        default: return c64 ? launch_stream_batch_t<4, true>(c, nsteps, coop) : launch_stream_batch_t<4, false>(c, nsteps, coop);
+    }
+}
+
 template <int M, bool C64, int NX>
 cudaError_t launch_stream_tile(qp_ctx *c) {
     switch (c->stream_tile) {
@@ -3179,7 +3442,9 @@ cudaError_t launch_stream_t(qp_ctx *c, cudaEvent_t *ev) {
         cudaEventRecord(ev[2], c->stream);
     }
     cudaError_t e;
-    if constexpr (M == 2) {
+    if (c->P.n_inst > 1) {
+        e = launch_stream_batch_t<M, C64>(c, 1, false);
+    } else if constexpr (M == 2) {
         e = c->stream_nx == 4 ? launch_stream_tile<M, C64, 4>(c) : launch_stream_tile<M, C64, 1>(c);
     } else {
         e = launch_stream_tile<M, C64, 1>(c);
@@ -3358,11 +3623,14 @@ void set_mask_params(qp_ctx *c) {
     const int nextra = (int)Pp.size() - k;
     P.prefmask = (b * k >= 64) ? ~0ull : ((1ull << (b * k)) - 1ull);
     P.x_shift = nextra == 1 ? b * Pp[k] : -1;
-    c->stream_nx = (P.n_inst == 1 && (nextra == 0 || (nextra == 1 && c->cfg.M == 2))) ? (nextra ? 4 : 1) : 0;
-    // regular steps (see Params): no filter; the merge form needs P' = all
-    // positions but the oldest and a complete key set that fits the buffers
-    P.reg_fill = c->cfg.theta == 0.0 ? 1 : 0;
-    P.reg_merge = (c->cfg.theta == 0.0 && c->cfg.dkmax >= 2 && nextra == 0 && k == c->cfg.dkmax - 1) ? 1 : 0;
+    // (batches: the prefix alone)
+    if (P.n_inst == 1) c->stream_nx = (nextra == 0 || (nextra == 1 && c->cfg.M == 2)) ? (nextra ? 4 : 1) : 0;
+    else c->stream_nx = nextra == 0 ? 1 : 0;
+    // regular steps (see Params, single problems): no filter; the merge form
+    // needs P' = all positions but the oldest and a complete key set that
+    // fits the buffers
+    P.reg_fill = (c->cfg.theta == 0.0 && P.n_inst == 1) ? 1 : 0;
+    P.reg_merge = (P.reg_fill && c->cfg.dkmax >= 2 && nextra == 0 && k == c->cfg.dkmax - 1) ? 1 : 0;
     P.full_n = 0;
     if (2.0 * c->cfg.dkmax * std::log2((double)c->cfg.M) < 62.0) {
         unsigned long long f = 1;
@@ -3502,7 +3770,8 @@ qp_status qp_create(const qp_config *cfg, void *d_workspace, size_t bytes, void 
     P.inst_shift = P.b * cfg->dkmax;
     P.instmask = P.n_inst > 1 ? (((1ull << inst_bits(P.n_inst)) - 1ull) << P.inst_shift) : 0ull;
     P.lut_stride = L.nlut;
-    P.region_cap = (cfg->max_paths / (M * M)) & ~15ll;   // region bases 16-entry aligned (vector loads)
+    P.region_cap = (cfg->max_paths / ((long long)P.n_inst * M * M)) & ~15ll;   // region bases 16-entry aligned
+    P.reg_n = reinterpret_cast<unsigned long long *>(c->ws + L.reg_n);
     P.tile_state = reinterpret_cast<unsigned long long *>(c->ws + L.tile_state);
     P.max_tiles = L.max_tiles;
     P.etab_stride = L.nlut * (size_t)std::max(1, L.nd);
@@ -3780,7 +4049,7 @@ qp_status qp_set_rho0(qp_ctx *c, const double *re, const double *im) {
     // engine of this propagation
     if (!c->P.post && c->cfg.engine == QP_ENGINE_STREAM && c->stream_nx == 0)
         return fail(c, QP_ERR_ARG, "the stream engine needs a mask whose P' is a prefix {0..k-1} plus at most one "
-                                   "extra position (M = 2) and a single instance");
+                                   "extra position (M = 2; batches: the prefix alone)");
     c->use_stream = !c->P.post && !c->sym &&
                     (c->cfg.engine == QP_ENGINE_STREAM || (c->cfg.engine == QP_ENGINE_AUTO && c->stream_nx > 0));
     if (c->use_stream && c->P.region_cap < 1) return fail(c, QP_ERR_CAPACITY, "max_paths < 16 M*M (stream engine)");
@@ -3802,16 +4071,21 @@ qp_status qp_set_rho0(qp_ctx *c, const double *re, const double *im) {
     const void *asrc = c->cfg.precision == QP_C64 ? (const void *)af.data() : (const void *)amps.data();
     DevState s{};
     s.n_cur = n;
-    if (c->use_stream) {   // one path per region (newest point a*M + b)
+    if (c->use_stream) {   // one path per region (instance, newest point a*M + b); keys without the instance
+        std::vector<unsigned long long> rn((size_t)2 * NI * MM, 0ull);
         for (size_t i = 0; i < n; ++i) {
             const int a = (int)(keys[i] & ((1u << bs) - 1u)), b = (int)((keys[i] >> bs) & ((1u << bs) - 1u));
-            const size_t reg = (size_t)(a * M + b);
+            const int inst = NI > 1 ? (int)(keys[i] >> c->P.inst_shift) : 0;
+            const size_t reg = (size_t)inst * MM + (size_t)(a * M + b);
+            keys[i] &= ~c->P.instmask;
             QP_CUDA(c, cudaMemcpyAsync(c->P.keys[0] + reg * c->P.region_cap, &keys[i], 8, cudaMemcpyHostToDevice,
                                        c->stream));
             QP_CUDA(c, cudaMemcpyAsync(static_cast<char *>(c->P.amps[0]) + reg * c->P.region_cap * ab,
                                        static_cast<const char *>(asrc) + i * ab, ab, cudaMemcpyHostToDevice, c->stream));
-            s.reg_n[0][reg] = 1;
+            rn[reg] = 1;
         }
+        QP_CUDA(c, cudaMemcpyAsync(c->P.reg_n, rn.data(), rn.size() * 8, cudaMemcpyHostToDevice, c->stream));
+        QP_CUDA(c, cudaStreamSynchronize(c->stream));   // rn and keys are host temporaries
     } else {
         QP_CUDA(c, cudaMemcpyAsync(c->P.keys[0], keys.data(), n * 8, cudaMemcpyHostToDevice, c->stream));
         QP_CUDA(c, cudaMemcpyAsync(c->P.amps[0], asrc, n * ab, cudaMemcpyHostToDevice, c->stream));
@@ -3864,6 +4138,11 @@ qp_status qp_step(qp_ctx *c, int nsteps) {
     c->host_t += nsteps;
     if (c->use_persistent && !c->use_stream && !c->P.post) {
         const cudaError_t e = launch_persistent(c, nsteps);
+        if (e != cudaSuccess) return fail(c, QP_ERR_CUDA, std::string("persistent launch: ") + cudaGetErrorString(e));
+        return QP_OK;
+    }
+    if (c->use_persistent && c->use_stream && c->P.n_inst > 1) {   // batched stream engine: all steps, one launch
+        const cudaError_t e = launch_stream_batch(c, nsteps, true);
         if (e != cudaSuccess) return fail(c, QP_ERR_CUDA, std::string("persistent launch: ") + cudaGetErrorString(e));
         return QP_OK;
     }
@@ -4070,9 +4349,18 @@ qp_status qp_export_paths(qp_ctx *c, uint64_t *keys, double *amps, int64_t cap, 
     const int MM = c->cfg.M * c->cfg.M;
     // contiguous pieces: the flat array, or the M*M regions of the stream engine
     std::vector<std::pair<size_t, size_t>> pieces;   // (device offset, count)
+    std::vector<int> piece_inst;                       // stream batches: the instance of each piece
     if (c->use_stream) {
-        for (int r = 0; r < MM; ++r)
-            if (s.reg_n[buf][r]) pieces.push_back({(size_t)r * c->P.region_cap, (size_t)s.reg_n[buf][r]});
+        const int nreg = c->P.n_inst * MM;
+        std::vector<unsigned long long> rn((size_t)nreg);
+        QP_CUDA(c, cudaMemcpyAsync(rn.data(), c->P.reg_n + (size_t)buf * nreg, (size_t)nreg * 8, cudaMemcpyDeviceToHost,
+                                   c->stream));
+        QP_CUDA(c, cudaStreamSynchronize(c->stream));
+        for (int r = 0; r < nreg; ++r)
+            if (rn[r]) {
+                pieces.push_back({(size_t)r * c->P.region_cap, (size_t)rn[r]});
+                piece_inst.push_back(r / MM);
+            }
     } else if (cnt) {
         pieces.push_back({0, cnt});
     }
@@ -4091,6 +4379,12 @@ qp_status qp_export_paths(qp_ctx *c, uint64_t *keys, double *amps, int64_t cap, 
     }
     QP_CUDA(c, cudaStreamSynchronize(c->stream));
     if (o != cnt) return fail(c, QP_ERR_STATE, "region counts do not add up to the stored count");
+    if (c->P.n_inst > 1 && c->use_stream) {   // the instance index above the path bits, as the merge-table engine keeps it
+        size_t e = 0;
+        for (size_t i = 0; i < pieces.size(); ++i)
+            for (size_t j = 0; j < pieces[i].second; ++j, ++e)
+                keys[e] |= (unsigned long long)piece_inst[i] << c->P.inst_shift;
+    }
     for (size_t i = 0; i < tmp.size(); ++i) {
         amps[2 * i] = tmp[i].x;
         amps[2 * i + 1] = tmp[i].y;
@@ -4237,6 +4531,16 @@ qp_status qp_autotune(qp_ctx *c, int trial_steps, int use_cache, qp_tuning *best
     if (c->P.post) {   // the sort engine: blocks per SM of the extension
         for (int be : {2, 4, 8})
             if (c->nsm * be <= kMaxExpandBlocks) cand.push_back(qp_tuning{QP_LAUNCH_GRAPH, c->bps_ins, be, c->persist_grid, gs, tl, 0, 0});
+    } else if (c->use_stream && c->P.n_inst > 1) {   // batches: tile size; graphs of steps or one persistent launch
+        for (int tile : {512, 1024}) {
+            for (int be : {1, 2, 4})
+                if (c->nsm * be <= kMaxExpandBlocks)
+                    cand.push_back(qp_tuning{QP_LAUNCH_GRAPH, c->bps_ins, be, c->persist_grid, gs, tl, 0, tile});
+            if (c->persist_max > 0)
+                for (int pb : {1, 2})
+                    cand.push_back(qp_tuning{QP_LAUNCH_PERSISTENT, c->bps_ins, c->bps_exp,
+                                             std::min(c->persist_max, pb * c->nsm), gs, tl, 0, tile});
+        }
     } else if (c->use_stream) {   // one kernel per step: tile size and blocks per SM
         for (int tile : {256, 512, 1024})
             for (int be : {1, 2, 4, 8}) {

@@ -1,5 +1,8 @@
 """GPU: the batched form (several independent instances in one context),
 the launch-shape autotuner and the bounded waits of the persistent kernel.
+"auto" runs batches whose P' is a prefix of the window on the stream
+engine (tests/test_batched_stream_gpu.py covers it in depth), the others on
+the merge-table engine; "hash" forces the merge-table engine.
 
 Each instance of a batch must reproduce, within the FP64 parity bar, the
 oracle run of that instance alone, with the same per-instance path counts;
@@ -25,9 +28,9 @@ build.build()
 TOL = 1e-10
 
 
-def _batch(case, etas, mask, theta, steps, precision="fp64", launch=None):
+def _batch(case, etas, mask, theta, steps, precision="fp64", launch=None, engine="auto"):
     M, dk = case["M"], case["dkmax"]
-    p = Propagator(M, dk, case["dt"], case["q"], case["hs"], theta, precision, max_paths=1 << 20,
+    p = Propagator(M, dk, case["dt"], case["q"], case["hs"], theta, precision, engine=engine, max_paths=1 << 20,
                    n_inst=len(etas))
     p.set_eta(etas[0])
     for i, e in enumerate(etas):
@@ -48,13 +51,14 @@ def _batch(case, etas, mask, theta, steps, precision="fp64", launch=None):
 @pytest.mark.parametrize("M,dkmax,mask,theta,steps,ninst", [(2, 6, (0, 1, 2, 4), 1e-5, 12, 5),
                                                             (3, 4, None, 1e-6, 8, 3), (2, 8, None, 0.0, 11, 4)])
 @pytest.mark.parametrize("launch", [None, dict(mode=abi.QP_LAUNCH_PERSISTENT)], ids=["graph", "persistent"])
-def test_batch_instances_match_oracle(M, dkmax, mask, theta, steps, ninst, launch):
+@pytest.mark.parametrize("engine", ["hash", "auto"])
+def test_batch_instances_match_oracle(M, dkmax, mask, theta, steps, ninst, launch, engine):
     case = W.random_case(100 + M + dkmax, M, dkmax)
     rng = np.random.default_rng(7)
     etas = [W.random_eta(rng, dkmax, 0.05 + 0.02 * i) for i in range(ninst)]
     if launch:
         launch = dict(launch, persistent_blocks=152)
-    rho, counts, stats = _batch(case, etas, mask, theta, steps, launch=launch)
+    rho, counts, stats = _batch(case, etas, mask, theta, steps, launch=launch, engine=engine)
     total_kept = np.zeros(steps + 1, dtype=np.int64)
     for i, e in enumerate(etas):
         o = iquapi.propagate(M, case["q"], case["hs"], case["dt"], e, dkmax, mask, theta, case["rho0"], steps)
