@@ -169,7 +169,7 @@ def algorithmic_bytes(stats_rows, M, amp_bytes, merge, engine="hash"):
     the merge-table kernels read the stored set and the slots they touch."""
     E = 8 + amp_bytes
     ins = tie = exp = 0
-    for (t, groups, extended, kept), n_in in stats_rows:
+    for (t, groups, extended, kept, *_), n_in in stats_rows:
         if engine == "stream":
             exp += n_in * E + kept * E
         elif merge(t):
@@ -339,36 +339,61 @@ def run_ours(args, rank, world, precision):
 
 
 def run_batched_sweep(n_inst=64, reps=3):
-    """The resonance sweep (n_inst instances of the 8-step model) as one
-    batched context in complex64, autotuned, each trajectory (all steps) one
-    timed qp_step call after an L2 flush; against the plain FP64 path running
-    the instances one after another.  Returns the summary object."""
+    """The coupling sweep (n_inst instances of the 8-step model whose path
+    counts differ by more than 2x) as one batched context in complex64 on
+    the stream engine, autotuned (graph launches per step or one persistent
+    launch per call), each trajectory (all steps) one timed qp_step call
+    after an L2 flush; the other launch mode and the merge-table engine's
+    batch timed the same way; against the plain FP64 path running the
+    instances one after another.  Returns the summary object."""
     import torch
-    from paper_2506_03127_gb300 import Propagator, batch_from_workloads
+    from paper_2506_03127_gb300 import Propagator, abi, batch_from_workloads
 
-    ws = W.resonance_sweep(n_inst)
+    ws = W.coupling_sweep(n_inst)
     w0 = ws[0]
     T = w0.steps
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+
+    def trajectory_ms(p):
+        times = []
+        for _ in range(reps):
+            p.set_rho0(w0.rho0_array())
+            with torch.cuda.stream(p.stream):
+                flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(p.stream)
+            p.step(T)
+            e1.record(p.stream)
+            p.sync()
+            times.append(e0.elapsed_time(e1))
+        return float(np.median(times))
+
+    def launch_name(t):
+        return "persistent kernel (one launch per call)" if t.mode == abi.QP_LAUNCH_PERSISTENT else \
+            "CUDA graphs of %d steps" % t.graph_steps
+
     p = batch_from_workloads(ws, precision="c64", max_paths=1 << 23, rho_history=max(4096, T + 1))
+    engine = "stream" if p.tuning().engine == abi.QP_ENGINE_STREAM else "merge-table"
     p.step(w0.dkmax + 2)
     best, tune_ms = p.autotune(trial_steps=4, use_cache=False)
-    times = []
-    for _ in range(reps):
-        p.set_rho0(w0.rho0_array())
-        with torch.cuda.stream(p.stream):
-            flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(p.stream)
-        p.step(T)
-        e1.record(p.stream)
-        p.sync()
-        times.append(e0.elapsed_time(e1))
+    t_b = trajectory_ms(p)
     ext = float(sum(r[2] for r in p.stats(1, T)))
     rho_b = p.rho(0, T + 1)
     counts = p.instance_counts(T)
+    # the other launch mode, same tile size
+    if best.mode == abi.QP_LAUNCH_PERSISTENT:
+        p.set_tuning(mode=abi.QP_LAUNCH_GRAPH, expand_blocks_per_sm=2)
+    else:
+        p.set_tuning(mode=abi.QP_LAUNCH_PERSISTENT, persistent_blocks=2 * torch.cuda.get_device_properties(0).multi_processor_count)
+    other = p.tuning()
+    t_other = trajectory_ms(p)
     p.close()
-    t_b = float(np.median(times))
+    # the merge-table engine's batch (the same instances)
+    h = batch_from_workloads(ws, precision="c64", max_paths=1 << 23, rho_history=max(4096, T + 1), engine="hash")
+    h.step(w0.dkmax + 2)
+    h.autotune(trial_steps=4, use_cache=False)
+    t_h = trajectory_ms(h)
+    h.close()
     # plain FP64 path, one instance at a time
     t_s, ext_s, err = 0.0, 0.0, 0.0
     for i, w in enumerate(ws):
@@ -384,12 +409,15 @@ def run_batched_sweep(n_inst=64, reps=3):
         ext_s += float(sum(r[2] for r in q.stats(1, T)))
         err = max(err, float(np.abs(q.rho(0, T + 1) - rho_b[:, i]).max()))
         q.close()
-    return {"workload": f"resonance_sweep{n_inst}", "instances": n_inst, "steps": T, "theta": w0.theta,
+    return {"workload": f"coupling_sweep{n_inst}", "instances": n_inst, "steps": T, "theta": w0.theta,
             "value": ext / (t_b / 1e3), "unit": "paths/s", "ms_per_trajectory": t_b, "precision": "c64",
-            "launch": "one qp_step call for all steps (tuned: %s)" % ("persistent kernel" if best.mode else
-                                                                    "CUDA graphs of %d steps" % best.graph_steps),
-            "tuning": best.as_dict(), "l2": "flushed before each timed trajectory",
-            "kept_per_instance": {"min": int(counts.min()), "max": int(counts.max())},
+            "engine": engine, "launch": launch_name(best) + " (autotuned)", "tuning": best.as_dict(),
+            "other_launch": {"launch": launch_name(other), "ms_per_trajectory": t_other},
+            "merge_table_batch_ms_per_trajectory": t_h,
+            "l2": "flushed before each timed trajectory",
+            "kept_per_instance": {"min": int(counts.min()), "max": int(counts.max()),
+                                  "max_over_min": float(counts.max() / max(1, counts.min())),
+                                  "all": [int(c) for c in counts]},
             "fp64_one_by_one": {"value": ext_s / (t_s / 1e3), "ms_total": t_s},
             "speedup_vs_fp64_one_by_one": (ext / (t_b / 1e3)) / (ext_s / (t_s / 1e3)),
             "rho_max_abs_err_vs_fp64": err}

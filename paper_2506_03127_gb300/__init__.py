@@ -145,15 +145,16 @@ class Propagator:
             pass
 
 
-def batch_from_workloads(ws, precision="c64", max_paths=1 << 22, **kw):
+def batch_from_workloads(ws, precision="c64", max_paths=1 << 22, engine="auto", **kw):
     """One batched Propagator over instances that differ only in their bath
-    (e.g. workloads.resonance_sweep): eta per instance from libqp."""
+    (e.g. workloads.resonance_sweep): eta per instance from libqp.  "auto"
+    takes the stream engine when P' is a prefix of the window."""
     w0 = ws[0]
     for w in ws[1:]:
         if (w.M, w.q, w.hs, w.dt, w.dkmax, w.mask, w.theta, w.rho0) != (w0.M, w0.q, w0.hs, w0.dt, w0.dkmax, w0.mask,
                                                                          w0.theta, w0.rho0):
             raise ValueError("batched instances must share everything but the bath")
-    p = Propagator(w0.M, w0.dkmax, w0.dt, w0.q, w0.hs_array(), w0.theta, precision, "auto", max_paths,
+    p = Propagator(w0.M, w0.dkmax, w0.dt, w0.q, w0.hs_array(), w0.theta, precision, engine, max_paths,
                    n_inst=len(ws), **kw)
     p.set_eta(eta_from_bath(w0.bath, w0.dt, w0.dkmax))
     for i, w in enumerate(ws):

@@ -12,7 +12,8 @@ import bench  # noqa: E402
 
 
 def test_algorithmic_bytes_stream_engine_reads_the_set_once_and_writes_the_survivors():
-    rows = [((100, 60000, 250000, 150000), 140000), ((101, 61000, 252000, 151000), 150000)]
+    # rows as qp_read_stats returns them: (t, groups, extended, kept, intermediate)
+    rows = [((100, 60000, 250000, 150000, 150000), 140000), ((101, 61000, 252000, 151000, 151000), 150000)]
     b = bench.algorithmic_bytes(rows, 2, 8, lambda t: True, engine="stream")
     E = 16
     assert b[0] == 0 and b[1] == 0 and b[3] == 0
@@ -20,7 +21,7 @@ def test_algorithmic_bytes_stream_engine_reads_the_set_once_and_writes_the_survi
 
 
 def test_algorithmic_bytes_merge_table_engine():
-    rows = [((5, 0, 400, 400), 100), ((20, 30, 120, 90), 100)]   # a filling step, then a merging one
+    rows = [((5, 0, 400, 400, 400), 100), ((20, 30, 120, 90, 90), 100)]   # a filling step, then a merging one
     b = bench.algorithmic_bytes(rows, 2, 16, lambda t: t >= 16, engine="hash")
     E = 24
     assert b[0] == 100 * (E + 4) + 30 * 32
