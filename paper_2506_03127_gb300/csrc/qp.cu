@@ -2258,48 +2258,78 @@ __device__ __forceinline__ void stream_step_body(const Params &P, int lut_smem) 
         const bool withhold = stall != 0u && (long long)stall == ticket + 1;   // test hook: publish nothing
         if (threadIdx.x == 0) s_lbfail = 0;
         __syncthreads();
-        for (int c = warp; c < MM; c += NW) {
-            unsigned long long *bucket = P.tile_state + (size_t)c * P.max_tiles;
-            const unsigned long long tot = s_tot[c];
-            if (lane == 0 && !withhold) atomicExch(bucket + ticket, lb_word(epoch, ticket == lb0 ? kLbInc : kLbAgg, tot));
-            unsigned long long excl = 0;
-            long long pred = ticket - 1;
+        // buckets c = warp + j * NW (KB per warp: two for M = 3, 4) are
+        // looked back in the same rounds: their loads are issued together
+        constexpr int KB = (MM + NW - 1) / NW;
+        if ((int)warp < MM) {
+            unsigned long long excl[KB];
+            long long pred[KB];
+            bool done[KB];
+#pragma unroll
+            for (int j = 0; j < KB; ++j) {
+                const int c = (int)warp + j * NW;
+                excl[j] = 0;
+                pred[j] = ticket - 1;
+                done[j] = c >= MM || pred[j] < lb0;
+                if (c < MM && lane == 0 && !withhold)
+                    atomicExch(P.tile_state + (size_t)c * P.max_tiles + ticket,
+                               lb_word(epoch, ticket == lb0 ? kLbInc : kLbAgg, s_tot[c]));
+            }
             const long long t0 = clock64();
             bool timeout = false, abort = false;   // abort: another block raised an error
-            while (pred >= lb0) {
-                unsigned wv[LBK];   // (state << 30) | count of this step; 0: not yet published
+            for (;;) {
+                unsigned wv[KB][LBK];   // (state << 30) | count of this step; 0: not yet published
 #pragma unroll
-                for (int j = 0; j < LBK; ++j) {
-                    const long long idx = pred - (long long)j * 32 - lane;
-                    if (idx < lb0) {
-                        wv[j] = kLbInc << 30;   // before the instance's first tile: an inclusive prefix of 0
-                    } else {
-                        const unsigned long long w = ld_relaxed_gpu(bucket + idx);
-                        wv[j] = (unsigned)(w >> 32) == epoch ? (unsigned)w : 0u;
+                for (int j = 0; j < KB; ++j) {
+                    const unsigned long long *bucket = P.tile_state + (size_t)((int)warp + j * NW) * P.max_tiles;
+#pragma unroll
+                    for (int k = 0; k < LBK; ++k) {
+                        const long long idx = pred[j] - (long long)k * 32 - lane;
+                        if (done[j] || idx < lb0) {
+                            wv[j][k] = kLbInc << 30;   // before the instance's first tile: an inclusive prefix of 0
+                        } else {
+                            const unsigned long long w = ld_relaxed_gpu(bucket + idx);
+                            wv[j][k] = (unsigned)(w >> 32) == epoch ? (unsigned)w : 0u;
+                        }
                     }
                 }
-                int u = WIN, i = WIN;   // nearest unpublished / inclusive position
+                bool wait = false, all = true;
 #pragma unroll
-                for (int j = LBK - 1; j >= 0; --j) {
-                    const unsigned um = __ballot_sync(0xffffffffu, wv[j] == 0u);
-                    const unsigned im = __ballot_sync(0xffffffffu, (wv[j] >> 30) == kLbInc);
-                    if (um) u = j * 32 + __ffs(um) - 1;
-                    if (im) i = j * 32 + __ffs(im) - 1;
+                for (int j = 0; j < KB; ++j) {
+                    if (done[j]) continue;
+                    int u = WIN, i = WIN;   // nearest unpublished / inclusive position
+#pragma unroll
+                    for (int k = LBK - 1; k >= 0; --k) {
+                        const unsigned um = __ballot_sync(0xffffffffu, wv[j][k] == 0u);
+                        const unsigned im = __ballot_sync(0xffffffffu, (wv[j][k] >> 30) == kLbInc);
+                        if (um) u = k * 32 + __ffs(um) - 1;
+                        if (im) i = k * 32 + __ffs(im) - 1;
+                    }
+                    const bool fin = i < u;
+                    const int lim = fin ? i + 1 : u;   // positions summed this round
+                    if (lim > 0) {
+                        unsigned long long part = 0;
+#pragma unroll
+                        for (int k = 0; k < LBK; ++k)
+                            if (k * 32 + (int)lane < lim) part += wv[j][k] & ((1u << 30) - 1u);
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+                        excl[j] += __shfl_sync(0xffffffffu, part, 0);
+                    }
+                    if (fin) {
+                        done[j] = true;
+                        continue;
+                    }
+                    pred[j] -= lim;
+                    if (pred[j] < lb0) {
+                        done[j] = true;
+                        continue;
+                    }
+                    all = false;
+                    if (lim < WIN) wait = true;   // waiting on tile pred[j]: bounded
                 }
-                const bool done = i < u;
-                const int lim = done ? i + 1 : u;   // positions summed this round
-                if (lim > 0) {
-                    unsigned long long part = 0;
-#pragma unroll
-                    for (int j = 0; j < LBK; ++j)
-                        if (j * 32 + (int)lane < lim) part += wv[j] & ((1u << 30) - 1u);
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
-                    excl += __shfl_sync(0xffffffffu, part, 0);
-                }
-                if (done) break;
-                pred -= lim;
-                if (lim < WIN) {   // waiting on tile pred: bounded
+                if (all) break;
+                if (wait) {
                     if (*(volatile unsigned *)&st->err) {
                         abort = true;
                         break;
@@ -2316,9 +2346,17 @@ __device__ __forceinline__ void stream_step_body(const Params &P, int lut_smem) 
                 if (timeout || abort) {
                     s_lbfail = 1;   // offsets unknown: this tile writes nothing (the step fails)
                 } else {
-                    if (ticket > lb0 && !withhold) atomicExch(bucket + ticket, lb_word(epoch, kLbInc, excl + tot));
-                    s_base[c] = excl;
-                    if (ticket == tlast) P.reg_n[(size_t)outp * R + rb + c] = excl + tot;   // the last tile knows the sizes
+#pragma unroll
+                    for (int j = 0; j < KB; ++j) {
+                        const int c = (int)warp + j * NW;
+                        if (c >= MM) continue;
+                        const unsigned long long tot = s_tot[c];
+                        if (ticket > lb0 && !withhold)
+                            atomicExch(P.tile_state + (size_t)c * P.max_tiles + ticket,
+                                       lb_word(epoch, kLbInc, excl[j] + tot));
+                        s_base[c] = excl[j];
+                        if (ticket == tlast) P.reg_n[(size_t)outp * R + rb + c] = excl[j] + tot;   // the last tile knows the sizes
+                    }
                 }
             }
         }
