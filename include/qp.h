@@ -69,17 +69,18 @@ enum { QP_FP64 = 0,       /* complex128 amplitudes, FP64 everywhere */
                              once to FP32, the precision of the children   */
 
 enum { QP_ENGINE_AUTO = 0,    /* library picks: the stream engine where the
-                                 mask allows it (single problems), else the
-                                 merge table; the workspace holds both        */
+                                 mask allows it, else the merge table; the
+                                 workspace holds both                         */
        QP_ENGINE_HASH = 1,    /* device open-addressing table keyed by the
                                  masked key (any mask, batches)                 */
        QP_ENGINE_STREAM = 2   /* order-preserving stream: groups stay
                                  contiguous, merge = segmented reduction
-                                 (single problems; masks whose P' is a prefix
-                                 {0..k-1}, for M = 2 plus one more position).
-                                 Stored paths live in M*M regions of
-                                 max_paths / (M*M) entries, by newest point.
-                                 The workspace holds no merge table: about
+                                 (masks whose P' is a prefix {0..k-1}; single
+                                 problems with M = 2 also allow one more
+                                 position).  Stored paths live in n_inst * M*M
+                                 regions of max_paths / (n_inst * M*M)
+                                 entries, by (instance, newest point).  The
+                                 workspace holds no merge table: about
                                  2 * (8 + amplitude bytes) per path.          */ };
 
 typedef struct {
@@ -99,8 +100,9 @@ typedef struct {
                               one problem; at most 128).  All instances share M,
                               q, H_S, dt, dkmax, mask and theta; each has its own
                               eta (qp_set_eta_instance).  The instance index is
-                              stored above the path bits of the key, so
-                              b*dkmax + ceil(log2 n_inst) <= 64.               */
+                              stored above the path bits of the key (the stream
+                              engine keeps it in the region and adds it on
+                              export), so b*dkmax + ceil(log2 n_inst) <= 64.   */
     int scheme;            /* QP_PREMERGE (0) or QP_POSTMERGE: the order of merging
                               and propagation (see below)                      */
 } qp_config;
@@ -145,9 +147,12 @@ typedef struct {
 } qp_step_stats;
 
 /* Launch shape and table size of the step (qp_set_tuning / qp_autotune). */
-enum { QP_LAUNCH_GRAPH = 0,        /* CUDA graph of the four step kernels        */
+enum { QP_LAUNCH_GRAPH = 0,        /* CUDA graphs of the step's kernels          */
        QP_LAUNCH_PERSISTENT = 1 }; /* one cooperative kernel for all steps of a
-                                      qp_step call, grid barriers between phases */
+                                      qp_step call, bounded grid barriers between
+                                      phases (merge-table engine) or steps
+                                      (batches on the stream engine); single
+                                      problems on the stream engine run graphs  */
 typedef struct {
     int mode;                  /* QP_LAUNCH_*                                     */
     int insert_blocks_per_sm;  /* pre-merge kernels (graph mode)                 */
@@ -159,9 +164,10 @@ typedef struct {
                                   or QP_ENGINE_STREAM; read-only, set at
                                   qp_set_rho0 from qp_config.engine and the mask) */
     int stream_tile;           /* stream engine: stored paths per tile, 256, 512
-                                  or 1024 (0 in qp_set_tuning: unchanged); its
-                                  grid is min(expand_blocks_per_sm, co-resident
-                                  blocks per SM) blocks per SM               */
+                                  or 1024 (0 in qp_set_tuning: unchanged;
+                                  batches take 512 for 256); its grid is
+                                  min(expand_blocks_per_sm, co-resident blocks
+                                  per SM) blocks per SM                      */
 } qp_tuning;
 
 typedef struct qp_ctx qp_ctx;
