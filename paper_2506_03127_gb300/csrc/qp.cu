@@ -1625,6 +1625,7 @@ __device__ __forceinline__ void stream_step_body(const Params &P, int lut_smem) 
     static_assert(NX <= 16, "slot map: 4 bits of x");
     static_assert(NW == kStreamWarps, "warp partials");
     static_assert(!BATCH || NX == 1, "batches: P' a prefix of the window");
+    constexpr bool kTileAccS = !BATCH && M * M >= 9;   // per-warp tile sums of rho (see the accumulators)
     DevState *st = P.st;
     // (device state read through L2: the persistent batch kernel runs
     // several steps in one launch)
@@ -1671,6 +1672,7 @@ __device__ __forceinline__ void stream_step_body(const Params &P, int lut_smem) 
     __shared__ unsigned s_ticket, s_nseg, s_ng, s_hw[NW];
     __shared__ int s_St;   // tile size of this step
     __shared__ float4 s_rt[NW][MM];
+    __shared__ float4 s_wrho[kTileAccS ? NW : 1][MM];   // M >= 3 single problems: per-warp sums of rho(t+1)
     __shared__ bool s_last;
     __shared__ int s_any;   // the block processed a tile
     __shared__ int s_lbfail;   // the tile's look-back gave up (timeout, or another block's error)
@@ -1712,6 +1714,8 @@ __device__ __forceinline__ void stream_step_body(const Params &P, int lut_smem) 
         }
     }
     if (threadIdx.x == 0) s_any = 0;
+    if constexpr (kTileAccS)
+        for (int i = threadIdx.x; i < NW * MM; i += NT) (&s_wrho[0][0])[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     if constexpr (BATCH) {
         for (int i = threadIdx.x; i < P.n_inst * (MM + 1); i += NT) s_acc[i] = make_double2(0.0, 0.0);
         stream_batch_tiles<NT, EPT>(P.reg_n + (size_t)in * R, P.reg_n + (size_t)outp * R, R, MM, s_t0, &s_St);
@@ -1774,15 +1778,23 @@ __device__ __forceinline__ void stream_step_body(const Params &P, int lut_smem) 
     };
     const int St = s_St, ept = St / NT;   // entries per thread this step (<= EPT)
     // rho(t+1) accumulators of this thread: FP64, or on the C64 path FP32
-    // with a Kahan compensation term (M = 2; for M >= 3 plain FP32 sums, to
-    // stay within the register budget of two blocks per SM), widened to
-    // FP64 once at the end
+    // with a Kahan compensation term (M = 2; plain FP32 sums for M >= 3).
+    // Single problems with M = 2 keep them for the whole kernel and widen
+    // them once at the end.  For M >= 3 and for batches they live for one
+    // tile's write pass (kept across the tile loop, M*M accumulators do not
+    // stay in registers: every child's addition went through local memory)
+    // and are summed per tile: batches into their instance's block sums,
+    // M >= 3 by a warp sum added to a per-warp FP32 pair (TwoSum), FP64
+    // sums in FP64
     constexpr bool kKahan = C64 && M == 2;
-    typename X::AccT racc[MM], rcmp[kKahan ? MM : 1];
+    constexpr bool kTileAcc = BATCH || MM >= 9;
+    typename X::AccT racc[kTileAcc ? 1 : MM], rcmp[kKahan && !kTileAcc ? MM : 1];
+    if constexpr (!kTileAcc) {
 #pragma unroll
-    for (int k = 0; k < MM; ++k) {
-        racc[k].x = racc[k].y = 0;
-        if constexpr (kKahan) rcmp[k].x = rcmp[k].y = 0;
+        for (int k = 0; k < MM; ++k) {
+            racc[k].x = racc[k].y = 0;
+            if constexpr (kKahan) rcmp[k].x = rcmp[k].y = 0;
+        }
     }
     const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
     unsigned long long block_kept = 0;
@@ -2373,6 +2385,14 @@ __device__ __forceinline__ void stream_step_body(const Params &P, int lut_smem) 
             }
         }
         // pass B: write the survivors to their regions
+        typename X::AccT tacc[kTileAcc ? MM : 1], tcmp[kTileAcc && kKahan ? MM : 1];
+        if constexpr (kTileAcc) {
+#pragma unroll
+            for (int k = 0; k < MM; ++k) {
+                tacc[k].x = tacc[k].y = 0;
+                if constexpr (kKahan) tcmp[k].x = tcmp[k].y = 0;
+            }
+        }
         for (int g = g0; g < (lbfail ? g0 : g1); ++g) {
             const unsigned keep = s_keep[g];
             if (!keep) continue;
@@ -2399,7 +2419,14 @@ __device__ __forceinline__ void stream_step_body(const Params &P, int lut_smem) 
                 const unsigned long long code = (unsigned long long)((c / M) | ((c % M) << P.bs));
                 keys_out[(rb + c) * G + o] = (shifted | code) & wmask;
                 amps_out[(rb + c) * G + o] = v[c];
-                if constexpr (kKahan) {
+                if constexpr (kTileAcc) {
+                    if constexpr (kKahan) {
+                        X::kahan_add(tacc[c], tcmp[c], v[c]);
+                    } else {
+                        tacc[c].x += v[c].x;
+                        tacc[c].y += v[c].y;
+                    }
+                } else if constexpr (kKahan) {
                     X::kahan_add(racc[c], rcmp[c], v[c]);
                 } else {
                     racc[c].x += v[c].x;
@@ -2413,11 +2440,10 @@ __device__ __forceinline__ void stream_step_body(const Params &P, int lut_smem) 
             double2 *acc = s_acc + (size_t)inst * (MM + 1);
 #pragma unroll
             for (int k = 0; k < MM; ++k) {
-                double x = to_d(racc[k].x), y = to_d(racc[k].y);
+                double x = to_d(tacc[k].x), y = to_d(tacc[k].y);
                 if constexpr (kKahan) {
-                    x -= to_d(rcmp[k].x);
-                    y -= to_d(rcmp[k].y);
-                    rcmp[k].x = rcmp[k].y = 0;
+                    x -= to_d(tcmp[k].x);
+                    y -= to_d(tcmp[k].y);
                 }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
@@ -2428,12 +2454,37 @@ __device__ __forceinline__ void stream_step_body(const Params &P, int lut_smem) 
                     atomicAdd(&acc[k].x, x);
                     atomicAdd(&acc[k].y, y);
                 }
-                racc[k].x = racc[k].y = 0;
             }
             if (threadIdx.x == 0 && !lbfail) {
                 unsigned long long kt = 0;
                 for (int c = 0; c < MM; ++c) kt += s_tot[c];
                 atomicAdd(&acc[MM].x, (double)kt);
+            }
+        }
+        if constexpr (kTileAccS) {
+            // the tile's rho(t+1): warp sums (plain), added by lane 0 to the
+            // warp's pair (C64: TwoSum, the error kept; FP64: FP64)
+#pragma unroll
+            for (int k = 0; k < MM; ++k) {
+                auto x = tacc[k].x, y = tacc[k].y;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    x += __shfl_down_sync(0xffffffffu, x, o);
+                    y += __shfl_down_sync(0xffffffffu, y, o);
+                }
+                if (lane == 0) {
+                    float4 a = s_wrho[warp][k];
+                    if constexpr (C64) {
+                        two_sum_acc(a.x, a.y, x);
+                        two_sum_acc(a.z, a.w, y);
+                    } else {
+                        double2 d = *reinterpret_cast<const double2 *>(&a);
+                        d.x += x;
+                        d.y += y;
+                        a = *reinterpret_cast<const float4 *>(&d);
+                    }
+                    s_wrho[warp][k] = a;
+                }
             }
         }
         __syncthreads();
@@ -2467,18 +2518,45 @@ __device__ __forceinline__ void stream_step_body(const Params &P, int lut_smem) 
     // processed no tile writes zeros without reducing (s_any: thread 0 holds
     // block_kept; the barrier below orders it)
     float4 *mine = spart_of(P, tn, MM) + (size_t)blockIdx.x * MM;
-    if (threadIdx.x == 0) s_any = block_kept > 0 || s_any;
-    __syncthreads();
-    if (s_any) {
-        float2 lo[MM];
-#pragma unroll
-        for (int k = 0; k < MM; ++k) {
-            if constexpr (kKahan) lo[k] = make_float2(-rcmp[k].x, -rcmp[k].y);
-            else lo[k] = make_float2(0.f, 0.f);
+    if constexpr (kTileAccS) {   // the warps' pairs merged in order (thread k: end point k; zeros without a tile)
+        if ((int)threadIdx.x < MM) {
+            const int k = threadIdx.x;
+            if constexpr (C64) {
+                float4 a = s_wrho[0][k];
+                for (int w = 1; w < NW; ++w) {
+                    const float4 b = s_wrho[w][k];
+                    const float tx = a.x + b.x, vx = tx - a.x;
+                    a.y += b.y + ((a.x - (tx - vx)) + (b.x - vx));
+                    a.x = tx;
+                    const float ty = a.z + b.z, vy = ty - a.z;
+                    a.w += b.w + ((a.z - (ty - vy)) + (b.z - vy));
+                    a.z = ty;
+                }
+                mine[k] = a;
+            } else {
+                double2 a = *reinterpret_cast<const double2 *>(&s_wrho[0][k]);
+                for (int w = 1; w < NW; ++w) {
+                    const double2 b = *reinterpret_cast<const double2 *>(&s_wrho[w][k]);
+                    a.x += b.x;
+                    a.y += b.y;
+                }
+                reinterpret_cast<double2 *>(mine)[k] = a;
+            }
         }
-        block_rho_pair<MM, NW, C64>(racc, lo, s_rt, mine);
-    } else if ((int)threadIdx.x < MM) {
-        mine[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+        if (threadIdx.x == 0) s_any = block_kept > 0 || s_any;
+        __syncthreads();
+        if (s_any) {
+            float2 lo[MM];
+#pragma unroll
+            for (int k = 0; k < MM; ++k) {
+                if constexpr (kKahan) lo[k] = make_float2(-rcmp[k].x, -rcmp[k].y);
+                else lo[k] = make_float2(0.f, 0.f);
+            }
+            block_rho_pair<MM, NW, C64>(racc, lo, s_rt, mine);
+        } else if ((int)threadIdx.x < MM) {
+            mine[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
     }
     if (threadIdx.x == 0) scount_of(P, tn)[blockIdx.x] = (long long)block_kept;
 }
