@@ -1625,7 +1625,7 @@ __device__ __forceinline__ void stream_step_body(const Params &P, int lut_smem) 
     static_assert(NX <= 16, "slot map: 4 bits of x");
     static_assert(NW == kStreamWarps, "warp partials");
     static_assert(!BATCH || NX == 1, "batches: P' a prefix of the window");
-    constexpr bool kTileAccS = !BATCH && M * M >= 9;   // per-warp tile sums of rho (see the accumulators)
+    constexpr bool kTileAccS = !BATCH && M * M >= 9 && C64;   // per-warp tile sums of rho (see the accumulators)
     DevState *st = P.st;
     // (device state read through L2: the persistent batch kernel runs
     // several steps in one launch)
@@ -1779,15 +1779,15 @@ __device__ __forceinline__ void stream_step_body(const Params &P, int lut_smem) 
     const int St = s_St, ept = St / NT;   // entries per thread this step (<= EPT)
     // rho(t+1) accumulators of this thread: FP64, or on the C64 path FP32
     // with a Kahan compensation term (M = 2; plain FP32 sums for M >= 3).
-    // Single problems with M = 2 keep them for the whole kernel and widen
-    // them once at the end.  For M >= 3 and for batches they live for one
-    // tile's write pass (kept across the tile loop, M*M accumulators do not
-    // stay in registers: every child's addition went through local memory)
-    // and are summed per tile: batches into their instance's block sums,
-    // M >= 3 by a warp sum added to a per-warp FP32 pair (TwoSum), FP64
-    // sums in FP64
+    // Single problems keep them for the whole kernel and widen them once at
+    // the end, except C64 with M >= 3 (two blocks per SM, 128 registers:
+    // kept across the tile loop, the M*M accumulators were spilled and every
+    // child's addition went through local memory), where they live for one
+    // tile's write pass and a warp sum per tile is added to a per-warp FP32
+    // pair (TwoSum).  Batches sum them per tile into their instance's block
+    // sums
     constexpr bool kKahan = C64 && M == 2;
-    constexpr bool kTileAcc = BATCH || MM >= 9;
+    constexpr bool kTileAcc = BATCH || kTileAccS;
     typename X::AccT racc[kTileAcc ? 1 : MM], rcmp[kKahan && !kTileAcc ? MM : 1];
     if constexpr (!kTileAcc) {
 #pragma unroll
@@ -2255,6 +2255,15 @@ __device__ __forceinline__ void stream_step_body(const Params &P, int lut_smem) 
         __syncthreads();
 #pragma unroll
         for (int c = 0; c < MM; ++c) tb[c] += s_wsum[warp][c];
+        // M >= 3: the thread's offsets wait in the tile's key and amplitude
+        // buffers (free since pass A, contiguous) while the look-back runs,
+        // [c][thread], where they fit
+        constexpr bool kTbShared = MM >= 9 && (size_t)MM * NT * 4 <= Lay::stg - Lay::key;
+        unsigned *s_tb = reinterpret_cast<unsigned *>(s_dyn + Lay::key);
+        if constexpr (kTbShared) {
+#pragma unroll
+            for (int c = 0; c < MM; ++c) s_tb[c * NT + threadIdx.x] = tb[c];
+        }
         // decoupled look-back, one warp per bucket (buckets c, c + NW, ...):
         // publish the tile's aggregate, then read a window of 32 * LBK
         // predecessors: position p = j * 32 + lane is tile pred - p, so each
@@ -2385,6 +2394,10 @@ __device__ __forceinline__ void stream_step_body(const Params &P, int lut_smem) 
             }
         }
         // pass B: write the survivors to their regions
+        if constexpr (kTbShared) {
+#pragma unroll
+            for (int c = 0; c < MM; ++c) tb[c] = s_tb[c * NT + threadIdx.x];
+        }
         typename X::AccT tacc[kTileAcc ? MM : 1], tcmp[kTileAcc && kKahan ? MM : 1];
         if constexpr (kTileAcc) {
 #pragma unroll
@@ -2462,8 +2475,8 @@ __device__ __forceinline__ void stream_step_body(const Params &P, int lut_smem) 
             }
         }
         if constexpr (kTileAccS) {
-            // the tile's rho(t+1): warp sums (plain), added by lane 0 to the
-            // warp's pair (C64: TwoSum, the error kept; FP64: FP64)
+            // the tile's rho(t+1): warp sums (plain FP32), added by lane 0 to
+            // the warp's pair with TwoSum (the error kept)
 #pragma unroll
             for (int k = 0; k < MM; ++k) {
                 auto x = tacc[k].x, y = tacc[k].y;
@@ -2474,15 +2487,8 @@ __device__ __forceinline__ void stream_step_body(const Params &P, int lut_smem) 
                 }
                 if (lane == 0) {
                     float4 a = s_wrho[warp][k];
-                    if constexpr (C64) {
-                        two_sum_acc(a.x, a.y, x);
-                        two_sum_acc(a.z, a.w, y);
-                    } else {
-                        double2 d = *reinterpret_cast<const double2 *>(&a);
-                        d.x += x;
-                        d.y += y;
-                        a = *reinterpret_cast<const float4 *>(&d);
-                    }
+                    two_sum_acc(a.x, a.y, x);
+                    two_sum_acc(a.z, a.w, y);
                     s_wrho[warp][k] = a;
                 }
             }
@@ -2521,27 +2527,17 @@ __device__ __forceinline__ void stream_step_body(const Params &P, int lut_smem) 
     if constexpr (kTileAccS) {   // the warps' pairs merged in order (thread k: end point k; zeros without a tile)
         if ((int)threadIdx.x < MM) {
             const int k = threadIdx.x;
-            if constexpr (C64) {
-                float4 a = s_wrho[0][k];
-                for (int w = 1; w < NW; ++w) {
-                    const float4 b = s_wrho[w][k];
-                    const float tx = a.x + b.x, vx = tx - a.x;
-                    a.y += b.y + ((a.x - (tx - vx)) + (b.x - vx));
-                    a.x = tx;
-                    const float ty = a.z + b.z, vy = ty - a.z;
-                    a.w += b.w + ((a.z - (ty - vy)) + (b.z - vy));
-                    a.z = ty;
-                }
-                mine[k] = a;
-            } else {
-                double2 a = *reinterpret_cast<const double2 *>(&s_wrho[0][k]);
-                for (int w = 1; w < NW; ++w) {
-                    const double2 b = *reinterpret_cast<const double2 *>(&s_wrho[w][k]);
-                    a.x += b.x;
-                    a.y += b.y;
-                }
-                reinterpret_cast<double2 *>(mine)[k] = a;
+            float4 a = s_wrho[0][k];
+            for (int w = 1; w < NW; ++w) {
+                const float4 b = s_wrho[w][k];
+                const float tx = a.x + b.x, vx = tx - a.x;
+                a.y += b.y + ((a.x - (tx - vx)) + (b.x - vx));
+                a.x = tx;
+                const float ty = a.z + b.z, vy = ty - a.z;
+                a.w += b.w + ((a.z - (ty - vy)) + (b.z - vy));
+                a.z = ty;
             }
+            mine[k] = a;
         }
     } else {
         if (threadIdx.x == 0) s_any = block_kept > 0 || s_any;
