@@ -205,7 +205,8 @@ def run_ours(args, rank, world, precision):
         p.set_tuning(**kw)
         tuning = p.tuning()
     else:
-        tuning, _ = p.autotune(trial_steps=8, use_cache=True)
+        p.autotune(trial_steps=8, use_cache=True)
+        tuning = p.tuning()   # as applied, with the propagation's engine
     p.sync()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=f"cuda:{dev}")
     for _ in range(args.warmup):
@@ -375,7 +376,8 @@ def run_batched_sweep(n_inst=64, reps=3):
     p = batch_from_workloads(ws, precision="c64", max_paths=1 << 23, rho_history=max(4096, T + 1))
     engine = "stream" if p.tuning().engine == abi.QP_ENGINE_STREAM else "merge-table"
     p.step(w0.dkmax + 2)
-    best, tune_ms = p.autotune(trial_steps=4, use_cache=False)
+    p.autotune(trial_steps=4, use_cache=False)
+    best = p.tuning()   # as applied, with the propagation's engine
     t_b = trajectory_ms(p)
     ext = float(sum(r[2] for r in p.stats(1, T)))
     rho_b = p.rho(0, T + 1)
