@@ -30,9 +30,10 @@ static void matmul(int M, const cplx *A, const cplx *B, cplx *C) {
         }
 }
 
-std::vector<cplx> short_time_propagator(int M, const std::vector<cplx> &H, double dt) {
+void short_time_propagator(int M, const cplx *H, double dt, cplx *U) {
+    // M <= 4: fixed arrays, no allocation (the allocation-free step uses it)
     // A = -i H dt, scaled by 2^-s so that its 1-norm is below 1/4
-    std::vector<cplx> A(M * M), T(M * M), P(M * M), tmp(M * M);
+    cplx A[16], T[16], P[16], tmp[16];
     double norm = 0.0;
     for (int j = 0; j < M; ++j) {
         double col = 0.0;
@@ -47,14 +48,20 @@ std::vector<cplx> short_time_propagator(int M, const std::vector<cplx> &H, doubl
     for (int i = 0; i < M * M; ++i) { T[i] = 0.0; P[i] = 0.0; }
     for (int i = 0; i < M; ++i) { T[i * M + i] = 1.0; P[i * M + i] = 1.0; }
     for (int k = 1; k <= 20; ++k) {
-        matmul(M, P.data(), A.data(), tmp.data());
+        matmul(M, P, A, tmp);
         for (int i = 0; i < M * M; ++i) { P[i] = tmp[i] / double(k); T[i] += P[i]; }
     }
     for (int r = 0; r < s; ++r) {
-        matmul(M, T.data(), T.data(), tmp.data());
-        T = tmp;
+        matmul(M, T, T, tmp);
+        for (int i = 0; i < M * M; ++i) T[i] = tmp[i];
     }
-    return T;
+    for (int i = 0; i < M * M; ++i) U[i] = T[i];
+}
+
+std::vector<cplx> short_time_propagator(int M, const std::vector<cplx> &H, double dt) {
+    std::vector<cplx> U(M * M);
+    short_time_propagator(M, H.data(), dt, U.data());
+    return U;
 }
 
 // ------------------------------------------------------------------ bath

@@ -15,6 +15,8 @@ using cplx = std::complex<double>;
 // squaring of the Taylor series.  The short-time system propagator of Eq.
 // SysP (hbar = 1).
 std::vector<cplx> short_time_propagator(int M, const std::vector<cplx> &H, double dt);
+// the same into U[M*M] for M <= 4, without allocating
+void short_time_propagator(int M, const cplx *H, double dt, cplx *U);
 
 // Spectral density J(w) of the bath (ohmic part + Eq. sharpSD resonance).
 double spectral_density(const qp_bath &b, double w);

@@ -4871,47 +4871,6 @@ __global__ void k_na_setup(NaSetup s, double2 *eta, double *q, double2 *U, doubl
     }
 }
 
-// U = exp(-i H dt) for M <= 4 on fixed arrays (scaling and squaring of the
-// Taylor series, as in host_numerics.cpp).
-void na_propagator(int M, const qp::cplx *H, double dt, qp::cplx *U) {
-    qp::cplx A[16], P[16], T[16];
-    double norm = 0.0;
-    for (int j = 0; j < M; ++j) {
-        double col = 0.0;
-        for (int i = 0; i < M; ++i) col += std::abs(H[i * M + j]) * std::fabs(dt);
-        norm = std::max(norm, col);
-    }
-    int s = 0;
-    while (norm > 0.25) { norm *= 0.5; ++s; }
-    const double scale = std::ldexp(1.0, -s);
-    for (int i = 0; i < M * M; ++i) {
-        A[i] = qp::cplx(0.0, -1.0) * H[i] * dt * scale;
-        T[i] = P[i] = 0.0;
-    }
-    for (int i = 0; i < M; ++i) T[i * M + i] = P[i * M + i] = 1.0;
-    for (int k = 1; k <= 20; ++k) {
-        qp::cplx nx[16];
-        for (int i = 0; i < M; ++i)
-            for (int j = 0; j < M; ++j) {
-                qp::cplx acc = 0.0;
-                for (int l = 0; l < M; ++l) acc += P[i * M + l] * A[l * M + j];
-                nx[i * M + j] = acc / double(k);
-            }
-        for (int i = 0; i < M * M; ++i) { P[i] = nx[i]; T[i] += nx[i]; }
-    }
-    for (int r = 0; r < s; ++r) {
-        qp::cplx sq[16];
-        for (int i = 0; i < M; ++i)
-            for (int j = 0; j < M; ++j) {
-                qp::cplx acc = 0.0;
-                for (int l = 0; l < M; ++l) acc += T[i * M + l] * T[l * M + j];
-                sq[i * M + j] = acc;
-            }
-        for (int i = 0; i < M * M; ++i) T[i] = sq[i];
-    }
-    for (int i = 0; i < M * M; ++i) U[i] = T[i];
-}
-
 }  // namespace
 
 extern "C" qp_status qp_step_noalloc(const qp_config *cfg, const double *eta_re, const double *eta_im, int n_eta,
@@ -5005,7 +4964,7 @@ extern "C" qp_status qp_step_noalloc(const qp_config *cfg, const double *eta_re,
     {
         qp::cplx H[16], U[16];
         for (int i = 0; i < M * M; ++i) H[i] = qp::cplx(cfg->hs_re[i], cfg->hs_im ? cfg->hs_im[i] : 0.0);
-        na_propagator(M, H, cfg->dt, U);
+        qp::short_time_propagator(M, H, cfg->dt, U);   // fixed arrays: no allocation
         for (int i = 0; i < M * M; ++i) su.U[i] = make_double2(U[i].real(), U[i].imag());
         signed char dsel[16];
         for (int k = 0; k < 16; ++k) dsel[k] = -1;
