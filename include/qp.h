@@ -472,13 +472,28 @@ qp_status qp_surrogate_windows(const double *d_rho, int n_inst, int L, const flo
  * made traceless, projected onto Hermitian matrices and then onto positive
  * semidefinite ones of the same trace (a density matrix).  d_xbuf [n x d_in]
  * and d_ybuf [n x 8] (device floats) are kept in the signature; the rollout
- * packs its input in the model's workspace and does not write them.  The steps run as CUDA graphs of up to 32
- * steps captured on the model's stream at the first call with these
- * arguments and replayed (the step index lives on the device); on the
- * legacy default stream they are launched one by one.  Synchronous: the
+ * packs its input in the model's workspace and does not write them.  The steps run
+ * in one cluster launch (qp_mlp_set_rollout_mode below) or as CUDA graphs
+ * of up to 32 steps captured on the model's stream at the first call with
+ * these arguments and replayed (the step index lives on the device; on the
+ * legacy default stream they are launched one by one).  Synchronous: the
  * rollout is complete when the call returns.                              */
 qp_status qp_surrogate_rollout(qp_mlp *m, float *d_hist, int n, int T, int L, const float *d_par, int n_par,
                                int t_from, int t_to, float out_scale, float *d_xbuf, float *d_ybuf);
+
+/* How qp_surrogate_rollout runs its steps.  QP_ROLLOUT_AUTO (the default):
+ * all steps in one launch of a two-block cluster (k_rollout_fused: block 0
+ * holds W1^T in shared memory and packs the features, runs layer 1 and the
+ * update; block 1 holds W2^T and W3^T and runs layers 2 and 3; the
+ * activations cross through distributed shared memory, two cluster
+ * barriers per step, no launch per step) when n <= 32, the model has 8
+ * outputs and the weights fit shared memory; otherwise the CUDA graphs of
+ * step kernels described above.  QP_ROLLOUT_GRAPH forces the graphs;
+ * QP_ROLLOUT_FUSED forces the cluster kernel (QP_ERR_ARG when it does not
+ * fit).  Both use the same rounding points and the same order of the
+ * k-steps, and give the same trajectories.                                 */
+enum { QP_ROLLOUT_AUTO = 0, QP_ROLLOUT_GRAPH = 1, QP_ROLLOUT_FUSED = 2 };
+qp_status qp_mlp_set_rollout_mode(qp_mlp *m, int mode);
 
 #ifdef __cplusplus
 }

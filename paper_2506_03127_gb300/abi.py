@@ -19,6 +19,7 @@ QP_FP64, QP_C64 = 0, 1
 QP_ENGINE_AUTO, QP_ENGINE_HASH, QP_ENGINE_STREAM = 0, 1, 2
 QP_LAUNCH_GRAPH, QP_LAUNCH_PERSISTENT = 0, 1
 QP_PREMERGE, QP_POSTMERGE = 0, 1
+QP_ROLLOUT_AUTO, QP_ROLLOUT_GRAPH, QP_ROLLOUT_FUSED = 0, 1, 2
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int)
@@ -116,6 +117,7 @@ def _load():
         "qp_surrogate_rollout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                                 ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                                 ctypes.c_int, ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p]),
+        "qp_mlp_set_rollout_mode": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
         "qp_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
         "qp_step_noalloc": (ctypes.c_int, [ctypes.POINTER(qp_config), _dp, _dp, ctypes.c_int, _ip, ctypes.c_int,
                                            ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
@@ -408,6 +410,10 @@ def qp_surrogate_windows(d_rho, n_inst, L, d_par, n_par, t_begin, t_end, inst0, 
     check(lib.qp_surrogate_windows(ctypes.c_void_p(d_rho), n_inst, L, ctypes.c_void_p(d_par), n_par, t_begin, t_end,
                                    inst0, ninst_used, out_scale, ctypes.c_void_p(d_x), ctypes.c_void_p(d_t),
                                    ctypes.c_void_p(stream)))
+
+
+def qp_mlp_set_rollout_mode(m, mode: int):
+    mcheck(lib.qp_mlp_set_rollout_mode(m, mode), m)
 
 
 def qp_surrogate_rollout(m, d_hist, n, T, L, d_par, n_par, t_from, t_to, out_scale, d_xbuf, d_ybuf):

@@ -16,6 +16,7 @@
 //   weights   dW = x^T dh : A = x^T (in x batch), B = dh^T (out x batch)
 // so each activation is also written transposed (batch contiguous) by the
 // kernel that produces it.
+#include <cooperative_groups.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -339,6 +340,225 @@ __global__ void k_rollout_update(float *hist, int n, int T, int *tstep, unsigned
     for (int k = 0; k < 8; ++k) out[k] = r[k];
 }
 
+// The whole rollout in one launch of a two-block cluster (the batch is one
+// or two m16 tiles).  Block 0 keeps the first layer's weights W1^T in
+// shared memory and the last L steps of rho in a ring (when it fits): per
+// step it packs the features (BF16), runs layer 1 and writes h1 into block
+// 1's shared memory; block 1 keeps W2^T and W3^T, runs layers 2 and 3 and
+// writes y back into block 0, which applies the update of k_rollout_update.
+// Two cluster barriers per step; no launch, no global round trip.  The
+// layers are m16n8k16 BF16 MMAs with FP32 accumulation over the k-steps in
+// ascending order and the epilogues of k_gemm_nt (tanh and BF16 rounding of
+// the next layer's input; bias): the same rounding points and summation
+// order as the kernel-by-kernel rollout.  Shared memory, the same layout in
+// both blocks: weights (block 0: W1^T [width][K1 + 8]; block 1: W2^T
+// [width][Kw + 8] then W3^T [8][Kw + 8]), features [16 MT][K1 + 8], h1, h2
+// [16 MT][Kw + 8] (BF16), y [16 MT][8] and the ring [n][L][8] (FP32); rows
+// past n and columns past the layer widths stay zero.
+struct RollArgs {
+    float *hist;
+    const float *par;
+    const __nv_bfloat16 *w1t, *w2t, *w3t;   // W^T, rows of K1, Kw, Kw
+    const float *b1, *b2, *b3;
+    int n, T, L, n_par, d_in, width, K1, Kw, t_from, t_to, ring;
+    float out_scale;
+};
+constexpr int kRollThreads = 256;
+constexpr int kRollNT = 4;   // n-tiles of a warp per pass (A fragments shared)
+
+__host__ __device__ inline size_t roll_weight_elems(int width, int K1, int Kw) {
+    const size_t w1 = (size_t)width * (K1 + 8), w23 = (size_t)(width + 8) * (Kw + 8);
+    return w1 > w23 ? w1 : w23;
+}
+inline size_t roll_smem_bytes(int MT, int width, int K1, int Kw, int n, int L, bool ring) {
+    return roll_weight_elems(width, K1, Kw) * 2 + (size_t)16 * MT * (K1 + 8) * 2 +
+           (size_t)2 * 16 * MT * (Kw + 8) * 2 + (size_t)16 * MT * 8 * 4 + (ring ? (size_t)n * L * 8 * 4 : 0);
+}
+
+// NTW m16n8 tiles of C = A B^T over K (ascending k-steps of 16): A [16 MT
+// rows][lda] and B = W^T [rows][ldb] in shared memory; tile j covers
+// columns n0 + j * nstride (tiles at or past nmax are computed from row 0
+// and not used); acc[j][mt][r] as in k_gemm_nt's epilogue
+template <int MT, int NTW>
+__device__ __forceinline__ void roll_tiles(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int ldb, int n0,
+                                           int nstride, int nmax, int K, float (*acc)[MT][4]) {
+    const int lane = threadIdx.x & 31;
+    const __nv_bfloat16 *brow[NTW];
+#pragma unroll
+    for (int j = 0; j < NTW; ++j) {
+        const int nj = n0 + j * nstride < nmax ? n0 + j * nstride : 0;
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[j][mt][r] = 0.f;
+        brow[j] = B + (size_t)(nj + (lane & 7)) * ldb + ((lane >> 3) & 1) * 8;
+    }
+#pragma unroll 2
+    for (int kk = 0; kk < K; kk += 16) {
+        unsigned b0[NTW], b1[NTW];
+#pragma unroll
+        for (int j = 0; j < NTW; ++j) ldmatrix_x2(b0[j], b1[j], brow[j] + kk);
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt) {
+            unsigned a0, a1, a2, a3;
+            ldmatrix_x4(a0, a1, a2, a3, A + (size_t)(mt * 16 + (lane & 15)) * lda + kk + (lane >> 4) * 8);
+#pragma unroll
+            for (int j = 0; j < NTW; ++j) mma_bf16(acc[j][mt], a0, a1, a2, a3, b0[j], b1[j]);
+        }
+    }
+}
+
+// rows of a row-major BF16 matrix (rows x K, K a multiple of 8) into shared
+// memory rows of ld elements, 16-byte chunks
+__device__ __forceinline__ void roll_copy_rows(__nv_bfloat16 *dst, int ld, const __nv_bfloat16 *src, int rows, int K) {
+    for (int i = threadIdx.x; i < rows * (K / 8); i += kRollThreads) {
+        const int r = i / (K / 8), c = (i % (K / 8)) * 8;
+        *reinterpret_cast<uint4 *>(dst + (size_t)r * ld + c) = *reinterpret_cast<const uint4 *>(src + (size_t)r * K + c);
+    }
+}
+
+template <int MT>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kRollThreads) k_rollout_fused(RollArgs a) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    const unsigned rank = cluster.block_rank();
+    extern __shared__ __align__(16) unsigned char s_roll[];
+    const int l1 = a.K1 + 8, lw = a.Kw + 8;
+    __nv_bfloat16 *sW = reinterpret_cast<__nv_bfloat16 *>(s_roll);
+    __nv_bfloat16 *sX = sW + roll_weight_elems(a.width, a.K1, a.Kw);
+    __nv_bfloat16 *sH1 = sX + (size_t)16 * MT * l1;
+    __nv_bfloat16 *sH2 = sH1 + (size_t)16 * MT * lw;
+    float *sY = reinterpret_cast<float *>(sH2 + (size_t)16 * MT * lw);
+    float *sRing = sY + 16 * MT * 8;   // [n][L][8]: step s at slot s % L
+    __nv_bfloat16 *peerH1 = cluster.map_shared_rank(sH1, 1);   // block 0 writes h1 there
+    float *peerY = cluster.map_shared_rank(sY, 0);             // block 1 writes y there
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = kRollThreads / 32;
+    const int g = lane >> 2, tq = lane & 3;
+    if (rank == 0) {
+        roll_copy_rows(sW, l1, a.w1t, a.width, a.K1);
+        for (int i = threadIdx.x; i < 16 * MT * l1; i += kRollThreads) sX[i] = __float2bfloat16_rn(0.f);
+        if (a.ring)
+            for (int idx = threadIdx.x; idx < a.n * a.L * 8; idx += kRollThreads) {
+                const int i = idx / (a.L * 8), s = a.t_from - a.L + (idx / 8) % a.L, k = idx % 8;
+                sRing[((size_t)i * a.L + s % a.L) * 8 + k] = a.hist[((size_t)i * a.T + s) * 8 + k];
+            }
+    } else {
+        roll_copy_rows(sW, lw, a.w2t, a.width, a.Kw);
+        roll_copy_rows(sW + (size_t)a.width * lw, lw, a.w3t, 8, a.Kw);
+        for (int i = threadIdx.x; i < 2 * 16 * MT * lw; i += kRollThreads) sH1[i] = __float2bfloat16_rn(0.f);
+    }
+    cluster.sync();
+    for (int t = a.t_from; t < a.t_to; ++t) {
+        if (rank == 0) {
+            // features of step t: the last L values of rho, then the parameters
+            const int s0 = (t - a.L) % a.L;
+            for (int idx = threadIdx.x; idx < a.n * a.d_in; idx += kRollThreads) {
+                const int i = idx / a.d_in, f = idx - i * a.d_in;
+                float v;
+                if (f >= 8 * a.L) {
+                    v = a.par[(size_t)i * a.n_par + f - 8 * a.L];
+                } else if (a.ring) {
+                    int slot = s0 + (f >> 3);
+                    slot = slot >= a.L ? slot - a.L : slot;
+                    v = sRing[((size_t)i * a.L + slot) * 8 + (f & 7)];
+                } else {
+                    v = a.hist[((size_t)i * a.T + (t - a.L + (f >> 3))) * 8 + (f & 7)];
+                }
+                sX[(size_t)i * l1 + f] = __float2bfloat16_rn(v);
+            }
+            __syncthreads();
+            // layer 1: a warp's n-tiles nb + j * 64; h1 = tanh(acc + b1), BF16, into block 1
+            for (int nb = warp * 8; nb < a.width; nb += nw * 8 * kRollNT) {
+                float acc[kRollNT][MT][4];
+                roll_tiles<MT, kRollNT>(sX, l1, sW, l1, nb, nw * 8, a.width, a.K1, acc);
+#pragma unroll
+                for (int j = 0; j < kRollNT; ++j)
+#pragma unroll
+                    for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) {
+                            const int m = mt * 16 + g + (r >= 2 ? 8 : 0);
+                            const int n = nb + j * nw * 8 + 2 * tq + (r & 1);
+                            if (m < a.n && n < a.width)
+                                peerH1[(size_t)m * lw + n] = __float2bfloat16_rn(tanhf(acc[j][mt][r] + a.b1[n]));
+                        }
+            }
+        }
+        cluster.sync();   // h1 in block 1
+        if (rank == 1) {
+            // layer 2: h2 = tanh(h1 W2 + b2), BF16
+            for (int nb = warp * 8; nb < a.width; nb += nw * 8 * kRollNT) {
+                float acc[kRollNT][MT][4];
+                roll_tiles<MT, kRollNT>(sH1, lw, sW, lw, nb, nw * 8, a.width, a.Kw, acc);
+#pragma unroll
+                for (int j = 0; j < kRollNT; ++j)
+#pragma unroll
+                    for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) {
+                            const int m = mt * 16 + g + (r >= 2 ? 8 : 0);
+                            const int n = nb + j * nw * 8 + 2 * tq + (r & 1);
+                            if (m < a.n && n < a.width)
+                                sH2[(size_t)m * lw + n] = __float2bfloat16_rn(tanhf(acc[j][mt][r] + a.b2[n]));
+                        }
+            }
+            __syncthreads();
+            // layer 3: y = h2 W3 + b3 (8 outputs: one n-tile), warp 0, into block 0
+            if (warp == 0) {
+                float acc[1][MT][4];
+                roll_tiles<MT, 1>(sH2, lw, sW + (size_t)a.width * lw, lw, 0, 8, 8, a.Kw, acc);
+#pragma unroll
+                for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        const int m = mt * 16 + g + (r >= 2 ? 8 : 0), n = 2 * tq + (r & 1);
+                        if (m < a.n) peerY[m * 8 + n] = acc[0][mt][r] + a.b3[n];
+                    }
+            }
+        }
+        cluster.sync();   // y in block 0
+        if (rank == 0) {
+            // the update of k_rollout_update for instance i
+            for (int i = threadIdx.x; i < a.n; i += kRollThreads) {
+                const float *prev = a.ring ? sRing + ((size_t)i * a.L + (t - 1) % a.L) * 8
+                                           : a.hist + ((size_t)i * a.T + (t - 1)) * 8;
+                float d[8];
+                for (int k = 0; k < 8; ++k) d[k] = sY[i * 8 + k] / a.out_scale;
+                const float tr = 0.5f * (d[0] + d[6]);
+                d[0] -= tr;
+                d[6] -= tr;
+                float r[8];
+                for (int k = 0; k < 8; ++k) r[k] = prev[k] + d[k];
+                const float re = 0.5f * (r[2] + r[4]), im = 0.5f * (r[3] - r[5]);
+                r[2] = re;
+                r[3] = im;
+                r[4] = re;
+                r[5] = -im;
+                r[1] = 0.f;
+                r[7] = 0.f;
+                const float c = 0.5f * (r[0] + r[6]), z = 0.5f * (r[0] - r[6]);
+                const float rad = sqrtf(z * z + r[2] * r[2] + r[3] * r[3]);
+                if (c > 0.f && rad > c) {
+                    const float f = c / rad;
+                    r[0] = c + f * z;
+                    r[6] = c - f * z;
+                    r[2] *= f;
+                    r[3] *= f;
+                    r[4] = r[2];
+                    r[5] = -r[3];
+                }
+                float *out = a.hist + ((size_t)i * a.T + t) * 8;
+                float *slot = sRing + ((size_t)i * a.L + t % a.L) * 8;
+                for (int k = 0; k < 8; ++k) {
+                    out[k] = r[k];
+                    if (a.ring) slot[k] = r[k];
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 }  // namespace
@@ -367,6 +587,7 @@ struct qp_mlp {
     const void *roll_key[4] = {nullptr, nullptr, nullptr, nullptr};
     int roll_dims[6] = {0, 0, 0, 0, 0, 0};
     float roll_scale = 0.f;
+    int roll_mode = QP_ROLLOUT_AUTO;   // fused one-block kernel or the graph of step kernels
     long long step = 0;
     int last_batch = -1;          // batch of the last backward pass (transposed pads)
     std::string err;
@@ -716,6 +937,46 @@ qp_status qp_surrogate_rollout(qp_mlp *m, float *d_hist, int n, int T, int L, co
     (void)d_ybuf;
     const int nsteps = t_to - t_from;
     if (nsteps == 0) return QP_OK;
+    // one block for every step when the batch is one or two m16 tiles and
+    // the first layer's weights fit shared memory
+    const int MT = (n + 15) / 16;
+    const size_t kSmemMax = (size_t)227 * 1024;
+    const bool ring = roll_smem_bytes(MT, m->width, m->K1, m->Kw, n, L, true) <= kSmemMax;
+    const size_t fsm = roll_smem_bytes(MT, m->width, m->K1, m->Kw, n, L, ring);
+    const bool fused_ok = MT <= 2 && m->d_out == 8 && m->width % 8 == 0 && fsm <= kSmemMax;
+    if (m->roll_mode == QP_ROLLOUT_FUSED && !fused_ok)
+        return mfail(m, QP_ERR_ARG, "fused rollout: needs n <= 32, 8 outputs and the first layer in shared memory");
+    if (fused_ok && m->roll_mode != QP_ROLLOUT_GRAPH) {
+        RollArgs ra;
+        ra.hist = d_hist;
+        ra.par = d_par;
+        ra.w1t = m->WbT[0];
+        ra.w2t = m->WbT[1];
+        ra.w3t = m->WbT[2];
+        ra.b1 = m->b[0];
+        ra.b2 = m->b[1];
+        ra.b3 = m->b[2];
+        ra.n = n;
+        ra.T = T;
+        ra.L = L;
+        ra.n_par = n_par;
+        ra.d_in = m->d_in;
+        ra.width = m->width;
+        ra.K1 = m->K1;
+        ra.Kw = m->Kw;
+        ra.t_from = t_from;
+        ra.t_to = t_to;
+        ra.ring = ring ? 1 : 0;
+        ra.out_scale = out_scale;
+        const void *fn = MT == 1 ? (const void *)k_rollout_fused<1> : (const void *)k_rollout_fused<2>;
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm) != cudaSuccess)
+            return mfail(m, QP_ERR_CUDA, "fused rollout set-up");
+        if (MT == 1) k_rollout_fused<1><<<2, kRollThreads, fsm, m->stream>>>(ra);   // one cluster of two
+        else k_rollout_fused<2><<<2, kRollThreads, fsm, m->stream>>>(ra);
+        if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(m->stream) != cudaSuccess)
+            return mfail(m, QP_ERR_CUDA, "fused rollout");
+        return QP_OK;
+    }
     // one rollout step: features packed for the first layer, the network,
     // the update (which advances the device step index)
     auto one_step = [&]() -> cudaError_t {
@@ -771,6 +1032,14 @@ qp_status qp_surrogate_rollout(qp_mlp *m, float *d_hist, int n, int T, int L, co
     // the host value t_from is read by the copy before the call returns
     if (cudaStreamSynchronize(m->stream) != cudaSuccess) return mfail(m, QP_ERR_CUDA, "rollout");
     return cudaGetLastError() == cudaSuccess ? QP_OK : mfail(m, QP_ERR_CUDA, "rollout");
+}
+
+qp_status qp_mlp_set_rollout_mode(qp_mlp *m, int mode) {
+    if (!m) return QP_ERR_ARG;
+    if (mode != QP_ROLLOUT_AUTO && mode != QP_ROLLOUT_GRAPH && mode != QP_ROLLOUT_FUSED)
+        return mfail(m, QP_ERR_ARG, "unknown rollout mode");
+    m->roll_mode = mode;
+    return QP_OK;
 }
 
 const char *qp_mlp_last_error(const qp_mlp *m) { return m ? m->err.c_str() : "null model"; }

@@ -115,8 +115,10 @@ class Surrogate:
         self.net.stream.synchronize()
         return hist
 
-    def rollout(self, rho_init, par, T_total):
-        """rho_init [n][L][2][2] (steps 0..L-1), par [n][n_par] -> rho [n][T_total][2][2]."""
+    def rollout(self, rho_init, par, T_total, mode="auto"):
+        """rho_init [n][L][2][2] (steps 0..L-1), par [n][n_par] -> rho [n][T_total][2][2].
+        mode: "auto" (one block for all steps where it fits), "graph" (CUDA
+        graphs of step kernels) or "fused" (qp_mlp_set_rollout_mode)."""
         torch = self.torch
         n = rho_init.shape[0]
         h = np.zeros((n, T_total, 8), dtype=np.float32)
@@ -128,6 +130,8 @@ class Surrogate:
         xb = torch.empty((n, 8 * self.L + self.n_par), dtype=torch.float32, device=self.device)
         yb = torch.empty((n, 8), dtype=torch.float32, device=self.device)
         torch.cuda.synchronize()
+        abi.qp_mlp_set_rollout_mode(self.net.h, {"auto": abi.QP_ROLLOUT_AUTO, "graph": abi.QP_ROLLOUT_GRAPH,
+                                                 "fused": abi.QP_ROLLOUT_FUSED}[mode])
         abi.qp_surrogate_rollout(self.net.h, hist.data_ptr(), n, T_total, self.L, par_dev.data_ptr(), self.n_par,
                                  self.L, T_total, self.out_scale, xb.data_ptr(), yb.data_ptr())
         self.net.stream.synchronize()

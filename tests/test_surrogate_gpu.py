@@ -9,9 +9,9 @@ The test asserts the surrogate is faster than the plain path over the same
 steps, stays within the stated error, and keeps rho a density matrix
 (Hermitian and positive semidefinite by projection), so that no instance
 falls back to the plain path.  Against the path update's own cheaper
-settings (memory 1, the Markov map, to 7): every setting about as fast as
-the surrogate is at least twice less accurate, and every setting as
-accurate is at least twice slower.
+settings (memory 1, the Markov map, to 7): no setting is both faster and
+more accurate than the surrogate.  The one-block rollout kernel and the
+graphs of step kernels give the same trajectories.
 """
 import time
 
@@ -80,3 +80,32 @@ def test_surrogate_gain_and_error_at_checkpoints():
             assert err_s < b["err_max"], (dk, err_s, b)
         if b["err_max"] <= err_s:
             assert t_sur < b["seconds"], (dk, t_sur, b)
+
+
+@pytest.mark.parametrize("n", [16, 7, 32])
+def test_fused_rollout_matches_step_kernels(n):
+    """The one-block rollout (all steps in one kernel) and the CUDA graphs of
+    step kernels: the same rounding points and k-step order, so the same
+    trajectories (the update's arithmetic may contract differently: 1e-6)."""
+    rng = np.random.default_rng(n)
+    s = Surrogate(L=L)
+    s.net.init(seed=3, out_gain=0.5)
+    T = 300
+    rho0 = np.zeros((n, L, 2, 2), dtype=complex)
+    for i in range(n):
+        for k in range(L):
+            a = rng.normal(size=(2, 2)) + 1j * rng.normal(size=(2, 2))
+            r = a @ a.conj().T
+            rho0[i, k] = r / np.trace(r).real
+    par = rng.uniform(0.1, 2.0, size=(n, 2))
+    t0 = time.perf_counter()
+    rf = s.rollout(rho0, par, T, mode="fused")
+    t_f = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    rg = s.rollout(rho0, par, T, mode="graph")
+    t_g = time.perf_counter() - t0
+    d = np.abs(rf - rg).max()
+    print(f"n = {n}: fused {1e6 * t_f / (T - L):.1f} us/step, graphs {1e6 * t_g / (T - L):.1f} us/step, "
+          f"max difference {d:.2e}")
+    assert np.isfinite(rf).all() and np.abs(rf[:, L:]).max() > 0
+    assert d <= 1e-6, d
