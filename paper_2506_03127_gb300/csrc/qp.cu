@@ -2203,8 +2203,11 @@ __device__ __forceinline__ void stream_step_body(const Params &P, int lut_smem) 
         // pass A: children of a contiguous range of groups per thread, once;
         // survivors counted per new point, amplitudes kept in shared memory
         // for pass B (the first NSTG groups)
-        const int gpt = (ngroups + NT - 1) / NT;
-        const int g0 = min(ngroups, (int)threadIdx.x * gpt), g1 = min(ngroups, g0 + gpt);
+        // (contiguous ranges in thread order, so that the survivors are written
+        // in group order; the first ngroups % NT threads take one more)
+        const int gq = ngroups / NT, gr = ngroups - gq * NT;
+        const int g0 = (int)threadIdx.x * gq + min((int)threadIdx.x, gr);
+        const int g1 = g0 + gq + ((int)threadIdx.x < gr ? 1 : 0);
         unsigned cntc[MM];
 #pragma unroll
         for (int c = 0; c < MM; ++c) cntc[c] = 0;
