@@ -253,6 +253,12 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+// 16-byte copy of which only the first src_bytes are read (the rest of the
+// destination is zero-filled)
+__device__ __forceinline__ void cp_async16_part(void *smem, const void *gmem, unsigned src_bytes) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(sa), "l"(gmem), "r"(src_bytes) : "memory");
+}
 
 
 __device__ __forceinline__ unsigned long long table_index(const Params &P, unsigned long long mk) {
@@ -1855,9 +1861,20 @@ __device__ __forceinline__ void stream_step_body(const Params &P, int lut_smem) 
         // load the tile; warp 0 prefetches the 32 paths past its end (the
         // last run may continue there), thread 0 the key before it; slots of
         // the previous tile are free (the loop ends with a barrier)
-        for (int i = threadIdx.x; i < cnt; i += NT) {
-            s_key[i] = __ldcg(kin + e0 + i);
-            s_amp[i] = __ldcg(ain + e0 + i);
+        // (16-byte asynchronous copies, all in flight at once, no registers:
+        // region bases and tile starts are 16-entry aligned; a ragged end
+        // reads only its entries; waited for before the barrier below)
+        {
+            const int kc = (cnt * 8 + 15) / 16, ac = (cnt * (int)sizeof(AmpT) + 15) / 16;
+            const char *kg = reinterpret_cast<const char *>(kin + e0), *ag = reinterpret_cast<const char *>(ain + e0);
+            char *ks = reinterpret_cast<char *>(s_key), *as = reinterpret_cast<char *>(s_amp);
+            for (int c = threadIdx.x; c < kc + ac; c += NT) {
+                if (c < kc) cp_async16_part(ks + 16 * c, kg + 16 * c, (unsigned)min(16, cnt * 8 - 16 * c));
+                else {
+                    const int d = c - kc;
+                    cp_async16_part(as + 16 * d, ag + 16 * d, (unsigned)min(16, cnt * (int)sizeof(AmpT) - 16 * d));
+                }
+            }
         }
         if (warp == 0) {
             const bool ok = cnt == St && e0 + St + lane < nr;
@@ -1878,6 +1895,7 @@ __device__ __forceinline__ void stream_step_body(const Params &P, int lut_smem) 
             for (int i = threadIdx.x; i < S; i += NT) s_xm[i] = 0u;
             for (int i = threadIdx.x; i < St * NX / 4; i += NT) reinterpret_cast<uint4 *>(s_xmask)[i] = make_uint4(0u, 0u, 0u, 0u);
         }
+        cp_async_wait_all();   // the tile's copies (and, at the first tile, the staged tables)
         __syncthreads();
         // run heads (ept consecutive entries per thread), block scan of their count
         unsigned hmask = 0;
