@@ -135,7 +135,11 @@ def premerge(paths: Paths, Pp, M: int):
     """Merge paths identical on the window positions Pp.
 
     Returns (rep_sp, rep_sm, S, near_tie): the representative path of each
-    group (largest |amp|, reading R4) and the summed amplitude S."""
+    group (largest |amp|, reading R4) and the summed amplitude S.  Keys
+    wider than 64 bits (b * window > 64, e.g. M = 8 with 12 points) go
+    through premerge_rows, which does not pack them."""
+    if state_bits(M)[1] * paths.sp.shape[1] > 64:
+        return premerge_rows(paths, Pp, M)
     cols = list(Pp)
     gkey = packed_keys(paths.sp[:, cols], paths.sm[:, cols], M)
     _, inv = np.unique(gkey, return_inverse=True)
@@ -156,6 +160,41 @@ def premerge(paths: Paths, Pp, M: int):
     idx = np.nonzero(is_rep)[0]
     rep_of = np.empty(G, dtype=np.int64)
     rep_of[inv[idx]] = idx
+    return paths.sp[rep_of], paths.sm[rep_of], S, near_tie
+
+
+def premerge_rows(paths: Paths, Pp, M: int):
+    """premerge without packed keys (any key width): groups are the distinct
+    rows of the P' columns; the representative is the member of largest
+    weight, ties (R4) to the member whose packed key would be smallest,
+    i.e. the smallest in the order that compares the oldest position first
+    and, within a position, the backward point before the forward one (the
+    order of the packed key for any number of bits per point)."""
+    cols = list(Pp)
+    gk = np.concatenate([paths.sp[:, cols], paths.sm[:, cols]], axis=1)
+    if gk.shape[0] == 0:
+        return paths.sp[:0], paths.sm[:0], np.zeros(0, dtype=np.complex128), 0
+    _, inv = np.unique(gk, axis=0, return_inverse=True)
+    inv = np.asarray(inv).reshape(-1)
+    G = int(inv.max()) + 1
+    S = np.zeros(G, dtype=np.complex128)
+    np.add.at(S, inv, paths.amp)
+    w2 = paths.amp.real ** 2 + paths.amp.imag ** 2
+    wmax = np.zeros(G)
+    np.maximum.at(wmax, inv, w2)
+    edge = (1.0 - TIE_REL) * wmax[inv]
+    eligible = w2 >= edge
+    near_tie = int(np.count_nonzero((np.abs(w2 - edge) <= 1e-13 * np.maximum(edge, 1e-300))
+                                    & (w2 != wmax[inv])))
+    idx = np.nonzero(eligible)[0]
+    L = paths.sp.shape[1]
+    keys = []   # least significant first (np.lexsort takes the last key as primary)
+    for p in range(L):
+        keys += [paths.sp[idx, p], paths.sm[idx, p]]
+    order = idx[np.lexsort(tuple(keys) + (inv[idx],))]
+    first = np.r_[True, inv[order][1:] != inv[order][:-1]]
+    rep_of = np.empty(G, dtype=np.int64)
+    rep_of[inv[order[first]]] = order[first]
     return paths.sp[rep_of], paths.sm[rep_of], S, near_tie
 
 

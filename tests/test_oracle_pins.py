@@ -593,3 +593,74 @@ def test_planted_symmetric_splitting_mistake_is_caught(name):
 
 def test_unmutated_oracle_passes_symmetric_harness():
     assert _sym_pins_pass(iquapi)
+
+
+# ---------------------------------------------------------------- wide keys (M up to 8)
+
+def _random_set(rng, M, L, n=3000):
+    sp = rng.integers(0, M, size=(n, L))
+    sm = rng.integers(0, M, size=(n, L))
+    amp = rng.normal(size=n) + 1j * rng.normal(size=n)
+    amp[::7] = 10.0 * amp[::7] / np.abs(amp[::7])   # equal largest weights: the tie rule decides
+    return iquapi.Paths(sp, sm, amp)
+
+
+def _same_premerge(a, b):
+    ka = sorted(map(tuple, np.hstack([a[0], a[1]])))
+    kb = sorted(map(tuple, np.hstack([b[0], b[1]])))
+    return ka == kb and np.allclose(np.sort_complex(a[2]), np.sort_complex(b[2]), rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("M,L,Pp", [(2, 6, [0, 1, 3]), (3, 5, [0, 1]), (4, 4, [0, 2]), (5, 4, [0, 1]),
+                                    (6, 3, [0, 2]), (8, 3, [0])])
+def test_premerge_without_packing_equals_packed_premerge(M, L, Pp):
+    """premerge_rows (keys of any width) against the packed-key premerge
+    where both apply: the same groups, sums and representatives, ties
+    included."""
+    rng = np.random.default_rng(M * 10 + L)
+    P = _random_set(rng, M, L)
+    assert _same_premerge(iquapi.premerge(P, Pp, M), iquapi.premerge_rows(P, Pp, M))
+
+
+@pytest.mark.parametrize("M,dkmax,N,seed", [(5, 2, 3, 1), (5, 3, 3, 2), (6, 2, 3, 3)])
+def test_iterative_equals_brute_force_larger_M(M, dkmax, N, seed):
+    c = W.random_case(seed, M, dkmax)
+    rb = brute.rho_by_enumeration(M, c["q"], c["hs"], c["dt"], c["eta"], dkmax, c["rho0"], N)
+    r = iquapi.propagate(M, c["q"], c["hs"], c["dt"], c["eta"], dkmax, None, 0.0, c["rho0"], N)
+    assert np.abs(r.rho[N] - rb).max() <= 2e-14
+
+
+def test_wide_keys_go_through_premerge_rows():
+    """M = 8 at 11 points: 66 key bits, beyond a packed 64-bit key; the
+    step uses premerge_rows and agrees with a run whose window columns are
+    reordered (a relabelling that leaves the physics unchanged is not
+    available, so the check is the equality of the two premerge forms on
+    the step's own input)."""
+    rng = np.random.default_rng(3)
+    P = _random_set(rng, 8, 11, n=4000)
+    a = iquapi.premerge(P, [0, 1], 8)
+    assert _same_premerge(a, iquapi.premerge_rows(P, [0, 1], 8))
+    # the packed form cannot hold these keys
+    assert iquapi.state_bits(8)[1] * 11 > 64
+
+
+ROWS_MUTATIONS = {
+    "backward point before forward within a position reversed": ("keys += [paths.sp[idx, p], paths.sm[idx, p]]",
+                                                                  "keys += [paths.sm[idx, p], paths.sp[idx, p]]"),
+    "groups ignore the backward points": ("gk = np.concatenate([paths.sp[:, cols], paths.sm[:, cols]], axis=1)",
+                                          "gk = np.concatenate([paths.sp[:, cols], paths.sp[:, cols]], axis=1)"),
+    "newest position compared first": ("for p in range(L):\n        keys +=", "for p in reversed(range(L)):\n        keys +="),
+}
+
+
+@pytest.mark.parametrize("name", sorted(ROWS_MUTATIONS))
+def test_planted_premerge_rows_mistake_is_caught(name):
+    old, new = ROWS_MUTATIONS[name]
+    mod = _mutant(old, new)
+    rng = np.random.default_rng(11)
+    caught = False
+    for M, L, Pp in [(2, 6, [0, 1, 3]), (3, 5, [0, 1]), (5, 4, [0, 1])]:
+        P = _random_set(rng, M, L)
+        if not _same_premerge(iquapi.premerge(P, Pp, M), mod.premerge_rows(P, Pp, M)):
+            caught = True
+    assert caught
