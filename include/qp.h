@@ -495,6 +495,45 @@ qp_status qp_surrogate_rollout(qp_mlp *m, float *d_hist, int n, int T, int L, co
 enum { QP_ROLLOUT_AUTO = 0, QP_ROLLOUT_GRAPH = 1, QP_ROLLOUT_FUSED = 2 };
 qp_status qp_mlp_set_rollout_mode(qp_mlp *m, int mode);
 
+/* ------------------------------------------------------------------------
+ * Wide keys: the path update with keys of up to 128 bits (M <= 8 states,
+ * dkmax <= 16 points; the production models of Sec. 4.3 need M = 8 at
+ * dkmax = 12, beyond one 64-bit word).  A separate context over the same
+ * qp_config (precision, theta, max_paths, max_groups, rho_history; single
+ * problems, pre-merging order): the merge-table form, with the pre-merge on
+ * a 64-bit key of 6 bits per position of P' (so P' may hold at most 10
+ * positions, and at most 10 positions may lie outside it) and the tie rule
+ * of the narrow engines (reading R4: the smallest key among the members
+ * within the tie window of the largest weight).
+ *
+ * Key layout (exported as two words per path, lo then hi): one byte per
+ * window position p = 0 .. dkmax-1 (0 = newest point), byte p of the
+ * 128-bit number lo + 2^64 hi; forward state in its low nibble, backward
+ * state in its high nibble.  Numerically this orders keys as the narrow
+ * packing does (oldest position first, backward state before forward).
+ * Semantics of eta, the mask and rho0 as the narrow calls above.          */
+typedef struct qp_wide qp_wide;
+qp_status qp_wide_workspace_size(const qp_config *cfg, size_t *bytes);
+/* d_workspace: device memory of at least qp_wide_workspace_size bytes,
+ * owned by the caller and alive until qp_wide_destroy; q and hs are copied. */
+qp_status qp_wide_create(const qp_config *cfg, void *d_workspace, size_t bytes, void *cuda_stream, qp_wide **out);
+void qp_wide_destroy(qp_wide *w);
+qp_status qp_wide_set_eta(qp_wide *w, const double *eta_re, const double *eta_im, int n);
+/* Default: the full mask, refused at qp_wide_set_rho0 when its P' holds more
+ * than 10 positions (set a mask first).                                    */
+qp_status qp_wide_set_mask(qp_wide *w, const int *positions, int n);
+qp_status qp_wide_set_rho0(qp_wide *w, const double *rho0_re, const double *rho0_im);
+/* nsteps steps on the context's stream; reads the step index first
+ * (synchronises once per call).  Capacity overflows surface as
+ * QP_ERR_CAPACITY at the next synchronising call.                          */
+qp_status qp_wide_step(qp_wide *w, int nsteps);
+qp_status qp_wide_current(qp_wide *w, int64_t *t, int64_t *n);
+qp_status qp_wide_read_rho(qp_wide *w, int64_t t0, int count, double *re, double *im);
+qp_status qp_wide_read_stats(qp_wide *w, int64_t t0, int count, qp_step_stats *out);
+/* keys[2 cap] (lo, hi per path), amps[2 cap] (re, im, FP64).               */
+qp_status qp_wide_export_paths(qp_wide *w, uint64_t *keys, double *amps, int64_t cap, int64_t *n);
+const char *qp_wide_last_error(const qp_wide *w);
+
 #ifdef __cplusplus
 }
 #endif

@@ -12,7 +12,7 @@ import importlib
 
 import numpy as np
 
-__all__ = ["abi", "Propagator", "eta_from_bath", "batch_from_workloads"]
+__all__ = ["abi", "Propagator", "WidePropagator", "eta_from_bath", "batch_from_workloads"]
 
 
 def _abi():
@@ -162,3 +162,63 @@ def batch_from_workloads(ws, precision="c64", max_paths=1 << 22, engine="auto", 
     p.set_mask(w0.mask)
     p.set_rho0(w0.rho0_array())
     return p
+
+
+class WidePropagator:
+    """The path update with keys of up to 128 bits (M up to 8, windows up to
+    16 points): a qp_wide context (see qp.h) with its device workspace and
+    stream from PyTorch.  Single problems, pre-merging order."""
+
+    def __init__(self, M, dkmax, dt, q, hs, theta=0.0, precision="fp64", max_paths=1 << 20, max_groups=0,
+                 rho_history=4096, device=None, stream=None):
+        import torch
+        from . import abi
+        if not torch.cuda.is_available():
+            raise RuntimeError("WidePropagator needs a CUDA device")
+        self.M, self.dkmax = M, dkmax
+        prec = {"fp64": abi.QP_FP64, "c64": abi.QP_C64}[precision]
+        self._cfg, self._keep = abi.make_config(M, dkmax, dt, q, hs, theta, prec, abi.QP_ENGINE_HASH, max_paths,
+                                                max_groups, rho_history, 1, abi.QP_PREMERGE)
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+            self.nbytes = abi.qp_wide_workspace_size(self._cfg)
+            self.workspace = torch.empty(self.nbytes, dtype=torch.uint8, device=self.device)
+            self.ctx = abi.qp_wide_create(self._cfg, self.workspace.data_ptr(), self.nbytes, self.stream.cuda_stream)
+
+    def set_eta(self, eta):
+        _abi().qp_wide_set_eta(self.ctx, eta)
+
+    def set_mask(self, positions):
+        _abi().qp_wide_set_mask(self.ctx, positions)
+
+    def set_rho0(self, rho0):
+        _abi().qp_wide_set_rho0(self.ctx, rho0)
+
+    def step(self, nsteps=1):
+        _abi().qp_wide_step(self.ctx, nsteps)
+
+    def current(self):
+        return _abi().qp_wide_current(self.ctx)
+
+    def rho(self, t0, count=1):
+        return _abi().qp_wide_read_rho(self.ctx, t0, count, self.M)
+
+    def stats(self, t0, count=1):
+        return _abi().qp_wide_read_stats(self.ctx, t0, count)
+
+    def export_paths(self, cap=None):
+        if cap is None:
+            cap = self.current()[1]
+        return _abi().qp_wide_export_paths(self.ctx, cap)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            _abi().lib.qp_wide_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -118,6 +118,20 @@ def _load():
                                                 ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                                 ctypes.c_int, ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p]),
         "qp_mlp_set_rollout_mode": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+        "qp_wide_workspace_size": (ctypes.c_int, [ctypes.POINTER(qp_config), ctypes.POINTER(ctypes.c_size_t)]),
+        "qp_wide_create": (ctypes.c_int, [ctypes.POINTER(qp_config), ctypes.c_void_p, ctypes.c_size_t,
+                                          ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+        "qp_wide_destroy": (None, [ctypes.c_void_p]),
+        "qp_wide_set_eta": (ctypes.c_int, [ctypes.c_void_p, _dp, _dp, ctypes.c_int]),
+        "qp_wide_set_mask": (ctypes.c_int, [ctypes.c_void_p, _ip, ctypes.c_int]),
+        "qp_wide_set_rho0": (ctypes.c_int, [ctypes.c_void_p, _dp, _dp]),
+        "qp_wide_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+        "qp_wide_current": (ctypes.c_int, [ctypes.c_void_p, _i64p, _i64p]),
+        "qp_wide_read_rho": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, _dp, _dp]),
+        "qp_wide_read_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
+                                              ctypes.POINTER(qp_step_stats)]),
+        "qp_wide_export_paths": (ctypes.c_int, [ctypes.c_void_p, _u64p, _dp, ctypes.c_int64, _i64p]),
+        "qp_wide_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
         "qp_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
         "qp_step_noalloc": (ctypes.c_int, [ctypes.POINTER(qp_config), _dp, _dp, ctypes.c_int, _ip, ctypes.c_int,
                                            ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
@@ -419,3 +433,75 @@ def qp_mlp_set_rollout_mode(m, mode: int):
 def qp_surrogate_rollout(m, d_hist, n, T, L, d_par, n_par, t_from, t_to, out_scale, d_xbuf, d_ybuf):
     mcheck(lib.qp_surrogate_rollout(m, ctypes.c_void_p(d_hist), n, T, L, ctypes.c_void_p(d_par), n_par, t_from, t_to,
                                     out_scale, ctypes.c_void_p(d_xbuf), ctypes.c_void_p(d_ybuf)), m)
+
+
+# ---------------------------------------------------------------- wide keys (M up to 8, 128-bit keys)
+
+def wcheck(status, w=None):
+    if status != QP_OK:
+        raise QPError(status, lib.qp_wide_last_error(w).decode() if w else "")
+
+
+def qp_wide_workspace_size(cfg) -> int:
+    n = ctypes.c_size_t()
+    wcheck(lib.qp_wide_workspace_size(ctypes.byref(cfg), ctypes.byref(n)))
+    return n.value
+
+
+def qp_wide_create(cfg, d_workspace: int, nbytes: int, stream: int):
+    h = ctypes.c_void_p()
+    wcheck(lib.qp_wide_create(ctypes.byref(cfg), ctypes.c_void_p(d_workspace), nbytes, ctypes.c_void_p(stream),
+                              ctypes.byref(h)))
+    return h
+
+
+def qp_wide_set_eta(w, eta):
+    e = np.ascontiguousarray(np.asarray(eta, dtype=np.complex128))
+    re, im = np.ascontiguousarray(e.real), np.ascontiguousarray(e.imag)
+    wcheck(lib.qp_wide_set_eta(w, _ptr(re), _ptr(im), e.size), w)
+
+
+def qp_wide_set_mask(w, positions):
+    if positions is None:
+        wcheck(lib.qp_wide_set_mask(w, None, 0), w)
+        return
+    p = np.ascontiguousarray(np.asarray(positions, dtype=np.int32))
+    wcheck(lib.qp_wide_set_mask(w, _ptr(p, _ip), p.size), w)
+
+
+def qp_wide_set_rho0(w, rho0):
+    r = np.asarray(rho0, dtype=np.complex128)
+    re, im = np.ascontiguousarray(r.real.ravel()), np.ascontiguousarray(r.imag.ravel())
+    wcheck(lib.qp_wide_set_rho0(w, _ptr(re), _ptr(im)), w)
+
+
+def qp_wide_step(w, nsteps: int):
+    wcheck(lib.qp_wide_step(w, nsteps), w)
+
+
+def qp_wide_current(w):
+    t, n = ctypes.c_int64(), ctypes.c_int64()
+    wcheck(lib.qp_wide_current(w, ctypes.byref(t), ctypes.byref(n)), w)
+    return t.value, n.value
+
+
+def qp_wide_read_rho(w, t0: int, count: int, M: int) -> np.ndarray:
+    re, im = np.zeros(count * M * M), np.zeros(count * M * M)
+    wcheck(lib.qp_wide_read_rho(w, t0, count, _ptr(re), _ptr(im)), w)
+    return (re + 1j * im).reshape(count, M, M)
+
+
+def qp_wide_read_stats(w, t0: int, count: int):
+    arr = (qp_step_stats * count)()
+    wcheck(lib.qp_wide_read_stats(w, t0, count, arr), w)
+    return [(s.t, s.groups, s.extended, s.kept, s.intermediate) for s in arr]
+
+
+def qp_wide_export_paths(w, cap: int):
+    """(keys [n, 2] uint64 as (lo, hi), amplitudes [n] complex128)."""
+    keys = np.zeros(2 * cap, dtype=np.uint64)
+    amps = np.zeros(2 * cap, dtype=np.float64)
+    n = ctypes.c_int64()
+    wcheck(lib.qp_wide_export_paths(w, _ptr(keys, _u64p), _ptr(amps), cap, ctypes.byref(n)), w)
+    k = n.value
+    return keys[:2 * k].reshape(k, 2).copy(), amps[0:2 * k:2] + 1j * amps[1:2 * k:2]

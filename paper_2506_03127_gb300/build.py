@@ -2,7 +2,7 @@
 
     python -m paper_2506_03127_gb300.build
 
-The three translation units (qp.cu, mlp.cu, host_numerics.cpp) are compiled in parallel, then linked into
+The four translation units (qp.cu, mlp.cu, wide.cu, host_numerics.cpp) are compiled in parallel, then linked into
 paper_2506_03127_gb300/libqp.so.  A rebuild happens only when a source is
 newer than the library (or force=True).
 """
@@ -21,7 +21,7 @@ LIB = os.path.join(PKG, "libqp.so")
 BUILD = os.path.join(PKG, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["qp.cu", "mlp.cu", "host_numerics.cpp"]
+SOURCES = ["qp.cu", "mlp.cu", "wide.cu", "host_numerics.cpp"]
 HEADERS = ["internal.h"]
 
 

@@ -31,9 +31,9 @@ static void matmul(int M, const cplx *A, const cplx *B, cplx *C) {
 }
 
 void short_time_propagator(int M, const cplx *H, double dt, cplx *U) {
-    // M <= 4: fixed arrays, no allocation (the allocation-free step uses it)
+    // M <= 8: fixed arrays, no allocation (the allocation-free step uses it)
     // A = -i H dt, scaled by 2^-s so that its 1-norm is below 1/4
-    cplx A[16], T[16], P[16], tmp[16];
+    cplx A[64], T[64], P[64], tmp[64];
     double norm = 0.0;
     for (int j = 0; j < M; ++j) {
         double col = 0.0;

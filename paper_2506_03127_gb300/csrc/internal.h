@@ -15,7 +15,7 @@ using cplx = std::complex<double>;
 // squaring of the Taylor series.  The short-time system propagator of Eq.
 // SysP (hbar = 1).
 std::vector<cplx> short_time_propagator(int M, const std::vector<cplx> &H, double dt);
-// the same into U[M*M] for M <= 4, without allocating
+// the same into U[M*M] for M <= 8, without allocating
 void short_time_propagator(int M, const cplx *H, double dt, cplx *U);
 
 // Spectral density J(w) of the bath (ohmic part + Eq. sharpSD resonance).
