@@ -425,6 +425,53 @@ def run_batched_sweep(n_inst=64, reps=3):
             "rho_max_abs_err_vs_fp64": err}
 
 
+def run_wide(steps=30, tail=10):
+    """The reaction-coordinate model of Sec. 4.3 (M = 8, Delta k_max = 12:
+    keys of 96 bits, the qp_wide context) at the paper's converged settings
+    (Delta k_eff = 10, theta = 1e-9), complex64 and FP64 over the same first
+    `steps` steps (the window fills at t = 12; the set then holds ~3e8
+    paths); time per step over the last `tail` steps (CUDA events, one
+    qp_wide_step call each), stored and extended paths, and rho of the two
+    precisions compared.  The paper's run of this model: ~32 h on 96 cores
+    (Sec. 4.3), 2.5e8 paths on average."""
+    import torch
+    from paper_2506_03127_gb300 import WidePropagator, eta_from_bath
+
+    w = W.reaction_coordinate()
+    eta = eta_from_bath(w.bath, w.dt, w.dkmax)
+    out = {"workload": w.name, "M": w.M, "dkmax": w.dkmax, "mask": list(w.mask), "theta": w.theta, "dt": w.dt,
+           "steps": steps, "key_bits": 8 * w.dkmax}
+    rhos = {}
+    for prec, mp in (("c64", 1 << 30), ("fp64", 1 << 30)):
+        p = WidePropagator(w.M, w.dkmax, w.dt, w.q, w.hs_array(), w.theta, prec, max_paths=mp, max_groups=mp // 4)
+        p.set_eta(eta)
+        p.set_mask(w.mask)
+        p.set_rho0(w.rho0_array())
+        ms = []
+        for k in range(steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(p.stream)
+            p.step(1)
+            e1.record(p.stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        t, n = p.current()
+        st = p.stats(t - tail + 1, tail)
+        ext = float(sum(r[2] for r in st))
+        t_tail = float(sum(ms[-tail:]))
+        rhos[prec] = p.rho(0, t + 1)
+        out[prec] = {"ms_per_step": t_tail / tail, "stored_paths_last": int(n),
+                     "extended_paths_per_s": ext / (t_tail / 1e3), "workspace_gb": p.nbytes / 1e9,
+                     "trace_last": float(np.trace(rhos[prec][-1]).real)}
+        p.close()
+        del p
+        torch.cuda.empty_cache()
+    out["rho_max_abs_diff_c64_vs_fp64"] = float(np.abs(rhos["c64"] - rhos["fp64"]).max())
+    out["note"] = ("keys beyond 64 bits; parity with the oracle on smaller cases of the same key width "
+                   "(tests/test_wide_gpu.py); the paper: ~32 h on 96 cores for the converged run of this model")
+    return out
+
+
 def run_surrogate(T_train=100, T_long=1000, L=32, epochs=2000):
     """The learned surrogate: train (libqp kernels) on 100-step trajectories of
     48 sweep instances, roll 16 held-out instances out to t = 1000 and judge
@@ -761,6 +808,7 @@ def main():
         line["batched_sweep"] = run_batched_sweep()
         line["surrogate"] = run_surrogate()
         line["pre_vs_post"] = run_pre_vs_post()
+        line["wide_keys"] = run_wide()
     line.update({"metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": args.gpus, "steps": args.steps,
                  "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
                  "scaling": "weak", "vs_baseline": None, "dtype": "c64" if args.precision == "c64" else "f64",
