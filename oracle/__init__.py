@@ -24,7 +24,9 @@ Contents
 Parity status: every function is pinned by tests/test_oracle_pins.py against
 closed forms or brute force; the filter (its rule |amp| >= theta and its
 place before rho) by the filtered Markov map at memory length 1 and a
-hand-made set.  The masked pre-merge together with a nonzero bath has no
+hand-made set; the pre-merge of keys wider than 64 bits (premerge_rows, no
+packing) by equality with the packed pre-merge wherever both apply, ties at
+the group maxima included.  The masked pre-merge together with a nonzero bath has no
 value the paper prints ("parity unpinned" for that combination; it is
 pinned only by invariants: exactness at zero coupling, trace conservation
 without a filter, reduction to the unmasked result for the full mask).
