@@ -15,7 +15,7 @@
 //               FP64 sums, largest weight (Sec. 3.1 "Pre-merging");
 //   k_w_tie     members within the tie window of the largest weight compete
 //               on a 64-bit tie key (the positions outside P', in key order);
-//   k_w_rep     the winner becomes the group's representative;
+//   (k_w_tie<true>: the winner becomes the group's representative)
 //   k_w_expand  one thread per group: the history part H of the influence
 //               exponent from per-position tables, then the M^2 children
 //               (Eqs. SysP, inf_fun) one at a time, filtered (|amp| >= theta,
@@ -28,6 +28,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <cstdint>
 #include <cstring>
 #include <string>
@@ -40,6 +41,7 @@ namespace {
 constexpr int kWMaxM = 8, kWMaxDk = 16, kWMaxMM = 64;
 constexpr int kWThreads = 256;
 constexpr int kWProbe = 64;
+constexpr int kWMaxTabDelta = 16;   // distinct coupling differences up to which a group tabulates its factors
 constexpr unsigned long long kWEmpty = ~0ull;
 constexpr unsigned kWErrPaths = 1u, kWErrGroups = 2u, kWErrProbe = 4u;
 
@@ -62,6 +64,9 @@ struct WParams {
     double theta2, tie_rel;
     float theta2f;
     double q[kWMaxM];
+    int ndelta;                        // distinct nonzero q_a - q_b (tabulated per group when <= kWMaxTabDelta)
+    double delta[kWMaxMM];
+    signed char dsel[kWMaxMM];         // child c -> its difference (-1: q_a = q_b)
     unsigned long long *klo[2], *khi[2];
     void *amps[2];
     unsigned int *slot_of, *groups, *trep;
@@ -175,8 +180,16 @@ __global__ void k_w_tie(WParams P) {
 
 // children of one group, appended in warp-aggregated blocks; thread-uniform
 // loops (every lane of a warp runs every child, valid or not)
-template <bool C64>
+template <bool C64, bool TAB>
 __global__ void __launch_bounds__(kWThreads) k_w_expand(WParams P, int merge) {
+    // TAB: the influence factors exp(-delta H) of the group's distinct
+    // coupling differences, computed once per group (the same arithmetic as
+    // per child), in shared memory [delta][thread]
+    using CT = typename std::conditional<C64, float2, double2>::type;
+    extern __shared__ __align__(16) unsigned char s_wtab[];
+    CT *sE = reinterpret_cast<CT *>(s_wtab);
+    __shared__ unsigned s_wc[kWThreads / 32];
+    __shared__ unsigned long long s_base;
     WState *st = P.st;
     if (st->err) return;
     const unsigned long long t = st->t, tn = t + 1;
@@ -241,6 +254,24 @@ __global__ void __launch_bounds__(kWThreads) k_w_expand(WParams P, int merge) {
                 Hy += e.y;
             }
         }
+        if constexpr (TAB) {
+            for (int d = 0; d < P.ndelta; ++d) {
+                if constexpr (C64) {
+                    const float dqf = (float)P.delta[d];
+                    const float zr = -dqf * hx, zi = -dqf * hy;
+                    float sn, cs;
+                    sincosf(zi, &sn, &cs);
+                    const float m = expf(zr);
+                    sE[d * kWThreads + threadIdx.x] = make_float2(m * cs, m * sn);
+                } else {
+                    const double zr = -P.delta[d] * Hx, zi = -P.delta[d] * Hy;
+                    double sn, cs;
+                    sincos(zi, &sn, &cs);
+                    const double m = exp(zr);
+                    sE[d * kWThreads + threadIdx.x] = make_double2(m * cs, m * sn);
+                }
+            }
+        }
         // child key: the parent shifted up one position, the new point in
         // the lowest byte, cut to L_child positions
         unsigned long long chi = (hi << 8) | (lo >> 56), clo = lo << 8;
@@ -250,48 +281,94 @@ __global__ void __launch_bounds__(kWThreads) k_w_expand(WParams P, int merge) {
         } else if (8 * L_child < 128) {
             chi &= (1ull << (8 * L_child - 64)) - 1ull;
         }
-        for (int c = 0; c < MM; ++c) {
+        // child c of the group: its amplitude and whether it survives the filter
+        auto child_of = [&](int c, double2 &child) -> bool {
             const int a = c / M, b = c % M;
             const double dq = P.q[a] - P.q[b];
-            double2 child;
-            float wcf = 0.f;
             if constexpr (C64) {
-                const float dqf = (float)dq;
-                const float zr = -dqf * hx, zi = -dqf * hy;
-                float sn, cs;
-                sincosf(zi, &sn, &cs);
-                const float m = expf(zr);
-                const float fx = m * cs, fy = m * sn;
+                float fx, fy;
+                if constexpr (TAB) {
+                    const int d = P.dsel[c];
+                    const float2 e = d < 0 ? make_float2(1.f, 0.f) : sE[d * kWThreads + threadIdx.x];
+                    fx = e.x;
+                    fy = e.y;
+                } else {
+                    const float dqf = (float)dq;
+                    const float zr = -dqf * hx, zi = -dqf * hy;
+                    float sn, cs;
+                    sincosf(zi, &sn, &cs);
+                    const float m = expf(zr);
+                    fx = m * cs;
+                    fy = m * sn;
+                }
                 const float4 wv = P.wf[(size_t)c * MM + parc];
                 const float Sx = (float)S.x, Sy = (float)S.y;
                 // S (W_hi + W_lo) f
                 const float px = fmaf(Sx, wv.x, -Sy * wv.y) + fmaf(Sx, wv.z, -Sy * wv.w);
                 const float py = fmaf(Sx, wv.y, Sy * wv.x) + fmaf(Sx, wv.w, Sy * wv.z);
                 const float ox = px * fx - py * fy, oy = px * fy + py * fx;
-                wcf = ox * ox + oy * oy;
                 child = make_double2(ox, oy);
+                return ox * ox + oy * oy >= P.theta2f;
             } else {
-                const double zr = -dq * Hx, zi = -dq * Hy;
-                double sn, cs;
-                sincos(zi, &sn, &cs);
-                const double m = exp(zr);
+                double fx, fy;
+                if constexpr (TAB) {
+                    const int d = P.dsel[c];
+                    const double2 e = d < 0 ? make_double2(1.0, 0.0) : sE[d * kWThreads + threadIdx.x];
+                    fx = e.x;
+                    fy = e.y;
+                } else {
+                    const double zr = -dq * Hx, zi = -dq * Hy;
+                    double sn, cs;
+                    sincos(zi, &sn, &cs);
+                    const double m = exp(zr);
+                    fx = m * cs;
+                    fy = m * sn;
+                }
                 const double2 wv = P.w[(size_t)c * MM + parc];
                 const double px = S.x * wv.x - S.y * wv.y, py = S.x * wv.y + S.y * wv.x;
-                child = make_double2(px * m * cs - py * m * sn, px * m * sn + py * m * cs);
+                child = make_double2(px * fx - py * fy, px * fy + py * fx);
+                return child.x * child.x + child.y * child.y >= P.theta2;
             }
-            const bool keep = valid && (C64 ? wcf >= P.theta2f : child.x * child.x + child.y * child.y >= P.theta2);
-            const unsigned km = __ballot_sync(0xffffffffu, keep);
-            if (!km) continue;
-            unsigned long long o0 = 0;
-            if (lane == 0) o0 = atomicAdd(&st->n_out, (unsigned long long)__popc(km));
-            o0 = __shfl_sync(0xffffffffu, o0, 0);
-            if (!keep) continue;
-            const unsigned long long o = o0 + __popc(km & ((1u << lane) - 1u));
-            if ((long long)o >= P.max_paths) {
-                atomicOr(&st->err, kWErrPaths);
-                continue;
+        };
+        // pass 1: the survivors of each group, counted; one output range per
+        // block and round (a block scan and one atomic), then pass 2 forms
+        // the survivors again (the same arithmetic) and writes them
+        unsigned long long kmask = 0ull;
+        if (valid)
+            for (int c = 0; c < MM; ++c) {
+                double2 child;
+                if (child_of(c, child)) kmask |= 1ull << c;
             }
-            P.klo[outp][o] = clo | (unsigned long long)(a | (b << 4));
+        const unsigned cnt = (unsigned)__popcll(kmask);
+        unsigned inc = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
+            if ((int)lane >= o) inc += y;
+        }
+        if (lane == 31) s_wc[threadIdx.x >> 5] = inc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long tot = 0;
+            for (int w = 0; w < kWThreads / 32; ++w) {
+                const unsigned v = s_wc[w];
+                s_wc[w] = (unsigned)tot;
+                tot += v;
+            }
+            s_base = tot ? atomicAdd(&st->n_out, tot) : 0ull;
+        }
+        __syncthreads();
+        unsigned long long o = s_base + s_wc[threadIdx.x >> 5] + (inc - cnt);
+        __syncthreads();   // s_wc and s_base are rewritten in the next round
+        if (cnt && (long long)(o + cnt) > P.max_paths) {
+            atomicOr(&st->err, kWErrPaths);
+            kmask = 0ull;
+        }
+        for (unsigned long long m = kmask; m; m &= m - 1ull, ++o) {
+            const int c = __ffsll((long long)m) - 1;
+            double2 child;
+            child_of(c, child);
+            P.klo[outp][o] = clo | (unsigned long long)((c / M) | ((c % M) << 4));
             P.khi[outp][o] = chi;
             if constexpr (C64) static_cast<float2 *>(P.amps[outp])[o] = make_float2((float)child.x, (float)child.y);
             else static_cast<double2 *>(P.amps[outp])[o] = child;
@@ -581,6 +658,21 @@ qp_status qp_wide_create(const qp_config *cfg, void *d_workspace, size_t bytes, 
     P.theta2f = (float)P.theta2;
     P.tie_rel = cfg->precision == QP_C64 ? 1e-6 : 1e-12;   // the narrow engines' windows (reading R4, R11)
     for (int i = 0; i < M; ++i) P.q[i] = cfg->q[i];
+    P.ndelta = 0;
+    for (int a = 0; a < M; ++a)
+        for (int b = 0; b < M; ++b) {
+            const double d = cfg->q[a] - cfg->q[b];   // as the kernel forms it
+            int k = -1;
+            if (d != 0.0) {
+                for (int j = 0; j < P.ndelta; ++j)
+                    if (P.delta[j] == d) k = j;
+                if (k < 0) {
+                    k = P.ndelta;
+                    P.delta[P.ndelta++] = d;
+                }
+            }
+            P.dsel[a * M + b] = (signed char)k;
+        }
     char *ws = w->ws;
     for (int k = 0; k < 2; ++k) {
         P.klo[k] = reinterpret_cast<unsigned long long *>(ws + L.klo[k]);
@@ -610,6 +702,13 @@ qp_status qp_wide_create(const qp_config *cfg, void *d_workspace, size_t bytes, 
         // the full mask of a long window does not fit a 64-bit group key:
         // a mask must be set before qp_wide_set_rho0
         w->P.npp = -1;
+    }
+    if (cudaFuncSetAttribute(k_w_expand<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kWMaxTabDelta * kWThreads * 16) != cudaSuccess ||
+        cudaFuncSetAttribute(k_w_expand<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kWMaxTabDelta * kWThreads * 8) != cudaSuccess) {
+        delete w;
+        return QP_ERR_CUDA;
     }
     *out = w;
     return QP_OK;
@@ -735,8 +834,15 @@ qp_status qp_wide_step(qp_wide *w, int nsteps) {
             k_w_tie<false><<<g, kWThreads, 0, w->stream>>>(w->P);
             k_w_tie<true><<<g, kWThreads, 0, w->stream>>>(w->P);
         }
-        if (w->P.c64) k_w_expand<true><<<g, kWThreads, 0, w->stream>>>(w->P, merge);
-        else k_w_expand<false><<<g, kWThreads, 0, w->stream>>>(w->P, merge);
+        const bool tab = w->P.ndelta <= kWMaxTabDelta;
+        const size_t tsm = tab ? (size_t)w->P.ndelta * kWThreads * (w->P.c64 ? 8 : 16) : 0;
+        if (w->P.c64) {
+            if (tab) k_w_expand<true, true><<<g, kWThreads, tsm, w->stream>>>(w->P, merge);
+            else k_w_expand<true, false><<<g, kWThreads, 0, w->stream>>>(w->P, merge);
+        } else {
+            if (tab) k_w_expand<false, true><<<g, kWThreads, tsm, w->stream>>>(w->P, merge);
+            else k_w_expand<false, false><<<g, kWThreads, 0, w->stream>>>(w->P, merge);
+        }
         k_w_rho<<<g, kWThreads, 0, w->stream>>>(w->P);
         k_w_finalize<<<1, 64, 0, w->stream>>>(w->P, g, merge);
         QW_CUDA(w, cudaGetLastError());

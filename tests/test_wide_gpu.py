@@ -170,3 +170,39 @@ def test_wide_mask_limits():
     p.set_rho0(c["rho0"])
     p.step(2)
     p.close()
+
+
+@pytest.mark.parametrize("precision,tol,tie", [("fp64", TOL, None), ("c64", 1e-5, 1e-6)])
+def test_wide_reaction_coordinate_matches_oracle(precision, tol, tie, monkeypatch):
+    """The reaction-coordinate model of Sec. 4.3 (M = 8, the production mask
+    at Delta k_max = 12: 96-bit keys; its position eigenvalues come in equal
+    pairs, so the children's influence factors are tabulated per distinct
+    coupling difference), at theta = 1e-4 so that the oracle runs it; eta
+    from each side's own quadrature (they agree to 1e-13).  This model has
+    group members whose weights agree to between 1e-12 and 1e-9: the
+    complex64 form, whose tie window is 1e-6 (reading R11), is compared with
+    the oracle run with the same window (the oracle with its FP64 window of
+    1e-12 resolves those groups by weight and differs from either by 2e-3)."""
+    if tie is not None:
+        monkeypatch.setattr(iquapi, "TIE_REL", tie)
+    from oracle.bath import eta_coefficients
+    from paper_2506_03127_gb300 import eta_from_bath
+
+    w = W.reaction_coordinate(theta=1e-4)
+    steps = 14
+    p = WidePropagator(w.M, w.dkmax, w.dt, w.q, w.hs_array(), w.theta, precision, max_paths=1 << 20)
+    p.set_eta(eta_from_bath(w.bath, w.dt, w.dkmax))
+    p.set_mask(w.mask)
+    p.set_rho0(w.rho0_array())
+    p.step(steps)
+    rho = p.rho(0, steps + 1)
+    stats = p.stats(1, steps)
+    keys, _ = p.export_paths()
+    p.close()
+    o = iquapi.propagate(w.M, w.q, w.hs_array(), w.dt, eta_coefficients(w.bath, w.dt, w.dkmax), w.dkmax, w.mask,
+                         w.theta, w.rho0_array(), steps)
+    assert np.abs(rho - o.rho).max() <= tol
+    if precision == "fp64":
+        assert [s[3] for s in stats] == [s.kept for s in o.stats]
+        assert set(zip(keys[:, 0].tolist(), keys[:, 1].tolist())) == _wide_keys_of(o.paths.sp, o.paths.sm)
+        assert int(keys[:, 1].max()) > 0
