@@ -55,6 +55,13 @@ struct WState {
 
 struct WRec { long long t, groups, extended, kept, inter; };
 
+// a merge-table slot: group key, largest weight (FP64 bits) and the FP64
+// sum in one 32-byte sector
+struct __align__(32) WSlot {
+    unsigned long long gk, wm;
+    double sre, sim;
+};
+
 struct WParams {
     int M, dkmax, c64, rho_hist;
     long long max_paths, max_groups;
@@ -70,8 +77,8 @@ struct WParams {
     unsigned long long *klo[2], *khi[2];
     void *amps[2];
     unsigned int *slot_of, *groups, *trep;
-    unsigned long long *tkey, *twm, *ttie;
-    double2 *tsum;
+    WSlot *slots;
+    unsigned long long *ttie;
     const double2 *lut;                // [dkmax][dkmax - 1][256] FP64 history tables
     const float2 *lutf, *lutlo;        // FP32 hi part and residual
     const double2 *w;                  // [M*M child][M*M parent newest]
@@ -135,9 +142,9 @@ __global__ void k_w_insert(WParams P) {
         unsigned long long h = wmix(gk) & P.tcap_mask;
         int probe = 0;
         for (; probe < kWProbe; ++probe, h = (h + 1) & P.tcap_mask) {
-            unsigned long long cur = P.tkey[h];
+            unsigned long long cur = P.slots[h].gk;
             if (cur == kWEmpty) {
-                cur = atomicCAS(&P.tkey[h], kWEmpty, gk);
+                cur = atomicCAS(&P.slots[h].gk, kWEmpty, gk);
                 if (cur == kWEmpty) {   // claimed: a new group
                     const unsigned long long g = atomicAdd(&st->n_groups, 1ull);
                     if ((long long)g < P.max_groups) P.groups[g] = (unsigned)h;
@@ -152,9 +159,9 @@ __global__ void k_w_insert(WParams P) {
             return;
         }
         const double2 a = amp_of(P, P.amps[in], i);
-        atomicAdd(&P.tsum[h].x, a.x);
-        atomicAdd(&P.tsum[h].y, a.y);
-        atomicMax(&P.twm[h], (unsigned long long)__double_as_longlong(weight_of(P, P.amps[in], i)));
+        atomicAdd(&P.slots[h].sre, a.x);
+        atomicAdd(&P.slots[h].sim, a.y);
+        atomicMax(&P.slots[h].wm, (unsigned long long)__double_as_longlong(weight_of(P, P.amps[in], i)));
         P.slot_of[i] = (unsigned)h;
     }
 }
@@ -170,7 +177,7 @@ __global__ void k_w_tie(WParams P) {
     for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
          i += (unsigned long long)gridDim.x * blockDim.x) {
         const unsigned h = P.slot_of[i];
-        const double wm = __longlong_as_double((long long)P.twm[h]);
+        const double wm = __longlong_as_double((long long)P.slots[h].wm);
         if (weight_of(P, P.amps[in], i) < (1.0 - P.tie_rel) * wm) continue;
         const unsigned long long tk = pack6(P.klo[in][i], P.khi[in][i], P.co, P.nco);
         if (!REP) atomicMin(&P.ttie[h], tk);
@@ -212,12 +219,14 @@ __global__ void __launch_bounds__(kWThreads) k_w_expand(WParams P, int merge) {
             if (merge) {
                 const unsigned h = P.groups[g];
                 r = P.trep[h];
-                S = P.tsum[h];
+                S = make_double2(P.slots[h].sre, P.slots[h].sim);
                 // the slot is read by this group only: reset it for the next step
-                P.tkey[h] = kWEmpty;
-                P.twm[h] = 0ull;
+                WSlot fresh;
+                fresh.gk = kWEmpty;
+                fresh.wm = 0ull;
+                fresh.sre = fresh.sim = 0.0;
+                P.slots[h] = fresh;
                 P.ttie[h] = kWEmpty;
-                P.tsum[h] = make_double2(0.0, 0.0);
             } else {
                 S = amp_of(P, P.amps[in], r);
             }
@@ -476,21 +485,22 @@ __global__ void k_w_build_w(double2 *w, float4 *wf, const double2 *U, const doub
     }
 }
 
-__global__ void k_w_clear_table(unsigned long long *tkey, unsigned long long *twm, unsigned long long *ttie,
-                                double2 *tsum, unsigned long long n) {
+__global__ void k_w_clear_table(WSlot *slots, unsigned long long *ttie, unsigned long long n) {
     for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
          i += (unsigned long long)gridDim.x * blockDim.x) {
-        tkey[i] = kWEmpty;
-        twm[i] = 0ull;
+        WSlot fresh;
+        fresh.gk = kWEmpty;
+        fresh.wm = 0ull;
+        fresh.sre = fresh.sim = 0.0;
+        slots[i] = fresh;
         ttie[i] = kWEmpty;
-        tsum[i] = make_double2(0.0, 0.0);
     }
 }
 
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct WLayout {
-    size_t klo[2], khi[2], amps[2], slot_of, groups, trep, tkey, twm, ttie, tsum, lut, lutf, lutlo, w, wf, U, eta, q,
+    size_t klo[2], khi[2], amps[2], slot_of, groups, trep, slots, ttie, lut, lutf, lutlo, w, wf, U, eta, q,
         rho_part, rho, stats, state, total;
     unsigned long long tcap;
 };
@@ -534,10 +544,8 @@ WLayout wide_layout(const qp_config *c) {
     L.slot_of = take(mp * 4);
     L.groups = take(mg * 4);
     L.trep = take(tcap * 4);
-    L.tkey = take(tcap * 8);
-    L.twm = take(tcap * 8);
+    L.slots = take(tcap * sizeof(WSlot));
     L.ttie = take(tcap * 8);
-    L.tsum = take(tcap * 16);
     L.lut = take(nlut * 16);
     L.lutf = take(nlut * 8);
     L.lutlo = take(nlut * 8);
@@ -682,10 +690,8 @@ qp_status qp_wide_create(const qp_config *cfg, void *d_workspace, size_t bytes, 
     P.slot_of = reinterpret_cast<unsigned *>(ws + L.slot_of);
     P.groups = reinterpret_cast<unsigned *>(ws + L.groups);
     P.trep = reinterpret_cast<unsigned *>(ws + L.trep);
-    P.tkey = reinterpret_cast<unsigned long long *>(ws + L.tkey);
-    P.twm = reinterpret_cast<unsigned long long *>(ws + L.twm);
+    P.slots = reinterpret_cast<WSlot *>(ws + L.slots);
     P.ttie = reinterpret_cast<unsigned long long *>(ws + L.ttie);
-    P.tsum = reinterpret_cast<double2 *>(ws + L.tsum);
     P.lut = reinterpret_cast<const double2 *>(ws + L.lut);
     P.lutf = reinterpret_cast<const float2 *>(ws + L.lutf);
     P.lutlo = reinterpret_cast<const float2 *>(ws + L.lutlo);
@@ -806,7 +812,7 @@ qp_status qp_wide_set_rho0(qp_wide *w, const double *re, const double *im) {
     QW_CUDA(w, cudaMemcpyAsync(w->P.rho_ring, rho.data(), MM * sizeof(double2), cudaMemcpyHostToDevice, w->stream));
     WRec r0{0, 0, 0, (long long)n, (long long)n};
     QW_CUDA(w, cudaMemcpyAsync(w->P.stats, &r0, sizeof(WRec), cudaMemcpyHostToDevice, w->stream));
-    k_w_clear_table<<<std::max(1, w->nsm) * 4, 256, 0, w->stream>>>(w->P.tkey, w->P.twm, w->P.ttie, w->P.tsum,
+    k_w_clear_table<<<std::max(1, w->nsm) * 4, 256, 0, w->stream>>>(w->P.slots, w->P.ttie,
                                                                     w->L.tcap);
     QW_CUDA(w, cudaGetLastError());
     QW_CUDA(w, cudaStreamSynchronize(w->stream));
