@@ -723,6 +723,8 @@ def main():
     ap.add_argument("--max-paths", type=int, default=1 << 21)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-sweep measurement")
+    ap.add_argument("--block", default=None, choices=["batched", "surrogate", "pre_vs_post", "wide"],
+                    help="run one detail block alone and print its JSON (no contract line)")
     ap.add_argument("--no-more-configs", action="store_true",
                     help="skip the three-level chain and full-memory TLS measurements")
     ap.add_argument("--paper-scale", action="store_true",
@@ -762,6 +764,13 @@ def main():
         print(json.dumps(line))
         return
 
+    if args.block:   # one detail block alone (profiling, quick looks)
+        from paper_2506_03127_gb300 import build
+        build.build()
+        fn = {"batched": run_batched_sweep, "surrogate": run_surrogate, "pre_vs_post": run_pre_vs_post,
+              "wide": run_wide}[args.block]
+        print(json.dumps({args.block: fn()}))
+        return
     if world > 1:
         import torch
         torch.distributed.init_process_group("nccl")
