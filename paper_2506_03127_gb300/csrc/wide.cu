@@ -188,10 +188,12 @@ __global__ void k_w_tie(WParams P) {
 // children of one group, appended in warp-aggregated blocks; thread-uniform
 // loops (every lane of a warp runs every child, valid or not)
 template <bool C64, bool TAB>
-__global__ void __launch_bounds__(kWThreads) k_w_expand(WParams P, int merge) {
-    // TAB: the influence factors exp(-delta H) of the group's distinct
-    // coupling differences, computed once per group (the same arithmetic as
-    // per child), in shared memory [delta][thread]
+__global__ void __launch_bounds__(kWThreads) k_w_expand(WParams P, int merge, int sub_n) {
+    // sub_n consecutive lanes share a group (a power of two dividing 32), lane
+    // s taking its children c = s, s + sub_n, ...; each lane forms the
+    // group's history sum itself.  TAB: the influence factors exp(-delta H)
+    // of the group's distinct coupling differences, computed once per lane
+    // (the same arithmetic as per child), in shared memory [delta][thread]
     using CT = typename std::conditional<C64, float2, double2>::type;
     extern __shared__ __align__(16) unsigned char s_wtab[];
     CT *sE = reinterpret_cast<CT *>(s_wtab);
@@ -208,30 +210,34 @@ __global__ void __launch_bounds__(kWThreads) k_w_expand(WParams P, int merge) {
     const int nb = P.dkmax - 1;                       // history bytes of a key
     const unsigned lane = threadIdx.x & 31u;
     const size_t row = (size_t)(n_act - 1) * nb * 256;
-    for (unsigned long long base = blockIdx.x * (unsigned long long)blockDim.x; base < ng;
+    const int sub = (int)(threadIdx.x & (unsigned)(sub_n - 1));
+    for (unsigned long long base = blockIdx.x * (unsigned long long)blockDim.x; base < ng * sub_n;
          base += (unsigned long long)gridDim.x * blockDim.x) {
-        const unsigned long long g = base + threadIdx.x;
+        const unsigned long long g = (base + threadIdx.x) / (unsigned)sub_n;
         const bool valid = g < ng;
         unsigned long long lo = 0, hi = 0;
         double2 S = make_double2(0.0, 0.0);
+        unsigned h = 0;
         if (valid) {
             unsigned long long r = g;
             if (merge) {
-                const unsigned h = P.groups[g];
+                h = P.groups[g];
                 r = P.trep[h];
                 S = make_double2(P.slots[h].sre, P.slots[h].sim);
-                // the slot is read by this group only: reset it for the next step
-                WSlot fresh;
-                fresh.gk = kWEmpty;
-                fresh.wm = 0ull;
-                fresh.sre = fresh.sim = 0.0;
-                P.slots[h] = fresh;
-                P.ttie[h] = kWEmpty;
             } else {
                 S = amp_of(P, P.amps[in], r);
             }
             lo = P.klo[in][r];
             hi = P.khi[in][r];
+        }
+        __syncwarp();   // every lane of the group has read the slot
+        if (valid && merge && sub == 0) {   // read by this group only: reset it for the next step
+            WSlot fresh;
+            fresh.gk = kWEmpty;
+            fresh.wm = 0ull;
+            fresh.sre = fresh.sim = 0.0;
+            P.slots[h] = fresh;
+            P.ttie[h] = kWEmpty;
         }
         const int par = (int)(lo & 0xffull);
         const int parc = (par & 15) * M + (par >> 4);   // (forward, backward) of the newest point
@@ -344,7 +350,7 @@ __global__ void __launch_bounds__(kWThreads) k_w_expand(WParams P, int merge) {
         // the survivors again (the same arithmetic) and writes them
         unsigned long long kmask = 0ull;
         if (valid)
-            for (int c = 0; c < MM; ++c) {
+            for (int c = sub; c < MM; c += sub_n) {
                 double2 child;
                 if (child_of(c, child)) kmask |= 1ull << c;
             }
@@ -833,6 +839,11 @@ qp_status qp_wide_step(qp_wide *w, int nsteps) {
     if (r != QP_OK) return r;
     unsigned long long t = s.t;
     const int g = w->nblk;
+    const int MMh = w->cfg.M * w->cfg.M;
+    // lanes per group in the expansion: complex64 is latency-bound (shorter
+    // chains per lane pay for the repeated per-group set-up); FP64 is bound
+    // by its pipe (1/64 of FP32), where the repeated set-up would cost more
+    const int sub_n = !w->P.c64 ? 1 : (MMh >= 32 ? 4 : (MMh >= 16 ? 2 : 1));
     for (int k = 0; k < nsteps; ++k, ++t) {
         const int merge = t + 1 >= (unsigned long long)w->cfg.dkmax ? 1 : 0;
         if (merge) {
@@ -843,11 +854,11 @@ qp_status qp_wide_step(qp_wide *w, int nsteps) {
         const bool tab = w->P.ndelta <= kWMaxTabDelta;
         const size_t tsm = tab ? (size_t)w->P.ndelta * kWThreads * (w->P.c64 ? 8 : 16) : 0;
         if (w->P.c64) {
-            if (tab) k_w_expand<true, true><<<g, kWThreads, tsm, w->stream>>>(w->P, merge);
-            else k_w_expand<true, false><<<g, kWThreads, 0, w->stream>>>(w->P, merge);
+            if (tab) k_w_expand<true, true><<<g, kWThreads, tsm, w->stream>>>(w->P, merge, sub_n);
+            else k_w_expand<true, false><<<g, kWThreads, 0, w->stream>>>(w->P, merge, sub_n);
         } else {
-            if (tab) k_w_expand<false, true><<<g, kWThreads, tsm, w->stream>>>(w->P, merge);
-            else k_w_expand<false, false><<<g, kWThreads, 0, w->stream>>>(w->P, merge);
+            if (tab) k_w_expand<false, true><<<g, kWThreads, tsm, w->stream>>>(w->P, merge, sub_n);
+            else k_w_expand<false, false><<<g, kWThreads, 0, w->stream>>>(w->P, merge, sub_n);
         }
         k_w_rho<<<g, kWThreads, 0, w->stream>>>(w->P);
         k_w_finalize<<<1, 64, 0, w->stream>>>(w->P, g, merge);
