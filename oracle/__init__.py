@@ -26,8 +26,14 @@ closed forms or brute force; the filter (its rule |amp| >= theta and its
 place before rho) by the filtered Markov map at memory length 1 and a
 hand-made set; the pre-merge of keys wider than 64 bits (premerge_rows, no
 packing) by equality with the packed pre-merge wherever both apply, ties at
-the group maxima included.  The masked pre-merge together with a nonzero bath has no
-value the paper prints ("parity unpinned" for that combination; it is
-pinned only by invariants: exactness at zero coupling, trace conservation
-without a filter, reduction to the unmasked result for the full mask).
+the group maxima included.  The masked merge together with a nonzero bath is
+pinned exactly where the mathematics fixes its result: on a prefix mask
+with eta vanishing from the lag where the dropped positions would first
+meet a new point, both orders equal unmasked QUAPI at that shorter memory
+(brute force), and the pre-merge is no longer exact one lag further while
+the merge after extension is, which pins the shift of P'.  Where the merge
+is an approximation (eta beyond that lag) the paper prints no value
+("parity unpinned" for that combination; pinned there only by invariants:
+exactness at zero coupling, trace conservation without a filter, reduction
+to the unmasked result for the full mask).
 """

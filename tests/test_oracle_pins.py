@@ -185,6 +185,87 @@ def _structured_case(M=2, dkmax=8):
     return q, hs, eta, rho0
 
 
+PREFIX_CASES = [   # (M, dkmax, k, extra mask positions): mask = {0 .. k-1} + extras, eta_d = 0 for d >= k
+    (2, 8, 3, (5,)), (2, 8, 4, (6, 7)), (2, 7, 2, (4,)), (3, 6, 3, (5,)), (3, 5, 2, (3,)), (5, 4, 2, (3,)),
+]
+
+
+def prefix_case(M, dkmax, k, extras, cut, seed=None):
+    """A random problem whose influence coefficients vanish from lag `cut`
+    on, with the mask {0 .. k-1} plus the given older positions."""
+    c = W.random_case(30 + dkmax + k if seed is None else seed, M, dkmax)
+    eta = np.array(c["eta"], dtype=complex)
+    eta[cut:] = 0.0
+    return dict(c, eta=eta, mask=tuple(range(k)) + tuple(extras))
+
+
+def prefix_cut(scheme, k):
+    """Largest memory at which merging on the prefix mask {0 .. k-1} is exact.
+    The pre-merge groups the parents on P' (Sec. 3.1), which drops parent
+    position k - 1 before the children are formed, and that position meets
+    the new point at lag k; the merge after extension (Sec. 2.1) groups the
+    children on P, which drops child position k, first met at lag k + 1."""
+    return k if scheme == "pre" else k + 1
+
+
+@pytest.mark.parametrize("scheme", ["pre", "post"])
+@pytest.mark.parametrize("M,dkmax,k,extras", PREFIX_CASES)
+def test_masked_merge_exact_when_eta_ends_within_the_prefix(M, dkmax, k, extras, scheme):
+    """Masked propagation with a nonzero bath, where the merge is exact: the
+    positions a merge drops enter later influence factors (Eq. inf_fun)
+    only through lags at or beyond the cut (prefix_cut), where eta vanishes,
+    so summing a group's members loses nothing and the masked run on a
+    window of dkmax points equals QUAPI with memory `cut` (Eq.
+    quapi_red_rho), given by brute-force enumeration.  Groups have many
+    members here (M^2 per dropped position), unlike the zero-coupling and
+    pure-dephasing pins."""
+    cut = prefix_cut(scheme, k)
+    c = prefix_case(M, dkmax, k, extras, cut)
+    n_brute = {2: 6, 3: 4, 5: 3}[M]
+    steps = {2: 14, 3: 10, 5: 6}[M]
+    r = iquapi.propagate(M, c["q"], c["hs"], c["dt"], c["eta"], dkmax, c["mask"], 0.0, c["rho0"], steps,
+                         scheme=scheme)
+    rb = brute.rho_by_enumeration(M, c["q"], c["hs"], c["dt"], c["eta"][:cut], cut, c["rho0"], n_brute)
+    np.testing.assert_allclose(r.rho[n_brute], rb, rtol=0, atol=2e-14)
+    short = iquapi.propagate(M, c["q"], c["hs"], c["dt"], c["eta"][:cut], cut, None, 0.0, c["rho0"], steps)
+    np.testing.assert_allclose(r.rho, short.rho, rtol=0, atol=1e-14)
+    # groups really merged members: fewer than the stored paths they came from
+    if scheme == "pre":
+        assert r.stats[-1].groups * M <= r.stats[-2].kept
+    else:
+        assert r.stats[-1].merged * M <= r.stats[-1].kept
+
+
+@pytest.mark.parametrize("M,dkmax,k,extras", PREFIX_CASES)
+def test_premerge_is_not_exact_one_lag_further(M, dkmax, k, extras):
+    """The pre-merge on P' (the shifted mask) drops parent position k - 1,
+    which meets the new point at lag k: with eta_k nonzero the masked run
+    is an approximation of QUAPI with memory k + 1, while the merge after
+    extension on P is still exact there.  A pre-merge on P itself (no
+    shift) would be exact here as well."""
+    c = prefix_case(M, dkmax, k, extras, k + 1)
+    steps = {2: 14, 3: 10, 5: 6}[M]
+    short = iquapi.propagate(M, c["q"], c["hs"], c["dt"], c["eta"][:k + 1], k + 1, None, 0.0, c["rho0"], steps)
+    pre = iquapi.propagate(M, c["q"], c["hs"], c["dt"], c["eta"], dkmax, c["mask"], 0.0, c["rho0"], steps)
+    post = iquapi.propagate(M, c["q"], c["hs"], c["dt"], c["eta"], dkmax, c["mask"], 0.0, c["rho0"], steps,
+                            scheme="post")
+    assert np.abs(pre.rho - short.rho).max() > 1e-6
+    assert np.abs(post.rho - short.rho).max() <= 1e-14
+
+
+def _prefix_pins_pass(mod, scheme):
+    """The two prefix-mask facts above on one case (mutation harnesses)."""
+    M, dkmax, k, extras = 2, 7, 2, (4,)
+    for cut in (k, k + 1):
+        c = prefix_case(M, dkmax, k, extras, cut)
+        r = mod.propagate(M, c["q"], c["hs"], c["dt"], c["eta"], dkmax, c["mask"], 0.0, c["rho0"], 10, scheme=scheme)
+        short = iquapi.propagate(M, c["q"], c["hs"], c["dt"], c["eta"][:cut], cut, None, 0.0, c["rho0"], 10)
+        exact = np.abs(r.rho - short.rho).max() <= 1e-14
+        if exact != (cut <= prefix_cut(scheme, k)):
+            return False
+    return True
+
+
 @pytest.mark.parametrize("M,mask", [(2, (0, 1, 2, 5)), (2, (0, 1, 4, 6)), (3, (0, 1, 3))])
 def test_trace_conserved_by_masked_merge(M, mask):
     q, hs, eta, rho0 = _structured_case(M, 8 if M == 2 else 5)
@@ -461,6 +542,8 @@ MUTATIONS = {
     "new point enters the history sum": ("for d in range(1, n_act):", "for d in range(0, n_act):"),
     "theta not squared in the filter": ("keep = w2 >= th2", "keep = w2 >= theta"),
     "rho summed before the filter": ("rho[a, b] = child[keep].sum()", "rho[a, b] = child.sum()"),
+    "pre-merge on P without the shift": ("return sorted(set([p - 1 for p in P if p >= 1] + [0]))",
+                                         "return sorted(set(P))"),
 }
 
 
@@ -500,7 +583,7 @@ def _pins_pass(mod):
                                  theta, 2)
             if not np.array_equal(np.diag(rho), [amps[0] if 0 in kept else 0, amps[3] if 3 in kept else 0]):
                 return False
-        return True
+        return _prefix_pins_pass(mod, "pre")
     except Exception:
         return False
 
@@ -521,6 +604,8 @@ POST_MUTATIONS = {
     "post: merged on one position too few": ("out, near_tie = merge_on(unmerged, sorted(P), M)",
                                              "out, near_tie = merge_on(unmerged, sorted(P)[:-1], M)"),
     "post: never merged": ("if L_child == dkmax and unmerged.amp.size:", "if False:"),
+    "post: merged on P' instead of P": ("out, near_tie = merge_on(unmerged, sorted(P), M)",
+                                        "out, near_tie = merge_on(unmerged, premerge_positions(P, dkmax), M)"),
     "post: backward branch not conjugated": ("prop = U[a, paths.sp[:, 0]] * np.conj(U[b, paths.sm[:, 0]])",
                                              "prop = U[a, paths.sp[:, 0]] * U[b, paths.sm[:, 0]]"),
     "post: rho summed before the filter": ("            rho[a, b] = child[keep].sum()\n            k = int(np.count_nonzero(keep))\n            new_sp.append(np.hstack([np.full",
@@ -545,7 +630,7 @@ def _post_pins_pass(mod):
                                      rho0, c["steps"])
         r = mod.propagate(2, c["q"], hs, c["dt"], np.array([c["e0"]]), 1, None, c["theta"], rho0, c["steps"],
                           scheme="post")
-        return np.abs(r.rho - want).max() <= 1e-14
+        return np.abs(r.rho - want).max() <= 1e-14 and _prefix_pins_pass(mod, "post")
     except Exception:
         return False
 
