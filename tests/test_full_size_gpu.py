@@ -1,0 +1,108 @@
+"""GPU: the benchmark's full sizes, in the launch configuration the bench
+times (autotuned), checked by results fixed at any size.
+
+* The full-memory TLS model at Delta k_max = 14 (4^14 = 2^28 stored paths,
+  the regular streaming kernel) with the system Hamiltonian switched off:
+  pure dephasing, whose rho(t) is closed-form in the influence coefficients
+  at every step (the factors of Eq. inf_fun collapse to the triangle sum
+  of eta along the constant path), while the stored set still grows to
+  2^28 paths and is merged every step once the window is full.
+* The three-level chain (Delta k_max = 12, mask {0 .. 8}, theta = 1e-10)
+  through the bench's timed steps (after its autotuner), ~1.7e7 stored
+  paths: the stream engine's tile
+  kernel and the merge-table engine compute the same step (FP64: rho within
+  1e-10, equal survivor counts), and the complex64 form stays within its
+  stated bound of the FP64 result.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import bath
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU container
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_2506_03127_gb300 import Propagator, build  # noqa: E402
+
+build.build()
+
+
+def pure_dephasing_rho(rho0, q, eta, dkmax, n):
+    """rho_ab(n) for H_S = 0: the only path with nonzero weight stays at
+    (a, b); its influence exponent is -(q_a - q_b)(q_a Q - q_b Q*) with
+    Q = n eta_0 + sum_{d=1}^{min(n, dkmax)-1} (n - d) eta_d (lags beyond
+    the memory cut)."""
+    Q = n * eta[0] + sum((n - d) * eta[d] for d in range(1, min(n, dkmax)))
+    return rho0 * np.exp(-(q[:, None] - q[None, :]) * (q[:, None] * Q - q[None, :] * np.conj(Q)))
+
+
+@pytest.mark.parametrize("precision,tol", [("c64", 2e-6), ("fp64", 1e-12)])
+def test_full_memory_tls_dk14_pure_dephasing_at_full_size(precision, tol):
+    w = W.TLS_OHMIC_FULL_DK14
+    q = np.asarray(w.q, dtype=float)
+    eta = bath.eta_coefficients(w.bath, w.dt, w.dkmax)
+    rho0 = np.array([[0.6, 0.3 - 0.2j], [0.3 + 0.2j, 0.4]])
+    p = Propagator(w.M, w.dkmax, w.dt, w.q, np.zeros((2, 2)), 0.0, precision, "stream", max_paths=1 << 28)
+    p.set_eta(eta)
+    p.set_mask(None)
+    p.set_rho0(rho0)
+    p.step(w.dkmax)
+    p.sync()
+    p.autotune(trial_steps=2, use_cache=True)
+    p.step(3)
+    p.sync()
+    T, n = p.current()
+    assert T >= w.dkmax + 3 and n == 4 ** w.dkmax
+    rho = p.rho(0, T + 1)
+    kept = [s[3] for s in p.stats(1, T)]
+    p.close()
+    assert kept == [4 ** min(t + 1, w.dkmax) for t in range(1, T + 1)]
+    err = max(np.abs(rho[t] - pure_dephasing_rho(rho0, q, eta, w.dkmax, t)).max() for t in range(T + 1))
+    assert err <= tol, err
+
+
+def _chain_start(precision, engine, tune):
+    """The chain propagated to t = 40 (the bench's start), then autotuned as
+    the bench does (the autotuner advances the propagation)."""
+    w = W.CHAIN3_STRUCTURED_DK12
+    p = Propagator(w.M, w.dkmax, w.dt, w.q, w.hs_array(), w.theta, precision, engine, max_paths=1 << 26)
+    p.set_eta(bath.eta_coefficients(w.bath, w.dt, w.dkmax))
+    p.set_mask(w.mask)
+    p.set_rho0(w.rho0_array())
+    p.step(40)
+    p.sync()
+    if tune:
+        p.autotune(trial_steps=8, use_cache=True)
+    return p
+
+
+def _chain_finish(p, T):
+    t, _ = p.current()
+    assert t <= T
+    p.step(T - t)
+    p.sync()
+    assert p.current()[0] == T
+    st = p.stats(1, T)
+    out = p.rho(0, T + 1), [s[3] for s in st], [s[1] for s in st]
+    p.close()
+    return out
+
+
+def test_chain3_dk12_full_size_engines_and_precisions_agree():
+    ps = _chain_start("fp64", "stream", True)
+    T = ps.current()[0] + 53     # the bench's 3 warm-up and 50 timed steps after the autotuner
+    rho_s, kept_s, groups_s = _chain_finish(ps, T)
+    rho_h, kept_h, groups_h = _chain_finish(_chain_start("fp64", "hash", False), T)
+    rho_c, kept_c, _ = _chain_finish(_chain_start("c64", "auto", True), T)
+    assert kept_s[-1] > 10 ** 7                       # full size: ~1.7e7 stored paths
+    assert np.abs(rho_s - rho_h).max() <= 1e-10
+    assert kept_s == kept_h and groups_s == groups_h
+    assert np.abs(rho_c - rho_s).max() <= 5e-6
+    assert all(abs(a - b) <= max(2, b // 1000) for a, b in zip(kept_c, kept_s))
+    tr = np.trace(rho_s, axis1=1, axis2=2)
+    assert np.abs(tr - 1).max() < 1e-3                # changed only by the filter at 1e-10
+    assert max(groups_s) <= 9 ** 8                    # P' = {0 .. 7}: at most M^(2 |P'|) groups
