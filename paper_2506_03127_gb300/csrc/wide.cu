@@ -16,10 +16,12 @@
 //   k_w_tie     members within the tie window of the largest weight compete
 //               on a 64-bit tie key (the positions outside P', in key order);
 //   (k_w_tie<true>: the winner becomes the group's representative)
-//   k_w_expand  one thread per group: the history part H of the influence
-//               exponent from per-position tables, then the M^2 children
-//               (Eqs. SysP, inf_fun) one at a time, filtered (|amp| >= theta,
-//               Sec. 2.1) and appended (warp-aggregated);
+//   k_w_expand  the M^2 children of each group (Eqs. SysP, inf_fun), one at
+//               a time: one lane per group, or sub_n lanes sharing a group,
+//               each forming every sub_n-th child; the history part H of the
+//               influence exponent from per-position tables; filtered
+//               (|amp| >= theta, Sec. 2.1) and appended in output ranges
+//               reserved once per block and round;
 //   k_w_rho     rho(t) from the appended children by newest point (Eq.
 //               quapi_red_rho), per-block sums;
 //   k_w_finalize the step's rho, counts and state.
