@@ -474,11 +474,11 @@ def run_wide(steps=30, tail=10):
 
 def run_surrogate(T_train=100, T_long=1000, L=32, epochs=2000):
     """The learned surrogate: train (libqp kernels) on 100-step trajectories of
-    48 sweep instances, roll 16 held-out instances out to t = 1000 and judge
+    48 sweep instances, roll 16 held-out instances out to t = 1000 and check
     them against the plain path at checkpoints; times of both."""
     import torch
     from paper_2506_03127_gb300 import batch_from_workloads
-    from paper_2506_03127_gb300.surrogate import Surrogate, bath_features, judge, truncated_memory_baselines
+    from paper_2506_03127_gb300.surrogate import Surrogate, bath_features, checkpoint_errors, truncated_memory_baselines
 
     ws = W.resonance_sweep(64)
     p = batch_from_workloads(ws, precision="c64", max_paths=1 << 23)
@@ -502,7 +502,7 @@ def run_surrogate(T_train=100, T_long=1000, L=32, epochs=2000):
     t0 = time.perf_counter()
     rs = s.rollout(rp[:L].transpose(1, 0, 2, 3), par[48:], T_long)
     t_sur = time.perf_counter() - t0
-    errs, raw, fb = judge(rs, rp, (200, 400, 600, 800, 999))
+    errs, raw, fb = checkpoint_errors(rs, rp, (200, 400, 600, 800, 999))
     # the path update's own cheaper settings on the same instances: shorter
     # memory (1 = the Markov map) at the same filter, against the full path
     base = truncated_memory_baselines(ws[48:], T_long, rp, (200, 400, 600, 800, 999))

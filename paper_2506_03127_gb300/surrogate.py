@@ -4,7 +4,7 @@ Every computation (window assembly, forward and backward passes, Adam,
 rollout) runs in libqp; this module holds device buffers (PyTorch tensors),
 loops and bookkeeping only.  The paper has no counterpart: the surrogate
 extends the propagation of the path update in time, and the path update is
-its judge at checkpoints and its fallback.
+its check at checkpoints and its fallback.
 
 Features of one prediction: the last L values of rho(t) (8 reals each: Re,
 Im of rho_00, rho_01, rho_10, rho_11) and the instance's bath parameters
@@ -139,8 +139,8 @@ class Surrogate:
         return (out[..., 0::2] + 1j * out[..., 1::2]).reshape(n, T_total, 2, 2)
 
 
-def judge(rho_sur, rho_plain, checkpoints, trace_tol=0.05, eig_tol=0.02):
-    """Judge the surrogate at checkpoints against the plain path.  An instance
+def checkpoint_errors(rho_sur, rho_plain, checkpoints, trace_tol=0.05, eig_tol=0.02):
+    """Check the surrogate at checkpoints against the plain path.  An instance
     falls back to the plain path (its result is the plain one) when at any
     checkpoint its trace deviates from the plain trace by more than
     trace_tol or rho has an eigenvalue below -eig_tol.  Returns (errors of

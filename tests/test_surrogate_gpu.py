@@ -4,7 +4,7 @@ Trained by libqp's own kernels on 100-step trajectories of 48 instances of
 the resonance sweep (computed by the batched path update), it rolls 16
 held-out instances out from their first 32 steps to t = 1000 (10x the
 training length).  The plain path update propagates the same instances to
-t = 1000 and judges the surrogate at the checkpoints 200, 400, ..., 1000.
+t = 1000 and checks the surrogate at the checkpoints 200, 400, ..., 1000.
 The test asserts the surrogate is faster than the plain path over the same
 steps, stays within the stated error, and keeps rho a density matrix
 (Hermitian and positive semidefinite by projection), so that no instance
@@ -29,7 +29,7 @@ if not torch.cuda.is_available():  # pragma: no cover - CPU container
 from paper_2506_03127_gb300 import batch_from_workloads, build  # noqa: E402
 
 build.build()
-from paper_2506_03127_gb300.surrogate import Surrogate, bath_features, judge, truncated_memory_baselines  # noqa: E402
+from paper_2506_03127_gb300.surrogate import Surrogate, bath_features, checkpoint_errors, truncated_memory_baselines  # noqa: E402
 
 T_TRAIN, T_LONG, L = 100, 1000, 32
 CHECKPOINTS = (200, 400, 600, 800, 999)
@@ -56,7 +56,7 @@ def test_surrogate_gain_and_error_at_checkpoints():
     t0 = time.perf_counter()
     rs = s.rollout(rp[:L].transpose(1, 0, 2, 3), par[48:], T_LONG)
     t_sur = time.perf_counter() - t0
-    combined, raw, fallback = judge(rs, rp, CHECKPOINTS)
+    combined, raw, fallback = checkpoint_errors(rs, rp, CHECKPOINTS)
     # instances that fall back cost the plain path's time on top
     t_eff = t_sur + fallback.mean() * t_plain
     assert t_eff < t_plain / 2, (t_sur, t_plain, fallback.sum())
