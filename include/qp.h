@@ -423,7 +423,7 @@ qp_status qp_step_noalloc(const qp_config *cfg, const double *eta_re, const doub
 /* Learned surrogate of rho(t).  The paper has no counterpart: a small MLP
  * over the last L steps of rho(t) and the bath parameters, trained on
  * trajectories of the path update above, extends propagation in time; the
- * path update judges it at checkpoints and is its fallback.
+ * path update checks it at checkpoints and is its fallback.
  *
  * Network: x (d_in) -> tanh(x W1 + b1) (width) -> tanh(. W2 + b2) (width)
  * -> . W3 + b3 (d_out); loss = mean squared error.  Parameters are FP32;

@@ -128,3 +128,64 @@ def test_library_Q_at_half_steps_matches_oracle(w):
     ql = abi.qp_Q_from_bath(w.bath, 0.5 * w.dt, n)
     qo = np.concatenate([[0.0], B.Q_of_t(w.bath, 0.5 * w.dt * np.arange(1, n))])
     np.testing.assert_allclose(ql, qo, rtol=0, atol=1e-13)
+
+
+def _wcfg(**kw):
+    M = kw.pop("M", 8)
+    args = dict(M=M, dkmax=12, dt=0.06, q=np.arange(M, dtype=float), hs=np.eye(M), theta=1e-9, max_paths=1 << 16)
+    args.update(kw)
+    return abi.make_config(**args)
+
+
+def test_wide_workspace_size_follows_capacity_and_precision():
+    """Wide keys: the workspace grows with max_paths; complex64 amplitudes
+    save 8 bytes per entry in each of the two ping-pong amplitude buffers;
+    per path at least the two buffers of a 16-byte key and an FP64
+    amplitude plus a merge table of 32-byte slots for twice the groups."""
+    (a, ka), (b, kb), (c, kc) = _wcfg(max_paths=1 << 12), _wcfg(), _wcfg(precision=abi.QP_C64)
+    sa, sb, sc = abi.qp_wide_workspace_size(a), abi.qp_wide_workspace_size(b), abi.qp_wide_workspace_size(c)
+    assert 0 < sa < sb
+    assert sb - sc == 2 * 8 * (1 << 16)
+    big, kbig = _wcfg(max_paths=1 << 20)
+    assert abi.qp_wide_workspace_size(big) >= (2 * (16 + 16) + 2 * 32) * (1 << 20)
+
+
+@pytest.mark.parametrize("bad", [dict(M=1, q=[0.0], hs=np.eye(1)), dict(M=9, q=np.arange(9.0), hs=np.eye(9)),
+                                 dict(dkmax=0), dict(dkmax=17), dict(dt=0.0), dict(theta=-1.0), dict(precision=5),
+                                 dict(max_paths=8), dict(n_inst=2), dict(scheme=abi.QP_POSTMERGE)],
+                         ids=lambda d: ",".join(d))
+def test_wide_config_checks(bad):
+    cfg, keep = _wcfg(**bad)
+    n = ctypes.c_size_t()
+    assert abi.lib.qp_wide_workspace_size(ctypes.byref(cfg), ctypes.byref(n)) == abi.QP_ERR_ARG
+
+
+def test_wide_create_rejects_small_or_missing_workspace():
+    """Refused before any device call: a workspace one byte short
+    (QP_ERR_OOM) or none (QP_ERR_ARG); no context is returned."""
+    cfg, keep = _wcfg()
+    need = abi.qp_wide_workspace_size(cfg)
+    h = ctypes.c_void_p()
+    assert abi.lib.qp_wide_create(ctypes.byref(cfg), ctypes.c_void_p(256 * 1000), need - 1, None,
+                                  ctypes.byref(h)) == abi.QP_ERR_OOM
+    assert abi.lib.qp_wide_create(ctypes.byref(cfg), None, need, None, ctypes.byref(h)) == abi.QP_ERR_ARG
+    assert h.value is None
+
+
+def test_mlp_workspace_size_and_checks():
+    """The surrogate's workspace grows with the batch and holds at least the
+    FP32 parameters, their gradient and the two Adam moments; dimensions
+    out of range, a short or misaligned workspace are refused before any
+    device call."""
+    s1, s2 = abi.qp_mlp_workspace_size(258, 256, 8, 64), abi.qp_mlp_workspace_size(258, 256, 8, 4096)
+    npar = 258 * 256 + 256 + 256 * 256 + 256 + 256 * 8 + 8
+    assert 4 * 4 * npar <= s1 < s2
+    n = ctypes.c_size_t()
+    for bad in [(0, 256, 8, 64), (258, 0, 8, 64), (258, 256, 0, 64), (258, 256, 8, 0), (5000, 256, 8, 64),
+                (258, 256, 8, (1 << 20) + 1)]:
+        assert abi.lib.qp_mlp_workspace_size(*bad, ctypes.byref(n)) == abi.QP_ERR_ARG
+    h = ctypes.c_void_p()
+    assert abi.lib.qp_mlp_create(258, 256, 8, 64, ctypes.c_void_p(256 * 1000), s1 - 1, None,
+                                 ctypes.byref(h)) == abi.QP_ERR_OOM
+    assert abi.lib.qp_mlp_create(258, 256, 8, 64, ctypes.c_void_p(256 * 1000 + 8), s1, None,
+                                 ctypes.byref(h)) == abi.QP_ERR_ARG
