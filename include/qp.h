@@ -93,9 +93,14 @@ typedef struct {
     int precision;         /* QP_FP64 or QP_C64                                     */
     int engine;            /* QP_ENGINE_*                                            */
     double theta;          /* filter threshold on |amplitude| (0 = keep all)        */
-    int64_t max_paths;     /* capacity of each stored-path buffer, entries          */
-    int64_t max_groups;    /* capacity of the merge table, groups (0 = max_paths)   */
-    int rho_history;       /* rho(t) slots kept on the device, ring (0 = 4096)      */
+    int64_t max_paths;     /* capacity of each stored-path buffer, entries,
+                              1 .. 2^40 (post-merging: below 2^32)           */
+    int64_t max_groups;    /* capacity of the merge table, groups (0 = max_paths),
+                              at most 2^30: with max_paths > 2^30 it must be
+                              set unless engine is QP_ENGINE_STREAM (which has
+                              no merge table)                                */
+    int rho_history;       /* rho(t) slots kept on the device, ring (0 = 4096),
+                              at most 2^24                                   */
     int n_inst;            /* independent instances propagated together (0 or 1 =
                               one problem; at most 128).  All instances share M,
                               q, H_S, dt, dkmax, mask and theta; each has its own
@@ -179,7 +184,9 @@ int qp_version(void);
 const char *qp_status_string(qp_status s);
 
 /* Device bytes the caller must provide to qp_create for this configuration.
- * Validates cfg (QP_ERR_ARG on an invalid one).  Host only, no GPU needed.  */
+ * Validates cfg against the limits stated on the fields of qp_config
+ * (QP_ERR_ARG on an invalid one; no context exists yet to hold the reason).
+ * Host only, no GPU needed.                                                 */
 qp_status qp_workspace_size(const qp_config *cfg, size_t *bytes);
 
 /* Create a context on the current CUDA device.  d_workspace: device pointer,

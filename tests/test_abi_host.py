@@ -189,3 +189,24 @@ def test_mlp_workspace_size_and_checks():
                                  ctypes.byref(h)) == abi.QP_ERR_OOM
     assert abi.lib.qp_mlp_create(258, 256, 8, 64, ctypes.c_void_p(256 * 1000 + 8), s1, None,
                                  ctypes.byref(h)) == abi.QP_ERR_ARG
+
+
+def test_capacity_limits_as_documented():
+    """max_paths up to 2^40; beyond 2^30 paths the merge table needs an
+    explicit max_groups (at most 2^30) unless the stream engine, which has
+    none, is asked for; the post-merging order keeps max_paths below 2^32."""
+    def size(**kw):
+        cfg, keep = _cfg(**kw)
+        n = ctypes.c_size_t()
+        st = abi.lib.qp_workspace_size(ctypes.byref(cfg), ctypes.byref(n))
+        return st, n.value
+
+    assert size(max_paths=1 << 32, engine=abi.QP_ENGINE_AUTO)[0] == abi.QP_ERR_ARG
+    assert size(max_paths=1 << 32, engine=abi.QP_ENGINE_HASH, max_groups=1 << 28)[0] == abi.QP_OK
+    assert size(max_paths=1 << 32, engine=abi.QP_ENGINE_HASH, max_groups=(1 << 30) + 1)[0] == abi.QP_ERR_ARG
+    st, n = size(max_paths=1 << 40, engine=abi.QP_ENGINE_STREAM, precision=abi.QP_C64)
+    assert st == abi.QP_OK and n >= 2 * (8 + 8) * (1 << 40)       # 64-bit sizes, no overflow
+    assert size(max_paths=(1 << 40) + 1, engine=abi.QP_ENGINE_STREAM)[0] == abi.QP_ERR_ARG
+    assert size(max_paths=1 << 32, scheme=abi.QP_POSTMERGE)[0] == abi.QP_ERR_ARG
+    assert size(max_paths=(1 << 32) - 1, scheme=abi.QP_POSTMERGE, max_groups=1 << 20)[0] == abi.QP_OK
+    assert size(rho_history=(1 << 24) + 1)[0] == abi.QP_ERR_ARG
