@@ -198,7 +198,8 @@ qp_status qp_create(const qp_config *cfg, void *d_workspace, size_t bytes,
                     void *cuda_stream, qp_ctx **out);
 
 /* Release the host side of the context (the workspace stays the caller's).
- * Safe on NULL.                                                              */
+ * Does not wait for work already queued on the context's stream: synchronise
+ * that stream before the workspace is freed or reused.  Safe on NULL.       */
 void qp_destroy(qp_ctx *ctx);
 
 /* Influence coefficients eta_0 .. eta_{n-1} from a spectral density (paper
@@ -444,6 +445,8 @@ typedef struct qp_mlp qp_mlp;
 qp_status qp_mlp_workspace_size(int d_in, int width, int d_out, int max_batch, size_t *bytes);
 qp_status qp_mlp_create(int d_in, int width, int d_out, int max_batch, void *d_workspace, size_t bytes,
                         void *cuda_stream, qp_mlp **out);
+/* Release the host side (as qp_destroy: synchronise the stream before the
+ * workspace is freed or reused).                                           */
 void qp_mlp_destroy(qp_mlp *m);
 qp_status qp_mlp_num_params(const qp_mlp *m, int64_t *n);
 /* Host FP32 parameters in (resets the Adam moments and step count) / out. */
@@ -524,6 +527,8 @@ qp_status qp_wide_workspace_size(const qp_config *cfg, size_t *bytes);
 /* d_workspace: device memory of at least qp_wide_workspace_size bytes,
  * owned by the caller and alive until qp_wide_destroy; q and hs are copied. */
 qp_status qp_wide_create(const qp_config *cfg, void *d_workspace, size_t bytes, void *cuda_stream, qp_wide **out);
+/* Release the host side (as qp_destroy: synchronise the stream before the
+ * workspace is freed or reused).                                           */
 void qp_wide_destroy(qp_wide *w);
 qp_status qp_wide_set_eta(qp_wide *w, const double *eta_re, const double *eta_im, int n);
 /* Default: the full mask, refused at qp_wide_set_rho0 when its P' holds more

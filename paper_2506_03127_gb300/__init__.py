@@ -135,6 +135,9 @@ class Propagator:
 
     def close(self):
         if getattr(self, "ctx", None):
+            # work still queued on the context's stream uses the workspace,
+            # which PyTorch may hand out again once this object is gone
+            self.stream.synchronize()
             _abi().qp_destroy(self.ctx)
             self.ctx = None
 
@@ -214,6 +217,7 @@ class WidePropagator:
 
     def close(self):
         if getattr(self, "ctx", None):
+            self.stream.synchronize()   # queued work still uses the workspace
             _abi().lib.qp_wide_destroy(self.ctx)
             self.ctx = None
 

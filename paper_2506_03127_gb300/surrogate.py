@@ -69,6 +69,7 @@ class MLP:
 
     def close(self):
         if getattr(self, "h", None):
+            self.stream.synchronize()   # queued work still uses the workspace
             abi.lib.qp_mlp_destroy(self.h)
             self.h = None
 
