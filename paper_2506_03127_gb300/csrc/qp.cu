@@ -1,10 +1,22 @@
 // libqp: GB300 (sm_103a) kernels and C ABI of the MACGIC-iQUAPI path update.
 //
 // One propagation step Omega(t-1) -> Omega(t) (paper Sec. 3.1, routines
-// premerging() and propagation()) runs as a short, fixed sequence of kernels
-// on the context's stream.  Every kernel reads the step index and the path
-// counts from a small device-resident state block, so the host never waits
-// on a count and one captured CUDA graph replays any step:
+// premerging() and propagation()).  Three engines compute it:
+//   stream engine (the default where the mask allows it): the stored set
+//     kept sorted in M^2 regions by newest point, so that every pre-merge
+//     group is a run; k_stream_step (tiles, segmented group sums, survivors
+//     compacted in order by a decoupled look-back), k_stream_regular (the
+//     unfiltered full-memory step as a streaming map) and k_stream_batch
+//     (independent instances in n_inst * M^2 regions);
+//   merge-table engine (any mask, the symmetric splitting, sharded steps):
+//     the kernels listed below;
+//   post-merging engine (the order of Sec. 2.1): k_post_*, a device radix
+//     sort (k_rs_*) and a reduction by key (k_rbk_*).
+// Also here: the partition of a stored set by owner rank (k_part_*), the
+// allocation-free step (qp_step_noalloc) and the C ABI.  Every kernel reads
+// the step index and the path counts from a small device-resident state
+// block, so the host never waits on a count and one captured CUDA graph
+// replays any step.  The merge-table engine's sequence:
 //
 //   k_insert    pre-merge pass 1 (window full only): each stored path
 //               inserts its masked key into the merge table (open
@@ -12,8 +24,9 @@
 //               group sum (FP64 atomics) and raises the group's maximum
 //               |amp|^2 (atomicMax on the FP64 bit pattern; non-negative
 //               doubles order like uint64).
-//   k_tiebreak  pre-merge pass 2: paths whose |amp|^2 is within a relative
-//               1e-12 of the group maximum compete for the representative
+//   k_tiebreak  pre-merge pass 2: paths whose |amp|^2 is within the tie
+//               window of the group maximum (1e-12 relative in FP64, 1e-6
+//               in complex64) compete for the representative
 //               with atomicMin on the packed key (deterministic choice
 //               among equal weights).
 //   k_expand    per group (or per stored path while the window fills): the
