@@ -16,6 +16,20 @@
 //   weights   dW = x^T dh : A = x^T (in x batch), B = dh^T (out x batch)
 // so each activation is also written transposed (batch contiguous) by the
 // kernel that produces it.
+//
+// Rollout (qp_surrogate_rollout): for up to 32 instances all steps run in
+// one launch of a two-block cluster (k_rollout_fused: block 0 keeps W1^T and
+// the last L steps of rho in shared memory and runs the feature packing,
+// layer 1 and the update; block 1 keeps W2^T and W3^T and runs layers 2 and
+// 3; activations cross through distributed shared memory); larger batches
+// replay CUDA graphs of the per-step kernels.  Both round at the same points
+// and add the k-steps in the same order.
+//
+// Tensor-core form: warp-level mma.sync fragments.  These GEMMs are small
+// (at most a few thousand rows by 258 x 256 in training, 16 rows per
+// rollout step); tcgen05.mma issues 64- or 128-row tiles through tensor
+// memory, which a 16-row step would fill to a quarter while adding a
+// tensor-memory round trip to a step whose cost is latency.
 #include <cooperative_groups.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
