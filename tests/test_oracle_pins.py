@@ -527,6 +527,41 @@ def test_symmetric_splitting_pure_dephasing_exact(mask):
     assert bath.beta == beta
 
 
+
+def _splitting_order_ratios(bath, t_end, mod=iquapi, Ns=(2, 4, 8)):
+    """rho(t_end) with the full memory (no truncation) at dt = t_end/N for
+    N = 2, 4, 8, in the right-box reading and with the symmetric splitting;
+    the ratio of successive differences, |rho_2 - rho_4| / |rho_4 - rho_8|,
+    is 2^p for a method of order p in dt."""
+    hs = np.array([[0, 0.5], [0.5, 0]], dtype=complex)
+    q = np.array([1.0, -1.0])
+    rho0 = np.array([[1, 0], [0, 0]], dtype=complex)
+    res = {}
+    for N in Ns:
+        dt = t_end / N
+        eta = B.eta_coefficients(bath, dt, N)
+        Qh = B.Q_of_t(bath, 0.5 * dt * np.arange(2 * N + 3))
+        res[N] = (mod.propagate(2, q, hs, dt, eta, N, None, 0.0, rho0, N).rho[N],
+                  mod.propagate(2, q, hs, dt, eta, N, None, 0.0, rho0, N, Qh=Qh).rho[N])
+    return [np.abs(res[Ns[0]][k] - res[Ns[1]][k]).max() / np.abs(res[Ns[1]][k] - res[Ns[2]][k]).max()
+            for k in (0, 1)]
+
+
+@pytest.mark.parametrize("alpha,wc,beta,t_end", [(0.05, 3.0, 2.0, 1.6), (0.02, 2.0, 1.0, 2.0), (0.1, 2.0, 0.5, 1.0)])
+def test_symmetric_splitting_is_second_order_in_dt(alpha, wc, beta, t_end):
+    """The splitting of the short-time propagator between H_S and the bath
+    (Eq. quapi_red_rho) decides the order in dt of the exact-memory path sum:
+    the right-box reading (R1: the system propagates over a step, the bath
+    sees the new point over the whole step) is a one-sided splitting, first
+    order; the symmetric splitting (R17: intervals centred on the points,
+    half intervals at both ends) is second order.  The ratio of successive
+    differences at dt, dt/2, dt/4 must show it (2 and 4 asymptotically; the
+    steps here are coarse, so the bands are wide but do not overlap)."""
+    bath = W.Bath(beta=beta, ohmic_alpha=alpha, ohmic_wc=wc)
+    r_box, r_sym = _splitting_order_ratios(bath, t_end)
+    assert 1.6 < r_box < 3.0, r_box
+    assert 3.3 < r_sym < 6.0, r_sym
+
 # ---------------------------------------------------------------- planted mistakes
 
 MUTATIONS = {
@@ -665,7 +700,9 @@ def _sym_pins_pass(mod):
             rb = brute.rho_by_enumeration_symmetric(M, c["q"], c["hs"], c["dt"], Qh, dkmax, c["rho0"], N)
             if np.abs(r.rho[N] - rb).max() > 2e-14:
                 return False
-        return True
+        # second order in dt (a check of the reading itself, not of its code)
+        r_sym = _splitting_order_ratios(W.Bath(beta=2.0, ohmic_alpha=0.05, ohmic_wc=3.0), 1.6, mod)[1]
+        return 3.3 < r_sym < 6.0
     except Exception:
         return False
 
