@@ -210,3 +210,19 @@ def test_capacity_limits_as_documented():
     assert size(max_paths=1 << 32, scheme=abi.QP_POSTMERGE)[0] == abi.QP_ERR_ARG
     assert size(max_paths=(1 << 32) - 1, scheme=abi.QP_POSTMERGE, max_groups=1 << 20)[0] == abi.QP_OK
     assert size(rho_history=(1 << 24) + 1)[0] == abi.QP_ERR_ARG
+
+
+@pytest.mark.parametrize("kw", [dict(beta=100.0, ohmic_alpha=0.1, ohmic_wc=5.0), dict(beta=0.05, ohmic_alpha=0.1, ohmic_wc=5.0),
+                                dict(beta=5.0, ohmic_alpha=0.1, ohmic_wc=50.0), dict(beta=5.0, ohmic_alpha=0.1, ohmic_wc=0.5),
+                                dict(beta=50.0, res_w0=1.0, res_gamma=0.01, res_lambda=0.1),
+                                dict(beta=0.2, res_w0=3.0, res_gamma=0.5, res_lambda=0.3)],
+                         ids=lambda d: ",".join(f"{k}={v}" for k, v in d.items()))
+@pytest.mark.parametrize("dt", [0.02, 0.25])
+def test_library_eta_matches_oracle_at_extreme_baths(kw, dt):
+    """Cold and hot baths, wide and narrow cut-offs, a sharp and a broad
+    resonance: the library's quadrature and the oracle's agree to 1e-11
+    relative (measured at most 3e-12)."""
+    bath = W.Bath(**kw)
+    lib = abi.qp_eta_from_bath(bath, dt, 16)
+    orc = B.eta_coefficients(bath, dt, 16)
+    assert np.abs(lib - orc).max() <= 1e-11 * np.abs(orc).max()

@@ -55,7 +55,8 @@ def resonance_Q_closed(w0, gamma, lam, beta, t, nmat=400000):
 
 
 @pytest.mark.parametrize("alpha,wc,beta", [(0.1, 5.0, 5.0), (0.05, 5.0, 10.0),
-                                           (2 / 16 / math.pi ** 2, 10.0, 5.0), (0.3, 2.0, 0.7)])
+                                           (2 / 16 / math.pi ** 2, 10.0, 5.0), (0.3, 2.0, 0.7),
+                                           (0.1, 5.0, 100.0), (0.1, 5.0, 0.05), (0.1, 50.0, 5.0), (0.1, 0.5, 5.0)])
 def test_ohmic_Q_matches_closed_form(alpha, wc, beta):
     ts = np.array([0.05, 0.25, 0.5, 1.3, 2.25, 4.2])
     bath = W.Bath(beta=beta, ohmic_alpha=alpha, ohmic_wc=wc)
