@@ -221,8 +221,12 @@ def test_capacity_limits_as_documented():
 def test_library_eta_matches_oracle_at_extreme_baths(kw, dt):
     """Cold and hot baths, wide and narrow cut-offs, a sharp and a broad
     resonance: the library's quadrature and the oracle's agree to 1e-11
-    relative (measured at most 3e-12)."""
+    relative (measured at most 3e-12 for eta)."""
     bath = W.Bath(**kw)
     lib = abi.qp_eta_from_bath(bath, dt, 16)
     orc = B.eta_coefficients(bath, dt, 16)
     assert np.abs(lib - orc).max() <= 1e-11 * np.abs(orc).max()
+    # Q at half steps (the symmetric splitting's input): measured at most 8e-13
+    ql = abi.qp_Q_from_bath(bath, 0.5 * dt, 35)
+    qo = B.Q_of_t(bath, 0.5 * dt * np.arange(35))
+    assert np.abs(ql - qo).max() <= 1e-11 * np.abs(qo).max()
