@@ -212,12 +212,17 @@ def test_capacity_limits_as_documented():
     assert size(rho_history=(1 << 24) + 1)[0] == abi.QP_ERR_ARG
 
 
-@pytest.mark.parametrize("kw", [dict(beta=100.0, ohmic_alpha=0.1, ohmic_wc=5.0), dict(beta=0.05, ohmic_alpha=0.1, ohmic_wc=5.0),
-                                dict(beta=5.0, ohmic_alpha=0.1, ohmic_wc=50.0), dict(beta=5.0, ohmic_alpha=0.1, ohmic_wc=0.5),
-                                dict(beta=50.0, res_w0=1.0, res_gamma=0.01, res_lambda=0.1),
-                                dict(beta=0.2, res_w0=3.0, res_gamma=0.5, res_lambda=0.3)],
-                         ids=lambda d: ",".join(f"{k}={v}" for k, v in d.items()))
-@pytest.mark.parametrize("dt", [0.02, 0.25])
+EXTREME_BATHS = [dict(beta=100.0, ohmic_alpha=0.1, ohmic_wc=5.0), dict(beta=0.05, ohmic_alpha=0.1, ohmic_wc=5.0),
+                 dict(beta=5.0, ohmic_alpha=0.1, ohmic_wc=50.0), dict(beta=5.0, ohmic_alpha=0.1, ohmic_wc=0.5),
+                 dict(beta=50.0, res_w0=1.0, res_gamma=0.01, res_lambda=0.1),
+                 dict(beta=0.2, res_w0=3.0, res_gamma=0.5, res_lambda=0.3)]
+
+
+# (the hot broad resonance at the long step only at dt = 0.02: the oracle's
+# adaptive quadrature takes tens of seconds there)
+@pytest.mark.parametrize("kw,dt", [(kw, dt) for kw in EXTREME_BATHS for dt in (0.02, 0.25)
+                                   if not (kw["beta"] == 0.2 and dt == 0.25)],
+                         ids=lambda x: ",".join(f"{k}={v}" for k, v in x.items()) if isinstance(x, dict) else str(x))
 def test_library_eta_matches_oracle_at_extreme_baths(kw, dt):
     """Cold and hot baths, wide and narrow cut-offs, a sharp and a broad
     resonance: the library's quadrature and the oracle's agree to 1e-11
