@@ -276,6 +276,25 @@ def test_trace_conserved_by_masked_merge(M, mask):
     np.testing.assert_allclose(tr, np.ones_like(tr), atol=1e-13)
 
 
+
+@pytest.mark.parametrize("M,dkmax,steps", [(2, 8, 24), (3, 5, 12)])
+@pytest.mark.parametrize("theta", [0.0, 1e-5])
+def test_masked_result_converges_to_unmasked_as_the_mask_grows(M, dkmax, steps, theta):
+    """Sec. 3.1: the mask trades accuracy for paths, and the result
+    approaches the full iQUAPI one as Delta k_eff grows to Delta k_max.
+    On these seeded structured cases, prefix masks {0 .. k-1}: the largest
+    deviation from the unmasked run (same filter) falls with k (5 % slack
+    per step), by more than fourfold from the smallest mask to the largest
+    partial one (with a filter the different filter losses set a floor),
+    and vanishes for the full window."""
+    q, hs, eta, rho0 = _structured_case(M, dkmax)
+    ref = iquapi.propagate(M, q, hs, 0.2, eta, dkmax, None, theta, rho0, steps).rho
+    errs = [np.abs(iquapi.propagate(M, q, hs, 0.2, eta, dkmax, tuple(range(k)), theta, rho0, steps).rho
+                   - ref).max() for k in range(2, dkmax + 1)]
+    assert all(b <= 1.05 * a for a, b in zip(errs, errs[1:])), errs
+    assert errs[-2] * 4 < errs[0], errs
+    assert errs[-1] == 0.0
+
 def test_hermitian_without_mask():
     q, hs, eta, rho0 = _structured_case(2, 6)
     r = iquapi.propagate(2, q, hs, 0.2, eta, 6, None, 0.0, rho0, 12)
