@@ -35,5 +35,6 @@ the merge after extension is, which pins the shift of P'.  Where the merge
 is an approximation (eta beyond that lag) the paper prints no value
 ("parity unpinned" for that combination; pinned there only by invariants:
 exactness at zero coupling, trace conservation without a filter, reduction
-to the unmasked result for the full mask).
+to the unmasked result for the full mask, and convergence to it as the
+mask grows).
 """
